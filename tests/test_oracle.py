@@ -1,0 +1,340 @@
+"""Pins of the FP64 oracle against values fixed by the paper and by mathematics.
+
+Each check compares the oracle with something other than itself: hand-worked
+values (tests/golden), closed forms (the cubic B-spline basis image of
+Sec. 3.1.1, bilinear polynomials, Samuelson's bound), a dense solve of the
+spline system built from the basis function and the boundary rule, and numpy's
+median.  None of these tests needs a GPU.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_11486_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line)
+    return rows
+
+
+# ---------------------------------------------------------------- B-spline basis
+def test_bspline3_golden_values():
+    for row in _read_golden("bspline3_values.txt"):
+        t, num, den = row.split()
+        assert oracle.bspline3(float(t)) == pytest.approx(int(num) / int(den), abs=1e-15)
+
+
+def test_bspline3_partition_of_unity_and_moments():
+    # sum_k beta3(t - k) = 1 and sum_k k beta3(t - k) = t for every t
+    for t in np.linspace(-3.0, 3.0, 61):
+        w = [oracle.bspline3(t - k) for k in range(-6, 7)]
+        assert sum(w) == pytest.approx(1.0, abs=1e-14)
+        assert sum(k * wk for k, wk in zip(range(-6, 7), w)) == pytest.approx(t, abs=1e-13)
+
+
+def test_mirror_index():
+    assert [oracle.mirror(i, 5) for i in range(-4, 13)] == \
+        [4, 3, 2, 1, 0, 1, 2, 3, 4, 3, 2, 1, 0, 1, 2, 3, 4]
+    assert oracle.mirror(-7, 1) == 0 and oracle.mirror(5, 1) == 0
+    assert [oracle.mirror(i, 2) for i in range(-3, 4)] == [1, 0, 1, 0, 1, 0, 1]
+
+
+# ---------------------------------------------------------------- calibration
+def test_calibrate_golden_3x3():
+    rows = {r.split()[0]: r.split()[1:] for r in _read_golden("calibrate_3x3.txt")}
+    t = float(rows["t"][0])
+    raw = np.array(rows["raw"], dtype=np.float64).astype(np.uint16).reshape(3, 3)
+    bias = np.array(rows["bias"], dtype=np.float32).reshape(3, 3)
+    dark = np.array(rows["dark"], dtype=np.float32).reshape(3, 3)
+    flat = np.array(rows["flat"], dtype=np.float32).reshape(3, 3)
+    want = np.array(rows["v"], dtype=np.float64).reshape(3, 3)
+    got = oracle.calibrate(raw, bias, dark, flat, t)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-5)
+
+
+def test_calibrate_constant_closed_form_and_flat_normalisation():
+    raw = np.full((4, 6), 1234, np.uint16)
+    v = oracle.calibrate(raw, np.full((4, 6), 1000.5, np.float32), np.full((4, 6), 0.0625, np.float32),
+                         np.full((4, 6), 0.8, np.float32), 60.0)
+    # (1234 - 1000.5 - 3.75) / 0.8 = 229.75 / 0.8
+    np.testing.assert_allclose(v, 229.75 / np.float64(np.float32(0.8)), rtol=1e-15)
+    # normalised flat: flat' = flat / mean(flat); flat = [1, 3] -> mean 2 -> [0.5, 1.5]
+    flat = np.tile(np.array([1.0, 3.0], np.float32), (2, 1))
+    raw2 = np.full((2, 2), 1100, np.uint16)
+    v2 = oracle.calibrate(raw2, np.full((2, 2), 1000, np.float32), np.zeros((2, 2), np.float32),
+                          flat, 60.0, normalize_flat=True)
+    np.testing.assert_allclose(v2, [[200.0, 100.0 / 1.5]] * 2, rtol=1e-15)
+
+
+# ---------------------------------------------------------------- spline system
+def _dense_mirror_system(N):
+    """Matrix of the interpolation condition sum_i c_ext[i] beta3(j - i) = v[j],
+    c_ext the mirror extension of c, assembled from beta3 and the index map."""
+    A = np.zeros((N, N))
+    for j in range(N):
+        for i in range(j - 2, j + 3):
+            A[j, oracle.mirror(i, N)] += oracle.bspline3(j - i)
+    return A
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 17, 64])
+def test_spline_line_solve_equals_dense_system(N):
+    rng = np.random.default_rng(N)
+    v = rng.normal(size=N) * 100
+    c = oracle.spline_solve_line(v)
+    A = _dense_mirror_system(N)
+    np.testing.assert_allclose(c, np.linalg.solve(A, v), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(A @ c, v, rtol=1e-12, atol=1e-11)
+
+
+def test_spline_line_reproduces_basis_and_mirror_pair():
+    N = 20
+    # a basis function at an interior knot: coefficients are a unit impulse
+    v = np.array([oracle.bspline3(j - 9) for j in range(N)])
+    c = oracle.spline_solve_line(v)
+    want = np.zeros(N)
+    want[9] = 1.0
+    np.testing.assert_allclose(c, want, atol=1e-14)
+    # data symmetric about sample 0 (beta3(j-1)+beta3(j+1)) is consistent with the
+    # mirror boundary: its coefficients are the impulse at 1 alone
+    v = np.array([oracle.bspline3(j - 1) + oracle.bspline3(j + 1) for j in range(N)])
+    c = oracle.spline_solve_line(v)
+    want = np.zeros(N)
+    want[1] = 1.0
+    np.testing.assert_allclose(c, want, atol=1e-14)
+    # the same at the right end
+    v = np.array([oracle.bspline3(j - (N - 2)) + oracle.bspline3(j - N) for j in range(N)])
+    c = oracle.spline_solve_line(v)
+    want = np.zeros(N)
+    want[N - 2] = 1.0
+    np.testing.assert_allclose(c, want, atol=1e-14)
+
+
+def _bspline_basis_image(W, H, centres, amps, dx=0.0, dy=0.0):
+    """Sum of 2-D cubic B-spline basis functions sampled at (x+dx, y+dy)."""
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    img = np.zeros((H, W))
+    b = np.vectorize(oracle.bspline3)
+    for (cx, cy), a in zip(centres, amps):
+        img += a * b(xx + dx - cx) * b(yy + dy - cy)
+    return img
+
+
+def test_spline3_shift_exact_on_bspline_basis_image():
+    """Sec. 3.1.1: an image of cubic B-spline basis functions can be shifted
+    without interpolating; the spline shift must reproduce it (the paper's own
+    accuracy test).  Centres on the frame edge are mirror-consistent too."""
+    W, H = 40, 33
+    rng = np.random.default_rng(5)
+    centres = [(int(rng.integers(2, W - 2)), int(rng.integers(2, H - 2))) for _ in range(25)]
+    centres += [(0, 10), (W - 1, 20), (15, 0), (30, H - 1), (0, 0)]
+    amps = rng.uniform(100, 5000, size=len(centres))
+    img = _bspline_basis_image(W, H, centres, amps) + 300.0 * 0  # no offset term
+    for dx, dy in [(0.3, 0.2), (0.6, 0.7), (-1.75, 2.5), (3.0, -2.0), (0.0, 0.0)]:
+        a, valid = oracle.shift(img, dx, dy, "spline3")
+        want = _bspline_basis_image(W, H, centres, amps, dx, dy)
+        err = np.abs(a - want)[valid]
+        assert valid.sum() > 0.7 * W * H
+        assert err.max() <= 1e-11 * np.abs(img).max()
+
+
+def test_spline3_interpolates_at_integer_shift():
+    rng = np.random.default_rng(1)
+    v = rng.normal(300, 20, size=(21, 19))
+    a, valid = oracle.shift(v, 2.0, -3.0, "spline3")
+    np.testing.assert_allclose(a[valid], np.roll(np.roll(v, -2, 1), 3, 0)[valid], atol=1e-10)
+    assert valid[3:, :17].all() and not valid[:3].any() and not valid[:, 17:].any()
+
+
+def test_spline3_round_trip_magnitude_like_paper():
+    """Sec. 3.1.1 set B: shift by (0.6, 0.7) and back; the paper finds relative
+    differences of about 1e-2 to 1e-1 on sky-dominated frames."""
+    fs = synth.make_set(96, 96, 1, 0.0, 77)
+    v = oracle.calibrate(fs.raw[0], fs.bias, fs.dark, fs.flat, 60.0)
+    a, va = oracle.shift(v, 0.6, 0.7, "spline3")
+    b, vb = oracle.shift(a, -0.6, -0.7, "spline3")
+    d = np.abs(oracle.relative_difference(b, v))[20:-20, 20:-20]
+    q90 = np.quantile(d, 0.9)
+    assert 1e-3 < q90 < 2e-1
+
+
+# ---------------------------------------------------------------- nearest / bilinear
+@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3"])
+def test_zero_shift_is_identity(interp):
+    rng = np.random.default_rng(3)
+    v = rng.normal(300, 50, size=(13, 17))
+    a, valid = oracle.shift(v, 0.0, 0.0, interp)
+    assert valid.all()
+    if interp == "spline3":
+        np.testing.assert_allclose(a, v, atol=1e-10)
+    else:
+        assert np.array_equal(a, v)
+
+
+@pytest.mark.parametrize("interp", ["nearest", "bilinear"])
+def test_integer_shift_moves_pixels_exactly(interp):
+    rng = np.random.default_rng(4)
+    v = rng.normal(300, 50, size=(12, 15))
+    a, valid = oracle.shift(v, -3.0, 2.0, interp)
+    # output (x, y) = v(x - 3, y + 2): valid for x >= 3, y <= H - 3
+    assert np.array_equal(valid[:, 3:][:-2], np.ones((10, 12), bool))
+    assert not valid[:, :3].any() and not valid[-2:].any()
+    assert np.array_equal(a[:-2, 3:], v[2:, :-3])
+
+
+def test_bilinear_reproduces_bilinear_polynomials():
+    """f = a + b x + c y + d x y is reproduced exactly by bilinear weights; a
+    swapped or transposed weight breaks this."""
+    H, W = 14, 11
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    f = lambda x, y: 3.0 + 0.7 * x - 1.3 * y + 0.11 * x * y
+    v = f(xx, yy)
+    for dx, dy in [(0.25, 0.5), (-2.375, 1.625), (0.9, -0.1)]:
+        a, valid = oracle.shift(v, dx, dy, "bilinear")
+        np.testing.assert_allclose(a[valid], f(xx + dx, yy + dy)[valid], rtol=1e-13, atol=1e-12)
+
+
+def test_bilinear_midpoint_and_validity_edges():
+    H, W = 6, 9
+    ramp = np.tile(np.arange(W, dtype=np.float64) * 10, (H, 1))
+    a, valid = oracle.shift(ramp, 0.5, 0.0, "bilinear")
+    assert np.array_equal(a[:, :W - 1], ramp[:, :W - 1] + 5.0)
+    assert valid[:, :W - 1].all() and not valid[:, W - 1].any()
+    # dx = 1.5: i0 = x + 1, needs i0 + 1 <= W - 1 -> x <= W - 3
+    # dy = -2.25: floor = -3, fy = 0.75, j0 = y - 3 >= 0 and j0 + 1 = y - 2 <= H - 1 -> y >= 3
+    _, valid = oracle.shift(ramp, 1.5, -2.25, "bilinear")
+    want = np.zeros((H, W), bool)
+    want[3:H, 0:W - 2] = True
+    assert np.array_equal(valid, want)
+
+
+def test_nearest_rounds_half_away_from_zero():
+    W = 6
+    v = np.tile(np.arange(W, dtype=np.float64), (1, 1))
+    # dx = 0.5: position x + 0.5 rounds up -> x + 1
+    a, valid = oracle.shift(v, 0.5, 0.0, "nearest")
+    assert np.array_equal(a[0, :W - 1], np.arange(1, W)) and not valid[0, W - 1]
+    # dx = -0.5: position x - 0.5; x = 0 gives -0.5 -> -1 (invalid), x >= 1 -> x
+    a, valid = oracle.shift(v, -0.5, 0.0, "nearest")
+    assert not valid[0, 0] and np.array_equal(a[0, 1:], np.arange(1, W))
+    # dx = 0.49 -> x, dx = 0.51 -> x + 1
+    a, _ = oracle.shift(v, 0.49, 0.0, "nearest")
+    assert np.array_equal(a[0], np.arange(W))
+    a, valid = oracle.shift(v, 0.51, 0.0, "nearest")
+    assert np.array_equal(a[0, :W - 1], np.arange(1, W)) and not valid[0, W - 1]
+
+
+# ---------------------------------------------------------------- sigma clip / median
+def test_clip_golden_cases():
+    for row in _read_golden("clip_cases.txt"):
+        name, params, samples, expect = [s.strip() for s in row.split("|")]
+        klo, khi, it, center, ddof = params.split()
+        x = np.array(samples.split(), dtype=np.float64)
+        mean_want, kept_want = expect.split()
+        mean, kept, rej, _ = oracle.clip(x, kappa_lo=float(klo), kappa_hi=float(khi),
+                                         max_iter=int(it), center="median" if center == "1" else "mean",
+                                         ddof=int(ddof))
+        assert kept == int(kept_want), name
+        assert mean == pytest.approx(float(mean_want), abs=1e-12), name
+        assert rej.sum() == len(x) - kept, name
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 5, 9, 10])
+def test_clip_cannot_reject_at_kappa3_for_ten_or_fewer(m):
+    """Samuelson: |x - mu| <= sigma sqrt(m - 1) <= 3 sigma for m <= 10, so the
+    clipped mean is the plain mean."""
+    rng = np.random.default_rng(m)
+    for _ in range(50):
+        x = rng.standard_cauchy(size=m) * 100
+        mean, kept, _, _ = oracle.clip(x)
+        assert kept == m
+        assert mean == pytest.approx(np.mean(x), rel=1e-12, abs=1e-9)
+
+
+def test_clip_without_outliers_is_plain_mean():
+    x = np.linspace(-1.0, 1.0, 31) * 7 + 300
+    mean, kept, _, _ = oracle.clip(x)
+    assert kept == 31 and mean == pytest.approx(np.mean(x), rel=1e-15)
+
+
+def test_clip_invalid_samples_are_excluded():
+    x = np.array([1.0, 2.0, 1e9, 3.0])
+    mean, kept, _, _ = oracle.clip(x, valid=np.array([1, 1, 0, 1]))
+    assert kept == 3 and mean == pytest.approx(2.0)
+    mean, kept, _, _ = oracle.clip(x, valid=np.zeros(4))
+    assert kept == 0 and np.isnan(mean)
+    assert np.isnan(oracle.median(x, valid=np.zeros(4)))
+
+
+def test_clip_margin_reports_distance_to_threshold():
+    # case B of the golden file sits exactly on the threshold
+    _, _, _, mg = oracle.clip(np.array([0.0] * 9 + [10.0]))
+    assert mg == 0.0
+    _, _, _, mg = oracle.clip(np.array([5.0, 5.0]))
+    assert mg == np.inf
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 7, 10, 31, 40])
+def test_median_matches_numpy(m):
+    rng = np.random.default_rng(100 + m)
+    for _ in range(20):
+        x = rng.normal(size=m).astype(np.float32).astype(np.float64)
+        valid = rng.random(m) < 0.8
+        if not valid.any():
+            continue
+        assert oracle.median(x, valid) == np.median(x[valid])
+
+
+# ---------------------------------------------------------------- whole set
+@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3"])
+def test_reduce_set_constant_frames(interp):
+    fs = synth.make_const_set(24, 20, 6, 1500, 1000.0, 0.05, 0.8, 60.0,
+                              dx=[0.3, -1.7, 2.25, 0.0, -0.5, 1.0],
+                              dy=[0.1, 0.9, -2.5, 0.0, 1.5, -1.0])
+    out = oracle.reduce_set(fs, interp=interp)
+    want = (1500.0 - 1000.0 - np.float64(np.float32(0.05)) * 60.0) / np.float64(np.float32(0.8))
+    inner = np.s_[4:-4, 4:-4]
+    np.testing.assert_allclose(out["mean"][inner], want, rtol=1e-12)
+    np.testing.assert_allclose(out["median"][inner], want, rtol=1e-12)
+    assert (out["nkept"][inner] == 6).all()
+
+
+def test_reduce_set_composes_calibrate_shift_clip_median():
+    fs = synth.make_set(40, 36, 7, 3.0, 9)
+    full = oracle.reduce_set(fs, interp="bilinear", kappa=2.0, want_stack=True)
+    # stack = calibrate + shift of each frame
+    for k in range(fs.n):
+        v = oracle.calibrate(fs.raw[k], fs.bias, fs.dark, fs.flat, fs.exptime[k])
+        a, valid = oracle.shift(v, fs.dx[k], fs.dy[k], "bilinear")
+        assert np.array_equal(valid, full["valid"][k])
+        np.testing.assert_allclose(full["stack"][k][valid], a[valid], rtol=1e-15)
+    comb = oracle.combine_stack(full["stack"], full["valid"], kappa=2.0)
+    np.testing.assert_array_equal(comb["nkept"], full["nkept"])
+    np.testing.assert_allclose(comb["mean"], full["mean"], rtol=1e-15, equal_nan=True)
+    np.testing.assert_allclose(comb["median"], full["median"], rtol=1e-15, equal_nan=True)
+    # pixel-list mode agrees with the full grid
+    xs = np.array([0, 5, 39, 17], np.int32)
+    ys = np.array([0, 35, 12, 20], np.int32)
+    part = oracle.reduce_set(fs, interp="bilinear", kappa=2.0, pixels=(xs, ys))
+    np.testing.assert_array_equal(part["mean"], full["mean"][ys, xs])
+    np.testing.assert_array_equal(part["median"], full["median"][ys, xs])
+
+
+def test_reduce_set_aligns_dithered_stars():
+    """Offsets passed as the dither offsets line the scene up again: the
+    median of the aligned stack is smoother than any single frame."""
+    fs = synth.make_set(64, 64, 9, 4.0, 21, n_cr=0)
+    out = oracle.reduce_set(fs, interp="spline3")
+    v0 = oracle.calibrate(fs.raw[0], fs.bias, fs.dark, fs.flat, 60.0)
+    sl = np.s_[8:-8, 8:-8]
+    assert np.std(out["median"][sl]) < np.std(v0[sl])
