@@ -1,0 +1,232 @@
+/*
+ * irp.h -- C ABI of the GB300 image-reduction library.
+ *
+ * The library implements the data-parallel part of the image reduction of
+ * Niwano et al., "GPU-accelerated Image Reduction Pipeline" (PASJ 2020):
+ *
+ *   Sec. 2.1 / 2.2  bias subtraction, dark subtraction and flat fielding of raw
+ *                   16-bit CCD frames (the integers become floating point at the
+ *                   bias subtraction);
+ *   Sec. 2.1 / 2.2  alignment of the dithered frames by sub-pixel shifting with
+ *                   bicubic-spline interpolation (also nearest and bilinear,
+ *                   named as cheaper alternatives in Sec. 3.2.1);
+ *   Sec. 2.1 / 2.2  co-adding by a sigma-clipped mean, plus the median.
+ *
+ * Conventions shared by every entry point
+ *   - Images are row-major, x (column) fastest.  Pitches and frame strides are
+ *     in ELEMENTS of the buffer's own type.
+ *   - Every device buffer is allocated and owned by the caller.  Host arrays
+ *     (offsets, exposure times, frame pointer tables) are read during the call
+ *     only.  No entry point allocates device or host memory.
+ *   - Offsets: output pixel (x, y) samples frame k at (x + dx[k], y + dy[k]).
+ *     The offset is split as dx = ix + fx, ix = floor(dx), fx in [0, 1).
+ *   - A sample is valid iff every tap with non-zero weight lies inside the
+ *     frame (nearest, bilinear) or the source position lies inside
+ *     [0, W-1] x [0, H-1] (cubic spline).  Invalid samples do not enter the
+ *     combination; a pixel with no valid sample gets NaN (mean, median).
+ *   - The cubic spline is the interpolating cubic B-spline with mirror
+ *     (whole-sample symmetric) boundary conditions (Sec. 3.1.1, Sec. 3.2.1).
+ *   - Calibration: v = (raw - bias - dark_rate * t) * (flat_norm / flat) in
+ *     FP32, flat_norm = 1 or the FP64 mean of the flat (normalize_flat).
+ *   - Sigma clip: up to max_iter passes; centre = mean (or median) of the
+ *     survivors, sigma^2 = sum (x - centre)^2 / (m - ddof); x is rejected if
+ *     centre - x > kappa_lo sigma or x - centre > kappa_hi sigma; rejection is
+ *     cumulative; the loop stops when nothing is rejected or sigma = 0.  The
+ *     output is the mean of the survivors.  The median is taken over all valid
+ *     samples before clipping (even count: mean of the two middle values).
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued asynchronously; arguments are validated before anything is
+ *     enqueued, and a non-OK status means nothing was enqueued.
+ *   - Errors detected on the device (a non-finite or non-positive flat value,
+ *     a bounded wait that ran out) are latched into the status word at the
+ *     start of the caller's workspace and reported by irp_sync_status().
+ */
+#ifndef IRP_H
+#define IRP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IRP_VERSION 10000      /* 1.0.0 */
+#define IRP_MAX_FRAMES 64      /* frames per set on the register/shared-memory combine */
+
+typedef enum {
+  IRP_OK = 0,
+  IRP_ERR_INVALID_ARG = 1,   /* null required pointer, bad size, bad enum */
+  IRP_ERR_ALIGNMENT = 2,     /* a buffer is not aligned to its element size */
+  IRP_ERR_WORKSPACE = 3,     /* workspace missing or smaller than required */
+  IRP_ERR_UNSUPPORTED = 4,   /* a valid request this build does not implement */
+  IRP_ERR_BAD_MASTER = 5,    /* device: flat value <= 0 or not finite */
+  IRP_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+  IRP_ERR_TIMEOUT = 7        /* device: a bounded wait gave up */
+} irp_status;
+
+typedef enum { IRP_INTERP_NEAREST = 0, IRP_INTERP_BILINEAR = 1, IRP_INTERP_SPLINE3 = 2 } irp_interp;
+
+/* Element type of an intermediate (calibrated or aligned) stack.
+ * IRP_F16_SCALED: value = (float)h * scale[k] + offset[k], h an IEEE half. */
+typedef enum { IRP_F32 = 0, IRP_F16_SCALED = 1 } irp_stack_dtype;
+
+typedef struct {
+  float kappa_lo, kappa_hi;  /* rejection thresholds in sigma (3, 3)        */
+  int max_iter;              /* rejection passes (3)                        */
+  int center;                /* 0: mean, 1: median                          */
+  int ddof;                  /* 0: population sigma                         */
+} irp_clip_params;
+
+/* ---------------------------------------------------------------------------
+ * irp_calibrate -- Sec. 2.1 bias subtraction, dark subtraction, flat fielding.
+ *   raw      [n][H][raw_pitch] uint16 frames, frame k at raw + k*raw_frame_stride
+ *   bias, dark_rate, flat  [H][master_pitch] FP32 masters (dark in ADU/s)
+ *   exptime_host  [n] exposure times in s (host memory)
+ *   out      dt == IRP_F32:        float [n][H][out_pitch], frame stride out_frame_stride
+ *            dt == IRP_F16_SCALED: half  [n][H][out_pitch]; scale_out/offset_out
+ *            [n] (device) receive the per-frame scaling chosen on the device:
+ *            offset = FP64 mean of the frame, scale = power of two with
+ *            max |v - offset| / scale <= 16384.
+ *   workspace  >= irp_calibrate_workspace_size(n) bytes, 256-byte aligned.
+ * ------------------------------------------------------------------------- */
+irp_status irp_calibrate(const uint16_t* raw, int64_t raw_pitch, int64_t raw_frame_stride,
+                         int W, int H, int n,
+                         const float* bias, const float* dark_rate, const float* flat,
+                         int64_t master_pitch, const float* exptime_host, int normalize_flat,
+                         void* out, int64_t out_pitch, int64_t out_frame_stride,
+                         irp_stack_dtype dt, float* scale_out, float* offset_out,
+                         void* workspace, size_t ws_bytes, void* stream);
+size_t irp_calibrate_workspace_size(int n);
+
+/* ---------------------------------------------------------------------------
+ * irp_frame_stats -- FP64 frame-wide sums (sky level, normalisation).
+ *   frames   F32 or F16_SCALED [n][H][pitch]; NaN entries are skipped.
+ *   sum_out, sumsq_out [n] (device, double), count_out [n] (device, int64).
+ * ------------------------------------------------------------------------- */
+irp_status irp_frame_stats(const void* frames, int64_t pitch, int64_t frame_stride,
+                           int W, int H, int n, irp_stack_dtype dt,
+                           const float* scale, const float* offset,
+                           double* sum_out, double* sumsq_out, int64_t* count_out,
+                           void* stream);
+
+/* ---------------------------------------------------------------------------
+ * irp_shift -- Sec. 2.1 alignment: resamples each calibrated frame onto the
+ * reference grid.  in/out have the same dtype; F16_SCALED frames keep their
+ * per-frame scale/offset (interpolation weights sum to one).  Invalid samples
+ * are written as NaN; valid_out [n][H][out_pitch] (nullable) receives 0/1.
+ *   dx_host, dy_host [n] offsets in pixels (host).
+ *   workspace >= irp_shift_workspace_size(W, H, n, interp) bytes (the spline
+ *   coefficients, n*W*H floats, for IRP_INTERP_SPLINE3).
+ * ------------------------------------------------------------------------- */
+irp_status irp_shift(const void* in, int64_t in_pitch, int64_t in_frame_stride,
+                     int W, int H, int n, irp_stack_dtype dt,
+                     const float* scale, const float* offset,
+                     const double* dx_host, const double* dy_host, irp_interp interp,
+                     void* out, int64_t out_pitch, int64_t out_frame_stride,
+                     uint8_t* valid_out, void* workspace, size_t ws_bytes, void* stream);
+size_t irp_shift_workspace_size(int W, int H, int n, irp_interp interp);
+
+/* ---------------------------------------------------------------------------
+ * irp_combine -- Sec. 2.1 co-adding: sigma-clipped mean and median of an
+ * aligned stack [n][H][pitch] (F32 or F16_SCALED; NaN = invalid sample).
+ *   valid    nullable [n][H][pitch] uint8 mask, 0 excludes the sample.
+ *   mean_out, median_out  [H][out_pitch] float (either may be NULL).
+ *   nkept_out  nullable [H][out_pitch] uint16 survivors of the clip.
+ *   reject_out nullable [n][H][out_pitch] uint8, 1 where a valid sample was
+ *              rejected by the clip (debug output).
+ *   n <= IRP_MAX_FRAMES.
+ * ------------------------------------------------------------------------- */
+irp_status irp_combine(const void* stack, int64_t pitch, int64_t frame_stride,
+                       int W, int H, int n, irp_stack_dtype dt,
+                       const float* scale, const float* offset, const uint8_t* valid,
+                       const irp_clip_params* clip,
+                       float* mean_out, float* median_out, uint16_t* nkept_out,
+                       uint8_t* reject_out, int64_t out_pitch, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * irp_reduce_set -- the fused path: calibration, alignment and combination of
+ * one or more frame sets, each raw pixel read from HBM once (bilinear and
+ * nearest; cubic spline computes the spline coefficients of every calibrated
+ * frame into the workspace first and then resamples and combines them).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  const uint16_t* const* frames;  /* host array of n device pointers           */
+  int64_t raw_pitch;              /* elements, shared by the set's frames       */
+  int W, H, n;
+  const double* dx;               /* host [n] */
+  const double* dy;               /* host [n] */
+  const float* exptime;           /* host [n], seconds */
+  const float* bias;              /* device [H][master_pitch] */
+  const float* dark_rate;         /* device, ADU/s */
+  const float* flat;              /* device */
+  int64_t master_pitch;
+  float* mean_out;                /* device [H][out_pitch], may be NULL */
+  float* median_out;              /* device [H][out_pitch], may be NULL */
+  uint16_t* nkept_out;            /* device, nullable */
+  int64_t out_pitch;
+  float* stack_out;               /* device [n][H][out_pitch] aligned samples, NaN
+                                     = invalid; nullable (debug) */
+  const uint32_t* ready_flag;     /* device, nullable: the set's tiles wait until
+                                     *ready_flag >= ready_value (bounded wait) */
+  uint32_t ready_value;
+} irp_set;
+
+typedef struct {
+  irp_interp interp;
+  irp_clip_params clip;
+  int normalize_flat;             /* divide the flat by its FP64 mean */
+  int persistent;                 /* 1: persistent CTAs pulling (set, tile) work
+                                     items from an atomic counter, longest first */
+  int max_ctas;                   /* persistent grid size; 0 = SMs x occupancy  */
+  int wait_spin_limit;            /* bounded-wait polls before IRP_ERR_TIMEOUT; 0 = default */
+} irp_reduce_params;
+
+size_t irp_workspace_size(const irp_set* sets, int nsets, const irp_reduce_params* p);
+irp_status irp_reduce_set(const irp_set* sets, int nsets, const irp_reduce_params* p,
+                          void* workspace, size_t ws_bytes, void* stream);
+
+/* Two-step form of irp_reduce_set for CUDA-graph capture: irp_plan_encode
+ * writes the launch plan (descriptors, work list) into a caller-owned host
+ * buffer, pure host work; irp_plan_launch copies it into the workspace with
+ * one cudaMemcpyAsync and launches.  With plan_host in pinned memory the
+ * launch is capturable, and a captured graph re-reads plan_host at every
+ * replay, so the caller may re-encode into it between replays. */
+size_t irp_plan_bytes(const irp_set* sets, int nsets, const irp_reduce_params* p);
+irp_status irp_plan_encode(const irp_set* sets, int nsets, const irp_reduce_params* p,
+                           void* plan_host, size_t plan_bytes, void* workspace,
+                           size_t ws_bytes);
+irp_status irp_plan_launch(const void* plan_host, size_t plan_bytes, void* workspace,
+                           size_t ws_bytes, void* stream);
+
+/* Synchronises the stream, returns and clears the device status latched in
+ * the workspace's status word. */
+irp_status irp_sync_status(void* workspace, void* stream);
+
+const char* irp_status_string(irp_status s);
+int irp_version(void);
+
+/* Number of SMs of the current device (autotuning helper). */
+int irp_device_sm_count(void);
+
+/* Launch tracing: while enabled, every kernel the library launches is
+ * bracketed by CUDA events recorded on its stream.  irp_profile_read
+ * synchronises those events, writes per kernel kind the summed device time
+ * (ms) and the launch count, clears the record and returns the number of
+ * kinds written (at most max_kinds; kinds are the IRP_KERNEL_* values). */
+enum {
+  IRP_KERNEL_REDUCE = 0,     /* fused calibrate/resample/combine tile kernel */
+  IRP_KERNEL_PREFILTER = 1,  /* spline coefficients of raw frames            */
+  IRP_KERNEL_STATS = 2,      /* FP64 frame and master sums                   */
+  IRP_KERNEL_CALIBRATE = 3,
+  IRP_KERNEL_SHIFT = 4,      /* includes the spline prefilter of irp_shift   */
+  IRP_KERNEL_COMBINE = 5,
+  IRP_KERNEL_KINDS = 6
+};
+void irp_profile_enable(int on);
+int irp_profile_read(double* ms_out, int64_t* launches_out, int max_kinds);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IRP_H */

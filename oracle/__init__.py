@@ -82,6 +82,9 @@ def lib():
             L.oracle_clip.argtypes = [p, p, i, ctypes.POINTER(ClipParams), p, p, p, p]
             L.oracle_median.restype = d
             L.oracle_median.argtypes = [p, p, i]
+            L.oracle_combine_stack.restype = None
+            L.oracle_combine_stack.argtypes = [p, p, i, i64, ctypes.POINTER(ClipParams), i,
+                                               p, p, p, p, p]
             L.oracle_reduce_set.restype = i
             L.oracle_reduce_set.argtypes = [p, i64, i64, i, i, i, p, p, p, i64, p, p, p, i, i,
                                             ctypes.POINTER(ClipParams), i, i64, p, p,
@@ -174,23 +177,22 @@ def median(x, valid=None):
     return float(lib().oracle_median(_ptr(x), _ptr(valid), n))
 
 
-def combine_stack(stack, valid, **kw):
+def combine_stack(stack, valid, nthreads=1, **kw):
     """Per-pixel clip + median over an aligned stack [n, H, W] (FP64 in, FP64 out)."""
-    stack = np.asarray(stack, dtype=np.float64)
-    n, H, W = stack.shape
-    valid = np.asarray(valid, dtype=np.uint8)
-    mean = np.empty((H, W))
-    med = np.empty((H, W))
-    kept = np.empty((H, W), dtype=np.int32)
-    margin = np.empty((H, W))
-    rej = np.empty((n, H, W), dtype=bool)
-    for y in range(H):
-        for x in range(W):
-            m, k, r, g = clip(stack[:, y, x], valid[:, y, x], **kw)
-            mean[y, x], kept[y, x], margin[y, x] = m, k, g
-            rej[:, y, x] = r
-            med[y, x] = median(stack[:, y, x], valid[:, y, x])
-    return dict(mean=mean, median=med, nkept=kept, margin=margin, rejected=rej)
+    stack = np.ascontiguousarray(stack, dtype=np.float64)
+    n = stack.shape[0]
+    shape = stack.shape[1:]
+    P = int(np.prod(shape))
+    valid = np.ascontiguousarray(valid, dtype=np.uint8)
+    mean = np.empty(shape)
+    med = np.empty(shape)
+    kept = np.empty(shape, dtype=np.int32)
+    margin = np.empty(shape)
+    rej = np.empty(stack.shape, dtype=np.uint8)
+    cp = clip_params(**kw)
+    lib().oracle_combine_stack(_ptr(stack), _ptr(valid), n, P, ctypes.byref(cp), int(nthreads),
+                               _ptr(mean), _ptr(med), _ptr(kept), _ptr(margin), _ptr(rej))
+    return dict(mean=mean, median=med, nkept=kept, margin=margin, rejected=rej.astype(bool))
 
 
 def reduce_set(fs, interp="bilinear", kappa=3.0, max_iter=3, center="mean", ddof=0,

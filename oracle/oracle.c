@@ -398,3 +398,39 @@ int oracle_reduce_set(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stri
   free(src);
   return 0;
 }
+
+void oracle_combine_stack(const double* stack, const uint8_t* valid, int n, int64_t P,
+                          const oracle_clip_params* clip, int nthreads, double* mean,
+                          double* median, int32_t* nkept, double* min_margin,
+                          uint8_t* rejected) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel if (nthreads > 1)
+  {
+    double* x = (double*)malloc(sizeof(double) * (size_t)n);
+    uint8_t* ok = (uint8_t*)malloc((size_t)n);
+    uint8_t* rej = (uint8_t*)malloc((size_t)n);
+#pragma omp for schedule(dynamic, 1024)
+    for (int64_t o = 0; o < P; ++o) {
+      for (int k = 0; k < n; ++k) {
+        x[k] = stack[(int64_t)k * P + o];
+        ok[k] = valid[(int64_t)k * P + o];
+      }
+      int kept = 0;
+      double mg = INFINITY, mu = 0.0;
+      oracle_clip(x, ok, n, clip, &mu, &kept, rej, &mg);
+      mean[o] = mu;
+      nkept[o] = kept;
+      min_margin[o] = mg;
+      median[o] = oracle_median(x, ok, n);
+      if (rejected)
+        for (int k = 0; k < n; ++k) rejected[(int64_t)k * P + o] = rej[k];
+    }
+    free(x);
+    free(ok);
+    free(rej);
+  }
+}

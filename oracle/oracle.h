@@ -73,6 +73,12 @@ void oracle_clip(const double* x, const uint8_t* valid, int n, const oracle_clip
 /* Median of the valid entries (mean of the two middle values for even counts). */
 double oracle_median(const double* x, const uint8_t* valid, int n);
 
+/* Clip + median of every pixel of an aligned stack [n][P] (P pixels). */
+void oracle_combine_stack(const double* stack, const uint8_t* valid, int n, int64_t P,
+                          const oracle_clip_params* clip, int nthreads, double* mean,
+                          double* median, int32_t* nkept, double* min_margin,
+                          uint8_t* rejected);
+
 /* Whole frame set.  raw frame k starts at raw + k*frame_stride (elements).
  * If npix > 0 only the output pixels (px[i], py[i]) are computed and written at
  * index i; else the full W*H grid is written row-major.  stack/valid (nullable,

@@ -1,0 +1,819 @@
+// api.cu -- the C ABI declared in include/irp.h.
+//
+// Host responsibilities: validate arguments before anything is enqueued,
+// split every frame offset in FP64 into an integer tap origin, fractional
+// weights and a validity range, build the launch plan (set and frame
+// descriptors), and launch the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "unfused.h"
+
+using namespace irp;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr uint32_t kPlanMagic = 0x49525031u;  // "IRP1"
+constexpr int kMaxSub = 8;
+constexpr int kDefaultSpin = 1 << 20;  // polls of 1 us: about one second
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ------------------------------------------------------------------ tracing
+struct TraceRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+struct Tracer {
+  bool on = false;
+  std::vector<TraceRec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+Tracer& tracer() {
+  static Tracer t;
+  return t;
+}
+
+// Brackets the launches issued between construction and destruction.
+struct TraceScope {
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  TraceScope(int k, cudaStream_t st) : kind(k), s(st) {
+    if (tracer().on) {
+      a = tracer().get();
+      cudaEventRecord(a, s);
+    }
+  }
+  ~TraceScope() {
+    if (a) {
+      cudaEvent_t b = tracer().get();
+      cudaEventRecord(b, s);
+      tracer().recs.push_back(TraceRec{kind, a, b});
+    }
+  }
+};
+inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+inline irp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? IRP_OK : IRP_ERR_CUDA; }
+
+// Offset split along one axis: sample of output coordinate p is at
+// (p + o) + tap, o the integer origin; valid iff v0 <= p <= v1.
+struct Axis {
+  int o;
+  float f;
+  int v0, v1;
+  float w[4];
+};
+
+bool split_axis(double d, int N, int interp, Axis& a) {
+  if (!std::isfinite(d) || std::fabs(d) > 1.0e9) return false;
+  const double fl = std::floor(d);
+  const double f = d - fl;  // exact in FP64
+  const int ifl = (int)fl;
+  a.f = (float)f;
+  for (int i = 0; i < 4; ++i) a.w[i] = 0.0f;
+  if (interp == IRP_INTERP_NEAREST) {
+    // nearest integer to (p + ifl) + f, halves away from zero
+    if (f < 0.5) {
+      a.o = ifl;
+      a.v0 = -ifl;
+      a.v1 = N - 1 - ifl;
+    } else if (f > 0.5) {
+      a.o = ifl + 1;
+      a.v0 = -ifl - 1;
+      a.v1 = N - 2 - ifl;
+    } else {  // p + ifl + 0.5 rounds up iff p + ifl >= 0, else it is invalid
+      a.o = ifl + 1;
+      a.v0 = -ifl;
+      a.v1 = N - 2 - ifl;
+    }
+    a.w[0] = 1.0f;
+    return true;
+  }
+  // taps with non-zero weight must lie inside: i0 >= 0, i0 + (f > 0) <= N - 1
+  a.v0 = -ifl;
+  a.v1 = N - 1 - ifl - (f > 0.0 ? 1 : 0);
+  if (interp == IRP_INTERP_BILINEAR) {
+    a.o = ifl;
+    a.w[0] = (float)(1.0 - f);
+    a.w[1] = (float)f;
+  } else {  // cubic B-spline taps at i0 - 1 .. i0 + 2
+    a.o = ifl - 1;
+    for (int i = 0; i < 4; ++i) {
+      const double t = std::fabs(f + 1.0 - i);
+      double b = 0.0;
+      if (t < 1.0) b = 2.0 / 3.0 - t * t + 0.5 * t * t * t;
+      else if (t < 2.0) b = (2.0 - t) * (2.0 - t) * (2.0 - t) / 6.0;
+      a.w[i] = (float)b;
+    }
+  }
+  return true;
+}
+
+bool fill_geometry(FrameDesc& F, double dx, double dy, int W, int H, int interp) {
+  Axis ax, ay;
+  if (!split_axis(dx, W, interp, ax) || !split_axis(dy, H, interp, ay)) return false;
+  F.ox = ax.o;
+  F.oy = ay.o;
+  F.fx = ax.f;
+  F.fy = ay.f;
+  F.vx0 = std::max(ax.v0, 0);
+  F.vx1 = std::min(ax.v1, W - 1);
+  F.vy0 = std::max(ay.v0, 0);
+  F.vy1 = std::min(ay.v1, H - 1);
+  for (int i = 0; i < 4; ++i) {
+    F.wx[i] = ax.w[i];
+    F.wy[i] = ay.w[i];
+  }
+  return true;
+}
+
+int stencil_of(irp_interp i) {
+  return i == IRP_INTERP_NEAREST ? ST_NEAREST : (i == IRP_INTERP_BILINEAR ? ST_BILINEAR : ST_BSPLINE);
+}
+
+bool clip_ok(const irp_clip_params& c) {
+  return std::isfinite(c.kappa_lo) && std::isfinite(c.kappa_hi) && c.kappa_lo > 0.0f &&
+         c.kappa_hi > 0.0f && c.max_iter >= 0 && c.max_iter <= 1000 && (c.center == 0 || c.center == 1) &&
+         (c.ddof == 0 || c.ddof == 1);
+}
+
+irp_status check_set(const irp_set& s) {
+  if (!s.frames || s.W < 1 || s.H < 1 || s.n < 1) return IRP_ERR_INVALID_ARG;
+  if (s.n > IRP_MAX_FRAMES) return IRP_ERR_UNSUPPORTED;
+  if ((int64_t)s.W * s.H > (int64_t)1 << 31) return IRP_ERR_UNSUPPORTED;
+  if (s.raw_pitch < s.W || s.master_pitch < s.W) return IRP_ERR_INVALID_ARG;
+  if (!s.dx || !s.dy || !s.exptime || !s.bias || !s.dark_rate || !s.flat) return IRP_ERR_INVALID_ARG;
+  if (!s.mean_out && !s.median_out && !s.nkept_out && !s.stack_out) return IRP_ERR_INVALID_ARG;
+  if ((s.mean_out || s.median_out || s.nkept_out || s.stack_out) && s.out_pitch < s.W)
+    return IRP_ERR_INVALID_ARG;
+  if (!aligned(s.bias, 4) || !aligned(s.dark_rate, 4) || !aligned(s.flat, 4) ||
+      !aligned(s.mean_out, 4) || !aligned(s.median_out, 4) || !aligned(s.nkept_out, 2) ||
+      !aligned(s.stack_out, 4) || !aligned(s.ready_flag, 4))
+    return IRP_ERR_ALIGNMENT;
+  for (int k = 0; k < s.n; ++k) {
+    if (!s.frames[k]) return IRP_ERR_INVALID_ARG;
+    if (!aligned(s.frames[k], 2)) return IRP_ERR_ALIGNMENT;
+    if (!std::isfinite(s.exptime[k]) || !std::isfinite(s.dx[k]) || !std::isfinite(s.dy[k]) ||
+        std::fabs(s.dx[k]) > 1.0e9 || std::fabs(s.dy[k]) > 1.0e9)
+      return IRP_ERR_INVALID_ARG;
+  }
+  return IRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch plan of irp_reduce_set.  Sets are grouped by register bucket of
+// their frame count (one kernel instantiation each); within a group they are
+// ordered by decreasing frame count, so that a persistent launch hands out
+// the most expensive tiles first.
+// ---------------------------------------------------------------------------
+struct SubInfo {
+  uint64_t dev_off;     // offset of this sub-plan image inside the workspace
+  uint64_t img_off;     // offset of the image inside the plan file
+  uint64_t bytes;       // image size
+  uint64_t smem;        // dynamic shared memory of the reduce launch
+  int32_t bucket, stencil, grid, pgrid;
+  int32_t nitems, counter, nsets, nframes;
+};
+
+struct PlanFile {
+  uint32_t magic;
+  int32_t nsub, interp, normalize_flat;
+  int32_t nflat, persistent, pad[2];
+  uint64_t ws_required;
+  uint64_t flat_off;    // FrameStats[nflat] in the workspace
+  SubInfo sub[kMaxSub];
+};
+
+struct FlatJob {  // follows PlanFile: one FP64 flat sum per set (normalize_flat)
+  const float* flat;
+  int64_t pitch;
+  int32_t W, H;
+};
+
+struct Layout {
+  size_t flat_off, plan_off, coef_off, total;
+  std::vector<size_t> coef_frame_off;  // per set: offset of its first coefficient frame
+};
+
+size_t coef_frame_bytes(int W, int H) { return align_up((size_t)W * H * sizeof(float), kAlign); }
+
+void group_sets(const irp_set* sets, int nsets, std::vector<std::vector<int>>& groups) {
+  std::vector<int> order(nsets);
+  for (int i = 0; i < nsets; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sets[a].n > sets[b].n; });
+  groups.clear();
+  int cur_bucket = -1;
+  for (int i : order) {
+    const int b = reduce_bucket(sets[i].n);
+    if (b != cur_bucket) {
+      groups.emplace_back();
+      cur_bucket = b;
+    }
+    groups.back().push_back(i);
+  }
+}
+
+Layout make_layout(const irp_set* sets, int nsets, const irp_reduce_params* p,
+                   const std::vector<std::vector<int>>& groups) {
+  Layout L;
+  size_t off = sizeof(WsHeader);
+  L.flat_off = off;
+  off += align_up((size_t)nsets * sizeof(FrameStats), kAlign);
+  L.plan_off = off;
+  for (const auto& g : groups) {
+    int nf = 0;
+    for (int i : g) nf += sets[i].n;
+    off += align_up(plan_total_bytes((int)g.size(), nf), kAlign);
+  }
+  L.coef_off = off;
+  L.coef_frame_off.assign(nsets, 0);
+  if (p->interp == IRP_INTERP_SPLINE3) {
+    for (int i = 0; i < nsets; ++i) {
+      L.coef_frame_off[i] = off;
+      off += (size_t)sets[i].n * coef_frame_bytes(sets[i].W, sets[i].H);
+    }
+  }
+  L.total = off;
+  return L;
+}
+
+irp_status check_params(const irp_set* sets, int nsets, const irp_reduce_params* p) {
+  if (!sets || !p || nsets < 1) return IRP_ERR_INVALID_ARG;
+  if (p->interp < IRP_INTERP_NEAREST || p->interp > IRP_INTERP_SPLINE3) return IRP_ERR_INVALID_ARG;
+  if (!clip_ok(p->clip)) return IRP_ERR_INVALID_ARG;
+  if (p->max_ctas < 0 || p->wait_spin_limit < 0) return IRP_ERR_INVALID_ARG;
+  for (int i = 0; i < nsets; ++i) {
+    irp_status st = check_set(sets[i]);
+    if (st != IRP_OK) return st;
+  }
+  std::vector<std::vector<int>> groups;
+  group_sets(sets, nsets, groups);
+  if ((int)groups.size() > kMaxSub) return IRP_ERR_UNSUPPORTED;
+  return IRP_OK;
+}
+
+// Device count of SMs, cached per process.
+int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 1;
+  }
+  return sms;
+}
+
+size_t plan_file_bytes(const irp_set* sets, int nsets, const irp_reduce_params* p) {
+  std::vector<std::vector<int>> groups;
+  group_sets(sets, nsets, groups);
+  size_t off = align_up(sizeof(PlanFile) + (size_t)nsets * sizeof(FlatJob), 64);
+  for (const auto& g : groups) {
+    int nf = 0;
+    for (int i : g) nf += sets[i].n;
+    off += align_up(plan_total_bytes((int)g.size(), nf), 64);
+  }
+  (void)p;
+  return off;
+}
+
+// Encodes the plan file.  Needs the workspace address (descriptors point into
+// it) but touches neither the device nor the workspace contents.
+irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* p, uint8_t* buf,
+                       size_t buf_bytes, uint8_t* ws, size_t ws_bytes) {
+  std::vector<std::vector<int>> groups;
+  group_sets(sets, nsets, groups);
+  const Layout L = make_layout(sets, nsets, p, groups);
+  if (!ws || !aligned(ws, kAlign)) return IRP_ERR_WORKSPACE;
+  if (ws_bytes < L.total) return IRP_ERR_WORKSPACE;
+  if (buf_bytes < plan_file_bytes(sets, nsets, p)) return IRP_ERR_INVALID_ARG;
+  std::memset(buf, 0, plan_file_bytes(sets, nsets, p));
+  PlanFile* pf = (PlanFile*)buf;
+  pf->magic = kPlanMagic;
+  pf->nsub = (int)groups.size();
+  pf->interp = p->interp;
+  pf->normalize_flat = p->normalize_flat ? 1 : 0;
+  pf->nflat = p->normalize_flat ? nsets : 0;
+  pf->persistent = p->persistent ? 1 : 0;
+  pf->ws_required = L.total;
+  pf->flat_off = L.flat_off;
+  FlatJob* fj = (FlatJob*)(buf + sizeof(PlanFile));
+  for (int i = 0; i < nsets; ++i) {
+    fj[i].flat = sets[i].flat;
+    fj[i].pitch = sets[i].master_pitch;
+    fj[i].W = sets[i].W;
+    fj[i].H = sets[i].H;
+  }
+  const int stencil = stencil_of(p->interp);
+  const int taps = stencil == ST_BSPLINE ? 4 : (stencil == ST_BILINEAR ? 2 : 1);
+  WsHeader* wsh = (WsHeader*)ws;
+  size_t img_off = align_up(sizeof(PlanFile) + (size_t)nsets * sizeof(FlatJob), 64);
+  size_t dev_off = L.plan_off;
+  for (int gi = 0; gi < (int)groups.size(); ++gi) {
+    const auto& g = groups[gi];
+    int nf = 0, max_n = 0, mw_max = 0, mh_max = 0;
+    for (int i : g) {
+      nf += sets[i].n;
+      max_n = std::max(max_n, sets[i].n);
+    }
+    uint8_t* img = buf + img_off;
+    PlanHeader* h = (PlanHeader*)img;
+    SetDesc* sd = (SetDesc*)(img + plan_sets_offset());
+    FrameDesc* fd = (FrameDesc*)(img + plan_frames_offset((int)g.size()));
+    int frame0 = 0, tile0 = 0, ptile0 = 0;
+    for (int si = 0; si < (int)g.size(); ++si) {
+      const irp_set& s = sets[g[si]];
+      SetDesc& S = sd[si];
+      S.W = s.W;
+      S.H = s.H;
+      S.n = s.n;
+      S.frame0 = frame0;
+      S.src_pitch = stencil == ST_BSPLINE ? s.W : s.raw_pitch;  // spline reads coefficients
+      S.bias = s.bias;
+      S.dark = s.dark_rate;
+      S.flat = s.flat;
+      S.master_pitch = s.master_pitch;
+      S.flat_sum = p->normalize_flat
+                       ? (const double*)(ws + L.flat_off + (size_t)g[si] * sizeof(FrameStats))
+                       : nullptr;
+      S.mean_out = s.mean_out;
+      S.median_out = s.median_out;
+      S.nkept_out = s.nkept_out;
+      S.stack_out = s.stack_out;
+      S.out_pitch = s.out_pitch;
+      S.tiles_x = (s.W + kTW - 1) / kTW;
+      S.tiles_y = (s.H + kTH - 1) / kTH;
+      S.tile0 = tile0;
+      tile0 += S.tiles_x * S.tiles_y;
+      S.ptiles_x = (s.W + kPrefTile - 1) / kPrefTile;
+      S.ptiles_y = (s.H + kPrefTile - 1) / kPrefTile;
+      S.ptile0 = ptile0;
+      ptile0 += S.ptiles_x * S.ptiles_y * s.n;
+      S.ready_flag = s.ready_flag;
+      S.ready_value = s.ready_value;
+      int oxmin = INT32_MAX, oxmax = INT32_MIN, oymin = INT32_MAX, oymax = INT32_MIN;
+      for (int k = 0; k < s.n; ++k) {
+        FrameDesc& F = fd[frame0 + k];
+        if (!fill_geometry(F, s.dx[k], s.dy[k], s.W, s.H, p->interp)) return IRP_ERR_INVALID_ARG;
+        F.src = s.frames[k];
+        F.t = s.exptime[k];
+        F.scale = 1.0f;
+        F.offset = 0.0f;
+        F.coef = stencil == ST_BSPLINE
+                     ? (float*)(ws + L.coef_frame_off[g[si]] + (size_t)k * coef_frame_bytes(s.W, s.H))
+                     : nullptr;
+        oxmin = std::min(oxmin, F.ox);
+        oxmax = std::max(oxmax, F.ox);
+        oymin = std::min(oymin, F.oy);
+        oymax = std::max(oymax, F.oy);
+      }
+      // master union window: kept when it is at most twice the per-frame window
+      const int mw = kTW + (oxmax - oxmin) + taps - 1, mh = kTH + (oymax - oymin) + taps - 1;
+      if (stencil != ST_BSPLINE && (size_t)mw * mh <= (size_t)8 * (kTW + taps) * (kTH + taps)) {
+        S.mwin_w = mw;
+        S.mwin_h = mh;
+        S.mox = oxmin;
+        S.moy = oymin;
+        mw_max = std::max(mw_max, mw);
+        mh_max = std::max(mh_max, mh);
+      }
+      frame0 += s.n;
+    }
+    h->nsets = (int)g.size();
+    h->nframes = nf;
+    h->nitems = tile0;
+    h->npitems = ptile0;
+    h->stencil = stencil;
+    h->max_n = max_n;
+    h->persistent = p->persistent ? 1 : 0;
+    h->spin_limit = p->wait_spin_limit > 0 ? p->wait_spin_limit : kDefaultSpin;
+    h->src = stencil == ST_BSPLINE ? SRC_F32 : SRC_RAW;
+    h->kappa_lo = p->clip.kappa_lo;
+    h->kappa_hi = p->clip.kappa_hi;
+    h->max_iter = p->clip.max_iter;
+    h->center = p->clip.center;
+    h->ddof = p->clip.ddof;
+    h->smem_samples = max_n * kTilePx;
+    h->smem_master = 3 * mw_max * mh_max;
+    h->status = &wsh->status;
+    h->counter = &wsh->counters[gi];
+    SubInfo& si = pf->sub[gi];
+    si.dev_off = dev_off;
+    si.img_off = img_off;
+    si.bytes = plan_total_bytes((int)g.size(), nf);
+    si.bucket = reduce_bucket(max_n);
+    si.stencil = stencil;
+    si.smem = reduce_smem_bytes(stencil, max_n, mw_max, mh_max);
+    si.nitems = tile0;
+    si.counter = gi;
+    si.nsets = (int)g.size();
+    si.nframes = nf;
+    si.pgrid = stencil == ST_BSPLINE ? ptile0 : 0;
+    if (si.smem > 227 * 1024) return IRP_ERR_UNSUPPORTED;
+    if (p->persistent) {
+      const int occ = reduce_occupancy(si.bucket, stencil, si.smem);
+      int g_ctas = p->max_ctas > 0 ? p->max_ctas : occ * sm_count();
+      si.grid = std::max(1, std::min(g_ctas, tile0));
+    } else {
+      si.grid = tile0;
+    }
+    img_off += align_up(si.bytes, 64);
+    dev_off += align_up(si.bytes, kAlign);
+  }
+  return IRP_OK;
+}
+
+// Launches an encoded plan.  ``upload``: copy the sub-plan images into the
+// workspace (else every sub-plan is passed by value as a kernel parameter).
+irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream_t s, bool upload) {
+  const PlanFile* pf = (const PlanFile*)buf;
+  if (pf->magic != kPlanMagic || pf->nsub < 1 || pf->nsub > kMaxSub) return IRP_ERR_INVALID_ARG;
+  if (!ws || !aligned(ws, kAlign) || ws_bytes < pf->ws_required) return IRP_ERR_WORKSPACE;
+  WsHeader* wsh = (WsHeader*)ws;
+  cudaError_t e = cudaSuccess;
+  if (upload) {
+    // the images are contiguous in the file and in the workspace up to padding;
+    // copy them one by one (one copy per sub-plan)
+    for (int i = 0; i < pf->nsub && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(ws + pf->sub[i].dev_off, buf + pf->sub[i].img_off, pf->sub[i].bytes,
+                          cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return IRP_ERR_CUDA;
+  }
+  if (pf->nflat > 0) {
+    FrameStats* st = (FrameStats*)(ws + pf->flat_off);
+    const FlatJob* fj = (const FlatJob*)(buf + sizeof(PlanFile));
+    TraceScope tr(IRP_KERNEL_STATS, s);
+    e = launch_stats_init(st, pf->nflat, s);
+    for (int i = 0; i < pf->nflat && e == cudaSuccess; ++i)
+      e = launch_stats_frames(fj[i].flat, fj[i].pitch, 0, fj[i].W, fj[i].H, 1, false, nullptr,
+                              nullptr, nullptr, nullptr, nullptr, st + i, s);
+    if (e != cudaSuccess) return IRP_ERR_CUDA;
+  }
+  for (int i = 0; i < pf->nsub; ++i) {
+    const SubInfo& si = pf->sub[i];
+    const void* dev_plan = upload ? (const void*)(ws + si.dev_off) : nullptr;
+    InlinePlan inl;
+    if (!upload) {
+      // repack the image (header, sets, frames) into the fixed inline layout
+      const uint8_t* img = buf + si.img_off;
+      std::memset(&inl, 0, sizeof(inl));
+      std::memcpy(&inl.h, img, sizeof(PlanHeader));
+      std::memcpy(inl.sets, img + plan_sets_offset(), (size_t)si.nsets * sizeof(SetDesc));
+      std::memcpy(inl.frames, img + plan_frames_offset(si.nsets), (size_t)si.nframes * sizeof(FrameDesc));
+    } else {
+      std::memset(&inl.h, 0, sizeof(PlanHeader));
+    }
+    if (si.pgrid > 0) {
+      TraceScope tr(IRP_KERNEL_PREFILTER, s);
+      e = launch_prefilter_raw(&inl, dev_plan, si.pgrid, s);
+      if (e != cudaSuccess) return IRP_ERR_CUDA;
+    }
+    if (pf->persistent) {
+      e = cudaMemsetAsync(&wsh->counters[si.counter], 0, sizeof(uint32_t), s);
+      if (e != cudaSuccess) return IRP_ERR_CUDA;
+    }
+    {
+      TraceScope tr(IRP_KERNEL_REDUCE, s);
+      e = launch_reduce(si.bucket, si.stencil, &inl, dev_plan, si.grid, si.smem, s);
+    }
+    if (e != cudaSuccess) return IRP_ERR_CUDA;
+  }
+  return IRP_OK;
+}
+
+bool plan_fits_inline(const uint8_t* buf) {
+  const PlanFile* pf = (const PlanFile*)buf;
+  for (int i = 0; i < pf->nsub; ++i)
+    if (pf->sub[i].nsets > kMaxInlineSets || pf->sub[i].nframes > kMaxInlineFrames) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int irp_version(void) { return IRP_VERSION; }
+
+const char* irp_status_string(irp_status s) {
+  switch (s) {
+    case IRP_OK: return "ok";
+    case IRP_ERR_INVALID_ARG: return "invalid argument";
+    case IRP_ERR_ALIGNMENT: return "misaligned buffer";
+    case IRP_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case IRP_ERR_UNSUPPORTED: return "unsupported request";
+    case IRP_ERR_BAD_MASTER: return "flat master value not finite or not positive";
+    case IRP_ERR_CUDA: return "CUDA runtime error";
+    case IRP_ERR_TIMEOUT: return "bounded device wait timed out";
+  }
+  return "unknown status";
+}
+
+int irp_device_sm_count(void) { return sm_count(); }
+
+void irp_profile_enable(int on) { tracer().on = on != 0; }
+
+int irp_profile_read(double* ms_out, int64_t* launches_out, int max_kinds) {
+  const int kinds = std::min(max_kinds, (int)IRP_KERNEL_KINDS);
+  for (int k = 0; k < kinds; ++k) {
+    if (ms_out) ms_out[k] = 0.0;
+    if (launches_out) launches_out[k] = 0;
+  }
+  Tracer& t = tracer();
+  for (const TraceRec& r : t.recs) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess &&
+        r.kind < kinds) {
+      if (ms_out) ms_out[r.kind] += ms;
+      if (launches_out) launches_out[r.kind] += 1;
+    }
+    t.pool.push_back(r.a);
+    t.pool.push_back(r.b);
+  }
+  t.recs.clear();
+  return kinds;
+}
+
+size_t irp_workspace_size(const irp_set* sets, int nsets, const irp_reduce_params* p) {
+  if (check_params(sets, nsets, p) != IRP_OK) return 0;
+  std::vector<std::vector<int>> groups;
+  group_sets(sets, nsets, groups);
+  return make_layout(sets, nsets, p, groups).total;
+}
+
+size_t irp_plan_bytes(const irp_set* sets, int nsets, const irp_reduce_params* p) {
+  if (check_params(sets, nsets, p) != IRP_OK) return 0;
+  return plan_file_bytes(sets, nsets, p);
+}
+
+irp_status irp_plan_encode(const irp_set* sets, int nsets, const irp_reduce_params* p,
+                           void* plan_host, size_t plan_bytes, void* workspace, size_t ws_bytes) {
+  irp_status st = check_params(sets, nsets, p);
+  if (st != IRP_OK) return st;
+  if (!plan_host) return IRP_ERR_INVALID_ARG;
+  return encode_plan(sets, nsets, p, (uint8_t*)plan_host, plan_bytes, (uint8_t*)workspace, ws_bytes);
+}
+
+irp_status irp_plan_launch(const void* plan_host, size_t plan_bytes, void* workspace,
+                           size_t ws_bytes, void* stream) {
+  if (!plan_host || plan_bytes < sizeof(PlanFile)) return IRP_ERR_INVALID_ARG;
+  return run_plan((const uint8_t*)plan_host, (uint8_t*)workspace, ws_bytes, (cudaStream_t)stream,
+                  true);
+}
+
+irp_status irp_reduce_set(const irp_set* sets, int nsets, const irp_reduce_params* p,
+                          void* workspace, size_t ws_bytes, void* stream) {
+  irp_status st = check_params(sets, nsets, p);
+  if (st != IRP_OK) return st;
+  std::vector<uint8_t> buf(plan_file_bytes(sets, nsets, p));
+  st = encode_plan(sets, nsets, p, buf.data(), buf.size(), (uint8_t*)workspace, ws_bytes);
+  if (st != IRP_OK) return st;
+  // Small plans travel as kernel parameters; larger ones are copied from this
+  // pageable buffer (cudaMemcpyAsync then returns after staging the data).
+  return run_plan(buf.data(), (uint8_t*)workspace, ws_bytes, (cudaStream_t)stream,
+                  !plan_fits_inline(buf.data()));
+}
+
+irp_status irp_sync_status(void* workspace, void* stream) {
+  if (!workspace || !aligned(workspace, kAlign)) return IRP_ERR_WORKSPACE;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return IRP_ERR_CUDA;
+  uint32_t status = 0;
+  e = cudaMemcpy(&status, workspace, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return IRP_ERR_CUDA;
+  if (status != 0) {
+    e = cudaMemset(workspace, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) return IRP_ERR_CUDA;
+  }
+  return (irp_status)status;
+}
+
+// ------------------------------------------------------------------ calibrate
+size_t irp_calibrate_workspace_size(int n) {
+  if (n < 1) return 0;
+  return sizeof(WsHeader) + align_up((size_t)(n + 1) * sizeof(FrameStats), kAlign);
+}
+
+irp_status irp_calibrate(const uint16_t* raw, int64_t raw_pitch, int64_t raw_frame_stride,
+                         int W, int H, int n, const float* bias, const float* dark_rate,
+                         const float* flat, int64_t master_pitch, const float* exptime_host,
+                         int normalize_flat, void* out, int64_t out_pitch,
+                         int64_t out_frame_stride, irp_stack_dtype dt, float* scale_out,
+                         float* offset_out, void* workspace, size_t ws_bytes, void* stream) {
+  if (!raw || !bias || !dark_rate || !flat || !exptime_host || !out) return IRP_ERR_INVALID_ARG;
+  if (W < 1 || H < 1 || n < 1 || raw_pitch < W || master_pitch < W || out_pitch < W)
+    return IRP_ERR_INVALID_ARG;
+  if (raw_frame_stride < raw_pitch * H && n > 1) return IRP_ERR_INVALID_ARG;
+  if (out_frame_stride < out_pitch * H && n > 1) return IRP_ERR_INVALID_ARG;
+  if (dt != IRP_F32 && dt != IRP_F16_SCALED) return IRP_ERR_INVALID_ARG;
+  if (dt == IRP_F16_SCALED && (!scale_out || !offset_out)) return IRP_ERR_INVALID_ARG;
+  if (!aligned(raw, 2) || !aligned(bias, 4) || !aligned(dark_rate, 4) || !aligned(flat, 4) ||
+      !aligned(out, dt == IRP_F32 ? 4 : 2) || !aligned(scale_out, 4) || !aligned(offset_out, 4))
+    return IRP_ERR_ALIGNMENT;
+  for (int k = 0; k < n; ++k)
+    if (!std::isfinite(exptime_host[k])) return IRP_ERR_INVALID_ARG;
+  if (!workspace || !aligned(workspace, kAlign)) return IRP_ERR_WORKSPACE;
+  if (ws_bytes < irp_calibrate_workspace_size(n)) return IRP_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  WsHeader* wsh = (WsHeader*)workspace;
+  FrameStats* st = (FrameStats*)((uint8_t*)workspace + sizeof(WsHeader));
+  FrameStats* flat_st = st + n;
+  TraceScope tr(IRP_KERNEL_CALIBRATE, s);
+  cudaError_t e = launch_stats_init(st, n + 1, s);
+  if (e == cudaSuccess && normalize_flat)
+    e = launch_stats_frames(flat, master_pitch, 0, W, H, 1, false, nullptr, nullptr, nullptr,
+                            nullptr, nullptr, flat_st, s);
+  if (e != cudaSuccess) return IRP_ERR_CUDA;
+  CalibArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.raw = raw;
+  a.raw_pitch = raw_pitch;
+  a.raw_frame_stride = raw_frame_stride;
+  a.W = W;
+  a.H = H;
+  a.bias = bias;
+  a.dark = dark_rate;
+  a.flat = flat;
+  a.master_pitch = master_pitch;
+  a.flat_sum = normalize_flat ? &flat_st->sum : nullptr;
+  a.status = &wsh->status;
+  for (int k0 = 0; k0 < n; k0 += kCalibChunk) {
+    const int nk = std::min(kCalibChunk, n - k0);
+    a.k0 = k0;
+    for (int j = 0; j < nk; ++j) a.t[j] = exptime_host[k0 + j];
+    if (dt == IRP_F16_SCALED) {
+      e = launch_stats_raw(a, nk, st, s);
+      if (e != cudaSuccess) return IRP_ERR_CUDA;
+    }
+  }
+  if (dt == IRP_F16_SCALED) {
+    e = launch_f16_scaling(st, n, scale_out, offset_out, s);
+    if (e != cudaSuccess) return IRP_ERR_CUDA;
+  }
+  for (int k0 = 0; k0 < n; k0 += kCalibChunk) {
+    const int nk = std::min(kCalibChunk, n - k0);
+    a.k0 = k0;
+    for (int j = 0; j < nk; ++j) a.t[j] = exptime_host[k0 + j];
+    e = launch_calibrate(a, nk, dt == IRP_F16_SCALED, out, out_pitch, out_frame_stride, scale_out,
+                         offset_out, s);
+    if (e != cudaSuccess) return IRP_ERR_CUDA;
+  }
+  return IRP_OK;
+}
+
+irp_status irp_frame_stats(const void* frames, int64_t pitch, int64_t frame_stride, int W, int H,
+                           int n, irp_stack_dtype dt, const float* scale, const float* offset,
+                           double* sum_out, double* sumsq_out, int64_t* count_out, void* stream) {
+  if (!frames || !sum_out || W < 1 || H < 1 || n < 1 || pitch < W) return IRP_ERR_INVALID_ARG;
+  if (n > 1 && frame_stride < pitch * H) return IRP_ERR_INVALID_ARG;
+  if (dt != IRP_F32 && dt != IRP_F16_SCALED) return IRP_ERR_INVALID_ARG;
+  if (dt == IRP_F16_SCALED && (!scale || !offset)) return IRP_ERR_INVALID_ARG;
+  if (!aligned(frames, dt == IRP_F32 ? 4 : 2) || !aligned(sum_out, 8) || !aligned(sumsq_out, 8) ||
+      !aligned(count_out, 8))
+    return IRP_ERR_ALIGNMENT;
+  if (n > 65535) return IRP_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  TraceScope tr(IRP_KERNEL_STATS, s);
+  cudaError_t e = cudaMemsetAsync(sum_out, 0, sizeof(double) * n, s);
+  if (e == cudaSuccess && sumsq_out) e = cudaMemsetAsync(sumsq_out, 0, sizeof(double) * n, s);
+  if (e == cudaSuccess && count_out) e = cudaMemsetAsync(count_out, 0, sizeof(int64_t) * n, s);
+  if (e == cudaSuccess)
+    e = launch_stats_frames(frames, pitch, frame_stride, W, H, n, dt == IRP_F16_SCALED, scale,
+                            offset, sum_out, sumsq_out, (long long*)count_out, nullptr, s);
+  return cuda_status(e);
+}
+
+// ---------------------------------------------------------------------- shift
+size_t irp_shift_workspace_size(int W, int H, int n, irp_interp interp) {
+  if (W < 1 || H < 1 || n < 1) return 0;
+  if (interp != IRP_INTERP_SPLINE3) return 0;
+  return (size_t)n * coef_frame_bytes(W, H);
+}
+
+irp_status irp_shift(const void* in, int64_t in_pitch, int64_t in_frame_stride, int W, int H,
+                     int n, irp_stack_dtype dt, const float* scale, const float* offset,
+                     const double* dx_host, const double* dy_host, irp_interp interp, void* out,
+                     int64_t out_pitch, int64_t out_frame_stride, uint8_t* valid_out,
+                     void* workspace, size_t ws_bytes, void* stream) {
+  (void)scale;
+  (void)offset;
+  if (!in || !out || !dx_host || !dy_host) return IRP_ERR_INVALID_ARG;
+  if (W < 1 || H < 1 || n < 1 || in_pitch < W || out_pitch < W) return IRP_ERR_INVALID_ARG;
+  if (n > 1 && (in_frame_stride < in_pitch * H || out_frame_stride < out_pitch * H))
+    return IRP_ERR_INVALID_ARG;
+  if (dt != IRP_F32 && dt != IRP_F16_SCALED) return IRP_ERR_INVALID_ARG;
+  if (interp < IRP_INTERP_NEAREST || interp > IRP_INTERP_SPLINE3) return IRP_ERR_INVALID_ARG;
+  const size_t es = dt == IRP_F32 ? 4 : 2;
+  if (!aligned(in, es) || !aligned(out, es)) return IRP_ERR_ALIGNMENT;
+  if (in == out) return IRP_ERR_INVALID_ARG;
+  for (int k = 0; k < n; ++k)
+    if (!std::isfinite(dx_host[k]) || !std::isfinite(dy_host[k]) || std::fabs(dx_host[k]) > 1e9 ||
+        std::fabs(dy_host[k]) > 1e9)
+      return IRP_ERR_INVALID_ARG;
+  const size_t need = irp_shift_workspace_size(W, H, n, interp);
+  if (need > 0 && (!workspace || !aligned(workspace, kAlign) || ws_bytes < need))
+    return IRP_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  TraceScope tr(IRP_KERNEL_SHIFT, s);
+  const int stencil = stencil_of(interp);
+  const bool f16 = dt == IRP_F16_SCALED;
+  ShiftArgs sa;
+  std::memset(&sa, 0, sizeof(sa));
+  sa.in = in;
+  sa.in_pitch = in_pitch;
+  sa.in_fstride = in_frame_stride;
+  sa.W = W;
+  sa.H = H;
+  sa.out = out;
+  sa.out_pitch = out_pitch;
+  sa.out_fstride = out_frame_stride;
+  sa.valid_out = valid_out;
+  for (int k0 = 0; k0 < n; k0 += kShiftChunk) {
+    const int nk = std::min(kShiftChunk, n - k0);
+    sa.k0 = k0;
+    for (int j = 0; j < nk; ++j) {
+      FrameDesc& F = sa.frames[j];
+      std::memset(&F, 0, sizeof(F));
+      fill_geometry(F, dx_host[k0 + j], dy_host[k0 + j], W, H, interp);
+      F.src = (const uint8_t*)in + (size_t)(k0 + j) * in_frame_stride * es;
+      F.coef = stencil == ST_BSPLINE
+                   ? (float*)((uint8_t*)workspace + (size_t)(k0 + j) * coef_frame_bytes(W, H))
+                   : nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    if (stencil == ST_BSPLINE) {
+      InlinePlan inl;
+      std::memset(&inl, 0, sizeof(inl));
+      inl.h.nsets = 1;
+      inl.h.nframes = nk;
+      SetDesc& S = inl.sets[0];
+      S.W = W;
+      S.H = H;
+      S.n = nk;
+      S.src_pitch = in_pitch;
+      S.ptiles_x = (W + kPrefTile - 1) / kPrefTile;
+      S.ptiles_y = (H + kPrefTile - 1) / kPrefTile;
+      inl.h.npitems = S.ptiles_x * S.ptiles_y * nk;
+      for (int j = 0; j < nk; ++j) inl.frames[j] = sa.frames[j];
+      e = launch_prefilter_frames(&inl, inl.h.npitems, f16, s);
+    }
+    if (e == cudaSuccess) e = launch_shift(sa, nk, stencil, f16, s);
+    if (e != cudaSuccess) return IRP_ERR_CUDA;
+  }
+  return IRP_OK;
+}
+
+// -------------------------------------------------------------------- combine
+irp_status irp_combine(const void* stack, int64_t pitch, int64_t frame_stride, int W, int H, int n,
+                       irp_stack_dtype dt, const float* scale, const float* offset,
+                       const uint8_t* valid, const irp_clip_params* clip, float* mean_out,
+                       float* median_out, uint16_t* nkept_out, uint8_t* reject_out,
+                       int64_t out_pitch, void* stream) {
+  if (!stack || !clip || W < 1 || H < 1 || n < 1 || pitch < W || out_pitch < W)
+    return IRP_ERR_INVALID_ARG;
+  if (!mean_out && !median_out && !nkept_out && !reject_out) return IRP_ERR_INVALID_ARG;
+  if (n > 1 && frame_stride < pitch * H) return IRP_ERR_INVALID_ARG;
+  if (n > IRP_MAX_FRAMES) return IRP_ERR_UNSUPPORTED;
+  if (dt != IRP_F32 && dt != IRP_F16_SCALED) return IRP_ERR_INVALID_ARG;
+  if (dt == IRP_F16_SCALED && (!scale || !offset)) return IRP_ERR_INVALID_ARG;
+  if (!clip_ok(*clip)) return IRP_ERR_INVALID_ARG;
+  if (!aligned(stack, dt == IRP_F32 ? 4 : 2) || !aligned(mean_out, 4) || !aligned(median_out, 4) ||
+      !aligned(nkept_out, 2) || !aligned(scale, 4) || !aligned(offset, 4))
+    return IRP_ERR_ALIGNMENT;
+  if (H > 65535) return IRP_ERR_UNSUPPORTED;
+  CombineArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.stack = stack;
+  a.pitch = pitch;
+  a.fstride = frame_stride;
+  a.W = W;
+  a.H = H;
+  a.n = n;
+  a.scale = scale;
+  a.offset = offset;
+  a.valid = valid;
+  a.clip = ClipArgs{clip->kappa_lo, clip->kappa_hi, clip->max_iter, clip->center, clip->ddof};
+  a.mean_out = mean_out;
+  a.median_out = median_out;
+  a.nkept_out = nkept_out;
+  a.reject_out = reject_out;
+  a.out_pitch = out_pitch;
+  TraceScope tr(IRP_KERNEL_COMBINE, (cudaStream_t)stream);
+  return cuda_status(launch_combine(a, dt == IRP_F16_SCALED, (cudaStream_t)stream));
+}
+
+}  // extern "C"

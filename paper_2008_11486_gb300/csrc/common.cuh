@@ -1,0 +1,184 @@
+// common.cuh -- descriptors and device helpers shared by the sm_103a kernels.
+//
+// The fused path reduces frame sets tile by tile: one CTA owns a kTW x kTH
+// tile of the output grid of one set, walks the set's frames, calibrates and
+// resamples each frame's source window into shared memory, and finally
+// combines the per-pixel samples (sigma-clipped mean, median).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "irp.h"
+
+namespace irp {
+
+constexpr int kTW = 32;        // output tile width  (one warp spans a tile row)
+constexpr int kTH = 16;        // output tile height
+constexpr int kThreads = 256;  // 8 warps; each thread samples 2 rows of a column
+constexpr int kTilePx = kTW * kTH;
+constexpr int kWinStride = kTW + 8;  // staging-window row stride (floats)
+constexpr int kWinRows = kTH + 3;    // enough rows for the 4x4 spline stencil
+
+constexpr int kMaxInlineSets = 4;
+constexpr int kMaxInlineFrames = 64;
+
+enum Stencil : int { ST_NEAREST = 0, ST_BILINEAR = 1, ST_BSPLINE = 2 };
+enum Source : int { SRC_RAW = 0, SRC_F32 = 1, SRC_F16 = 2 };
+
+// Cubic-spline prefilter (Sec. 3.2.1's per-line tridiagonal system, solved in
+// the parallel recursive form): c = sqrt(3) (y+ + y- - v), y+ and y- the causal
+// and anti-causal first-order recursions with pole z1 = sqrt(3) - 2.
+constexpr float kZ1 = -0.26794919243112270f;
+constexpr float kSqrt3 = 1.7320508075688772f;
+constexpr int kPrefHalo = 16;  // recursion warm-up; |z1|^17 / (1 - |z1|) < 3e-10
+constexpr int kPrefTile = 64;  // prefilter output tile (square)
+constexpr int kPrefWin = kPrefTile + 2 * kPrefHalo;
+
+// One frame of a set, as the kernels see it (128 bytes).
+struct FrameDesc {
+  const void* src;     // raw uint16 frame (fused path) or FP32/F16 frame
+  float* coef;         // FP32 spline coefficients of the frame (workspace) or null
+  int32_t ox, oy;      // integer tap origin: the stencil's first tap is at
+                       // (x + ox, y + oy) for output pixel (x, y)
+  float fx, fy;        // fractional offsets in [0, 1)
+  float t;             // exposure time (s)
+  float scale, offset; // F16 frames: value = h * scale + offset
+  int32_t vx0, vx1;    // sample valid iff vx0 <= x <= vx1 ...
+  int32_t vy0, vy1;    //              ... and vy0 <= y <= vy1
+  float wx[4], wy[4];  // stencil weights (bilinear: 1-f, f; spline: beta3)
+  int32_t pad[9];
+};
+static_assert(sizeof(FrameDesc) == 128, "FrameDesc layout");
+
+// One frame set (192 bytes).
+struct SetDesc {
+  int32_t W, H, n, frame0;       // frame0: index of frame 0 in the frame table
+  int64_t src_pitch;             // elements of the frames' element type
+  const float* bias;
+  const float* dark;
+  const float* flat;
+  int64_t master_pitch;
+  const double* flat_sum;        // FP64 sum of the flat (normalise) or null
+  float* mean_out;
+  float* median_out;
+  uint16_t* nkept_out;
+  float* stack_out;
+  int64_t out_pitch;
+  int32_t tiles_x, tiles_y;      // output tiles (kTW x kTH)
+  int32_t tile0;                 // first work item of this set
+  int32_t mwin_w, mwin_h;        // master union window (0 = per-frame masters)
+  int32_t mox, moy;              // union window origin relative to the tile
+  int32_t ptiles_x, ptiles_y;    // prefilter tiles (kPrefTile squared)
+  int32_t ptile0;                // first prefilter work item of this set
+  const uint32_t* ready_flag;
+  uint32_t ready_value;
+  int32_t pad1[9];
+};
+static_assert(sizeof(SetDesc) == 192, "SetDesc layout");
+
+struct PlanHeader {
+  int32_t nsets, nframes, nitems, stencil;
+  int32_t max_n, persistent, spin_limit, src;
+  float kappa_lo, kappa_hi;
+  int32_t max_iter, center, ddof;
+  int32_t smem_samples;          // floats reserved per CTA for samples
+  int32_t smem_master;           // floats reserved per CTA for master windows
+  int32_t npitems;               // prefilter work items (spline)
+  uint32_t* status;              // device status word (workspace)
+  uint32_t* counter;             // persistent work counter (workspace)
+};
+static_assert(sizeof(PlanHeader) % 16 == 0, "PlanHeader alignment");
+
+// Plan passed by value as a kernel parameter for small launches.
+struct InlinePlan {
+  PlanHeader h;
+  SetDesc sets[kMaxInlineSets];
+  FrameDesc frames[kMaxInlineFrames];
+};
+
+// Plan in global memory (workspace) for large launches: PlanHeader (128 B),
+// then SetDesc[nsets], then FrameDesc[nframes].
+struct PlanView {
+  const PlanHeader* h;
+  const SetDesc* sets;
+  const FrameDesc* frames;
+};
+
+__host__ __device__ inline size_t plan_sets_offset() { return 128; }
+__host__ __device__ inline size_t plan_frames_offset(int nsets) {
+  return 128 + (size_t)nsets * sizeof(SetDesc);
+}
+__host__ __device__ inline size_t plan_total_bytes(int nsets, int nframes) {
+  return plan_frames_offset(nsets) + (size_t)nframes * sizeof(FrameDesc);
+}
+
+// Workspace header (first 256 bytes of every workspace).
+struct WsHeader {
+  uint32_t status;
+  uint32_t counters[15];
+  uint8_t pad[192];
+};
+static_assert(sizeof(WsHeader) == 256, "WsHeader layout");
+
+__device__ __forceinline__ void latch_status(uint32_t* status, uint32_t code) {
+  if (status) atomicCAS(status, 0u, code);
+}
+
+// Whole-sample symmetric index into [0, N).
+__device__ __forceinline__ int mirror_index(int i, int N) {
+  if (N <= 1) return 0;
+  if (i >= 0 && i < N) return i;
+  int period = 2 * (N - 1);
+  int r = i % period;
+  if (r < 0) r += period;
+  return r >= N ? period - r : r;
+}
+
+__device__ __forceinline__ float bspline3(float t) {
+  float a = fabsf(t);
+  if (a < 1.0f) return 2.0f / 3.0f - a * a + 0.5f * a * a * a;
+  if (a < 2.0f) {
+    float b = 2.0f - a;
+    return b * b * b * (1.0f / 6.0f);
+  }
+  return 0.0f;
+}
+
+// Locates the set owning work item ``item`` (sets ordered by tile0).
+__device__ __forceinline__ int find_set(const SetDesc* sets, int nsets, int item) {
+  int lo = 0, hi = nsets - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (sets[mid].tile0 <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Bounded wait for a set's ready flag; returns false (and latches
+// IRP_ERR_TIMEOUT) if the flag did not reach the value in ``limit`` polls.
+__device__ __forceinline__ bool wait_ready(const uint32_t* flag, uint32_t value, int limit,
+                                           uint32_t* status) {
+  if (!flag) return true;
+  for (int i = 0; i < limit; ++i) {
+    uint32_t v = *((volatile const uint32_t*)flag);
+    if ((int32_t)(v - value) >= 0) return true;
+    __nanosleep(1000);
+  }
+  latch_status(status, IRP_ERR_TIMEOUT);
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (implemented in the kernel files).
+// ---------------------------------------------------------------------------
+cudaError_t launch_reduce(int nmax_bucket, int stencil, const InlinePlan* inl,
+                          const void* plan_dev, int grid, size_t smem, cudaStream_t s);
+size_t reduce_smem_bytes(int stencil, int max_n, int mwin_w, int mwin_h);
+int reduce_bucket(int n);
+int reduce_occupancy(int nmax_bucket, int stencil, size_t smem);
+cudaError_t launch_prefilter_raw(const InlinePlan* inl, const void* plan_dev, int grid,
+                                 cudaStream_t s);
+
+}  // namespace irp

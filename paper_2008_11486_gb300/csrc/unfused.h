@@ -1,0 +1,73 @@
+// unfused.h -- argument blocks and launchers of the separate-step kernels.
+#pragma once
+
+#include "combine.cuh"
+#include "common.cuh"
+
+namespace irp {
+
+constexpr int kCalibChunk = 256;   // frames per calibration launch (times by value)
+constexpr int kShiftChunk = 64;    // frames per shift launch (descriptors by value)
+constexpr float kF16Range = 16384.0f;  // |h| bound of FP16 stacks (4x headroom)
+
+struct FrameStats {  // 32 bytes per frame, workspace
+  double sum, sumsq;
+  long long count;
+  int min_key, max_key;
+};
+
+struct CalibArgs {
+  const uint16_t* raw;
+  int64_t raw_pitch, raw_frame_stride;
+  int W, H, k0, pad;
+  const float* bias;
+  const float* dark;
+  const float* flat;
+  int64_t master_pitch;
+  const double* flat_sum;   // null: no flat normalisation
+  uint32_t* status;
+  float t[kCalibChunk];
+};
+
+struct ShiftArgs {
+  const void* in;
+  int64_t in_pitch, in_fstride;
+  int W, H, k0, pad;
+  void* out;
+  int64_t out_pitch, out_fstride;
+  uint8_t* valid_out;
+  FrameDesc frames[kShiftChunk];
+};
+
+struct CombineArgs {
+  const void* stack;
+  int64_t pitch, fstride;
+  int W, H, n, pad;
+  const float* scale;
+  const float* offset;
+  const uint8_t* valid;
+  ClipArgs clip;
+  float* mean_out;
+  float* median_out;
+  uint16_t* nkept_out;
+  uint8_t* reject_out;
+  int64_t out_pitch;
+};
+
+cudaError_t launch_stats_init(FrameStats* st, int n, cudaStream_t s);
+cudaError_t launch_stats_raw(const CalibArgs& a, int nk, FrameStats* st, cudaStream_t s);
+// Sums into FrameStats (st != null) or into the separate arrays sum/sumsq/count.
+cudaError_t launch_stats_frames(const void* frames, int64_t pitch, int64_t fstride, int W, int H,
+                                int n, bool f16, const float* scale, const float* offset,
+                                double* sum, double* sumsq, long long* count, FrameStats* st,
+                                cudaStream_t s);
+cudaError_t launch_f16_scaling(const FrameStats* st, int n, float* scale, float* offset,
+                               cudaStream_t s);
+cudaError_t launch_calibrate(const CalibArgs& a, int nk, bool f16, void* out, int64_t out_pitch,
+                             int64_t out_fstride, const float* scale, const float* offset,
+                             cudaStream_t s);
+cudaError_t launch_shift(const ShiftArgs& a, int nk, int stencil, bool f16, cudaStream_t s);
+cudaError_t launch_prefilter_frames(const InlinePlan* inl, int grid, bool f16, cudaStream_t s);
+cudaError_t launch_combine(const CombineArgs& a, bool f16, cudaStream_t s);
+
+}  // namespace irp

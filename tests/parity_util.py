@@ -1,0 +1,64 @@
+"""Shared helpers of the GPU parity tests: uploads, oracle runs and the
+tolerances derived from the FP32 arithmetic of the kernels.
+
+Tolerances (reasoning in DESIGN.md, "Parity tolerances"):
+  * clipped mean / median end to end:  |gpu - ref| <= max(1e-3 ADU, 1e-6 |ref|)
+    plus the per-sample bound below (the mean of samples is off by at most
+    the largest sample error);
+  * one resampled sample, nearest / bilinear: 8 u M3 + 1e-5, M3 = largest
+    |v| among the 3x3 source pixels around the tap origin (calibration and
+    two lerps, each a few roundings of values bounded by M3), u = 2^-24;
+  * one resampled sample, cubic spline: 64 u M9 + 1e-4, M9 = largest |v|
+    within 4 px of the tap origin (recursive prefilter of gain sqrt(3) per
+    direction and axis; error terms of farther pixels decay as 0.268^d);
+  * median on identical inputs: bit-exact; clip masks on identical inputs:
+    identical except at pixels the oracle marks within 1e-5 sigma of a
+    threshold.
+"""
+import numpy as np
+
+U = 2.0 ** -24
+
+
+def maxfilter(a, size):
+    from scipy.ndimage import maximum_filter
+    return maximum_filter(np.abs(a), size=size, mode="nearest")
+
+
+def sample_tolerance(fs, interp, oracle_mod):
+    """Per-sample tolerance [n,H,W] of the aligned stack on the output grid."""
+    n, H, W = fs.raw.shape
+    tol = np.empty((n, H, W))
+    size, coef, floor_ = (9, 64.0, 1e-4) if interp == "spline3" else (3, 8.0, 1e-5)
+    yy, xx = np.mgrid[0:H, 0:W]
+    for k in range(n):
+        v = oracle_mod.calibrate(fs.raw[k], fs.bias, fs.dark, fs.flat, fs.exptime[k])
+        M = maxfilter(v, size)
+        sx = np.clip(xx + int(np.floor(fs.dx[k])), 0, W - 1)
+        sy = np.clip(yy + int(np.floor(fs.dy[k])), 0, H - 1)
+        # the tap origin and its right/upper neighbour
+        sx1 = np.clip(sx + 1, 0, W - 1)
+        sy1 = np.clip(sy + 1, 0, H - 1)
+        m = np.maximum(np.maximum(M[sy, sx], M[sy, sx1]), np.maximum(M[sy1, sx], M[sy1, sx1]))
+        tol[k] = coef * U * m + floor_
+    return tol
+
+
+def mean_tolerance(ref):
+    return np.maximum(1e-3, 1e-6 * np.abs(ref))
+
+
+def compare(name, got, ref, tol, mask=None):
+    """Asserts |got - ref| <= tol where mask (and both finite); returns stats."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    both_nan = np.isnan(got) & np.isnan(ref)
+    m = ~both_nan if mask is None else (mask & ~both_nan)
+    assert not np.any(np.isnan(got[m]) != np.isnan(ref[m])), f"{name}: NaN pattern differs"
+    fin = m & np.isfinite(ref)
+    err = np.abs(got - ref)
+    bad = fin & (err > tol)
+    ratio = np.max(err[fin] / np.broadcast_to(tol, err.shape)[fin]) if fin.any() else 0.0
+    assert not bad.any(), (f"{name}: {bad.sum()} of {fin.sum()} outside tolerance, "
+                           f"worst err {err[bad].max():.3g} at ratio {ratio:.3g}")
+    return dict(max_err=float(err[fin].max()) if fin.any() else 0.0, max_ratio=float(ratio))

@@ -1,0 +1,147 @@
+"""The C ABI boundary on the CPU: the library builds and loads, exports every
+function include/irp.h declares, and rejects bad arguments with the exact
+status code before anything is enqueued (no GPU is touched)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2008_11486_gb300 import build as irp_build
+from paper_2008_11486_gb300 import _binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    irp_build.build()
+    return B.lib()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "irp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(irp_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared_functions()
+    assert "irp_reduce_set" in names and "irp_calibrate" in names and len(names) >= 15
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_version_and_status_strings(L):
+    assert L.irp_version() == 10000
+    for code in range(8):
+        assert L.irp_status_string(code)
+    assert L.irp_status_string(99) == b"unknown status"
+
+
+FAKE = 0x7f0000000000  # never dereferenced: validation fails before any launch
+
+
+def _set(n=3, W=64, H=48, frames=None, **kw):
+    ptrs = (ctypes.c_void_p * n)(*([FAKE + 4096 * k for k in range(n)] if frames is None else frames))
+    dx = np.zeros(n)
+    dy = np.zeros(n)
+    t = np.full(n, 60.0, np.float32)
+    s = B.IrpSet()
+    s.frames = ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p))
+    s.raw_pitch = W
+    s.W, s.H, s.n = W, H, n
+    s.dx = dx.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    s.dy = dy.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    s.exptime = t.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    s.bias, s.dark_rate, s.flat = FAKE, FAKE + 1024, FAKE + 2048
+    s.master_pitch = W
+    s.mean_out, s.median_out = FAKE + 8192, FAKE + 16384
+    s.out_pitch = W
+    for k, v in kw.items():
+        setattr(s, k, v)
+    s._keep = (ptrs, dx, dy, t)
+    return s
+
+
+def _params(interp=1, **kw):
+    p = B.ReduceParams(interp, B.ClipParams(3.0, 3.0, 3, 0, 0), 0, 0, 0, 0)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _reduce(L, sets, p, ws=FAKE, ws_bytes=1 << 30):
+    arr = (B.IrpSet * len(sets))(*sets)
+    return L.irp_reduce_set(arr, len(sets), ctypes.byref(p), ctypes.c_void_p(ws), ws_bytes, None)
+
+
+def test_reduce_set_validation_codes(L):
+    assert _reduce(L, [_set()], _params(), ws_bytes=0) == 3            # workspace too small
+    assert _reduce(L, [_set()], _params(), ws=FAKE + 8) == 3           # workspace misaligned
+    assert _reduce(L, [_set(n=65)], _params()) == 4                    # too many frames
+    assert _reduce(L, [_set()], _params(interp=7)) == 1                # bad interpolation
+    assert _reduce(L, [_set(W=0)], _params()) == 1                     # empty frame
+    assert _reduce(L, [_set(raw_pitch=10)], _params()) == 1            # pitch < W
+    assert _reduce(L, [_set(bias=FAKE + 2)], _params()) == 2           # misaligned master
+    assert _reduce(L, [_set(frames=[FAKE, 0, FAKE])], _params()) == 1  # null frame
+    assert _reduce(L, [_set(frames=[FAKE, FAKE + 1, FAKE])], _params()) == 2
+    bad = _params()
+    bad.clip.kappa_lo = -1.0
+    assert _reduce(L, [_set()], bad) == 1
+    bad = _params()
+    bad.clip.ddof = 5
+    assert _reduce(L, [_set()], bad) == 1
+    assert L.irp_reduce_set(None, 1, ctypes.byref(_params()), ctypes.c_void_p(FAKE), 1 << 30,
+                            None) == 1
+    s = _set()
+    s._keep[1][1] = np.nan  # non-finite offset
+    assert _reduce(L, [s], _params()) == 1
+
+
+def test_workspace_size_accounts_for_spline_coefficients(L):
+    s = _set(n=4, W=100, H=30)
+    arr = (B.IrpSet * 1)(s)
+    wb = L.irp_workspace_size(arr, 1, ctypes.byref(_params(interp=1)))
+    ws = L.irp_workspace_size(arr, 1, ctypes.byref(_params(interp=2)))
+    assert wb > 0
+    per_frame = -(-100 * 30 * 4 // 256) * 256
+    assert ws - wb == 4 * per_frame
+    assert L.irp_workspace_size(arr, 1, ctypes.byref(_params(interp=9))) == 0
+    assert L.irp_shift_workspace_size(100, 30, 4, 2) == 4 * per_frame
+    assert L.irp_shift_workspace_size(100, 30, 4, 1) == 0
+    assert L.irp_calibrate_workspace_size(10) >= 256 + 11 * 32
+
+
+def test_unfused_validation_codes(L):
+    clip = B.ClipParams(3.0, 3.0, 3, 0, 0)
+    f = ctypes.c_void_p(FAKE)
+    # combine: n above the register combine limit, null clip, bad dtype
+    assert L.irp_combine(f, 64, 64 * 64, 64, 64, 65, 0, None, None, None, ctypes.byref(clip),
+                         f, f, None, None, 64, None) == 4
+    assert L.irp_combine(f, 64, 64 * 64, 64, 64, 5, 0, None, None, None, None,
+                         f, f, None, None, 64, None) == 1
+    assert L.irp_combine(f, 64, 64 * 64, 64, 64, 5, 3, None, None, None, ctypes.byref(clip),
+                         f, f, None, None, 64, None) == 1
+    assert L.irp_combine(f, 64, 64 * 64, 64, 64, 5, 1, None, None, None, ctypes.byref(clip),
+                         f, f, None, None, 64, None) == 1    # f16 without scale/offset
+    # shift: in == out, bad interp, spline without workspace
+    dx = np.zeros(2)
+    dp = dx.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert L.irp_shift(f, 64, 4096, 64, 64, 2, 0, None, None, dp, dp, 1, f, 64, 4096, None,
+                       None, 0, None) == 1
+    g = ctypes.c_void_p(FAKE + (1 << 20))
+    assert L.irp_shift(f, 64, 4096, 64, 64, 2, 0, None, None, dp, dp, 5, g, 64, 4096, None,
+                       None, 0, None) == 1
+    assert L.irp_shift(f, 64, 4096, 64, 64, 2, 0, None, None, dp, dp, 2, g, 64, 4096, None,
+                       None, 0, None) == 3
+    # calibrate: misaligned raw, f16 without scale outputs, small workspace
+    t = np.full(2, 60.0, np.float32)
+    tp = t.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    assert L.irp_calibrate(ctypes.c_void_p(FAKE + 1), 64, 4096, 64, 64, 2, f, f, f, 64, tp, 0, g,
+                           64, 4096, 0, None, None, f, 4096, None) == 2
+    assert L.irp_calibrate(f, 64, 4096, 64, 64, 2, f, f, f, 64, tp, 0, g, 64, 4096, 1, None,
+                           None, f, 4096, None) == 1
+    assert L.irp_calibrate(f, 64, 4096, 64, 64, 2, f, f, f, 64, tp, 0, g, 64, 4096, 0, None,
+                           None, f, 16, None) == 3

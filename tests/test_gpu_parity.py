@@ -1,0 +1,346 @@
+"""Parity of the CUDA path with the FP64 oracle (needs a GPU: -m gpu).
+
+Every case runs the C ABI through the ctypes binding on seeded synthetic
+frame sets and compares element by element with the oracle on the same
+inputs, at sizes that span several tiles and ragged tile tails."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2008_11486_gb300 import build as irp_build
+from paper_2008_11486_gb300 import core, synth
+from parity_util import compare, mean_tolerance, sample_tolerance
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _native():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    irp_build.build()
+
+
+def run_fused(fs_list, interp, *, kappa=3.0, max_iter=3, persistent=False, want_stack=True,
+              normalize_flat=False, center="mean", ddof=0):
+    sets = [core.device_set(fs).alloc_outputs(want_stack=want_stack) for fs in fs_list]
+    params = core.reduce_params(interp, core.clip_params(kappa, max_iter, center, ddof),
+                                normalize_flat, persistent)
+    ws = core.reduce_sets(sets, params)
+    assert core.sync_status(ws) == 0
+    out = []
+    for s in sets:
+        d = dict(mean=s.mean.cpu().numpy(), median=s.median.cpu().numpy(),
+                 nkept=s.nkept.cpu().numpy().astype(np.int32))
+        if want_stack:
+            d["stack"] = s.stack.cpu().numpy()
+        out.append(d)
+    return out
+
+
+def check_against_oracle(fs, got, interp, kappa, max_iter, normalize_flat=False, check_stack=True):
+    ref = oracle.reduce_set(fs, interp=interp, kappa=kappa, max_iter=max_iter,
+                            normalize_flat=normalize_flat, want_stack=True)
+    stats = {}
+    st = got["stack"]
+    gvalid = ~np.isnan(st)
+    # validity of every sample is integer logic: bit-exact
+    assert np.array_equal(gvalid, ref["valid"]), "sample validity differs"
+    if check_stack and not normalize_flat:
+        tol = sample_tolerance(fs, interp, oracle)
+        stats["stack"] = compare("stack", st, np.where(ref["valid"], ref["stack"], np.nan), tol)
+    else:
+        tol = np.zeros(st.shape)
+    # combine on identical inputs: the oracle fed with the GPU's FP32 samples
+    same = oracle.combine_stack(np.where(gvalid, st, 0.0), gvalid, kappa=kappa,
+                                max_iter=max_iter)
+    med_ref = same["median"].astype(np.float32)
+    assert np.array_equal(np.isnan(got["median"]), np.isnan(med_ref))
+    fin = ~np.isnan(med_ref)
+    assert np.array_equal(got["median"][fin].view(np.uint32), med_ref[fin].view(np.uint32)), \
+        "median not bit-exact on identical inputs"
+    exempt = same["margin"] < 1e-5
+    assert exempt.mean() < 1e-3
+    kept_ok = (got["nkept"] == same["nkept"]) | exempt
+    assert kept_ok.all(), f"clip masks differ at {np.sum(~kept_ok)} non-exempt pixels"
+    agree = (got["nkept"] == same["nkept"])
+    stats["mean_same_inputs"] = compare("mean(same inputs)", got["mean"], same["mean"],
+                                        mean_tolerance(same["mean"]), agree)
+    # end to end against the oracle's own FP64 samples
+    e2e_mask = (ref["margin"] >= 1e-3) & (got["nkept"] == ref["nkept"])
+    assert e2e_mask.mean() > 0.99
+    samp = np.max(np.where(ref["valid"], tol, 0.0), axis=0)
+    stats["mean_e2e"] = compare("mean e2e", got["mean"], ref["mean"],
+                                mean_tolerance(ref["mean"]) + samp, e2e_mask)
+    stats["median_e2e"] = compare("median e2e", got["median"], ref["median"],
+                                  mean_tolerance(ref["median"]) + samp)
+    return stats
+
+
+@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3"])
+def test_fused_small_ragged(interp):
+    fs = synth.make_set(100, 70, 12, 5.0, 501, n_stars=40, n_cr=8)
+    got = run_fused([fs], interp, kappa=2.5)[0]
+    stats = check_against_oracle(fs, got, interp, 2.5, 3)
+    print(interp, stats)
+
+
+def test_fused_small_config_full_size():
+    """5 frames of 512x512, offsets +-5 px, bilinear, 3-sigma 3 iterations."""
+    fs = synth.workload_small()
+    got = run_fused([fs], "bilinear")[0]
+    print(check_against_oracle(fs, got, "bilinear", 3.0, 3))
+
+
+def test_fused_spline_band_full_size_sampled():
+    """One band of the multi-band workload: 10 frames of 1024^2, +-10 px,
+    spline; the oracle evaluates sampled pixels (and every edge pixel)."""
+    fs = synth.workload_bands(n=10)[0]
+    got = run_fused([fs], "spline3", want_stack=False)[0]
+    rng = np.random.default_rng(7)
+    H, W = fs.H, fs.W
+    xs = np.concatenate([rng.integers(0, W, 3000), np.arange(W), np.arange(W),
+                         np.zeros(H, int), np.full(H, W - 1)])
+    ys = np.concatenate([rng.integers(0, H, 3000), np.zeros(W, int), np.full(W, H - 1),
+                         np.arange(H), np.arange(H)])
+    ref = oracle.reduce_set(fs, interp="spline3", pixels=(xs, ys))
+    gm, gd, gk = got["mean"][ys, xs], got["median"][ys, xs], got["nkept"][ys, xs]
+    tol_full = sample_tolerance(fs, "spline3", oracle)
+    samp = tol_full.max(axis=0)[ys, xs]
+    assert np.array_equal(gk, ref["nkept"]) or np.all((gk == ref["nkept"]) | (ref["margin"] < 1e-3))
+    mask = ref["margin"] >= 1e-3
+    print(compare("spline mean", gm, ref["mean"], mean_tolerance(ref["mean"]) + samp, mask))
+    print(compare("spline median", gd, ref["median"], mean_tolerance(ref["median"]) + samp))
+
+
+def test_persistent_and_batch_invariance():
+    """Each set's output is bit-identical alone (plain launch) and inside a
+    persistent batch of uneven sets."""
+    shapes = [(3, 70, 50), (9, 64, 96), (17, 40, 33), (33, 48, 64), (5, 20, 130)]
+    fss = [synth.make_set(W, H, n, 4.0, 900 + i, n_stars=20, n_cr=4)
+           for i, (n, W, H) in enumerate(shapes)]
+    alone = [run_fused([fs], "bilinear", kappa=2.5, want_stack=False)[0] for fs in fss]
+    batch = run_fused(fss, "bilinear", kappa=2.5, persistent=True, want_stack=False)
+    for a, b in zip(alone, batch):
+        for key in ("mean", "median", "nkept"):
+            assert np.array_equal(a[key].view(np.uint8), b[key].view(np.uint8)), key
+    # and the batch matches the oracle
+    for fs, b in zip(fss, batch):
+        ref = oracle.reduce_set(fs, interp="bilinear", kappa=2.5)
+        m = (ref["margin"] >= 1e-3) & (b["nkept"] == ref["nkept"])
+        compare("batch mean", b["mean"], ref["mean"],
+                mean_tolerance(ref["mean"]) + 8 * 2.0 ** -24 * 7e4, m)
+
+
+def test_spline_batch_invariance_and_persistent():
+    fss = [synth.make_set(80, 72, n, 6.0, 300 + n, n_stars=20, n_cr=4) for n in (4, 11)]
+    alone = [run_fused([fs], "spline3", want_stack=False)[0] for fs in fss]
+    batch = run_fused(fss, "spline3", persistent=True, want_stack=False)
+    for a, b in zip(alone, batch):
+        assert np.array_equal(a["mean"].view(np.uint32), b["mean"].view(np.uint32))
+        assert np.array_equal(a["median"].view(np.uint32), b["median"].view(np.uint32))
+
+
+def test_normalize_flat():
+    fs = synth.make_set(70, 50, 6, 3.0, 41, n_stars=20)
+    fs.flat = (fs.flat * 1.7).astype(np.float32)   # not normalised to 1
+    got = run_fused([fs], "bilinear", normalize_flat=True)[0]
+    check_against_oracle(fs, got, "bilinear", 3.0, 3, normalize_flat=True)
+
+
+def test_clip_options_median_centre_and_ddof():
+    fs = synth.make_set(64, 48, 21, 3.0, 77, n_stars=20, n_cr=30)
+    for center, ddof in (("median", 0), ("mean", 1)):
+        got = run_fused([fs], "bilinear", kappa=2.0, center=center, ddof=ddof)[0]
+        st = got["stack"]
+        gvalid = ~np.isnan(st)
+        same = oracle.combine_stack(np.where(gvalid, st, 0.0), gvalid, kappa=2.0, center=center,
+                                    ddof=ddof)
+        ok = (got["nkept"] == same["nkept"]) | (same["margin"] < 1e-5)
+        assert ok.all()
+        compare("clip option mean", got["mean"], same["mean"], mean_tolerance(same["mean"]),
+                got["nkept"] == same["nkept"])
+
+
+# ------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3"])
+def test_edge_shapes_and_offsets(interp):
+    cases = [
+        synth.make_const_set(1, 1, 1, 1500, 1000.0, 0.05, 0.8, 60.0),
+        synth.make_const_set(9, 5, 2, 1500, 1000.0, 0.05, 0.8, 60.0, dx=[0.5, -0.5], dy=[0.0, 0.5]),
+        synth.make_set(9, 33, 3, 1.0, 5, n_stars=3, n_cr=1),
+        synth.make_set(40, 17, 2, 0.0, 6, n_stars=3, n_cr=1),
+    ]
+    # integer offsets: pure pixel moves; huge offsets: no valid sample at all
+    fs = synth.make_set(37, 19, 4, 0.0, 8, n_stars=5, n_cr=2)
+    fs.dx = np.array([0.0, 3.0, -2.0, 1.0])
+    fs.dy = np.array([0.0, -1.0, 2.0, 4.0])
+    cases.append(fs)
+    far = synth.make_set(20, 20, 3, 0.0, 9, n_stars=2, n_cr=0)
+    far.dx = np.array([50.0, -60.5, 1e6])
+    far.dy = np.array([0.0, 0.0, 0.0])
+    cases.append(far)
+    for fs in cases:
+        got = run_fused([fs], interp)[0]
+        ref = oracle.reduce_set(fs, interp=interp, want_stack=True)
+        assert np.array_equal(~np.isnan(got["stack"]), ref["valid"])
+        assert np.array_equal(got["nkept"], ref["nkept"])
+        assert np.array_equal(np.isnan(got["mean"]), np.isnan(ref["mean"]))
+        tol = sample_tolerance(fs, interp, oracle).max(axis=0) + mean_tolerance(ref["mean"])
+        compare("edge mean", got["mean"], ref["mean"], tol)
+    # integer shifts with bilinear/nearest are exact pixel moves of the calibrated frame
+    if interp != "spline3":
+        fs = cases[4]
+        got = run_fused([fs], interp)[0]
+        v1 = got["stack"][1]
+        v0 = got["stack"][0]
+        # frame 1 sampled at (x+3, y-1) equals frame 1's own calibration: compare with
+        # the identity-offset stack entry of a second run
+        fs2 = synth.FrameSet(raw=fs.raw[1:2], bias=fs.bias, dark=fs.dark, flat=fs.flat,
+                             exptime=fs.exptime[1:2], dx=np.zeros(1), dy=np.zeros(1))
+        ident = run_fused([fs2], interp)[0]["stack"][0]
+        H, W = v1.shape
+        assert np.array_equal(v1[1:, :W - 3], ident[:H - 1, 3:])
+        assert np.isnan(v0).sum() == 0
+
+
+def test_all_invalid_pixels_are_nan():
+    far = synth.make_set(20, 20, 3, 0.0, 9, n_stars=2, n_cr=0)
+    far.dx = np.array([500.0, -600.5, 1e6])
+    got = run_fused([far], "bilinear")[0]
+    assert np.isnan(got["mean"]).all() and np.isnan(got["median"]).all()
+    assert (got["nkept"] == 0).all()
+
+
+# ------------------------------------------------------------ status paths
+def test_bad_flat_master_is_latched():
+    fs = synth.make_set(40, 30, 3, 1.0, 10, n_stars=3)
+    fs.flat[5, 7] = 0.0
+    s = core.device_set(fs).alloc_outputs()
+    ws = core.reduce_sets([s], core.reduce_params("bilinear"))
+    assert core.sync_status(ws) == 5
+    assert core.sync_status(ws) == 0  # cleared after reading
+
+
+def test_bounded_wait_gives_up_with_timeout():
+    """A set whose ready flag nothing sets: the kernel's bounded wait ends,
+    IRP_ERR_TIMEOUT is latched, and the context stays usable."""
+    fs = synth.make_set(64, 32, 3, 1.0, 11, n_stars=3)
+    s = core.device_set(fs).alloc_outputs()
+    s.ready_flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s.ready_value = 1
+    ws = core.reduce_sets([s], core.reduce_params("bilinear", wait_spin_limit=2000))
+    assert core.sync_status(ws) == 7
+    s.ready_flag.fill_(1)
+    ws = core.reduce_sets([s], core.reduce_params("bilinear", wait_spin_limit=2000), ws=ws)
+    assert core.sync_status(ws) == 0
+    ref = oracle.reduce_set(fs, interp="bilinear")
+    compare("after timeout", s.mean.cpu().numpy(), ref["mean"],
+            mean_tolerance(ref["mean"]) + 1e-2)
+
+
+def test_plan_launch_and_graph_capture():
+    fss = [synth.make_set(96, 64, n, 4.0, 60 + n, n_stars=10) for n in (5, 12, 30)]
+    sets = [core.device_set(fs).alloc_outputs() for fs in fss]
+    params = core.reduce_params("bilinear", persistent=True)
+    plan = core.Plan(sets, params)
+    plan.launch()
+    torch.cuda.synchronize()
+    first = [s.mean.clone() for s in sets]
+    for s in sets:
+        s.mean.zero_()
+    g = torch.cuda.CUDAGraph()
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            plan.launch(stream=stream)
+    g.replay()
+    torch.cuda.synchronize()
+    for a, s in zip(first, sets):
+        assert torch.equal(a.view(torch.int32), s.mean.view(torch.int32))
+    assert core.sync_status(plan.ws) == 0
+
+
+# --------------------------------------------------------------- unfused path
+@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3"])
+def test_unfused_f32_matches_oracle(interp):
+    fs = synth.make_set(90, 66, 9, 4.0, 123, n_stars=30, n_cr=10)
+    d = core.device_set(fs)
+    raw = torch.stack(d.frames)
+    cal, _, _, _ = core.calibrate(raw, d.bias, d.dark, d.flat, fs.exptime)
+    cal_h = cal.cpu().numpy()
+    for k in range(fs.n):
+        v = oracle.calibrate(fs.raw[k], fs.bias, fs.dark, fs.flat, fs.exptime[k])
+        compare("calibrate", cal_h[k], v, 4 * 2.0 ** -24 * np.abs(v) + 1e-5)
+    stack, valid, _ = core.shift(cal, fs.dx, fs.dy, interp)
+    st = stack.cpu().numpy()
+    va = valid.cpu().numpy().astype(bool)
+    assert np.array_equal(va, ~np.isnan(st))
+    for k in range(fs.n):
+        a, ok = oracle.shift(cal_h[k].astype(np.float64), fs.dx[k], fs.dy[k], interp)
+        assert np.array_equal(ok, va[k])
+        M = np.abs(cal_h[k]).max()
+        coef = 64 if interp == "spline3" else 8
+        compare("shift", np.where(ok, st[k], np.nan), np.where(ok, a, np.nan),
+                coef * 2.0 ** -24 * M + 1e-4)
+    out = core.combine(stack, valid=valid, clip=core.clip_params(2.5), want_reject=True)
+    same = oracle.combine_stack(np.where(va, st, 0.0), va, kappa=2.5)
+    med = out["median"].cpu().numpy()
+    fin = ~np.isnan(same["median"])
+    assert np.array_equal(med[fin].view(np.uint32), same["median"].astype(np.float32)[fin].view(np.uint32))
+    kept = out["nkept"].cpu().numpy().astype(np.int32)
+    exempt = same["margin"] < 1e-5
+    assert ((kept == same["nkept"]) | exempt).all()
+    rej = out["reject"].cpu().numpy().astype(bool)
+    assert ((rej == same["rejected"]).all(axis=0) | exempt).all()
+    compare("combine mean", out["mean"].cpu().numpy(), same["mean"], mean_tolerance(same["mean"]),
+            kept == same["nkept"])
+
+
+@pytest.mark.parametrize("interp", ["bilinear", "spline3"])
+def test_unfused_f16_scaled_stack(interp):
+    """FP16 stack with per-frame power-of-two scale and FP64-mean offset."""
+    fs = synth.make_set(80, 60, 8, 4.0, 124, n_stars=30, n_cr=10)
+    d = core.device_set(fs)
+    raw = torch.stack(d.frames)
+    h, scale, offset, _ = core.calibrate(raw, d.bias, d.dark, d.flat, fs.exptime, dtype="f16")
+    sc = scale.cpu().numpy()
+    of = offset.cpu().numpy()
+    hh = h.cpu().numpy().astype(np.float32)
+    for k in range(fs.n):
+        v = oracle.calibrate(fs.raw[k], fs.bias, fs.dark, fs.flat, fs.exptime[k])
+        assert of[k] == pytest.approx(v.mean(), rel=1e-6, abs=1e-3)
+        assert np.abs((v - of[k]) / sc[k]).max() <= 16384.0
+        assert sc[k] == 2.0 ** np.round(np.log2(sc[k]))
+        deq = hh[k] * sc[k] + of[k]
+        # half has 11 significant bits: relative rounding 2^-11 of |v - offset|
+        compare("f16 calibrate", deq, v, 2.0 ** -11 * np.abs(v - of[k]) + 1e-3 + 1e-6 * np.abs(v))
+    stack, valid, _ = core.shift(h, fs.dx, fs.dy, interp, dtype="f16", scale=scale, offset=offset)
+    out = core.combine(stack, dtype="f16", scale=scale, offset=offset, valid=valid,
+                       clip=core.clip_params(3.0))
+    st = stack.cpu().numpy().astype(np.float32)
+    va = valid.cpu().numpy().astype(bool)
+    deq = st * sc[:, None, None] + of[:, None, None]
+    same = oracle.combine_stack(np.where(va, deq, 0.0), va, kappa=3.0)
+    med = out["median"].cpu().numpy()
+    fin = ~np.isnan(same["median"])
+    assert np.array_equal(med[fin].view(np.uint32), same["median"].astype(np.float32)[fin].view(np.uint32))
+    ref = oracle.reduce_set(fs, interp=interp)
+    m = (ref["margin"] >= 1e-2) & (out["nkept"].cpu().numpy() == ref["nkept"])
+    err = np.abs(out["mean"].cpu().numpy() - ref["mean"])[m]
+    # reported, bounded by the FP16 quantisation of |v - offset| (2^-11 relative)
+    assert np.all(err <= 2.0 ** -10 * np.abs(ref["mean"][m] - of.mean()) + 0.05 + 1e-3 * np.abs(ref["mean"][m]))
+
+
+def test_frame_stats_f64():
+    fs = synth.make_set(300, 200, 4, 2.0, 125, n_stars=30)
+    d = core.device_set(fs)
+    cal, _, _, _ = core.calibrate(torch.stack(d.frames), d.bias, d.dark, d.flat, fs.exptime)
+    s, q, c = core.frame_stats(cal)
+    h = cal.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(s.cpu().numpy(), h.reshape(4, -1).sum(1), rtol=1e-12)
+    np.testing.assert_allclose(q.cpu().numpy(), (h ** 2).reshape(4, -1).sum(1), rtol=1e-12)
+    assert (c.cpu().numpy() == 300 * 200).all()
