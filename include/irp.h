@@ -40,6 +40,11 @@
  *   - Errors detected on the device (a non-finite or non-positive flat value,
  *     a bounded wait that ran out) are latched into the status word at the
  *     start of the caller's workspace and reported by irp_sync_status().
+ *   - Workspaces: device memory, 256-byte aligned, owned by the caller.  The
+ *     first 256 bytes (status word, work counters) must be zero before the
+ *     workspace is first used; the library keeps them consistent afterwards
+ *     (irp_sync_status clears a latched status).  Calls that share a
+ *     workspace must be ordered (same stream or synchronised).
  */
 #ifndef IRP_H
 #define IRP_H
@@ -204,6 +209,9 @@ irp_status irp_plan_launch(const void* plan_host, size_t plan_bytes, void* works
 irp_status irp_sync_status(void* workspace, void* stream);
 
 const char* irp_status_string(irp_status s);
+/* Name and description of the CUDA error behind the last IRP_ERR_CUDA
+ * returned on the calling thread ("" if none). */
+const char* irp_last_cuda_error(void);
 int irp_version(void);
 
 /* Number of SMs of the current device (autotuning helper). */

@@ -105,6 +105,8 @@ def lib() -> ctypes.CDLL:
             L.irp_plan_launch.argtypes = [PP, c_sz, PP, c_sz, PP]
             L.irp_sync_status.restype = c_i
             L.irp_sync_status.argtypes = [PP, PP]
+            L.irp_last_cuda_error.restype = ctypes.c_char_p
+            L.irp_last_cuda_error.argtypes = []
             L.irp_profile_enable.restype = None
             L.irp_profile_enable.argtypes = [c_i]
             L.irp_profile_read.restype = c_i
@@ -115,4 +117,6 @@ def lib() -> ctypes.CDLL:
 
 def check(status: int, where: str) -> None:
     if status != IRP_OK:
+        if status == 6:
+            where = f"{where} [{lib().irp_last_cuda_error().decode()}]"
         raise IrpError(status, where)

@@ -39,7 +39,8 @@ def clip_params(kappa: float = 3.0, max_iter: int = 3, center: str = "mean", ddo
 
 
 def workspace(nbytes: int, device="cuda") -> torch.Tensor:
-    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    """Device workspace; its 256-byte header (status word, counters) starts at zero."""
+    return torch.zeros(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
 # ----------------------------------------------------------------- calibrate

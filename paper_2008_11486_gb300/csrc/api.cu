@@ -6,6 +6,7 @@
 // descriptors), and launch the kernels.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -68,7 +69,13 @@ struct TraceScope {
   }
 };
 inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
-inline irp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? IRP_OK : IRP_ERR_CUDA; }
+thread_local char g_last_cuda_error[256] = "";
+inline irp_status note_cuda(cudaError_t e) {
+  snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", cudaGetErrorName(e),
+           cudaGetErrorString(e));
+  return IRP_ERR_CUDA;
+}
+inline irp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? IRP_OK : note_cuda(e); }
 
 // Offset split along one axis: sample of output coordinate p is at
 // (p + o) + tap, o the integer origin; valid iff v0 <= p <= v1.
@@ -424,7 +431,7 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     si.nsets = (int)g.size();
     si.nframes = nf;
     si.pgrid = stencil == ST_BSPLINE ? ptile0 : 0;
-    if (si.smem > 227 * 1024) return IRP_ERR_UNSUPPORTED;
+    if (si.smem > 227 * 1024 - 1024) return IRP_ERR_UNSUPPORTED;  // opt-in limit less static smem
     if (p->persistent) {
       const int occ = reduce_occupancy(si.bucket, stencil, si.smem);
       int g_ctas = p->max_ctas > 0 ? p->max_ctas : occ * sm_count();
@@ -452,7 +459,7 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
     for (int i = 0; i < pf->nsub && e == cudaSuccess; ++i)
       e = cudaMemcpyAsync(ws + pf->sub[i].dev_off, buf + pf->sub[i].img_off, pf->sub[i].bytes,
                           cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return IRP_ERR_CUDA;
+    if (e != cudaSuccess) return note_cuda(e);
   }
   if (pf->nflat > 0) {
     FrameStats* st = (FrameStats*)(ws + pf->flat_off);
@@ -462,7 +469,7 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
     for (int i = 0; i < pf->nflat && e == cudaSuccess; ++i)
       e = launch_stats_frames(fj[i].flat, fj[i].pitch, 0, fj[i].W, fj[i].H, 1, false, nullptr,
                               nullptr, nullptr, nullptr, nullptr, st + i, s);
-    if (e != cudaSuccess) return IRP_ERR_CUDA;
+    if (e != cudaSuccess) return note_cuda(e);
   }
   for (int i = 0; i < pf->nsub; ++i) {
     const SubInfo& si = pf->sub[i];
@@ -481,17 +488,17 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
     if (si.pgrid > 0) {
       TraceScope tr(IRP_KERNEL_PREFILTER, s);
       e = launch_prefilter_raw(&inl, dev_plan, si.pgrid, s);
-      if (e != cudaSuccess) return IRP_ERR_CUDA;
+      if (e != cudaSuccess) return note_cuda(e);
     }
     if (pf->persistent) {
       e = cudaMemsetAsync(&wsh->counters[si.counter], 0, sizeof(uint32_t), s);
-      if (e != cudaSuccess) return IRP_ERR_CUDA;
+      if (e != cudaSuccess) return note_cuda(e);
     }
     {
       TraceScope tr(IRP_KERNEL_REDUCE, s);
       e = launch_reduce(si.bucket, si.stencil, &inl, dev_plan, si.grid, si.smem, s);
     }
-    if (e != cudaSuccess) return IRP_ERR_CUDA;
+    if (e != cudaSuccess) return note_cuda(e);
   }
   return IRP_OK;
 }
@@ -508,6 +515,8 @@ bool plan_fits_inline(const uint8_t* buf) {
 extern "C" {
 
 int irp_version(void) { return IRP_VERSION; }
+
+const char* irp_last_cuda_error(void) { return g_last_cuda_error; }
 
 const char* irp_status_string(irp_status s) {
   switch (s) {
@@ -591,13 +600,13 @@ irp_status irp_reduce_set(const irp_set* sets, int nsets, const irp_reduce_param
 irp_status irp_sync_status(void* workspace, void* stream) {
   if (!workspace || !aligned(workspace, kAlign)) return IRP_ERR_WORKSPACE;
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
-  if (e != cudaSuccess) return IRP_ERR_CUDA;
+  if (e != cudaSuccess) return note_cuda(e);
   uint32_t status = 0;
   e = cudaMemcpy(&status, workspace, sizeof(uint32_t), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return IRP_ERR_CUDA;
+  if (e != cudaSuccess) return note_cuda(e);
   if (status != 0) {
     e = cudaMemset(workspace, 0, sizeof(uint32_t));
-    if (e != cudaSuccess) return IRP_ERR_CUDA;
+    if (e != cudaSuccess) return note_cuda(e);
   }
   return (irp_status)status;
 }
@@ -637,7 +646,7 @@ irp_status irp_calibrate(const uint16_t* raw, int64_t raw_pitch, int64_t raw_fra
   if (e == cudaSuccess && normalize_flat)
     e = launch_stats_frames(flat, master_pitch, 0, W, H, 1, false, nullptr, nullptr, nullptr,
                             nullptr, nullptr, flat_st, s);
-  if (e != cudaSuccess) return IRP_ERR_CUDA;
+  if (e != cudaSuccess) return note_cuda(e);
   CalibArgs a;
   std::memset(&a, 0, sizeof(a));
   a.raw = raw;
@@ -657,12 +666,12 @@ irp_status irp_calibrate(const uint16_t* raw, int64_t raw_pitch, int64_t raw_fra
     for (int j = 0; j < nk; ++j) a.t[j] = exptime_host[k0 + j];
     if (dt == IRP_F16_SCALED) {
       e = launch_stats_raw(a, nk, st, s);
-      if (e != cudaSuccess) return IRP_ERR_CUDA;
+      if (e != cudaSuccess) return note_cuda(e);
     }
   }
   if (dt == IRP_F16_SCALED) {
     e = launch_f16_scaling(st, n, scale_out, offset_out, s);
-    if (e != cudaSuccess) return IRP_ERR_CUDA;
+    if (e != cudaSuccess) return note_cuda(e);
   }
   for (int k0 = 0; k0 < n; k0 += kCalibChunk) {
     const int nk = std::min(kCalibChunk, n - k0);
@@ -670,7 +679,7 @@ irp_status irp_calibrate(const uint16_t* raw, int64_t raw_pitch, int64_t raw_fra
     for (int j = 0; j < nk; ++j) a.t[j] = exptime_host[k0 + j];
     e = launch_calibrate(a, nk, dt == IRP_F16_SCALED, out, out_pitch, out_frame_stride, scale_out,
                          offset_out, s);
-    if (e != cudaSuccess) return IRP_ERR_CUDA;
+    if (e != cudaSuccess) return note_cuda(e);
   }
   return IRP_OK;
 }
@@ -772,7 +781,7 @@ irp_status irp_shift(const void* in, int64_t in_pitch, int64_t in_frame_stride, 
       e = launch_prefilter_frames(&inl, inl.h.npitems, f16, s);
     }
     if (e == cudaSuccess) e = launch_shift(sa, nk, stencil, f16, s);
-    if (e != cudaSuccess) return IRP_ERR_CUDA;
+    if (e != cudaSuccess) return note_cuda(e);
   }
   return IRP_OK;
 }

@@ -47,17 +47,28 @@ size_t reduce_smem_bytes(int stencil, int max_n, int mwin_w, int mwin_h) {
   return floats * sizeof(float);
 }
 
+// Raises the kernel's dynamic shared-memory opt-in to ``smem`` bytes when it
+// needs more than any earlier launch of the same instantiation.
+template <typename F>
+static cudaError_t ensure_smem(F fn, size_t smem, size_t& granted) {
+  if (smem <= granted || smem <= 48 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) granted = smem;
+  return e;
+}
+
+template <int NMAX, int ST, int SRC>
+static size_t& granted_smem() {
+  static size_t g = 0;
+  return g;
+}
+
 template <int NMAX, int ST, int SRC>
 static cudaError_t launch_one(const InlinePlan* inl, const void* plan_dev, int grid,
                               size_t smem, cudaStream_t s) {
   auto fn = k_reduce<NMAX, ST, SRC>;
-  static bool attr_done = false;  // one attribute call per instantiation
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  cudaError_t e = ensure_smem(fn, smem, granted_smem<NMAX, ST, SRC>());
+  if (e != cudaSuccess) return e;
   fn<<<grid, kThreads, smem, s>>>(*inl, plan_dev);
   return cudaGetLastError();
 }
@@ -85,8 +96,8 @@ cudaError_t launch_reduce(int bucket, int stencil, const InlinePlan* inl, const 
 template <int NMAX, int ST, int SRC>
 static int occ_one(size_t smem) {
   int blocks = 0;
-  cudaFuncSetAttribute(k_reduce<NMAX, ST, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       227 * 1024);
+  if (ensure_smem(k_reduce<NMAX, ST, SRC>, smem, granted_smem<NMAX, ST, SRC>()) != cudaSuccess)
+    return 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_reduce<NMAX, ST, SRC>, kThreads,
                                                     smem) != cudaSuccess)
     return 1;
@@ -113,14 +124,10 @@ int reduce_occupancy(int bucket, int stencil, size_t smem) {
 
 cudaError_t launch_prefilter_raw(const InlinePlan* inl, const void* plan_dev, int grid,
                                  cudaStream_t s) {
-  static bool attr_done = false;
+  static size_t granted = 0;
   const size_t smem = prefilter_smem_bytes();
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_prefilter<SRC_RAW>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  cudaError_t e = ensure_smem(k_prefilter<SRC_RAW>, smem, granted);
+  if (e != cudaSuccess) return e;
   k_prefilter<SRC_RAW><<<grid, kThreads, smem, s>>>(*inl, plan_dev);
   return cudaGetLastError();
 }
