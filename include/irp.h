@@ -204,6 +204,38 @@ irp_status irp_plan_encode(const irp_set* sets, int nsets, const irp_reduce_para
 irp_status irp_plan_launch(const void* plan_host, size_t plan_bytes, void* workspace,
                            size_t ws_bytes, void* stream);
 
+/* irp_reduce_set_noalloc -- irp_reduce_set for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this is a deployment aid.
+ *
+ * Some callers cannot create a workspace: a real-time reduction loop that
+ * reserves all device memory at start-up and must not allocate afterwards
+ * (an allocation can stall for milliseconds or fail once memory is
+ * fragmented), or a host framework that owns the device memory pool and hands
+ * a plug-in only its input and output buffers.  This entry point takes the
+ * same sets and parameters as irp_reduce_set but uses a scratch area of
+ * IRP_NOALLOC_SCRATCH_BYTES that the library holds in a static device array;
+ * every GPU that loads the library keeps that array until the process exits.
+ * It allocates no device memory: it calls no cudaMalloc, cudaFree or other
+ * allocating CUDA or library routine.
+ *   - The caller still passes all inputs and outputs (irp_set).
+ *   - status_out (device, nullable) receives the call's device status word
+ *     (IRP_OK, IRP_ERR_BAD_MASTER, IRP_ERR_TIMEOUT) when the call's work
+ *     completes on the stream.
+ *   - Requests whose workspace (irp_workspace_size) exceeds
+ *     IRP_NOALLOC_SCRATCH_BYTES, or whose plan exceeds the call's fixed host
+ *     plan buffer, return IRP_ERR_WORKSPACE with nothing enqueued; use
+ *     irp_reduce_set for those.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - All calls on a device share the one array, which keeps the contents of
+ *     the last call; each call clears the status word and work counters
+ *     before its kernels run.  Calls whose work overlaps on the GPU (other
+ *     streams, other host threads without ordering) race on the array. */
+#define IRP_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+irp_status irp_reduce_set_noalloc(const irp_set* sets, int nsets, const irp_reduce_params* p,
+                                  uint32_t* status_out, void* stream);
+
 /* Synchronises the stream, returns and clears the device status latched in
  * the workspace's status word. */
 irp_status irp_sync_status(void* workspace, void* stream);

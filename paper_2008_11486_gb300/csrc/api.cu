@@ -826,3 +826,70 @@ irp_status irp_combine(const void* stack, int64_t pitch, int64_t frame_stride, i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// irp_reduce_set_noalloc: the fused reduction with its scratch in a static
+// device array instead of a caller-provided workspace (see include/irp.h).
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+// The scratch.  In host code this name is only a stand-in for the symbol;
+// the device address is obtained per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[IRP_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+constexpr size_t kNoallocPlanBytes = 64 * 1024;  // fixed host plan buffer (no heap)
+
+// Device address of the scratch on the current device; looked up once per
+// device with that device current.
+cudaError_t noalloc_scratch(uint8_t** out) {
+  static std::mutex mu;
+  static uint8_t* addr[kNoallocMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    addr[dev] = (uint8_t*)p;
+  }
+  *out = addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" irp_status irp_reduce_set_noalloc(const irp_set* sets, int nsets,
+                                             const irp_reduce_params* p, uint32_t* status_out,
+                                             void* stream) {
+  irp_status st = check_params(sets, nsets, p);
+  if (st != IRP_OK) return st;
+  if (!aligned(status_out, 4)) return IRP_ERR_ALIGNMENT;
+  std::vector<std::vector<int>> groups;
+  group_sets(sets, nsets, groups);
+  const size_t need = make_layout(sets, nsets, p, groups).total;
+  const size_t plan_bytes = plan_file_bytes(sets, nsets, p);
+  if (need > IRP_NOALLOC_SCRATCH_BYTES || plan_bytes > kNoallocPlanBytes) return IRP_ERR_WORKSPACE;
+  uint8_t* ws = nullptr;
+  cudaError_t e = noalloc_scratch(&ws);
+  if (e != cudaSuccess) return note_cuda(e);
+  alignas(64) uint8_t buf[kNoallocPlanBytes];  // on the stack: no allocation
+  st = encode_plan(sets, nsets, p, buf, plan_bytes, ws, IRP_NOALLOC_SCRATCH_BYTES);
+  if (st != IRP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the status word and work counters must start at zero for every call
+  e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), s);
+  if (e != cudaSuccess) return note_cuda(e);
+  st = run_plan(buf, ws, IRP_NOALLOC_SCRATCH_BYTES, s, !plan_fits_inline(buf));
+  if (st != IRP_OK) return st;
+  if (status_out) {
+    e = cudaMemcpyAsync(status_out, ws, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return note_cuda(e);
+  }
+  return IRP_OK;
+}
