@@ -11,6 +11,8 @@
 #include <vector>
 
 #include "common.cuh"
+#include "prefilter.cuh"
+#include "spline.h"
 #include "unfused.h"
 
 using namespace irp;
@@ -195,6 +197,7 @@ struct SubInfo {
   uint64_t smem;        // dynamic shared memory of the reduce launch
   int32_t bucket, stencil, grid, pgrid;
   int32_t nitems, counter, nsets, nframes;
+  int32_t nrows, ncolsegs, row_e, pad;  // spline row / column passes
 };
 
 struct PlanFile {
@@ -215,9 +218,23 @@ struct FlatJob {  // follows PlanFile: one FP64 flat sum per set (normalize_flat
 struct Layout {
   size_t flat_off, plan_off, coef_off, total;
   std::vector<size_t> coef_frame_off;  // per set: offset of its first coefficient frame
+  std::vector<size_t> crow_frame_off;  // per set: offset of its first row-pass frame
 };
 
-size_t coef_frame_bytes(int W, int H) { return align_up((size_t)W * H * sizeof(float), kAlign); }
+// Spline prefilter of a set: row + column passes (1) or tiled (0).
+int spline_path(int W, int H) {
+  return (W >= kSplineMinSide && W <= kSplineMaxW && H >= kSplineMinSide) ? 1 : 0;
+}
+int64_t crow_pitch(int W) { return (int64_t)align_up((size_t)W, 4); }
+size_t crow_frame_bytes(int W, int H) {
+  return align_up((size_t)H * (size_t)crow_pitch(W) * sizeof(float), kAlign);
+}
+
+// Spline coefficients are stored with a 2-sample mirrored border on every side.
+int64_t coef_pitch(int W) { return (int64_t)align_up((size_t)W + 4, 4); }
+size_t coef_frame_bytes(int W, int H) {
+  return align_up((size_t)(H + 4) * (size_t)coef_pitch(W) * sizeof(float), kAlign);
+}
 
 void group_sets(const irp_set* sets, int nsets, std::vector<std::vector<int>>& groups) {
   std::vector<int> order(nsets);
@@ -249,10 +266,15 @@ Layout make_layout(const irp_set* sets, int nsets, const irp_reduce_params* p,
   }
   L.coef_off = off;
   L.coef_frame_off.assign(nsets, 0);
+  L.crow_frame_off.assign(nsets, 0);
   if (p->interp == IRP_INTERP_SPLINE3) {
     for (int i = 0; i < nsets; ++i) {
       L.coef_frame_off[i] = off;
       off += (size_t)sets[i].n * coef_frame_bytes(sets[i].W, sets[i].H);
+      if (spline_path(sets[i].W, sets[i].H)) {
+        L.crow_frame_off[i] = off;
+        off += (size_t)sets[i].n * crow_frame_bytes(sets[i].W, sets[i].H);
+      }
     }
   }
   L.total = off;
@@ -338,11 +360,21 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
       nf += sets[i].n;
       max_n = std::max(max_n, sets[i].n);
     }
+    const int bucket = reduce_bucket(max_n);
+    const int TWc = tile_cols(stencil), THr = tile_rows(bucket);
+    // prefilter work items: tiles x frame groups, enough groups to fill the GPU twice
+    int pgroups = 1;
+    if (stencil == ST_BSPLINE) {
+      int ptiles = 0;
+      for (int i : g)
+        ptiles += ((sets[i].W + kPrefTile - 1) / kPrefTile) * ((sets[i].H + kPrefTile - 1) / kPrefTile);
+      pgroups = std::max(1, std::min(max_n, (2 * sm_count() + ptiles - 1) / std::max(ptiles, 1)));
+    }
     uint8_t* img = buf + img_off;
     PlanHeader* h = (PlanHeader*)img;
     SetDesc* sd = (SetDesc*)(img + plan_sets_offset());
     FrameDesc* fd = (FrameDesc*)(img + plan_frames_offset((int)g.size()));
-    int frame0 = 0, tile0 = 0, ptile0 = 0;
+    int frame0 = 0, tile0 = 0, ptile0 = 0, nrows = 0, ncolsegs = 0, row_e = 32;
     for (int si = 0; si < (int)g.size(); ++si) {
       const irp_set& s = sets[g[si]];
       SetDesc& S = sd[si];
@@ -350,7 +382,8 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
       S.H = s.H;
       S.n = s.n;
       S.frame0 = frame0;
-      S.src_pitch = stencil == ST_BSPLINE ? s.W : s.raw_pitch;  // spline reads coefficients
+      S.src_pitch = s.raw_pitch;
+      S.coef_pitch = stencil == ST_BSPLINE ? coef_pitch(s.W) : 0;
       S.bias = s.bias;
       S.dark = s.dark_rate;
       S.flat = s.flat;
@@ -363,35 +396,53 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
       S.nkept_out = s.nkept_out;
       S.stack_out = s.stack_out;
       S.out_pitch = s.out_pitch;
-      S.tiles_x = (s.W + kTW - 1) / kTW;
-      S.tiles_y = (s.H + kTH - 1) / kTH;
+      S.tiles_x = (s.W + TWc - 1) / TWc;
+      S.tiles_y = (s.H + THr - 1) / THr;
       S.tile0 = tile0;
       tile0 += S.tiles_x * S.tiles_y;
       S.ptiles_x = (s.W + kPrefTile - 1) / kPrefTile;
       S.ptiles_y = (s.H + kPrefTile - 1) / kPrefTile;
       S.ptile0 = ptile0;
-      ptile0 += S.ptiles_x * S.ptiles_y * s.n;
+      S.pframes = std::max(1, (s.n + pgroups - 1) / pgroups);
+      if (stencil == ST_BSPLINE && !spline_path(s.W, s.H))
+        ptile0 += S.ptiles_x * S.ptiles_y * ((s.n + S.pframes - 1) / S.pframes);
       S.ready_flag = s.ready_flag;
       S.ready_value = s.ready_value;
+      S.mflags = (aligned(s.bias, 16) && aligned(s.dark_rate, 16) && aligned(s.flat, 16) &&
+                  s.master_pitch % 4 == 0) ? 1 : 0;
+      S.spath = stencil == ST_BSPLINE ? spline_path(s.W, s.H) : 0;
+      S.crow_pitch = S.spath ? crow_pitch(s.W) : 0;
+      S.row0 = nrows;
+      S.colseg0 = ncolsegs;
+      if (S.spath) {
+        nrows += ((s.n + kRowGroup - 1) / kRowGroup) * s.H;
+        ncolsegs += s.n * s.W * ((s.H + 31) / 32);
+        if (s.W > 1024) row_e = 64;
+      }
       int oxmin = INT32_MAX, oxmax = INT32_MIN, oymin = INT32_MAX, oymax = INT32_MIN;
       for (int k = 0; k < s.n; ++k) {
         FrameDesc& F = fd[frame0 + k];
         if (!fill_geometry(F, s.dx[k], s.dy[k], s.W, s.H, p->interp)) return IRP_ERR_INVALID_ARG;
         F.src = s.frames[k];
+        F.flags = (aligned(s.frames[k], 16) && s.raw_pitch % 8 == 0) ? 1 : 0;
         F.t = s.exptime[k];
         F.scale = 1.0f;
         F.offset = 0.0f;
         F.coef = stencil == ST_BSPLINE
                      ? (float*)(ws + L.coef_frame_off[g[si]] + (size_t)k * coef_frame_bytes(s.W, s.H))
                      : nullptr;
+        F.crow = (stencil == ST_BSPLINE && spline_path(s.W, s.H))
+                     ? (float*)(ws + L.crow_frame_off[g[si]] + (size_t)k * crow_frame_bytes(s.W, s.H))
+                     : nullptr;
         oxmin = std::min(oxmin, F.ox);
         oxmax = std::max(oxmax, F.ox);
         oymin = std::min(oymin, F.oy);
         oymax = std::max(oymax, F.oy);
       }
-      // master union window: kept when it is at most twice the per-frame window
-      const int mw = kTW + (oxmax - oxmin) + taps - 1, mh = kTH + (oymax - oymin) + taps - 1;
-      if (stencil != ST_BSPLINE && (size_t)mw * mh <= (size_t)8 * (kTW + taps) * (kTH + taps)) {
+      // master union window over all frames' taps ({bias, dark, 1/flat}, 16 B each),
+      // kept unless the offsets are so spread that it would exceed 64 KB
+      const int mw = 32 + (oxmax - oxmin), mh = THr + (oymax - oymin) + taps - 1;
+      if (stencil != ST_BSPLINE && (size_t)mw * mh * 16 <= (size_t)64 * 1024) {
         S.mwin_w = mw;
         S.mwin_h = mh;
         S.mox = oxmin;
@@ -405,6 +456,8 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     h->nframes = nf;
     h->nitems = tile0;
     h->npitems = ptile0;
+    h->nrows = nrows;
+    h->ncolsegs = ncolsegs;
     h->stencil = stencil;
     h->max_n = max_n;
     h->persistent = p->persistent ? 1 : 0;
@@ -415,22 +468,26 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     h->max_iter = p->clip.max_iter;
     h->center = p->clip.center;
     h->ddof = p->clip.ddof;
-    h->smem_samples = max_n * kTilePx;
-    h->smem_master = 3 * mw_max * mh_max;
+    h->smem_samples = max_n * THr * 32;
+    h->smem_master = mw_max * mh_max;  // float4 entries
     h->status = &wsh->status;
     h->counter = &wsh->counters[gi];
     SubInfo& si = pf->sub[gi];
     si.dev_off = dev_off;
     si.img_off = img_off;
     si.bytes = plan_total_bytes((int)g.size(), nf);
-    si.bucket = reduce_bucket(max_n);
+    si.bucket = bucket;
     si.stencil = stencil;
-    si.smem = reduce_smem_bytes(stencil, max_n, mw_max, mh_max);
+    si.smem = reduce_smem_bytes(stencil == ST_BSPLINE ? SRC_F32 : SRC_RAW, stencil, bucket, max_n,
+                                mw_max, mh_max);
     si.nitems = tile0;
     si.counter = gi;
     si.nsets = (int)g.size();
     si.nframes = nf;
     si.pgrid = stencil == ST_BSPLINE ? ptile0 : 0;
+    si.nrows = nrows;
+    si.ncolsegs = ncolsegs;
+    si.row_e = row_e;
     if (si.smem > 227 * 1024 - 1024) return IRP_ERR_UNSUPPORTED;  // opt-in limit less static smem
     if (p->persistent) {
       const int occ = reduce_occupancy(si.bucket, stencil, si.smem);
@@ -485,9 +542,11 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
     } else {
       std::memset(&inl.h, 0, sizeof(PlanHeader));
     }
-    if (si.pgrid > 0) {
+    if (si.pgrid > 0 || si.nrows > 0) {
       TraceScope tr(IRP_KERNEL_PREFILTER, s);
-      e = launch_prefilter_raw(&inl, dev_plan, si.pgrid, s);
+      if (si.pgrid > 0) e = launch_prefilter_raw(&inl, dev_plan, si.pgrid, s);
+      if (e == cudaSuccess && si.nrows > 0) e = launch_spline_rows(si.row_e, &inl, dev_plan, si.nrows, s);
+      if (e == cudaSuccess && si.ncolsegs > 0) e = launch_spline_cols(&inl, dev_plan, si.ncolsegs, s);
       if (e != cudaSuccess) return note_cuda(e);
     }
     if (pf->persistent) {
@@ -751,6 +810,7 @@ irp_status irp_shift(const void* in, int64_t in_pitch, int64_t in_frame_stride, 
   sa.out_pitch = out_pitch;
   sa.out_fstride = out_frame_stride;
   sa.valid_out = valid_out;
+  sa.coef_pitch = coef_pitch(W);
   for (int k0 = 0; k0 < n; k0 += kShiftChunk) {
     const int nk = std::min(kShiftChunk, n - k0);
     sa.k0 = k0;
@@ -774,9 +834,11 @@ irp_status irp_shift(const void* in, int64_t in_pitch, int64_t in_frame_stride, 
       S.H = H;
       S.n = nk;
       S.src_pitch = in_pitch;
+      S.coef_pitch = coef_pitch(W);
       S.ptiles_x = (W + kPrefTile - 1) / kPrefTile;
       S.ptiles_y = (H + kPrefTile - 1) / kPrefTile;
-      inl.h.npitems = S.ptiles_x * S.ptiles_y * nk;
+      S.pframes = 4;
+      inl.h.npitems = S.ptiles_x * S.ptiles_y * ((nk + S.pframes - 1) / S.pframes);
       for (int j = 0; j < nk; ++j) inl.frames[j] = sa.frames[j];
       e = launch_prefilter_frames(&inl, inl.h.npitems, f16, s);
     }

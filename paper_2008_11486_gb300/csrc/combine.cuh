@@ -97,15 +97,19 @@ __device__ __forceinline__ CombineOut combine_sorted(const float (&s)[N], int m,
   // the squared deviations carry no cancellation.
   const float r = a;
   int lo = 0, hi = m;
+  // Kahan-compensated sum S (+C) of the deviations over [lo, hi) (a cosmic ray
+  // in the first pass must not move the centre); `have` marks S as current.
+  float S = 0.0f, C = 0.0f;
+  bool have = false;
   for (int it = 0; it < c.max_iter; ++it) {
     const int mm = hi - lo;
     if (mm - c.ddof <= 0) break;
-    // Kahan-compensated sum of deviations (a cosmic ray in the first pass
-    // must not move the centre), plain sum of their squares (sigma only).
-    float S = 0.0f, C = 0.0f, Q = 0.0f;
+    float Q = 0.0f;
+    S = 0.0f;
+    C = 0.0f;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      const bool in = (j >= lo) & (j < hi);
+      const bool in = (unsigned)(j - lo) < (unsigned)mm;
       const float d = in ? __fsub_rn(s[j], r) : 0.0f;
       const float y = __fsub_rn(d, C);
       const float t = __fadd_rn(S, y);
@@ -113,6 +117,7 @@ __device__ __forceinline__ CombineOut combine_sorted(const float (&s)[N], int m,
       S = t;
       Q = __fmaf_rn(d, d, Q);
     }
+    have = true;
     float cd;  // centre - r
     if (c.center == 1) {
       const float qa = select_at(s, lo + ((mm - 1) >> 1));
@@ -127,10 +132,18 @@ __device__ __forceinline__ CombineOut combine_sorted(const float (&s)[N], int m,
     const float sigma = sqrtf(__fdiv_rn(ss, (float)(mm - c.ddof)));
     if (!(sigma > 0.0f)) break;
     const float tlo = c.kappa_lo * sigma, thi = c.kappa_hi * sigma;
+    // survivors are a run of the sorted samples, so the rejected ones are a
+    // prefix (below) and a suffix (above) of [lo, hi): when neither extreme
+    // is rejected, nothing is
+    {
+      const float elo = __fsub_rn(__fsub_rn(select_at(s, lo), r), cd);
+      const float ehi = __fsub_rn(__fsub_rn(select_at(s, hi - 1), r), cd);
+      if (!(-elo > tlo) && !(ehi > thi)) break;
+    }
     int nlo = 0, nhi = 0;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      const bool in = (j >= lo) & (j < hi);
+      const bool in = (unsigned)(j - lo) < (unsigned)mm;
       const float e = __fsub_rn(__fsub_rn(s[j], r), cd);
       nlo += (in & (-e > tlo)) ? 1 : 0;
       nhi += (in & (e > thi)) ? 1 : 0;
@@ -139,16 +152,20 @@ __device__ __forceinline__ CombineOut combine_sorted(const float (&s)[N], int m,
     lo += nlo;
     hi -= nhi;
     if (hi < lo) hi = lo;
+    have = false;
   }
-  // Compensated (Kahan) mean of the survivors' deviations from r.
-  float S = 0.0f, C = 0.0f;
+  if (!have) {
+    const int mm = hi - lo;
+    S = 0.0f;
+    C = 0.0f;
 #pragma unroll
-  for (int j = 0; j < N; ++j) {
-    const bool in = (j >= lo) & (j < hi);
-    const float y = __fsub_rn(in ? __fsub_rn(s[j], r) : 0.0f, C);
-    const float t = __fadd_rn(S, y);
-    C = __fsub_rn(__fsub_rn(t, S), y);
-    S = t;
+    for (int j = 0; j < N; ++j) {
+      const bool in = (unsigned)(j - lo) < (unsigned)mm;
+      const float y = __fsub_rn(in ? __fsub_rn(s[j], r) : 0.0f, C);
+      const float t = __fadd_rn(S, y);
+      C = __fsub_rn(__fsub_rn(t, S), y);
+      S = t;
+    }
   }
   o.kept = hi - lo;
   o.mean = o.kept > 0 ? __fadd_rn(r, __fdiv_rn(S, (float)o.kept)) : __int_as_float(0x7fffffff);

@@ -1,6 +1,6 @@
 // common.cuh -- descriptors and device helpers shared by the sm_103a kernels.
 //
-// The fused path reduces frame sets tile by tile: one CTA owns a kTW x kTH
+// The fused path reduces frame sets tile by tile: one CTA owns an output tile
 // tile of the output grid of one set, walks the set's frames, calibrates and
 // resamples each frame's source window into shared memory, and finally
 // combines the per-pixel samples (sigma-clipped mean, median).
@@ -14,12 +14,7 @@
 
 namespace irp {
 
-constexpr int kTW = 32;        // output tile width  (one warp spans a tile row)
-constexpr int kTH = 16;        // output tile height
-constexpr int kThreads = 256;  // 8 warps; each thread samples 2 rows of a column
-constexpr int kTilePx = kTW * kTH;
-constexpr int kWinStride = kTW + 8;  // staging-window row stride (floats)
-constexpr int kWinRows = kTH + 3;    // enough rows for the 4x4 spline stencil
+constexpr int kThreads = 256;  // 8 warps per CTA of the fused kernel
 
 constexpr int kMaxInlineSets = 4;
 constexpr int kMaxInlineFrames = 64;
@@ -34,7 +29,6 @@ constexpr float kZ1 = -0.26794919243112270f;
 constexpr float kSqrt3 = 1.7320508075688772f;
 constexpr int kPrefHalo = 16;  // recursion warm-up; |z1|^17 / (1 - |z1|) < 3e-10
 constexpr int kPrefTile = 64;  // prefilter output tile (square)
-constexpr int kPrefWin = kPrefTile + 2 * kPrefHalo;
 
 // One frame of a set, as the kernels see it (128 bytes).
 struct FrameDesc {
@@ -48,7 +42,9 @@ struct FrameDesc {
   int32_t vx0, vx1;    // sample valid iff vx0 <= x <= vx1 ...
   int32_t vy0, vy1;    //              ... and vy0 <= y <= vy1
   float wx[4], wy[4];  // stencil weights (bilinear: 1-f, f; spline: beta3)
-  int32_t pad[9];
+  int32_t flags;       // bit 0: raw frame 16-byte aligned with a pitch of 8k elements
+  float* crow;         // row-pass spline coefficients (workspace) or null
+  int32_t pad[6];
 };
 static_assert(sizeof(FrameDesc) == 128, "FrameDesc layout");
 
@@ -66,7 +62,7 @@ struct SetDesc {
   uint16_t* nkept_out;
   float* stack_out;
   int64_t out_pitch;
-  int32_t tiles_x, tiles_y;      // output tiles (kTW x kTH)
+  int32_t tiles_x, tiles_y;      // output tiles (tile_cols x tile_rows)
   int32_t tile0;                 // first work item of this set
   int32_t mwin_w, mwin_h;        // master union window (0 = per-frame masters)
   int32_t mox, moy;              // union window origin relative to the tile
@@ -74,7 +70,13 @@ struct SetDesc {
   int32_t ptile0;                // first prefilter work item of this set
   const uint32_t* ready_flag;
   uint32_t ready_value;
-  int32_t pad1[9];
+  int32_t pframes;               // frames per prefilter work item
+  int64_t coef_pitch;            // padded spline-coefficient frames: (H+4) rows
+  int64_t crow_pitch;            // row-pass coefficient frames (spath 1)
+  int32_t row0;                  // first row-pass work item (one warp per frame row)
+  int32_t colseg0;               // first column-pass work item
+  int32_t mflags;                // bit 0: masters 16-byte aligned, pitch of 4k elements
+  int32_t spath;                 // spline prefilter: 0 tiled, 1 row + column passes
 };
 static_assert(sizeof(SetDesc) == 192, "SetDesc layout");
 
@@ -84,12 +86,14 @@ struct PlanHeader {
   float kappa_lo, kappa_hi;
   int32_t max_iter, center, ddof;
   int32_t smem_samples;          // floats reserved per CTA for samples
-  int32_t smem_master;           // floats reserved per CTA for master windows
-  int32_t npitems;               // prefilter work items (spline)
+  int32_t smem_master;           // float4 entries reserved per CTA for master windows
+  int32_t npitems;               // tiled prefilter work items (spline)
+  int32_t nrows, ncolsegs;       // row-pass and column-pass work items (spline)
+  int32_t pad[2];
   uint32_t* status;              // device status word (workspace)
   uint32_t* counter;             // persistent work counter (workspace)
 };
-static_assert(sizeof(PlanHeader) % 16 == 0, "PlanHeader alignment");
+static_assert(sizeof(PlanHeader) % 16 == 0 && sizeof(PlanHeader) <= 128, "PlanHeader layout");
 
 // Plan passed by value as a kernel parameter for small launches.
 struct InlinePlan {
@@ -171,13 +175,15 @@ __device__ __forceinline__ bool wait_ready(const uint32_t* flag, uint32_t value,
 }
 
 // ---------------------------------------------------------------------------
-// Host-side launchers (implemented in the kernel files).
+// Host-side launchers and geometry (implemented in the kernel files).
 // ---------------------------------------------------------------------------
-cudaError_t launch_reduce(int nmax_bucket, int stencil, const InlinePlan* inl,
-                          const void* plan_dev, int grid, size_t smem, cudaStream_t s);
-size_t reduce_smem_bytes(int stencil, int max_n, int mwin_w, int mwin_h);
-int reduce_bucket(int n);
-int reduce_occupancy(int nmax_bucket, int stencil, size_t smem);
+int reduce_bucket(int n);                  // register bucket (sort size) for n frames
+int tile_cols(int stencil);                // output columns per tile
+int tile_rows(int bucket);                 // output rows per tile
+size_t reduce_smem_bytes(int src, int stencil, int bucket, int max_n, int mwin_w, int mwin_h);
+int reduce_occupancy(int bucket, int stencil, size_t smem);
+cudaError_t launch_reduce(int bucket, int stencil, const InlinePlan* inl, const void* plan_dev,
+                          int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_prefilter_raw(const InlinePlan* inl, const void* plan_dev, int grid,
                                  cudaStream_t s);
 

@@ -5,7 +5,7 @@
 
 #include "combine.cuh"
 #include "prefilter.cuh"
-#include "reduce_tile.cuh"
+#include "reduce_kernels.cuh"
 #include "unfused.h"
 
 namespace irp {
@@ -207,14 +207,16 @@ __global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
   if (ok) {
     const int i0 = x + F.ox, j0 = y + F.oy;
     if (ST == ST_BSPLINE) {
+      // padded coefficient frame: (x, y) at (y + 2) * pitch + x + 2
       const float* c = F.coef;
       float acc = 0.0f;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int64_t row = (int64_t)mirror_index(j0 + q, a.H) * a.W;
+        const int j = min(max(j0 + q, -2), a.H + 1);
+        const float* row = c + (int64_t)(j + 2) * a.coef_pitch + 2;
         float h = 0.0f;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) h = __fmaf_rn(F.wx[p], __ldg(c + row + mirror_index(i0 + p, a.W)), h);
+        for (int p = 0; p < 4; ++p) h = __fmaf_rn(F.wx[p], __ldg(row + min(max(i0 + p, -2), a.W + 1)), h);
         acc = __fmaf_rn(F.wy[q], h, acc);
       }
       val = acc;
@@ -359,26 +361,17 @@ cudaError_t launch_shift(const ShiftArgs& a, int nk, int stencil, bool f16, cuda
 }
 
 cudaError_t launch_prefilter_frames(const InlinePlan* inl, int grid, bool f16, cudaStream_t s) {
-  const size_t smem = prefilter_smem_bytes();
-  static bool attr32 = false, attr16 = false;
+  static size_t granted32 = 0, granted16 = 0;
+  const size_t smem = prefilter_smem_bytes(SRC_F32);
+  cudaError_t e;
   if (f16) {
-    if (!attr16) {
-      cudaError_t e = cudaFuncSetAttribute(k_prefilter<SRC_F16>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr16 = true;
-    }
-    k_prefilter<SRC_F16><<<grid, kThreads, smem, s>>>(*inl, nullptr);
+    e = ensure_smem(k_prefilter<SRC_F16>, smem, granted16);
+    if (e == cudaSuccess) k_prefilter<SRC_F16><<<grid, kPrefThreads, smem, s>>>(*inl, nullptr);
   } else {
-    if (!attr32) {
-      cudaError_t e = cudaFuncSetAttribute(k_prefilter<SRC_F32>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr32 = true;
-    }
-    k_prefilter<SRC_F32><<<grid, kThreads, smem, s>>>(*inl, nullptr);
+    e = ensure_smem(k_prefilter<SRC_F32>, smem, granted32);
+    if (e == cudaSuccess) k_prefilter<SRC_F32><<<grid, kPrefThreads, smem, s>>>(*inl, nullptr);
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int NMAX>

@@ -1,141 +1,177 @@
 // prefilter.cuh -- cubic-spline coefficients of calibrated frames.
+//
+// Sec. 3.2.1: cubic-spline interpolation solves one tridiagonal system per
+// row and per column, (c[i-1] + 4 c[i] + c[i+1]) / 6 = v[i].  With mirror
+// boundaries its exact solution is the convolution of the mirror-extended data
+// with h[k] = sqrt(3) z1^|k|, z1 = sqrt(3) - 2, i.e. c = sqrt(3)(y+ + y- - v)
+// with the causal recursion y+[i] = v[i] + z1 y+[i-1] and the anti-causal one
+// y-[i] = v[i] + z1 y-[i+1].  Both are run over independent segments that start
+// kPrefHalo samples early (|z1|^17 < 2e-10), so every thread owns a short,
+// fully unrolled recursion held in registers.  Positions outside the frame
+// read the mirror-extended data, which makes the frame edges exact.
+//
+// A CTA owns a kPrefTile^2 tile of coefficients and a group of frames of one
+// set: the tile's masters are staged in shared memory once and reused by the
+// group's frames (raw source).  The coefficients are written to frames padded
+// by 2 mirrored samples on every side, pitch S.coef_pitch (multiple of 4), so
+// that the resampling kernel reads taps i0-1 .. i0+2 without mirroring.
 #pragma once
 
 #include "reduce_tile.cuh"
 
 namespace irp {
 
-// ---------------------------------------------------------------------------
-// Cubic-spline prefilter of calibrated raw frames (Sec. 3.2.1: one tridiagonal
-// system per row and per column).  The exact solution of the mirror-boundary
-// system equals the convolution of the mirror-extended data with
-// h[k] = sqrt(3) z1^|k|, z1 = sqrt(3) - 2, which splits into a causal and an
-// anti-causal first-order recursion: c = sqrt(3) (y+ + y- - v).  Each CTA
-// computes the coefficients of a kPrefTile^2 tile of one frame from a window
-// with kPrefHalo samples of recursion warm-up on every side; positions outside
-// the frame read the mirror-extended data, so the frame edges are exact.
-// Rows first, then columns (the 2-D system is separable).
-// ---------------------------------------------------------------------------
-template <int SRC>
-__device__ __forceinline__ float pref_load(const SetDesc& S, const FrameDesc& F, int gx, int gy,
-                                           float flat_norm, uint32_t* status) {
-  if (SRC == SRC_RAW) {
-    const int64_t m = (int64_t)gy * S.master_pitch + gx;
-    const uint16_t q = __ldg((const uint16_t*)F.src + (int64_t)gy * S.src_pitch + gx);
-    const float rf = inv_flat(__ldg(S.flat + m), flat_norm, status);
-    return calibrate_px(q, __ldg(S.bias + m), __ldg(S.dark + m), F.t, rf);
-  } else if (SRC == SRC_F32) {
-    return __ldg((const float*)F.src + (int64_t)gy * S.src_pitch + gx);
-  } else {
-    const __half q = ((const __half*)F.src)[(int64_t)gy * S.src_pitch + gx];
-    return __half2float(q);  // spline of h; scale/offset are applied by the caller
-  }
-}
+constexpr int kPrefExt = kPrefTile + 4;               // coefficients computed per axis
+constexpr int kPrefW = kPrefExt + 2 * kPrefHalo;       // window per axis (100)
+constexpr int kPrefWS = kPrefW + 1;                    // window row stride
+constexpr int kPrefRS = kPrefExt + 1;                  // row-pass result stride
+constexpr int kPrefThreads = 288;
+constexpr int kPrefRowSeg = kPrefExt / 2;              // 34 outputs per row task
+constexpr int kPrefColSeg = kPrefExt / 4;              // 17 outputs per column task
+constexpr int kPrefPerThread = (kPrefW * kPrefW + kPrefThreads - 1) / kPrefThreads;  // 35
+static_assert(kPrefW * 2 <= kPrefThreads && kPrefExt * 4 <= kPrefThreads, "prefilter tasks");
 
-constexpr int kPrefWS = kPrefWin + 1;   // row stride of the window (bank spread)
-constexpr int kPrefTS = kPrefTile + 1;  // row stride of the partial-result arrays
-
-inline size_t prefilter_smem_bytes() {
-  return sizeof(float) * ((size_t)kPrefWin * kPrefWS + 2 * (size_t)kPrefWin * kPrefTS);
+inline size_t prefilter_smem_bytes(int src) {
+  size_t f = (size_t)kPrefW * kPrefWS + (size_t)kPrefW * kPrefRS;
+  if (src == SRC_RAW) f += 3 * (size_t)kPrefW * kPrefWS;
+  return f * sizeof(float);
 }
 
 template <int SRC>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kPrefThreads, 1)
     k_prefilter(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
   extern __shared__ float4 smem4[];
-  float* v = reinterpret_cast<float*>(smem4);  // [kPrefWin][kPrefWS]
-  float* A = v + kPrefWin * kPrefWS;            // [kPrefWin][kPrefTS]
-  float* B = A + kPrefWin * kPrefTS;            // [kPrefWin][kPrefTS]
+  float* v = reinterpret_cast<float*>(smem4);   // [kPrefW][kPrefWS]
+  float* R = v + kPrefW * kPrefWS;              // [kPrefW][kPrefRS]
+  float* mb = R + kPrefW * kPrefRS;             // masters (raw source)
+  float* md = mb + kPrefW * kPrefWS;
+  float* mr = md + kPrefW * kPrefWS;
   const PlanView P = make_view(inl, plan_dev);
   const int item = blockIdx.x;
   if (item >= P.h->npitems) return;
-  // locate the set by its first prefilter item
   int si = 0;
   {
     int lo = 0, hi = P.h->nsets - 1;
     while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
+      const int mid = (lo + hi + 1) >> 1;
       if (P.sets[mid].ptile0 <= item) lo = mid; else hi = mid - 1;
     }
     si = lo;
   }
   const SetDesc& S = P.sets[si];
-  const int per_frame = S.ptiles_x * S.ptiles_y;
+  const int ntiles = S.ptiles_x * S.ptiles_y;
   const int local = item - S.ptile0;
-  const int k = local / per_frame;
-  const int pt = local - k * per_frame;
-  const FrameDesc& F = P.frames[S.frame0 + k];
-  const int x0 = (pt % S.ptiles_x) * kPrefTile, y0 = (pt / S.ptiles_x) * kPrefTile;
+  const int grp = local / ntiles;
+  const int pt = local - grp * ntiles;
+  const int fpg = S.pframes;  // frames per group
+  const int k0 = grp * fpg, k1 = min(S.n, k0 + fpg);
+  const int tx = pt % S.ptiles_x, ty = pt / S.ptiles_x;
+  const int x0 = tx * kPrefTile, y0 = ty * kPrefTile;
   const int W = S.W, H = S.H;
-  float flat_norm = 1.0f;
-  if (SRC == SRC_RAW && S.flat_sum) flat_norm = (float)(*S.flat_sum / ((double)W * H));
+  const int wx0 = x0 - 2 - kPrefHalo, wy0 = y0 - 2 - kPrefHalo;  // window origin
+  const int tid = threadIdx.x;
   uint32_t* status = P.h->status;
 
-  // 1. calibrated, mirror-extended window
-  for (int e = threadIdx.x; e < kPrefWin * kPrefWin; e += kThreads) {
-    const int r = e / kPrefWin, c = e - r * kPrefWin;
-    const int gx = mirror_index(x0 - kPrefHalo + c, W);
-    const int gy = mirror_index(y0 - kPrefHalo + r, H);
-    v[r * kPrefWS + c] = pref_load<SRC>(S, F, gx, gy, flat_norm, status);
+  // window element offsets (frame-independent), mirrored at the frame edges
+  int goff[kPrefPerThread];
+#pragma unroll
+  for (int i = 0; i < kPrefPerThread; ++i) {
+    const int e = tid + i * kPrefThreads;
+    const int r = e / kPrefW, c = e - r * kPrefW;
+    const int gx = mirror_index(wx0 + c, W), gy = mirror_index(wy0 + r, H);
+    goff[i] = (e < kPrefW * kPrefW) ? gy * (int)S.src_pitch + gx : 0;
   }
-  __syncthreads();
-  // 2. row recursions: threads [0, W) causal, [W, 2W) anti-causal (W = window rows)
-  const int tid = threadIdx.x;
-  if (tid < kPrefWin) {
-    const float* row = v + tid * kPrefWS;
-    float y = 0.0f;
-#pragma unroll 4
-    for (int c = 0; c < kPrefHalo + kPrefTile; ++c) {
-      y = __fmaf_rn(kZ1, y, row[c]);
-      if (c >= kPrefHalo) A[tid * kPrefTS + c - kPrefHalo] = y;
-    }
-  } else if (tid < 2 * kPrefWin) {
-    const int r = tid - kPrefWin;
-    const float* row = v + r * kPrefWS;
-    float y = 0.0f;
-#pragma unroll 4
-    for (int c = kPrefWin - 1; c >= kPrefHalo; --c) {
-      y = __fmaf_rn(kZ1, y, row[c]);
-      if (c < kPrefHalo + kPrefTile) B[r * kPrefTS + c - kPrefHalo] = y;
+  if (SRC == SRC_RAW) {
+    const float flat_norm = S.flat_sum ? (float)(*S.flat_sum / ((double)W * H)) : 1.0f;
+    for (int e = tid; e < kPrefW * kPrefW; e += kPrefThreads) {
+      const int r = e / kPrefW, c = e - r * kPrefW;
+      const int gx = mirror_index(wx0 + c, W), gy = mirror_index(wy0 + r, H);
+      const int64_t o = (int64_t)gy * S.master_pitch + gx;
+      mb[r * kPrefWS + c] = __ldg(S.bias + o);
+      md[r * kPrefWS + c] = __ldg(S.dark + o);
+      mr[r * kPrefWS + c] = inv_flat(__ldg(S.flat + o), flat_norm, status);
     }
   }
-  __syncthreads();
-  // row coefficients of the tile's columns for every window row -> A
-  for (int e = tid; e < kPrefWin * kPrefTile; e += kThreads) {
-    const int r = e / kPrefTile, c = e - r * kPrefTile;
-    const float s = __fsub_rn(__fadd_rn(A[r * kPrefTS + c], B[r * kPrefTS + c]),
-                              v[r * kPrefWS + c + kPrefHalo]);
-    A[r * kPrefTS + c] = __fmul_rn(kSqrt3, s);
-  }
-  __syncthreads();
-  // 3. column recursions on A: causal -> B, anti-causal -> v (reused)
-  if (tid < kPrefTile) {
-    float y = 0.0f;
-#pragma unroll 4
-    for (int r = 0; r < kPrefHalo + kPrefTile; ++r) {
-      y = __fmaf_rn(kZ1, y, A[r * kPrefTS + tid]);
-      if (r >= kPrefHalo) B[r * kPrefTS + tid] = y;
+  // owned output range (the padded border belongs to the edge tiles)
+  const int ox0 = x0 - (x0 == 0 ? 2 : 0), ox1 = min(x0 + kPrefTile, W) + (x0 + kPrefTile >= W ? 2 : 0);
+  const int oy0 = y0 - (y0 == 0 ? 2 : 0), oy1 = min(y0 + kPrefTile, H) + (y0 + kPrefTile >= H ? 2 : 0);
+
+  for (int k = k0; k < k1; ++k) {
+    const FrameDesc& F = P.frames[S.frame0 + k];
+    __syncthreads();  // previous frame's passes are done with v and R
+    // 1. the frame's calibrated, mirror-extended window
+#pragma unroll
+    for (int i = 0; i < kPrefPerThread; ++i) {
+      const int e = tid + i * kPrefThreads;
+      if (e < kPrefW * kPrefW) {
+        const int r = e / kPrefW, c = e - r * kPrefW;
+        const int si_ = r * kPrefWS + c;
+        float val;
+        if (SRC == SRC_RAW) {
+          const uint16_t q = __ldg((const uint16_t*)F.src + goff[i]);
+          val = calibrate_px(q, mb[si_], md[si_], F.t, mr[si_]);
+        } else if (SRC == SRC_F32) {
+          val = __ldg((const float*)F.src + goff[i]);
+        } else {
+          val = __half2float(((const __half*)F.src)[goff[i]]);
+        }
+        v[si_] = val;
+      }
     }
-  } else if (tid < 2 * kPrefTile) {
-    const int c = tid - kPrefTile;
-    float y = 0.0f;
-#pragma unroll 4
-    for (int r = kPrefWin - 1; r >= kPrefHalo; --r) {
-      y = __fmaf_rn(kZ1, y, A[r * kPrefTS + c]);
-      if (r < kPrefHalo + kPrefTile) v[r * kPrefWS + c] = y;
+    __syncthreads();
+    // 2. rows: 2 tasks per window row, 34 outputs each
+    if (tid < 2 * kPrefW) {
+      const int r = tid >> 1, e0 = (tid & 1) * kPrefRowSeg;
+      const float* row = v + r * kPrefWS + e0;  // window col e0 + j <-> ext col e0 + j - 16
+      float yp[kPrefRowSeg];
+      float y = 0.0f;
+#pragma unroll
+      for (int j = 0; j < kPrefHalo; ++j) y = __fmaf_rn(kZ1, y, row[j]);
+#pragma unroll
+      for (int j = 0; j < kPrefRowSeg; ++j) {
+        y = __fmaf_rn(kZ1, y, row[kPrefHalo + j]);
+        yp[j] = y;
+      }
+      float ym = 0.0f;
+#pragma unroll
+      for (int j = kPrefRowSeg + 2 * kPrefHalo - 1; j >= kPrefRowSeg + kPrefHalo; --j)
+        ym = __fmaf_rn(kZ1, ym, row[j]);
+#pragma unroll
+      for (int j = kPrefRowSeg - 1; j >= 0; --j) {
+        const float vj = row[kPrefHalo + j];
+        ym = __fmaf_rn(kZ1, ym, vj);
+        R[r * kPrefRS + e0 + j] = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], ym), vj));
+      }
     }
-  }
-  __syncthreads();
-  // 4. c = sqrt(3) (y+ + y- - crow) on the tile, stored densely (pitch W)
-  float* out = F.coef;
-  for (int e = tid; e < kPrefTile * kPrefTile; e += kThreads) {
-    const int r = e / kPrefTile, c = e - r * kPrefTile;
-    const int gx = x0 + c, gy = y0 + r;
-    if (gx < W && gy < H) {
-      const int rr = r + kPrefHalo;
-      const float s = __fsub_rn(__fadd_rn(B[rr * kPrefTS + c], v[rr * kPrefWS + c]),
-                                A[rr * kPrefTS + c]);
-      out[(int64_t)gy * W + gx] = __fmul_rn(kSqrt3, s);
+    __syncthreads();
+    // 3. columns: 4 tasks per ext column, 17 outputs each, straight to HBM
+    if (tid < 4 * kPrefExt) {
+      const int c = tid % kPrefExt, e0 = (tid / kPrefExt) * kPrefColSeg;
+      const float* col = R + e0 * kPrefRS + c;  // window row e0 + j <-> ext row e0 + j - 16
+      float yp[kPrefColSeg];
+      float y = 0.0f;
+#pragma unroll
+      for (int j = 0; j < kPrefHalo; ++j) y = __fmaf_rn(kZ1, y, col[j * kPrefRS]);
+#pragma unroll
+      for (int j = 0; j < kPrefColSeg; ++j) {
+        y = __fmaf_rn(kZ1, y, col[(kPrefHalo + j) * kPrefRS]);
+        yp[j] = y;
+      }
+      float ym = 0.0f;
+#pragma unroll
+      for (int j = kPrefColSeg + 2 * kPrefHalo - 1; j >= kPrefColSeg + kPrefHalo; --j)
+        ym = __fmaf_rn(kZ1, ym, col[j * kPrefRS]);
+      const int gx = x0 - 2 + c;
+      float* out = F.coef;
+#pragma unroll
+      for (int j = kPrefColSeg - 1; j >= 0; --j) {
+        const float rj = col[(kPrefHalo + j) * kPrefRS];
+        ym = __fmaf_rn(kZ1, ym, rj);
+        const int gy = y0 - 2 + e0 + j;
+        if (gx >= ox0 && gx < ox1 && gy >= oy0 && gy < oy1)
+          out[(int64_t)(gy + 2) * S.coef_pitch + (gx + 2)] =
+              __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], ym), rj));
+      }
     }
   }
 }

@@ -36,6 +36,7 @@ struct ShiftArgs {
   void* out;
   int64_t out_pitch, out_fstride;
   uint8_t* valid_out;
+  int64_t coef_pitch;   // padded spline-coefficient frames ((H+4) rows)
   FrameDesc frames[kShiftChunk];
 };
 

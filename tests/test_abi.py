@@ -106,7 +106,8 @@ def test_workspace_size_accounts_for_spline_coefficients(L):
     wb = L.irp_workspace_size(arr, 1, ctypes.byref(_params(interp=1)))
     ws = L.irp_workspace_size(arr, 1, ctypes.byref(_params(interp=2)))
     assert wb > 0
-    per_frame = -(-100 * 30 * 4 // 256) * 256
+    # coefficient frames carry a 2-sample border: (H + 4) rows of align4(W + 4) floats
+    per_frame = -(-(30 + 4) * 104 * 4 // 256) * 256
     assert ws - wb == 4 * per_frame
     assert L.irp_workspace_size(arr, 1, ctypes.byref(_params(interp=9))) == 0
     assert L.irp_shift_workspace_size(100, 30, 4, 2) == 4 * per_frame
