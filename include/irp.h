@@ -185,6 +185,10 @@ typedef struct {
                                      items from an atomic counter, longest first */
   int max_ctas;                   /* persistent grid size; 0 = SMs x occupancy  */
   int wait_spin_limit;            /* bounded-wait polls before IRP_ERR_TIMEOUT; 0 = default */
+  int rows_per_warp;              /* tile height / 8: 0 = default of the frame-count
+                                     bucket (4 up to 16 frames, else 2); the other
+                                     accepted value is 2 (resp. 1); anything else
+                                     falls back to the default */
 } irp_reduce_params;
 
 size_t irp_workspace_size(const irp_set* sets, int nsets, const irp_reduce_params* p);

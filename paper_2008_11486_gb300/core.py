@@ -209,9 +209,10 @@ def _irp_sets(sets):
 
 
 def reduce_params(interp="bilinear", clip=None, normalize_flat=False, persistent=False,
-                  max_ctas=0, wait_spin_limit=0) -> ReduceParams:
+                  max_ctas=0, wait_spin_limit=0, rows_per_warp=0) -> ReduceParams:
     return ReduceParams(INTERP[interp], clip if clip is not None else clip_params(),
-                        int(normalize_flat), int(persistent), int(max_ctas), int(wait_spin_limit))
+                        int(normalize_flat), int(persistent), int(max_ctas), int(wait_spin_limit),
+                        int(rows_per_warp))
 
 
 def workspace_size(sets, params: ReduceParams) -> int:
@@ -249,7 +250,7 @@ class Plan:
     CUDA graph captured around ``launch()`` re-reads the pinned plan at each
     replay, so ``encode()`` may refresh offsets/pointers of the same shapes."""
 
-    def __init__(self, sets, params: ReduceParams, device="cuda"):
+    def __init__(self, sets, params: ReduceParams, device="cuda", ws=None):
         self.sets = list(sets)
         self.params = params
         arr, keep = _irp_sets(self.sets)
@@ -259,7 +260,8 @@ class Plan:
             raise ValueError("irp_plan_bytes rejected the sets/params")
         self.ws_bytes = int(L.irp_workspace_size(arr, len(self.sets), ctypes.byref(params)))
         self.host = torch.empty(self.nbytes, dtype=torch.uint8, pin_memory=True)
-        self.ws = workspace(self.ws_bytes, device)
+        self.ws = ws if (ws is not None and ws.numel() >= self.ws_bytes) else workspace(
+            self.ws_bytes, device)
         self.encode()
 
     def encode(self, sets=None):

@@ -197,7 +197,7 @@ struct SubInfo {
   uint64_t smem;        // dynamic shared memory of the reduce launch
   int32_t bucket, stencil, grid, pgrid;
   int32_t nitems, counter, nsets, nframes;
-  int32_t nrows, ncolsegs, row_e, pad;  // spline row / column passes
+  int32_t nrows, ncolsegs, row_e, py;   // spline row / column passes, rows per warp
 };
 
 struct PlanFile {
@@ -285,7 +285,7 @@ irp_status check_params(const irp_set* sets, int nsets, const irp_reduce_params*
   if (!sets || !p || nsets < 1) return IRP_ERR_INVALID_ARG;
   if (p->interp < IRP_INTERP_NEAREST || p->interp > IRP_INTERP_SPLINE3) return IRP_ERR_INVALID_ARG;
   if (!clip_ok(p->clip)) return IRP_ERR_INVALID_ARG;
-  if (p->max_ctas < 0 || p->wait_spin_limit < 0) return IRP_ERR_INVALID_ARG;
+  if (p->max_ctas < 0 || p->wait_spin_limit < 0 || p->rows_per_warp < 0) return IRP_ERR_INVALID_ARG;
   for (int i = 0; i < nsets; ++i) {
     irp_status st = check_set(sets[i]);
     if (st != IRP_OK) return st;
@@ -361,7 +361,8 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
       max_n = std::max(max_n, sets[i].n);
     }
     const int bucket = reduce_bucket(max_n);
-    const int TWc = tile_cols(stencil), THr = tile_rows(bucket);
+    const int py = rows_per_warp(bucket, p->rows_per_warp);
+    const int TWc = tile_cols(stencil), THr = tile_rows(bucket, py);
     // prefilter work items: tiles x frame groups, enough groups to fill the GPU twice
     int pgroups = 1;
     if (stencil == ST_BSPLINE) {
@@ -477,8 +478,9 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     si.img_off = img_off;
     si.bytes = plan_total_bytes((int)g.size(), nf);
     si.bucket = bucket;
+    si.py = py;
     si.stencil = stencil;
-    si.smem = reduce_smem_bytes(stencil == ST_BSPLINE ? SRC_F32 : SRC_RAW, stencil, bucket, max_n,
+    si.smem = reduce_smem_bytes(stencil == ST_BSPLINE ? SRC_F32 : SRC_RAW, stencil, py, max_n,
                                 mw_max, mh_max);
     si.nitems = tile0;
     si.counter = gi;
@@ -490,7 +492,7 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     si.row_e = row_e;
     if (si.smem > 227 * 1024 - 1024) return IRP_ERR_UNSUPPORTED;  // opt-in limit less static smem
     if (p->persistent) {
-      const int occ = reduce_occupancy(si.bucket, stencil, si.smem);
+      const int occ = reduce_occupancy(si.bucket, si.py, stencil, si.smem);
       int g_ctas = p->max_ctas > 0 ? p->max_ctas : occ * sm_count();
       si.grid = std::max(1, std::min(g_ctas, tile0));
     } else {
@@ -555,7 +557,7 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
     }
     {
       TraceScope tr(IRP_KERNEL_REDUCE, s);
-      e = launch_reduce(si.bucket, si.stencil, &inl, dev_plan, si.grid, si.smem, s);
+      e = launch_reduce(si.bucket, si.py, si.stencil, &inl, dev_plan, si.grid, si.smem, s);
     }
     if (e != cudaSuccess) return note_cuda(e);
   }

@@ -90,6 +90,37 @@ __device__ __forceinline__ CombineOut combine_sorted(const float (&s)[N], int m,
     o.hi_val = 0.0f;
     return o;
   }
+  if (m == N && c.center == 0 && c.max_iter > 0 && N - c.ddof > 0) {
+    // All N samples valid (the common case with an exact register bucket): the
+    // median and run ends have constant indices, and the first pass needs no
+    // range test.  It returns unless the first pass rejects something.
+    const float a = s[(N - 1) >> 1], b = s[N >> 1];
+    o.median = __fmul_rn(__fadd_rn(a, b), 0.5f);
+    const float r = a;
+    float S = 0.0f, C = 0.0f, Q = 0.0f;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const float d = __fsub_rn(s[j], r);
+      const float y = __fsub_rn(d, C);
+      const float t = __fadd_rn(S, y);
+      C = __fsub_rn(__fsub_rn(t, S), y);
+      S = t;
+      Q = __fmaf_rn(d, d, Q);
+    }
+    const float cd = __fdiv_rn(S, (float)N);
+    float ss = __fmaf_rn(cd, __fmaf_rn((float)N, cd, -2.0f * S), Q);
+    ss = fmaxf(ss, 0.0f);
+    const float sigma = sqrtf(__fdiv_rn(ss, (float)(N - c.ddof)));
+    const float elo = __fsub_rn(__fsub_rn(s[0], r), cd);
+    const float ehi = __fsub_rn(__fsub_rn(s[N - 1], r), cd);
+    if (!(sigma > 0.0f) || (!(-elo > c.kappa_lo * sigma) && !(ehi > c.kappa_hi * sigma))) {
+      o.kept = N;
+      o.mean = __fadd_rn(r, __fdiv_rn(S, (float)N));
+      o.lo_val = s[0];
+      o.hi_val = s[N - 1];
+      return o;
+    }
+  }
   const float a = select_at(s, (m - 1) >> 1);
   const float b = select_at(s, m >> 1);
   o.median = __fmul_rn(__fadd_rn(a, b), 0.5f);

@@ -6,7 +6,7 @@
 namespace irp {
 
 int reduce_bucket(int n) {
-  static const int kBuckets[] = {4, 6, 8, 10, 12, 16, 24, 32, 40, 48, 64};
+  static const int kBuckets[] = {4, 5, 6, 8, 10, 12, 16, 24, 32, 40, 48, 64};
   for (int b : kBuckets)
     if (n <= b) return b;
   return 64;
@@ -18,26 +18,31 @@ int tile_cols(int stencil) {
                                                          : StencilShape<ST_NEAREST>::tw);
 }
 
-int tile_rows(int bucket) { return 8 * (bucket <= 16 ? 4 : 2); }
-
-size_t reduce_smem_bytes(int src, int stencil, int bucket, int max_n, int mwin_w, int mwin_h) {
-  return fused_smem_bytes(src, stencil, bucket <= 16 ? 4 : 2, max_n, mwin_w, mwin_h);
+int rows_per_warp(int bucket, int requested) {
+  if (requested == rows_per_warp_alt(bucket)) return requested;
+  return rows_per_warp_default(bucket);
 }
 
-cudaError_t launch_reduce(int bucket, int stencil, const InlinePlan* inl, const void* plan_dev,
-                          int grid, size_t smem, cudaStream_t s) {
+int tile_rows(int bucket, int py) { return 8 * py; }
+
+size_t reduce_smem_bytes(int src, int stencil, int py, int max_n, int mwin_w, int mwin_h) {
+  return fused_smem_bytes(src, stencil, py, max_n, mwin_w, mwin_h);
+}
+
+cudaError_t launch_reduce(int bucket, int py, int stencil, const InlinePlan* inl,
+                          const void* plan_dev, int grid, size_t smem, cudaStream_t s) {
   switch (stencil) {
-    case ST_NEAREST: return launch_reduce_nearest(bucket, inl, plan_dev, grid, smem, s);
-    case ST_BILINEAR: return launch_reduce_bilinear(bucket, inl, plan_dev, grid, smem, s);
-    default: return launch_reduce_bspline(bucket, inl, plan_dev, grid, smem, s);
+    case ST_NEAREST: return launch_reduce_nearest(bucket, py, inl, plan_dev, grid, smem, s);
+    case ST_BILINEAR: return launch_reduce_bilinear(bucket, py, inl, plan_dev, grid, smem, s);
+    default: return launch_reduce_bspline(bucket, py, inl, plan_dev, grid, smem, s);
   }
 }
 
-int reduce_occupancy(int bucket, int stencil, size_t smem) {
+int reduce_occupancy(int bucket, int py, int stencil, size_t smem) {
   switch (stencil) {
-    case ST_NEAREST: return occupancy_reduce_nearest(bucket, smem);
-    case ST_BILINEAR: return occupancy_reduce_bilinear(bucket, smem);
-    default: return occupancy_reduce_bspline(bucket, smem);
+    case ST_NEAREST: return occupancy_reduce_nearest(bucket, py, smem);
+    case ST_BILINEAR: return occupancy_reduce_bilinear(bucket, py, smem);
+    default: return occupancy_reduce_bspline(bucket, py, smem);
   }
 }
 

@@ -3,13 +3,13 @@
 
 namespace irp {
 
-cudaError_t launch_reduce_bspline(int bucket, const InlinePlan* inl, const void* plan_dev, int grid,
-                                  size_t smem, cudaStream_t s) {
-  return launch_bucket_st<ST_BSPLINE, SRC_F32>(bucket, inl, plan_dev, grid, smem, s);
+cudaError_t launch_reduce_bspline(int bucket, int py, const InlinePlan* inl, const void* plan_dev,
+                                  int grid, size_t smem, cudaStream_t s) {
+  return launch_bucket_st<ST_BSPLINE, SRC_F32>(bucket, py, inl, plan_dev, grid, smem, s);
 }
 
-int occupancy_reduce_bspline(int bucket, size_t smem) {
-  return occupancy_bucket_st<ST_BSPLINE, SRC_F32>(bucket, smem);
+int occupancy_reduce_bspline(int bucket, int py, size_t smem) {
+  return occupancy_bucket_st<ST_BSPLINE, SRC_F32>(bucket, py, smem);
 }
 
 }  // namespace irp

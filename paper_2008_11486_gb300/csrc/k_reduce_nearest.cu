@@ -3,13 +3,13 @@
 
 namespace irp {
 
-cudaError_t launch_reduce_nearest(int bucket, const InlinePlan* inl, const void* plan_dev, int grid,
-                                  size_t smem, cudaStream_t s) {
-  return launch_bucket_st<ST_NEAREST, SRC_RAW>(bucket, inl, plan_dev, grid, smem, s);
+cudaError_t launch_reduce_nearest(int bucket, int py, const InlinePlan* inl, const void* plan_dev,
+                                  int grid, size_t smem, cudaStream_t s) {
+  return launch_bucket_st<ST_NEAREST, SRC_RAW>(bucket, py, inl, plan_dev, grid, smem, s);
 }
 
-int occupancy_reduce_nearest(int bucket, size_t smem) {
-  return occupancy_bucket_st<ST_NEAREST, SRC_RAW>(bucket, smem);
+int occupancy_reduce_nearest(int bucket, int py, size_t smem) {
+  return occupancy_bucket_st<ST_NEAREST, SRC_RAW>(bucket, py, smem);
 }
 
 }  // namespace irp

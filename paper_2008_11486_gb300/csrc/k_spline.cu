@@ -5,9 +5,9 @@
 // prefilter.cuh the mirror-boundary solution is c = sqrt(3)(y+ + y- - v) with
 // y+[i] = v[i] + z1 y+[i-1] and y-[i] = v[i] + z1 y-[i+1], z1 = sqrt(3) - 2.
 //
-// Row pass: one CTA per frame row and chunk of kRowGroup = 8 frames; the row's
-// masters and 1/flat are staged in shared memory once for the chunk, and
-// each warp reduces one frame of the row.  Lane l calibrates and holds the E
+// Row pass: one CTA per frame row and chunk of kRowGroup = 16 frames; the
+// row's masters and 1/flat are staged in shared memory once for the chunk,
+// and each warp reduces two frames of the row (both rows loaded up front).  Lane l calibrates and holds the E
 // columns [E l, E l + E) in registers and runs both recursions over them from
 // zero; the value entering from the neighbouring lane is added afterwards,
 // y+[E l + j] = local+[j] + z1^(j+1) y+[E l - 1] (and likewise for y-), which
@@ -51,7 +51,7 @@ __device__ __forceinline__ int find_by(const SetDesc* sets, int nsets, int item,
 }  // namespace
 
 template <int E>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_spline_rows(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
   // masters of the block's row, element x at [x % E][x / E] (stride 33): lane
   // l reads column E l + j from word j*33 + l, one bank per lane
@@ -63,7 +63,6 @@ __global__ void __launch_bounds__(256)
   const SetDesc& S = P.sets[find_by(P.sets, P.h->nsets, item, 0)];
   const int local = item - S.row0;
   const int g = local / S.H, y = local - g * S.H;  // frame chunk, row
-  const int k = g * kRowGroup + warp;
   const int W = S.W;
   const int x0 = lane * E;
   {
@@ -81,9 +80,27 @@ __global__ void __launch_bounds__(256)
     }
   }
   __syncthreads();
-  if (k >= S.n) return;
   constexpr ZPow<E> zp{};
-  {
+  // each warp reduces frames k and k + 8 of the chunk; both raw rows are
+  // requested before the first is used
+  constexpr int kQ = E / 8;  // 16-byte raw loads per lane and row
+  uint4 q[2][kQ];
+  int kf[2] = {g * kRowGroup + warp, g * kRowGroup + warp + 8};
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    if (kf[f] < S.n) {
+      const FrameDesc& F = P.frames[S.frame0 + kf[f]];
+      const uint16_t* raw = (const uint16_t*)F.src + (int64_t)y * S.src_pitch;
+      if ((F.flags & 1) && x0 + E <= W) {
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) q[f][i] = __ldg((const uint4*)(raw + x0) + i);
+      }
+    }
+  }
+#pragma unroll 1
+  for (int f = 0; f < 2; ++f) {
+    const int k = kf[f];
+    if (k >= S.n) break;
     const FrameDesc& F = P.frames[S.frame0 + k];
     const uint16_t* raw = (const uint16_t*)F.src + (int64_t)y * S.src_pitch;
     const float t = F.t;
@@ -91,8 +108,8 @@ __global__ void __launch_bounds__(256)
     if ((F.flags & 1) && x0 + E <= W) {
 #pragma unroll
       for (int j = 0; j < E; j += 8) {
-        const uint4 q = __ldg((const uint4*)(raw + x0 + j));
-        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+        const uint4 qq = f == 0 ? q[0][j / 8] : q[1][j / 8];
+        const uint32_t w[4] = {qq.x, qq.y, qq.z, qq.w};
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int si = (j + i) * 33 + lane;
@@ -163,7 +180,7 @@ __global__ void __launch_bounds__(256)
 
 constexpr int kColSeg = 32;  // output rows per column task
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_spline_cols(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
   const PlanView P = make_view(inl, plan_dev);
   const int item = blockIdx.x * 256 + threadIdx.x;
@@ -181,11 +198,18 @@ __global__ void __launch_bounds__(256)
   const int y0 = seg * kColSeg;
   constexpr int L = kColSeg + 2 * kPrefHalo;
   float v[L];
+  const bool inner = y0 - kPrefHalo >= 0 && y0 + kColSeg + kPrefHalo <= H;
+  if (inner) {
+    const float* p = in + (int64_t)(y0 - kPrefHalo) * ip;
 #pragma unroll
-  for (int j = 0; j < L; ++j) {
-    int yy = y0 - kPrefHalo + j;  // one reflection suffices: H >= kSplineMinSide > kPrefHalo
-    yy = yy < 0 ? -yy : (yy >= H ? 2 * H - 2 - yy : yy);
-    v[j] = __ldg(in + (int64_t)yy * ip);
+    for (int j = 0; j < L; ++j) v[j] = __ldg(p + (int64_t)j * ip);
+  } else {
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+      int yy = y0 - kPrefHalo + j;  // one reflection suffices: H >= kSplineMinSide > kPrefHalo
+      yy = yy < 0 ? -yy : (yy >= H ? 2 * H - 2 - yy : yy);
+      v[j] = __ldg(in + (int64_t)yy * ip);
+    }
   }
   float yp[kColSeg];
   float acc = 0.0f;
@@ -207,6 +231,18 @@ __global__ void __launch_bounds__(256)
   const int bx1 = x == 1 ? -1 : (x == W - 2 ? W : -100);
   const int bx2 = x == 2 ? -2 : (x == W - 3 ? W + 1 : -100);
   const bool xedge = bx1 != -100 || bx2 != -100;
+  const bool yedge = y0 < 3 || y0 + kColSeg > H - 3;
+  if (!xedge && !yedge && y0 + kColSeg <= H) {
+    float* o = out + (int64_t)(y0 + kColSeg - 1 + 2) * cp + (x + 2);
+#pragma unroll
+    for (int j = kColSeg - 1; j >= 0; --j) {
+      const float vj = v[kPrefHalo + j];
+      acc = __fmaf_rn(kZ1, acc, vj);
+      *o = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], acc), vj));
+      o -= cp;
+    }
+    return;
+  }
 #pragma unroll
   for (int j = kColSeg - 1; j >= 0; --j) {
     const float vj = v[kPrefHalo + j];

@@ -386,11 +386,12 @@ static cudaError_t combine_n(const CombineArgs& a, bool f16, cudaStream_t s) {
 
 cudaError_t launch_combine(const CombineArgs& a, bool f16, cudaStream_t s) {
   switch (reduce_bucket(a.n)) {
-    case 8: return combine_n<8>(a, f16, s);
-    case 16: return combine_n<16>(a, f16, s);
-    case 32: return combine_n<32>(a, f16, s);
-    default: return combine_n<64>(a, f16, s);
+#define IRP_CASE(B) \
+  case B: return combine_n<B>(a, f16, s);
+    IRP_FOR_BUCKETS(IRP_CASE)
+#undef IRP_CASE
   }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace irp

@@ -16,7 +16,7 @@ struct MinBlocks {
   static constexpr int value = NMAX <= 32 ? 2 : 1;
 };
 
-template <int NMAX, int STENCIL, int SRC>
+template <int NMAX, int STENCIL, int SRC, int PY>
 __global__ void __launch_bounds__(kThreads, MinBlocks<NMAX>::value)
     k_reduce(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
   extern __shared__ float4 smem4[];
@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<NMAX>::value)
   const PlanView P = make_view(inl, plan_dev);
   const int nitems = P.h->nitems;
   if (!P.h->persistent) {
-    if ((int)blockIdx.x < nitems) reduce_tile<NMAX, STENCIL, SRC>(P, blockIdx.x, smem);
+    if ((int)blockIdx.x < nitems) reduce_tile<NMAX, STENCIL, SRC, PY>(P, blockIdx.x, smem);
     return;
   }
   __shared__ int s_item;
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<NMAX>::value)
     const int item = s_item;
     __syncthreads();
     if (item >= nitems) break;
-    reduce_tile<NMAX, STENCIL, SRC>(P, item, smem);
+    reduce_tile<NMAX, STENCIL, SRC, PY>(P, item, smem);
   }
 }
 
@@ -49,7 +49,7 @@ inline cudaError_t ensure_smem(F fn, size_t smem, size_t& granted) {
   return e;
 }
 
-template <int NMAX, int ST, int SRC>
+template <int NMAX, int ST, int SRC, int PY>
 struct ReduceLauncher {
   static size_t& granted() {
     static size_t g = 0;
@@ -57,7 +57,7 @@ struct ReduceLauncher {
   }
   static cudaError_t launch(const InlinePlan* inl, const void* plan_dev, int grid, size_t smem,
                             cudaStream_t s) {
-    auto fn = k_reduce<NMAX, ST, SRC>;
+    auto fn = k_reduce<NMAX, ST, SRC, PY>;
     cudaError_t e = ensure_smem(fn, smem, granted());
     if (e != cudaSuccess) return e;
     fn<<<grid, kThreads, smem, s>>>(*inl, plan_dev);
@@ -65,22 +65,28 @@ struct ReduceLauncher {
   }
   static int occupancy(size_t smem) {
     int blocks = 0;
-    if (ensure_smem(k_reduce<NMAX, ST, SRC>, smem, granted()) != cudaSuccess) return 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_reduce<NMAX, ST, SRC>, kThreads,
+    if (ensure_smem(k_reduce<NMAX, ST, SRC, PY>, smem, granted()) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_reduce<NMAX, ST, SRC, PY>, kThreads,
                                                       smem) != cudaSuccess)
       return 1;
     return blocks > 0 ? blocks : 1;
   }
 };
 
-#define IRP_FOR_BUCKETS(X) X(4) X(6) X(8) X(10) X(12) X(16) X(24) X(32) X(40) X(48) X(64)
+#define IRP_FOR_BUCKETS(X) X(4) X(5) X(6) X(8) X(10) X(12) X(16) X(24) X(32) X(40) X(48) X(64)
 
+// py: rows per warp, rows_per_warp_default(bucket) or rows_per_warp_alt(bucket)
 template <int ST, int SRC>
-cudaError_t launch_bucket_st(int bucket, const InlinePlan* inl, const void* plan_dev, int grid,
-                             size_t smem, cudaStream_t s) {
+cudaError_t launch_bucket_st(int bucket, int py, const InlinePlan* inl, const void* plan_dev,
+                             int grid, size_t smem, cudaStream_t s) {
+  const bool alt = py != rows_per_warp_default(bucket);
   switch (bucket) {
-#define IRP_CASE(B) \
-  case B: return ReduceLauncher<B, ST, SRC>::launch(inl, plan_dev, grid, smem, s);
+#define IRP_CASE(B)                                                                           \
+  case B:                                                                                     \
+    return alt ? ReduceLauncher<B, ST, SRC, rows_per_warp_alt(B)>::launch(inl, plan_dev, grid, \
+                                                                          smem, s)            \
+               : ReduceLauncher<B, ST, SRC, rows_per_warp_default(B)>::launch(inl, plan_dev,  \
+                                                                              grid, smem, s);
     IRP_FOR_BUCKETS(IRP_CASE)
 #undef IRP_CASE
   }
@@ -88,10 +94,13 @@ cudaError_t launch_bucket_st(int bucket, const InlinePlan* inl, const void* plan
 }
 
 template <int ST, int SRC>
-int occupancy_bucket_st(int bucket, size_t smem) {
+int occupancy_bucket_st(int bucket, int py, size_t smem) {
+  const bool alt = py != rows_per_warp_default(bucket);
   switch (bucket) {
-#define IRP_CASE(B) \
-  case B: return ReduceLauncher<B, ST, SRC>::occupancy(smem);
+#define IRP_CASE(B)                                                               \
+  case B:                                                                         \
+    return alt ? ReduceLauncher<B, ST, SRC, rows_per_warp_alt(B)>::occupancy(smem) \
+               : ReduceLauncher<B, ST, SRC, rows_per_warp_default(B)>::occupancy(smem);
     IRP_FOR_BUCKETS(IRP_CASE)
 #undef IRP_CASE
   }
@@ -99,14 +108,14 @@ int occupancy_bucket_st(int bucket, size_t smem) {
 }
 
 // per-stencil entry points (k_reduce_<stencil>.cu)
-cudaError_t launch_reduce_nearest(int bucket, const InlinePlan* inl, const void* plan_dev, int grid,
-                                  size_t smem, cudaStream_t s);
-cudaError_t launch_reduce_bilinear(int bucket, const InlinePlan* inl, const void* plan_dev,
+cudaError_t launch_reduce_nearest(int bucket, int py, const InlinePlan* inl, const void* plan_dev,
+                                  int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_reduce_bilinear(int bucket, int py, const InlinePlan* inl, const void* plan_dev,
                                    int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_reduce_bspline(int bucket, const InlinePlan* inl, const void* plan_dev, int grid,
-                                  size_t smem, cudaStream_t s);
-int occupancy_reduce_nearest(int bucket, size_t smem);
-int occupancy_reduce_bilinear(int bucket, size_t smem);
-int occupancy_reduce_bspline(int bucket, size_t smem);
+cudaError_t launch_reduce_bspline(int bucket, int py, const InlinePlan* inl, const void* plan_dev,
+                                  int grid, size_t smem, cudaStream_t s);
+int occupancy_reduce_nearest(int bucket, int py, size_t smem);
+int occupancy_reduce_bilinear(int bucket, int py, size_t smem);
+int occupancy_reduce_bspline(int bucket, int py, size_t smem);
 
 }  // namespace irp

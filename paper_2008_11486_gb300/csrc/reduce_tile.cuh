@@ -83,10 +83,10 @@ struct StencilShape {
   static constexpr int tw = 33 - taps;
 };
 
-template <int NMAX>
-struct RowsPerWarp {
-  static constexpr int value = NMAX <= 16 ? 4 : 2;
-};
+// Output rows per warp (tile height / 8): the two choices of each register
+// bucket (the autotuner picks one; the first is the default).
+__host__ __device__ constexpr int rows_per_warp_default(int nmax) { return nmax <= 16 ? 4 : 2; }
+__host__ __device__ constexpr int rows_per_warp_alt(int nmax) { return nmax <= 16 ? 2 : 1; }
 
 constexpr int kStages = 4;           // cp.async ring depth (frames in flight)
 constexpr int kRawChunks = 5;        // 16-byte chunks per staged raw row (40 uint16)
@@ -114,55 +114,98 @@ __host__ __device__ inline size_t fused_smem_bytes(int src, int stencil, int py,
 }
 
 // ------------------------------------------------------------------ staging
-// Copies the warp's window of frame F into one stage: rows [gy0, gy0+rows),
-// 16-byte chunks from the aligned column xa.  Chunks outside the frame are
-// zero-filled; the frames of the raw source must be 16-byte aligned with a
-// pitch of a multiple of 8 elements, otherwise every lane copies elements.
-template <int SRC, int STENCIL, int PY>
-__device__ __forceinline__ void issue_stage(const SetDesc& S, const FrameDesc& F, int gx0, int gy0,
-                                            uint8_t* stage, int lane) {
-  using SS = StageShape<SRC, STENCIL, PY>;
+// What the frame loop needs of one frame for the current tile, built once per
+// tile in shared memory (128 bytes).
+struct FrameRec {
+  const uint8_t* base;   // staging source: element (ybase, xa) of the frame
+  const uint8_t* fbase;  // a valid address inside the frame (zero-byte copies)
+  int ybase, xa;         // first staged row / aligned first staged column
+  int off;               // tile's first source column inside the staged row
+  int mofs;              // union-window offset of the tile's first source pixel
+  int ox, oy;            // tap origin (masters read from global memory)
+  float fx, fy, t;
+  int vx0, vx1, vy0, vy1;
+  int flags;
+  float wx[4], wy[4];
+  int pad[6];
+};
+static_assert(sizeof(FrameRec) == 128, "FrameRec layout");
+
+template <int SRC>
+__device__ __forceinline__ FrameRec make_rec(const FrameDesc& F, int tx0, int ty0, int64_t pitch,
+                                             int mox, int moy, int mwin_w) {
+  FrameRec R;
+  const int gx0 = tx0 + F.ox, gy0 = ty0 + F.oy;
   if (SRC == SRC_RAW) {
-    const uint16_t* base = (const uint16_t*)F.src;
-    const int xa = gx0 & ~7;
-    if (F.flags & 1) {
-      for (int c = lane; c < SS::rows * kRawChunks; c += 32) {
-        const int r = c / kRawChunks, j = c - r * kRawChunks;
-        const int x = xa + 8 * j, y = gy0 + r;
-        int bytes = 0;
-        const uint16_t* src = base;
-        if (y >= 0 && y < S.H && x >= 0 && x < S.W) {
-          bytes = min(16, 2 * (S.W - x));
-          src = base + (int64_t)y * S.src_pitch + x;
-        }
-        cp_async16(stage + (r * kRawChunks + j) * 16, src, bytes);
-      }
-    } else {
-      uint16_t* dst = (uint16_t*)stage;
-      for (int e = lane; e < SS::rows * SS::elems; e += 32) {
-        const int r = e / SS::elems, i = e - r * SS::elems;
-        const int x = xa + i, y = gy0 + r;
-        dst[e] = (y >= 0 && y < S.H && x >= 0 && x < S.W) ? base[(int64_t)y * S.src_pitch + x]
-                                                           : (uint16_t)0;
-      }
+    R.xa = gx0 & ~7;
+    R.off = gx0 - R.xa;
+    R.ybase = gy0;
+    R.fbase = (const uint8_t*)F.src;
+    R.base = R.fbase + ((int64_t)gy0 * pitch + R.xa) * 2;
+  } else {  // padded coefficient frame: element (x, y) at ((y + 2) * pitch + x + 2)
+    R.xa = (gx0 + 2) & ~3;
+    R.off = gx0 + 2 - R.xa;
+    R.ybase = gy0 + 2;
+    R.fbase = (const uint8_t*)F.coef;
+    R.base = R.fbase + ((int64_t)R.ybase * pitch + R.xa) * 4;
+  }
+  R.mofs = (F.oy - moy) * mwin_w + (F.ox - mox);
+  R.ox = F.ox;
+  R.oy = F.oy;
+  R.fx = F.fx;
+  R.fy = F.fy;
+  R.t = F.t;
+  R.vx0 = F.vx0;
+  R.vx1 = F.vx1;
+  R.vy0 = F.vy0;
+  R.vy1 = F.vy1;
+  R.flags = F.flags;
+  for (int i = 0; i < 4; ++i) {
+    R.wx[i] = F.wx[i];
+    R.wy[i] = F.wy[i];
+  }
+  return R;
+}
+
+// Copies the warp's window of one frame into one stage.  Each lane owns up
+// to kIt fixed 16-byte chunks of the window (row delta, column delta and byte
+// offset precomputed per tile); chunks outside the frame are zero-filled.  Raw
+// frames that are not 16-byte aligned with a pitch of 8k elements are copied
+// element by element instead.
+template <int SRC, int kIt>
+struct LaneChunks {
+  int drow[kIt], dcol[kIt], soff[kIt];
+  int64_t goff[kIt];
+};
+
+template <int SRC, int STENCIL, int PY>
+__device__ __forceinline__ void issue_stage(const FrameRec& R, const LaneChunks<SRC, (StageShape<SRC, STENCIL, PY>::rows * StageShape<SRC, STENCIL, PY>::chunks + 31) / 32>& L,
+                                            int Hlim, int Wlim, int64_t pitch, uint8_t* stage,
+                                            int lane, int wrow) {
+  using SS = StageShape<SRC, STENCIL, PY>;
+  constexpr int kIt = (SS::rows * SS::chunks + 31) / 32;
+  if (SRC == SRC_RAW && !(R.flags & 1)) {
+    uint16_t* dst = (uint16_t*)stage;
+    const uint16_t* fb = (const uint16_t*)R.fbase;
+    for (int e = lane; e < SS::rows * SS::elems; e += 32) {
+      const int r = e / SS::elems, i = e - r * SS::elems;
+      const int y = R.ybase + wrow + r, xx = R.xa + i;
+      dst[e] = ((unsigned)y < (unsigned)Hlim && (unsigned)xx < (unsigned)Wlim)
+                   ? fb[(int64_t)y * pitch + xx] : (uint16_t)0;
     }
-  } else {
-    // padded coefficient frame: element (x, y) at ((y + 2) * pitch + x + 2)
-    const float* base = F.coef;
-    const int px = gx0 + 2, py = gy0 + 2;
-    const int xa = px & ~3;
-    const int Hp = S.H + 4;
-    for (int c = lane; c < SS::rows * kCoefChunks; c += 32) {
-      const int r = c / kCoefChunks, j = c - r * kCoefChunks;
-      const int x = xa + 4 * j, y = py + r;
-      int bytes = 0;
-      const float* src = base;
-      if (y >= 0 && y < Hp && x >= 0 && x < (int)S.coef_pitch) {
-        bytes = 16;
-        src = base + (int64_t)y * S.coef_pitch + x;
-      }
-      cp_async16(stage + (r * kCoefChunks + j) * 16, src, bytes);
+    return;
+  }
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    if (L.soff[it] < 0) continue;
+    const int y = R.ybase + L.drow[it], xx = R.xa + L.dcol[it];
+    int bytes = 0;
+    const uint8_t* src = R.fbase;
+    if ((unsigned)y < (unsigned)Hlim && (unsigned)xx < (unsigned)Wlim) {
+      bytes = SRC == SRC_RAW ? min(16, 2 * (Wlim - xx)) : 16;
+      src = R.base + L.goff[it];
     }
+    cp_async16(stage + L.soff[it], src, bytes);
   }
 }
 
@@ -185,9 +228,8 @@ __device__ __forceinline__ void stage_masters(const SetDesc& S, int tx0, int ty0
   }
 }
 
-template <int NMAX, int STENCIL, int SRC>
+template <int NMAX, int STENCIL, int SRC, int PY>
 __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* smem) {
-  constexpr int PY = RowsPerWarp<NMAX>::value;
   constexpr int TH = 8 * PY;
   constexpr int TW = StencilShape<STENCIL>::tw;
   constexpr int T = StencilShape<STENCIL>::taps;
@@ -202,12 +244,20 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wy0 = ty0 + warp * PY;  // first output row of this warp
   const int x = tx0 + lane;
+  // set fields used inside the frame loop, in registers
+  const int W = S.W, H = S.H;
+  const int mwin_w = S.mwin_w;
+  float* const stack_out = S.stack_out;
+  const int64_t out_pitch = S.out_pitch;
+  const int64_t pitch = SRC == SRC_RAW ? S.src_pitch : S.coef_pitch;
+  const int Hlim = SRC == SRC_RAW ? H : H + 4;
+  const int Wlim = SRC == SRC_RAW ? W : (int)S.coef_pitch;
 
   float* s_samples = smem;                                    // [n][TH][32]
   uint8_t* s_stage = (uint8_t*)(smem + h.smem_samples) + warp * kStages * SS::bytes;
   float4* s_mast = (float4*)((uint8_t*)(smem + h.smem_samples) +
                              (size_t)kStages * SS::bytes * (kThreads / 32));
-  FrameDesc* s_desc = (FrameDesc*)(s_mast + h.smem_master);  // the set's frames
+  FrameRec* s_rec = (FrameRec*)(s_mast + h.smem_master);    // the set's frames
 
   if (S.ready_flag) {
     __shared__ int s_ok;
@@ -215,25 +265,33 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
     __syncthreads();
     if (!s_ok) return;  // status latched; this tile's outputs are left untouched
   }
-  {
-    // frame descriptors of the set: one copy per tile, read from shared memory
-    const uint4* src = (const uint4*)(P.frames + S.frame0);
-    uint4* dst = (uint4*)s_desc;
-    for (int i = threadIdx.x; i < n * (int)(sizeof(FrameDesc) / 16); i += kThreads) dst[i] = src[i];
-  }
+  for (int k = threadIdx.x; k < n; k += kThreads)
+    s_rec[k] = make_rec<SRC>(P.frames[S.frame0 + k], tx0, ty0, pitch, S.mox, S.moy, mwin_w);
   float flat_norm = 1.0f;
   if (SRC == SRC_RAW && S.flat_sum) flat_norm = (float)(*S.flat_sum / ((double)S.W * S.H));
   if (SRC == SRC_RAW && S.mwin_w > 0) stage_masters(S, tx0, ty0, flat_norm, s_mast, h.status);
+  // this lane's staging chunks (frame-independent)
+  constexpr int kIt = (SS::rows * SS::chunks + 31) / 32;
+  LaneChunks<SRC, kIt> LC;
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int c = lane + 32 * it;
+    const int r = c / SS::chunks, j = c - r * SS::chunks;
+    const int colw = SRC == SRC_RAW ? 8 : 4, esz = SRC == SRC_RAW ? 2 : 4;
+    LC.drow[it] = warp * PY + r;
+    LC.dcol[it] = colw * j;
+    LC.soff[it] = c < SS::rows * SS::chunks ? c * 16 : -1;
+    LC.goff[it] = ((int64_t)LC.drow[it] * pitch + LC.dcol[it]) * esz;
+  }
   __syncthreads();
 
-  const FrameDesc* frames = s_desc;
+  const FrameRec* frames = s_rec;
   // prologue: frames 0 .. kStages-2 in flight
 #pragma unroll
   for (int k = 0; k < kStages - 1; ++k) {
-    if (k < n) {
-      const FrameDesc& F = frames[k];
-      issue_stage<SRC, STENCIL, PY>(S, F, tx0 + F.ox, wy0 + F.oy, s_stage + k * SS::bytes, lane);
-    }
+    if (k < n)
+      issue_stage<SRC, STENCIL, PY>(frames[k], LC, Hlim, Wlim, pitch, s_stage + k * SS::bytes,
+                                    lane, warp * PY);
     cp_async_commit();
   }
   const float kInf = __int_as_float(0x7f800000);
@@ -243,25 +301,23 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
     __syncwarp();
     {
       const int kn = k + kStages - 1;
-      if (kn < n) {
-        const FrameDesc& Fn = frames[kn];
-        issue_stage<SRC, STENCIL, PY>(S, Fn, tx0 + Fn.ox, wy0 + Fn.oy,
-                                      s_stage + (kn % kStages) * SS::bytes, lane);
-      }
+      if (kn < n)
+        issue_stage<SRC, STENCIL, PY>(frames[kn], LC, Hlim, Wlim, pitch,
+                                      s_stage + (kn % kStages) * SS::bytes, lane, warp * PY);
       cp_async_commit();
     }
-    const FrameDesc& F = frames[k];
+    const FrameRec& F = frames[k];
     const uint8_t* st = s_stage + (k % kStages) * SS::bytes;
     float v[SS::rows];
     if (SRC == SRC_RAW) {
-      const int off = (tx0 + F.ox) & 7;
+      const int off = F.off;
       const uint16_t* raw = (const uint16_t*)st;
       const float t = F.t;
-      if (S.mwin_w > 0) {
-        const int mrow = warp * PY + (F.oy - S.moy), mcol = lane + (F.ox - S.mox);
+      if (mwin_w > 0) {
+        const float4* mp = s_mast + F.mofs + warp * PY * mwin_w + lane;
 #pragma unroll
         for (int r = 0; r < SS::rows; ++r) {
-          const float4 m = s_mast[(mrow + r) * S.mwin_w + mcol];
+          const float4 m = mp[r * mwin_w];
           v[r] = calibrate_px(raw[r * SS::elems + lane + off], m.x, m.y, t, m.z);
         }
       } else {  // offsets too spread for a union window: masters from global memory
@@ -270,7 +326,7 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
         for (int r = 0; r < SS::rows; ++r) {
           const int gy = wy0 + F.oy + r;
           float b = 0.0f, d = 0.0f, rf = 0.0f;
-          if (gx >= 0 && gx < S.W && gy >= 0 && gy < S.H) {
+          if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
             const int64_t o = (int64_t)gy * S.master_pitch + gx;
             b = __ldg(S.bias + o);
             d = __ldg(S.dark + o);
@@ -280,7 +336,7 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
         }
       }
     } else {
-      const int off = (tx0 + F.ox + 2) & 3;
+      const int off = F.off;
       const float* cf = (const float*)st;
 #pragma unroll
       for (int r = 0; r < SS::rows; ++r) v[r] = cf[r * SS::elems + lane + off];
@@ -326,8 +382,8 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
       const int y = wy0 + q;
       const bool ok = xv & (y >= F.vy0) & (y <= F.vy1);
       sk[q * 32] = ok ? a[q] : kInf;
-      if (S.stack_out && lane < TW && x < S.W && y < S.H)
-        S.stack_out[((int64_t)k * S.H + y) * S.out_pitch + x] = ok ? a[q] : qnan;
+      if (stack_out && lane < TW && x < W && y < H)
+        stack_out[((int64_t)k * H + y) * out_pitch + x] = ok ? a[q] : qnan;
     }
   }
   cp_async_wait<0>();
@@ -335,11 +391,14 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
   (void)T;
 
   const ClipArgs ca{h.kappa_lo, h.kappa_hi, h.max_iter, h.center, h.ddof};
-  if (lane < TW && x < S.W) {
+  float* const mean_out = S.mean_out;
+  float* const median_out = S.median_out;
+  uint16_t* const nkept_out = S.nkept_out;
+  if (lane < TW && x < W) {
 #pragma unroll 1
     for (int q = 0; q < PY; ++q) {
       const int y = wy0 + q;
-      if (y >= S.H) break;
+      if (y >= H) break;
       const float* sp = s_samples + (size_t)(warp * PY + q) * 32 + lane;
       float s[NMAX];
       int m = 0;
@@ -350,10 +409,10 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
       }
       sort_network<NMAX>(s);
       const CombineOut o = combine_sorted<NMAX>(s, m, ca);
-      const int64_t oi = (int64_t)y * S.out_pitch + x;
-      if (S.mean_out) S.mean_out[oi] = o.mean;
-      if (S.median_out) S.median_out[oi] = o.median;
-      if (S.nkept_out) S.nkept_out[oi] = (uint16_t)o.kept;
+      const int64_t oi = (int64_t)y * out_pitch + x;
+      if (mean_out) mean_out[oi] = o.mean;
+      if (median_out) median_out[oi] = o.median;
+      if (nkept_out) nkept_out[oi] = (uint16_t)o.kept;
     }
   }
   __syncthreads();  // descriptors and union window are reused by the next tile

@@ -1,0 +1,228 @@
+"""Continuous-batching reduction service.
+
+A request is one exposure of a multi-chip camera: one new raw frame per chip
+plus its dither offset.  Each chip keeps its calibration masters resident on
+the device and a ring of its most recent raw frames; a request is reduced as
+one frame set per chip made of the new frame and the ``depth - 1`` previous
+ones (a rolling reference stack).
+
+Scheduling:
+  * admission: a request is admitted when an in-flight slot is free and the
+    device has room for it (``torch.cuda.mem_get_info`` minus a reserve);
+    admitted requests copy their new frames into the chip rings on a copy
+    stream (pinned host memory -> HBM);
+  * batching: at every scheduler tick all admitted requests whose copies have
+    landed are reduced together in one persistent launch (all their chip sets
+    in one plan), on the compute stream, while newer requests keep uploading;
+  * completion: an event per batch; a request's latency is the time from its
+    arrival to the host seeing its outputs ready.
+Each result depends only on its own frames and masters, so it is the same
+alone and inside any batch.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import threading
+import time
+
+import numpy as np
+import torch
+
+from . import core
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    frames: list          # per chip: pinned host uint16 [H, W]
+    dx: np.ndarray        # per chip offset of the new frame
+    dy: np.ndarray
+    exptime: float = 60.0
+    arrival: float = 0.0
+    done: float = 0.0
+    outputs: list = None  # per chip (mean, median) device tensors
+    status: int = 0
+
+
+class Chip:
+    """Resident masters and the raw-frame ring of one detector chip."""
+
+    def __init__(self, bias, dark, flat, depth: int, slots: int):
+        self.bias, self.dark, self.flat = bias, dark, flat
+        self.H, self.W = bias.shape
+        self.depth = depth
+        self.ring = torch.empty((slots, self.H, self.W), dtype=torch.uint16, device=bias.device)
+        self.slot_dx = np.zeros(slots)
+        self.slot_dy = np.zeros(slots)
+        self.slot_t = np.full(slots, 60.0, dtype=np.float32)
+        self.count = 0        # frames written so far
+        self.slots = slots
+
+    def next_slot(self) -> int:
+        return self.count % self.slots
+
+    def stack_slots(self, upto: int):
+        """Ring slots of the set ending with frame number ``upto`` (oldest first)."""
+        first = max(0, upto - self.depth + 1)
+        return [k % self.slots for k in range(first, upto + 1)]
+
+
+class Server:
+    def __init__(self, masters, depth=5, max_inflight=2, interp="bilinear", clip=None,
+                 hbm_reserve_bytes=2 << 30, device="cuda"):
+        self.device = torch.device(device)
+        self.depth = depth
+        self.max_inflight = max_inflight
+        self.interp = interp
+        self.clip = clip
+        self.reserve = hbm_reserve_bytes
+        # ring slots: depth for the stack plus one per request that may still be
+        # reading when the next one writes
+        self.chips = [Chip(b, d, f, depth, depth + max_inflight) for (b, d, f) in masters]
+        self.copy_stream = torch.cuda.Stream(device=self.device)
+        self.compute_stream = torch.cuda.Stream(device=self.device)
+        self.pending = collections.deque()   # arrived, not admitted
+        self.uploading = []                  # (request, frame numbers, copy event)
+        self.running = []                    # (requests, completion event, plan, ws)
+        self.done = []
+        self.lock = threading.Lock()
+        self.ws_free = []                    # workspaces of completed batches
+        self.ws_all = []
+        self.batches = 0
+
+    # ---------------------------------------------------------------- intake
+    def submit(self, req: Request):
+        req.arrival = time.perf_counter()
+        with self.lock:
+            self.pending.append(req)
+
+    def _request_bytes(self, req) -> int:
+        out = sum(2 * c.H * c.W * 4 for c in self.chips)
+        return out
+
+    def _inflight(self) -> int:
+        return len(self.uploading) + sum(len(r[0]) for r in self.running)
+
+    # -------------------------------------------------------------- scheduling
+    def _admit(self):
+        while True:
+            with self.lock:
+                if not self.pending or self._inflight() >= self.max_inflight:
+                    return
+                req = self.pending[0]
+            free, _ = torch.cuda.mem_get_info(self.device)
+            if free - self._request_bytes(req) < self.reserve:
+                return
+            with self.lock:
+                self.pending.popleft()
+            nums = []
+            with torch.cuda.stream(self.copy_stream):
+                for c, (chip, frame) in enumerate(zip(self.chips, req.frames)):
+                    slot = chip.next_slot()
+                    chip.ring[slot].copy_(frame, non_blocking=True)
+                    chip.slot_dx[slot] = req.dx[c]
+                    chip.slot_dy[slot] = req.dy[c]
+                    chip.slot_t[slot] = req.exptime
+                    nums.append(chip.count)
+                    chip.count += 1
+                ev = torch.cuda.Event()
+                ev.record(self.copy_stream)
+            self.uploading.append((req, nums, ev))
+
+    def _launch(self):
+        ready, waiting = [], []
+        for u in self.uploading:  # one query per upload, so none is lost in between
+            (ready if u[2].query() else waiting).append(u)
+        if not ready:
+            return
+        self.uploading = waiting
+        sets, reqs = [], []
+        for req, nums, ev in ready:
+            self.compute_stream.wait_event(ev)
+            req.outputs = []
+            for chip, num in zip(self.chips, nums):
+                slots = chip.stack_slots(num)
+                s = core.DeviceSet(frames=[chip.ring[k] for k in slots], bias=chip.bias,
+                                   dark=chip.dark, flat=chip.flat, exptime=chip.slot_t[slots],
+                                   dx=chip.slot_dx[slots], dy=chip.slot_dy[slots])
+                s.alloc_outputs(want_nkept=False)
+                sets.append(s)
+                req.outputs.append((s.mean, s.median))
+            reqs.append(req)
+        params = core.reduce_params(self.interp, self.clip, persistent=True)
+        need = core.workspace_size(sets, params)
+        ws = None
+        for i, w in enumerate(self.ws_free):
+            if w.numel() >= need:
+                ws = self.ws_free.pop(i)
+                break
+        if ws is None:
+            with torch.cuda.stream(self.compute_stream):  # zeroed in stream order
+                ws = core.workspace(need, self.device)
+            self.ws_all.append(ws)
+        plan = core.Plan(sets, params, device=self.device, ws=ws)  # pinned plan: no host wait
+        plan.launch(self.compute_stream)
+        done_ev = torch.cuda.Event()
+        done_ev.record(self.compute_stream)
+        self.running.append((reqs, done_ev, plan, ws))
+        self.batches += 1
+
+    def _complete(self):
+        still = []
+        for reqs, ev, plan, ws in self.running:
+            if ev.query():
+                t = time.perf_counter()
+                for r in reqs:
+                    r.done = t
+                    self.done.append(r)
+                self.ws_free.append(ws)
+            else:
+                still.append((reqs, ev, plan, ws))
+        self.running = still
+
+    def tick(self):
+        self._complete()
+        self._admit()
+        self._launch()
+
+    def idle(self) -> bool:
+        with self.lock:
+            return not self.pending and not self.uploading and not self.running
+
+    def drain(self, timeout_s=600.0):
+        t0 = time.perf_counter()
+        while not self.idle():
+            self.tick()
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError("server did not drain")
+            time.sleep(50e-6)
+        self._complete()
+
+    def status(self) -> int:
+        """Synchronises and returns the first non-OK device status of any batch."""
+        st = 0
+        for ws in self.ws_all:
+            s = core.sync_status(ws, self.compute_stream)
+            st = st or s
+        return st
+
+
+def run_poisson(server: Server, requests, rate_hz: float, seed: int = 11486004):
+    """Submits requests at Poisson arrival times (rate_hz) while driving the
+    scheduler; returns per-request latencies (s) and the wall time."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate_hz, size=len(requests))
+    t0 = time.perf_counter()
+    due = t0 + np.cumsum(gaps)
+    i = 0
+    while i < len(requests) or not server.idle():
+        now = time.perf_counter()
+        while i < len(requests) and now >= due[i]:
+            server.submit(requests[i])
+            i += 1
+        server.tick()
+        time.sleep(20e-6)
+    wall = time.perf_counter() - t0
+    lat = np.array([r.done - r.arrival for r in requests])
+    return lat, wall

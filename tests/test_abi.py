@@ -66,7 +66,7 @@ def _set(n=3, W=64, H=48, frames=None, **kw):
 
 
 def _params(interp=1, **kw):
-    p = B.ReduceParams(interp, B.ClipParams(3.0, 3.0, 3, 0, 0), 0, 0, 0, 0)
+    p = B.ReduceParams(interp, B.ClipParams(3.0, 3.0, 3, 0, 0), 0, 0, 0, 0, 0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p

@@ -1,0 +1,124 @@
+"""Batched and served forms on the GPU: a CUDA-graph-replayed persistent batch
+of uneven sets and the continuous-batching server must give each set exactly
+the result of a standalone reduction (the per-pixel arithmetic does not
+depend on what else is in the launch)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2008_11486_gb300 import batch, core, serve, synth
+from paper_2008_11486_gb300 import build as irp_build
+from parity_util import compare, mean_tolerance
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _native():
+    assert torch.cuda.is_available()
+    irp_build.build()
+
+
+def _alone(fs, interp):
+    s = core.device_set(fs).alloc_outputs()
+    ws = core.reduce_sets([s], core.reduce_params(interp))
+    assert core.sync_status(ws) == 0
+    return s.mean.cpu().numpy(), s.median.cpu().numpy()
+
+
+@pytest.mark.parametrize("interp", ["bilinear", "spline3"])
+def test_graph_batch_autotuned_equals_per_set(interp, tmp_path):
+    shapes = [(3, 70, 50), (9, 64, 96), (17, 40, 36), (33, 48, 64), (5, 130, 40), (12, 64, 64),
+              (40, 50, 50), (24, 36, 90)]
+    fss = [synth.make_set(W, H, n, 4.0, 700 + i, n_stars=15, n_cr=4)
+           for i, (n, W, H) in enumerate(shapes)]
+    sets = [core.device_set(fs).alloc_outputs() for fs in fss]
+    tuner = batch.Autotuner(str(tmp_path / "tune.json"), reps=1)
+    params, cfg = tuner.params_for(sets, interp)
+    assert cfg in batch.Autotuner.candidates(sets, True)
+    br = batch.BatchReducer(sets, params)
+    for _ in range(3):
+        br.run()
+    torch.cuda.synchronize()
+    assert br.status() == 0
+    for fs, s in zip(fss, sets):
+        m, d = _alone(fs, interp)
+        assert np.array_equal(s.mean.cpu().numpy().view(np.uint32), m.view(np.uint32))
+        assert np.array_equal(s.median.cpu().numpy().view(np.uint32), d.view(np.uint32))
+
+
+def test_rows_per_warp_choices_agree():
+    fs = synth.make_set(100, 90, 10, 4.0, 31, n_stars=20)
+    outs = []
+    for rpw in (0, 2, 4, 7):
+        s = core.device_set(fs).alloc_outputs()
+        ws = core.reduce_sets([s], core.reduce_params("bilinear", rows_per_warp=rpw))
+        assert core.sync_status(ws) == 0
+        outs.append(s.mean.cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o.view(np.uint32), outs[0].view(np.uint32))
+
+
+def _chip_frames(nchips, W, H, nreq, seed):
+    """Per chip: masters and a sequence of dithered frames of a fixed sky."""
+    chips = []
+    for c in range(nchips):
+        fs = synth.make_set(W, H, nreq, 3.0, seed + 31 * c, n_stars=20, n_cr=3)
+        chips.append(fs)
+    return chips
+
+
+def test_server_results_equal_standalone_reductions():
+    nchips, W, H, nreq, depth = 3, 96, 80, 8, 5
+    chips = _chip_frames(nchips, W, H, nreq, 4242)
+    masters = [tuple(torch.from_numpy(a).cuda() for a in (fs.bias, fs.dark, fs.flat))
+               for fs in chips]
+    srv = serve.Server(masters, depth=depth, max_inflight=3, interp="bilinear",
+                       hbm_reserve_bytes=0)
+    reqs = []
+    for r in range(nreq):
+        frames = [torch.from_numpy(fs.raw[r]).pin_memory() for fs in chips]
+        reqs.append(serve.Request(rid=r, frames=frames,
+                                  dx=np.array([fs.dx[r] for fs in chips]),
+                                  dy=np.array([fs.dy[r] for fs in chips])))
+    lat, wall = serve.run_poisson(srv, reqs, rate_hz=2000.0)
+    assert srv.status() == 0
+    assert len(srv.done) == nreq and np.all(lat > 0)
+    assert srv.batches <= nreq
+    for r, req in enumerate(reqs):
+        first = max(0, r - depth + 1)
+        for c, fs in enumerate(chips):
+            sub = synth.FrameSet(raw=fs.raw[first:r + 1], bias=fs.bias, dark=fs.dark,
+                                 flat=fs.flat, exptime=fs.exptime[first:r + 1],
+                                 dx=fs.dx[first:r + 1], dy=fs.dy[first:r + 1])
+            m, d = _alone(sub, "bilinear")
+            gm, gd = req.outputs[c]
+            assert np.array_equal(gm.cpu().numpy().view(np.uint32), m.view(np.uint32)), (r, c)
+            assert np.array_equal(gd.cpu().numpy().view(np.uint32), d.view(np.uint32)), (r, c)
+    # and one of them against the oracle
+    fs = chips[1]
+    sub = synth.FrameSet(raw=fs.raw[3:8], bias=fs.bias, dark=fs.dark, flat=fs.flat,
+                         exptime=fs.exptime[3:8], dx=fs.dx[3:8], dy=fs.dy[3:8])
+    ref = oracle.reduce_set(sub, interp="bilinear")
+    ok = ref["margin"] >= 1e-3
+    compare("served", reqs[7].outputs[1][0].cpu().numpy(), ref["mean"],
+            mean_tolerance(ref["mean"]) + 1e-2, ok)
+
+
+def test_server_admission_waits_for_hbm():
+    chips = _chip_frames(2, 64, 48, 2, 77)
+    masters = [tuple(torch.from_numpy(a).cuda() for a in (fs.bias, fs.dark, fs.flat))
+               for fs in chips]
+    free, total = torch.cuda.mem_get_info()
+    srv = serve.Server(masters, depth=5, max_inflight=2, hbm_reserve_bytes=total * 2)
+    req = serve.Request(rid=0, frames=[torch.from_numpy(fs.raw[0]).pin_memory() for fs in chips],
+                        dx=np.array([fs.dx[0] for fs in chips]),
+                        dy=np.array([fs.dy[0] for fs in chips]))
+    srv.submit(req)
+    for _ in range(20):
+        srv.tick()
+    assert len(srv.pending) == 1 and not srv.done   # not admitted: no room
+    srv.reserve = 0
+    srv.drain()
+    assert len(srv.done) == 1 and srv.status() == 0
