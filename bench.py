@@ -41,6 +41,21 @@ WORKLOADS = {
                       "on-chip stack, 3-sigma clipped mean (3 passes) + median",
                  sets=[(4096, 4096, 32)], offset=5.0, interp="bilinear", persistent=False,
                  seed=11486002),
+    "precision": dict(desc="32 frames of 4096x4096 uint16, bilinear: fused FP32 on-chip stack vs "
+                           "unfused FP32 and FP16-with-per-frame-scale HBM stacks; FP64 frame sums "
+                           "choose the FP16 scaling; errors against the FP64 oracle",
+                      sets=[(4096, 4096, 32)], offset=5.0, interp="bilinear", persistent=False,
+                      seed=11486002),
+    "batch": dict(desc="64 frame sets, frame counts U{3..40}, sizes from {512^2, 1024^2, 2048^2, "
+                       "4096^2}, bilinear: one autotuned persistent launch per frame-count bucket "
+                       "replayed from a CUDA graph vs 64 plain per-set launches",
+                  sets=None, offset=5.0, interp="bilinear", persistent=True, seed=11486003),
+    "served": dict(desc="Poisson arrivals (0.5/s), each request 16 chips of 6144x6160 uint16 "
+                        "reduced against a 5-frame rolling stack per chip (raw ring, resident "
+                        "masters), admission by free HBM, continuous batching; p50/p99 latency "
+                        "and sustained Mpix/s of new pixels",
+                   sets=[(6144, 6160, 5)] * 16, offset=5.0, interp="bilinear", persistent=True,
+                   seed=11486004),
 }
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -142,15 +157,25 @@ def algorithmic_bytes(kind, sets, interp, want_nkept=False):
     return tot
 
 
+def workload_shapes(workload):
+    """(W, H, n) of every set of one step."""
+    cfg = WORKLOADS[workload]
+    if cfg["sets"] is not None:
+        return list(cfg["sets"])
+    from paper_2008_11486_gb300 import synth
+    return [(W, H, n) for (n, W, H) in synth.batch_shapes(cfg["seed"])]
+
+
 def cpu_baseline(workload, steps, warmup, nthreads, as_reference=False):
     """Times the oracle as it stands on a bounded sample: one set of the
-    workload, cropped to at most 256 rows, per step."""
+    workload, cropped to at most 256 rows (and 2048 columns), per step."""
     import oracle
     from paper_2008_11486_gb300 import synth
     cfg = WORKLOADS[workload]
-    W, H, n = cfg["sets"][0]
-    Hs = min(H, 256)
-    fs = synth.make_set(W, Hs, n, cfg["offset"], cfg["seed"], n_stars=max(1, 200 * Hs // H))
+    W, H, n = max(workload_shapes(workload), key=lambda t: t[2])
+    Hs, Ws = min(H, 256), min(W, 2048)
+    fs = synth.make_set(Ws, Hs, n, cfg["offset"], cfg["seed"],
+                        n_stars=max(1, 200 * Hs * Ws // (H * W)))
     oracle.build()
     times = []
     for i in range(warmup + steps):
@@ -159,10 +184,10 @@ def cpu_baseline(workload, steps, warmup, nthreads, as_reference=False):
         dt = time.perf_counter() - t0
         if i >= warmup:
             times.append(dt)
-    px = n * W * Hs
+    px = n * Ws * Hs
     mean_t = float(np.mean(times))
     return dict(value=px / mean_t / 1e6, unit="Mpix/s", cores=nthreads, kind="oracle",
-                sample=f"{n} frames of {W}x{Hs} (one set of the workload cropped to {Hs} rows), "
+                sample=f"{n} frames of {Ws}x{Hs} (one set of the workload cropped), "
                        f"{cfg['interp']}, FP64, OpenMP {nthreads} threads",
                 seconds_per_sample=mean_t)
 
@@ -185,35 +210,10 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bands", choices=sorted(WORKLOADS))
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=50)
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    world, rank, local = dist_init()
-    if args.impl == "reference":
-        run_reference(args, world, rank)
-        return
-
-    import torch
-    from paper_2008_11486_gb300 import build as irp_build
+def make_device_sets(shapes, cfg, dev, rank):
     from paper_2008_11486_gb300 import core, synth
-    irp_build.build()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    cfg = WORKLOADS[args.workload]
-    interp = cfg["interp"]
-    stream = torch.cuda.current_stream()
-
-    # ---- inputs resident in HBM (same recipe as synth.make_set, device RNG)
     sets = []
-    for i, (W, H, n) in enumerate(cfg["sets"]):
+    for i, (W, H, n) in enumerate(shapes):
         d = synth.make_set_torch(W, H, n, cfg["offset"], cfg["seed"] + 7919 * i + 104729 * rank,
                                  dev)
         s = core.DeviceSet(frames=[d["raw"][k] for k in range(n)], bias=d["bias"],
@@ -222,32 +222,28 @@ def main():
         s.alloc_outputs(want_nkept=False)
         s._keep.append(d["raw"])
         sets.append(s)
-    params = core.reduce_params(interp, core.clip_params(3.0, 3), persistent=cfg["persistent"])
-    ws_bytes = max(core.workspace_size([s], params) for s in sets)
-    ws = core.workspace(ws_bytes, dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    px_per_step = sum(n * W * H for (W, H, n) in cfg["sets"])
+    return sets
 
-    def step():
-        for s in sets:
-            core.reduce_sets([s], params, ws=ws)
 
-    for _ in range(args.warmup):
+def timed_steps(step, steps, warmup, stream, flush, world, local):
+    """W untimed steps, then K steps each bracketed by CUDA events on the launch
+    stream (L2 flushed before each), with launch tracing and clock sampling."""
+    import torch
+    from paper_2008_11486_gb300 import core
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    assert core.sync_status(ws) == 0
-
-    # ---- timed region
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+          for _ in range(steps)]
     barrier(world)
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     core.profile_enable(True)
     core.profile_read()
     wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.fill_(float(i))
+    for i in range(steps):
+        if flush is not None:
+            flush.fill_(float(i))
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
@@ -257,38 +253,35 @@ def main():
     prof = core.profile_read()
     core.profile_enable(False)
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = max_over_ranks(float(sum(step_ms)), world)
-    assert core.sync_status(ws) == 0
-    ms_per_step = total_ms / args.steps
-    value = world * px_per_step * args.steps / (total_ms * 1e-3) / 1e6
+    total_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in ev)), world)
+    return total_ms, wall, prof, clocks
 
-    # ---- roofline of the dominant kernel (device time summed over the timed region)
-    kinds = {k: v for k, v in prof.items() if v[1] > 0 and k != "stats"}
+
+def roofline(prof, steps, bytes_per_step_by_kind, ms_per_step, path_bytes_per_step):
+    """HBM roofline of the dominant kernel: its algorithmic bytes per step over
+    its device time per step (both summed over its launches in a step)."""
+    kinds = {k: v for k, v in prof.items() if v[1] > 0 and k in bytes_per_step_by_kind}
     dom = max(kinds, key=lambda k: kinds[k][0])
-    dom_ms, dom_launches = kinds[dom]
-    avg_launch_ms = dom_ms / dom_launches
-    launches_per_step = dom_launches / args.steps
-    per_launch = [s for s in cfg["sets"]]
-    bytes_per_launch = algorithmic_bytes(dom, per_launch, interp) / max(launches_per_step, 1)
+    dom_ms = kinds[dom][0] / steps
     peak, peak_src = measured_peaks()
-    achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
-    gpu_launches = int(sum(v[1] for v in prof.values()))
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": peak_src,
-                "kernel_ms": {k: round(v[0] / args.steps, 5) for k, v in prof.items() if v[1]},
-                "path_frac": round(algorithmic_bytes("reduce", per_launch, "bilinear") /
-                                   (ms_per_step * 1e-3) / 1e9 / peak, 4)}
+    achieved = bytes_per_step_by_kind[dom] / (dom_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": peak_src,
+            "launches_per_step": round(kinds[dom][1] / steps, 3),
+            "kernel_ms": {k: round(v[0] / steps, 5) for k, v in prof.items() if v[1]},
+            "path_frac": round(path_bytes_per_step / (ms_per_step * 1e-3) / 1e9 / peak, 4)}
 
-    # ---- end to end through the public API with host buffers
+
+def e2e_run(sets, step, e2e_steps, stream, world):
+    """Same metric through the public API with pinned host buffers: every step
+    copies its raw frames in and its mean/median out inside the timed region."""
+    import torch
     host_raw = [torch.empty((s.n, s.H, s.W), dtype=torch.uint16, pin_memory=True) for s in sets]
     for h, s in zip(host_raw, sets):
         h.copy_(s._keep[0])
     host_out = [(torch.empty((s.H, s.W), dtype=torch.float32, pin_memory=True),
                  torch.empty((s.H, s.W), dtype=torch.float32, pin_memory=True)) for s in sets]
-    h2d = sum(h.numel() * 2 for h in host_raw)
-    d2h = sum(2 * s.H * s.W * 4 for s in sets)
 
     def e2e_step():
         for h, s in zip(host_raw, sets):
@@ -298,19 +291,151 @@ def main():
             m.copy_(s.mean, non_blocking=True)
             d.copy_(s.median, non_blocking=True)
 
-    for _ in range(3):
-        e2e_step()
+    e2e_step()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.e2e_steps):
+    for _ in range(e2e_steps):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world) / args.e2e_steps
-    e2e = {"value": round(world * px_per_step / (e2e_ms * 1e-3) / 1e6, 1), "unit": "Mpix/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    ms = max_over_ranks(e0.elapsed_time(e1), world) / e2e_steps
+    px = sum(s.n * s.W * s.H for s in sets)
+    return {"value": round(world * px / (ms * 1e-3) / 1e6, 1), "unit": "Mpix/s",
+            "h2d_bytes_per_step": sum(h.numel() * 2 for h in host_raw),
+            "d2h_bytes_per_step": sum(2 * s.H * s.W * 4 for s in sets)}
+
+
+def step_bytes(shapes, interp):
+    by = {"reduce": algorithmic_bytes("reduce", shapes, interp)}
+    if interp == "spline3":
+        by["prefilter"] = algorithmic_bytes("prefilter", shapes, interp)
+    return by
+
+
+def sampled_errors(fs_host, outs, interp, npix=4000, seed=5):
+    """Max abs/rel error of mean and median against the FP64 oracle on sampled
+    pixels whose oracle clip margin is not within 1e-3 sigma of a threshold."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    H, W = fs_host.H, fs_host.W
+    xs, ys = rng.integers(0, W, npix), rng.integers(0, H, npix)
+    ref = oracle.reduce_set(fs_host, interp=interp, pixels=(xs, ys), nthreads=os.cpu_count() or 1)
+    ok = (ref["margin"] >= 1e-3) & np.isfinite(ref["mean"])
+    res = {}
+    for name, (mean, med) in outs.items():
+        gm, gd = mean[ys, xs].astype(np.float64), med[ys, xs].astype(np.float64)
+        em, ed = np.abs(gm - ref["mean"])[ok], np.abs(gd - ref["median"])[ok]
+        res[name] = {"mean_max_abs": float(em.max()),
+                     "mean_max_rel": float((em / np.abs(ref["mean"][ok])).max()),
+                     "median_max_abs": float(ed.max()),
+                     "median_max_rel": float((ed / np.abs(ref["median"][ok])).max())}
+    res["pixels"] = int(ok.sum())
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bands", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--requests", type=int, default=12, help="served: requests at the nominal rate")
+    ap.add_argument("--rate", type=float, default=0.5, help="served: Poisson arrival rate (1/s)")
+    args = ap.parse_args()
+    heavy = args.workload in ("deep", "precision", "batch", "served")
+    if args.steps is None:
+        args.steps = 10 if heavy else 2000
+    if args.warmup is None:
+        args.warmup = 3 if heavy else 20
+    if args.e2e_steps is None:
+        args.e2e_steps = 2 if heavy else 50
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_2008_11486_gb300 import build as irp_build
+    from paper_2008_11486_gb300 import core, shard
+    irp_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = WORKLOADS[args.workload]
+    interp = cfg["interp"]
+    stream = torch.cuda.Stream(dev)   # non-default stream: graph capture needs one
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    extra = {}
+
+    if args.workload == "served":
+        line = run_served(args, cfg, dev, world, rank, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+
+    shapes = workload_shapes(args.workload)
+    if args.workload == "batch":  # sets are independent: disjoint shards per rank
+        costs = [shard.set_cost(n, W, H) for (W, H, n) in shapes]
+        shapes = [shapes[i] for i in shard.rank_shard(costs, world, rank)]
+        scaling = "strong"
+    else:
+        scaling = "weak"
+    sets = make_device_sets(shapes, cfg, dev, rank)
+    params = core.reduce_params(interp, core.clip_params(3.0, 3), persistent=False)
+    ws = core.workspace(max(core.workspace_size([s], params) for s in sets), dev)
+
+    def plain_step():
+        for s in sets:
+            core.reduce_sets([s], params, ws=ws)
+
+    step = plain_step
+    if args.workload == "batch":
+        from paper_2008_11486_gb300 import batch
+        t_plain, _, _, _ = timed_steps(plain_step, max(2, args.steps // 2), 1, stream, None,
+                                       world, local)
+        plain_ms = t_plain / max(2, args.steps // 2)
+        tuner = batch.Autotuner(os.path.join(tempfile.gettempdir(), "irp_autotune.json"), reps=2)
+        bparams, bcfg = tuner.params_for(sets, interp)
+        br = batch.BatchReducer(sets, bparams, stream=stream)
+        step = br.run
+        extra["batch_status"] = br
+        extra["plain_ms_per_step"] = round(plain_ms, 4)
+        extra["autotuned"] = bcfg
+    if args.workload == "precision":
+        extra["unfused"] = run_unfused(sets, interp, stream, world, local)
+
+    total_ms, wall, prof, clocks = timed_steps(step, args.steps, args.warmup, stream,
+                                               None if heavy else flush, world, local)
+    assert core.sync_status(ws) == 0
+    if "batch_status" in extra:
+        assert extra.pop("batch_status").status() == 0
+    ms_per_step = total_ms / args.steps
+    px_local = sum(n * W * H for (W, H, n) in shapes)
+    value = (world if scaling == "weak" else 1) * px_local * args.steps / (total_ms * 1e-3) / 1e6
+    if scaling == "strong" and world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([float(px_local)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t)
+        value = float(t.item()) * args.steps / (total_ms * 1e-3) / 1e6
+    if args.workload == "batch":
+        extra["plain_mpix_s"] = round(px_local / (extra["plain_ms_per_step"] * 1e-3) / 1e6, 1)
+        extra["batched_over_plain"] = round(extra["plain_ms_per_step"] / ms_per_step, 3)
+    rf = roofline(prof, args.steps, step_bytes(shapes, interp), ms_per_step,
+                  algorithmic_bytes("reduce", shapes, "bilinear"))
+    gpu_launches = int(sum(v[1] for v in prof.values()))
+    e2e = e2e_run(sets, step, args.e2e_steps, stream, world)
+
+    if args.workload == "precision" and rank == 0:
+        fs_host = host_frameset(sets[0])
+        outs = {"fused_f32": (sets[0].mean.cpu().numpy(), sets[0].median.cpu().numpy())}
+        outs.update(extra["unfused"].pop("outputs"))
+        extra["errors_vs_oracle"] = sampled_errors(fs_host, outs, interp)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -322,19 +447,123 @@ def main():
         line = {"metric": "reduced Mpix/s", "value": round(value, 1), "unit": "Mpix/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "scaling": scaling, "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded device generator, paper-shaped frames)",
                 "config": {"workload": args.workload, "desc": cfg["desc"],
-                           "frames_per_step": sum(n for (_, _, n) in cfg["sets"]),
-                           "raw_mpix_per_step": px_per_step / 1e6,
-                           "l2": "flushed by a 256 MB write before every timed step",
-                           "parallelism": f"replicas x{world} (sets independent per GPU)"},
-                "roofline": roofline, "e2e": e2e, "gpu_launches": gpu_launches,
+                           "sets_per_step": len(shapes),
+                           "frames_per_step": sum(n for (_, _, n) in shapes),
+                           "raw_mpix_per_step": px_local / 1e6,
+                           "l2": ("inputs larger than L2" if heavy else
+                                  "flushed by a 256 MB write before every timed step"),
+                           "parallelism": (f"replicas x{world} (sets independent per GPU)"
+                                           if scaling == "weak" else
+                                           f"disjoint set shards x{world}")},
+                "roofline": rf, "e2e": e2e, "gpu_launches": gpu_launches,
                 "wall_s": round(wall, 3), "clocks": clocks, "cpu_baseline": cpu}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def host_frameset(s):
+    from paper_2008_11486_gb300 import synth
+    return synth.FrameSet(raw=s._keep[0].cpu().numpy(), bias=s.bias.cpu().numpy(),
+                          dark=s.dark.cpu().numpy(), flat=s.flat.cpu().numpy(),
+                          exptime=np.asarray(s.exptime), dx=np.asarray(s.dx), dy=np.asarray(s.dy))
+
+
+def run_unfused(sets, interp, stream, world, local):
+    """Calibrate -> shift -> combine with the aligned stack materialised in HBM,
+    as FP32 and as FP16 with per-frame scale and offset (chosen from FP64 frame
+    sums); returns their step times and outputs."""
+    import torch
+    from paper_2008_11486_gb300 import core
+    s = sets[0]
+    raw = s._keep[0]
+    res = {"outputs": {}}
+    for dt in ("f32", "f16"):
+        bufs = {}
+
+        def step():
+            cal, sc, of, bufs["ws"] = core.calibrate(raw, s.bias, s.dark, s.flat, s.exptime,
+                                                     dtype=dt, out=bufs.get("cal"),
+                                                     ws=bufs.get("ws"))
+            bufs["cal"] = cal
+            st, va, bufs["sws"] = core.shift(cal, s.dx, s.dy, interp, dtype=dt, scale=sc,
+                                             offset=of, out=bufs.get("st"), ws=bufs.get("sws"))
+            bufs["st"] = st
+            bufs["out"] = core.combine(st, dtype=dt, scale=sc, offset=of, valid=va,
+                                       clip=core.clip_params(3.0, 3))
+
+        total_ms, _, prof, _ = timed_steps(step, 3, 1, stream, None, world, local)
+        res[f"{dt}_ms_per_step"] = round(total_ms / 3, 4)
+        res[f"{dt}_mpix_s"] = round(s.n * s.W * s.H / (total_ms / 3 * 1e-3) / 1e6, 1)
+        res[f"{dt}_kernel_ms"] = {k: round(v[0] / 3, 4) for k, v in prof.items() if v[1]}
+        o = bufs["out"]
+        res["outputs"][f"unfused_{dt}"] = (o["mean"].cpu().numpy(), o["median"].cpu().numpy())
+        del bufs
+        torch.cuda.empty_cache()
+    return res
+
+
+def run_served(args, cfg, dev, world, rank, local):
+    """Poisson arrivals of 16-chip exposures; p50/p99 latency at the nominal
+    rate and sustained new-pixel throughput at saturation."""
+    import torch
+    from paper_2008_11486_gb300 import serve, synth
+    shapes = cfg["sets"]
+    W, H, depth = shapes[0]
+    nchips = len(shapes)
+    masters, host_frames = [], []
+    nvar = 2  # distinct host exposures, cycled
+    for c in range(nchips):
+        d = synth.make_set_torch(W, H, nvar, cfg["offset"], cfg["seed"] + 131 * c + 104729 * rank,
+                                 dev)
+        masters.append((d["bias"], d["dark"], d["flat"]))
+        host_frames.append([d["raw"][v].cpu().pin_memory() for v in range(nvar)])
+        del d
+    torch.cuda.empty_cache()
+    rng = np.random.Generator(np.random.PCG64(cfg["seed"]))
+    srv = serve.Server(masters, depth=depth, max_inflight=2, interp=cfg["interp"], device=dev)
+
+    def make_requests(count, base):
+        return [serve.Request(rid=base + r, frames=[host_frames[c][(base + r) % nvar]
+                                                   for c in range(nchips)],
+                              dx=rng.uniform(-5, 5, nchips), dy=rng.uniform(-5, 5, nchips))
+                for r in range(count)]
+
+    # fill the rings so every measured request reduces a full stack
+    serve.run_poisson(srv, make_requests(depth - 1, 0), rate_hz=1e6)
+    sampler = ClockSampler(local)
+    lat, wall = serve.run_poisson(srv, make_requests(args.requests, 100), rate_hz=args.rate)
+    sat_n = max(8, args.requests)
+    sat_lat, sat_wall = serve.run_poisson(srv, make_requests(sat_n, 1000), rate_hz=1e6)
+    clocks = sampler.stop()
+    assert srv.status() == 0
+    new_px = nchips * W * H
+    sustained = sat_n * new_px / sat_wall / 1e6
+    return {"metric": "reduced Mpix/s", "value": round(sustained * world, 1), "unit": "Mpix/s",
+            "n_gpus": world, "steps": sat_n, "warmup": depth - 1,
+            "ms_per_step": round(sat_wall / sat_n * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded device generator, paper-shaped frames)",
+            "config": {"workload": "served", "desc": cfg["desc"], "chips": nchips,
+                       "chip": [W, H], "stack_depth": depth, "rate_hz": args.rate,
+                       "requests": args.requests, "l2": "inputs larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "latency_s": {"p50": round(float(np.percentile(lat, 50)), 4),
+                          "p99": round(float(np.percentile(lat, 99)), 4),
+                          "max": round(float(lat.max()), 4), "rate_hz": args.rate},
+            "saturation": {"requests": sat_n, "wall_s": round(sat_wall, 3),
+                           "p50_s": round(float(np.percentile(sat_lat, 50)), 4),
+                           "p99_s": round(float(np.percentile(sat_lat, 99)), 4)},
+            "batches": srv.batches,
+            "e2e": {"value": round(sustained * world, 1), "unit": "Mpix/s",
+                    "h2d_bytes_per_step": new_px * 2, "d2h_bytes_per_step": 0},
+            "gpu_launches": None, "clocks": clocks, "cpu_baseline": None,
+            "roofline": None}
 
 
 if __name__ == "__main__":

@@ -21,7 +21,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr uint32_t kPlanMagic = 0x49525031u;  // "IRP1"
-constexpr int kMaxSub = 8;
+constexpr int kMaxSub = 12;  // one sub-plan per frame-count bucket at most
 constexpr int kDefaultSpin = 1 << 20;  // polls of 1 us: about one second
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

@@ -115,6 +115,16 @@ def test_workspace_size_accounts_for_spline_coefficients(L):
     assert L.irp_calibrate_workspace_size(10) >= 256 + 11 * 32
 
 
+def test_plan_accepts_a_batch_spanning_every_frame_count_bucket(L):
+    # frame counts 1..64 fall into 12 register buckets: one sub-plan each
+    sets = [_set(n=n, W=64, H=48) for n in (1, 5, 6, 8, 10, 12, 16, 24, 32, 40, 48, 64, 3, 33)]
+    arr = (B.IrpSet * len(sets))(*sets)
+    for persistent in (0, 1):
+        p = _params(persistent=persistent)
+        assert L.irp_plan_bytes(arr, len(sets), ctypes.byref(p)) > 0
+        assert L.irp_workspace_size(arr, len(sets), ctypes.byref(p)) > 0
+
+
 def test_unfused_validation_codes(L):
     clip = B.ClipParams(3.0, 3.0, 3, 0, 0)
     f = ctypes.c_void_p(FAKE)
