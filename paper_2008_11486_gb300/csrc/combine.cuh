@@ -76,6 +76,124 @@ struct CombineOut {
   float lo_val, hi_val;  // survivors are the valid samples within [lo_val, hi_val]
 };
 
+// ---------------------------------------------------------------------------
+// Clip with a compile-time count M of valid samples (the interior of a set
+// whose frame count is M).  The deviations from the lower median are summed
+// outward from the median, the lower half downward and the upper half
+// upward, so the extreme samples are added last; the running sums are kept
+// after each of the K outermost samples of either side.  A pass then needs no
+// loop over the samples: the survivors [nlo, M - nhi) have the sums
+// SL[nlo] + SU[nhi], and the rejected counts come from the K + 1 outermost
+// samples of each side.  The outliers never enter the sums of the survivors,
+// so there is no cancellation to compensate.  Returns false (the caller runs
+// the general loop) when a side rejects more than K samples.
+// ---------------------------------------------------------------------------
+constexpr int kClipK = 3;
+
+__host__ __device__ constexpr int clip_min(int a, int b) { return a < b ? a : b; }
+
+template <int N, int M>
+__device__ __forceinline__ bool clip_fixed_count(const float (&s)[N], const ClipArgs& c,
+                                                 CombineOut& o) {
+  static_assert(M >= 3 && M <= N, "fixed-count clip needs 3..N samples");
+  constexpr int h = (M + 1) / 2;                    // lower half [0, h), lower median at h - 1
+  constexpr int KL = clip_min(kClipK, h - 1);       // partials cover nlo <= KL
+  constexpr int KU = clip_min(kClipK, M - h - 1);   // and nhi <= KU
+  const float a = s[(M - 1) / 2], b = s[M / 2];
+  const float r = a;
+  float SL[KL + 1], QL[KL + 1], SU[KU + 1], QU[KU + 1];
+  {
+    float S = 0.0f, Q = 0.0f;
+#pragma unroll
+    for (int j = h - 1; j >= 0; --j) {
+      const float d = __fsub_rn(s[j], r);
+      S = __fadd_rn(S, d);
+      Q = __fmaf_rn(d, d, Q);
+      if (j <= KL) {
+        SL[j] = S;
+        QL[j] = Q;
+      }
+    }
+  }
+  {
+    float S = 0.0f, Q = 0.0f;
+#pragma unroll
+    for (int j = h; j < M; ++j) {
+      const float d = __fsub_rn(s[j], r);
+      S = __fadd_rn(S, d);
+      Q = __fmaf_rn(d, d, Q);
+      if (j >= M - 1 - KU) {
+        SU[M - 1 - j] = S;
+        QU[M - 1 - j] = Q;
+      }
+    }
+  }
+  int nlo = 0, nhi = 0;
+#pragma unroll 1
+  for (int it = 0; it < c.max_iter; ++it) {
+    const int mm = M - nlo - nhi;
+    if (mm - c.ddof <= 0) break;
+    const float S = __fadd_rn(select_at(SL, nlo), select_at(SU, nhi));
+    const float Q = __fadd_rn(select_at(QL, nlo), select_at(QU, nhi));
+    const float cd = __fdiv_rn(S, (float)mm);  // centre - r
+    // sum (x - centre)^2 = Q - 2 cd S + mm cd^2
+    float ss = __fmaf_rn(cd, __fmaf_rn((float)mm, cd, -2.0f * S), Q);
+    ss = fmaxf(ss, 0.0f);
+    const float sigma = sqrtf(__fdiv_rn(ss, (float)(mm - c.ddof)));
+    if (!(sigma > 0.0f)) break;
+    const float tlo = c.kappa_lo * sigma, thi = c.kappa_hi * sigma;
+    // the rejected samples below (above) the centre are a prefix (suffix) of
+    // the sorted run, so counting over all of the outermost samples and
+    // keeping the larger count gives the cumulative rejection
+    int clo = 0, chi = 0;
+#pragma unroll
+    for (int j = 0; j <= KL; ++j) clo += (-__fsub_rn(__fsub_rn(s[j], r), cd) > tlo) ? 1 : 0;
+#pragma unroll
+    for (int k = 0; k <= KU; ++k)
+      chi += (__fsub_rn(__fsub_rn(s[M - 1 - k], r), cd) > thi) ? 1 : 0;
+    if (clo > KL || chi > KU) return false;
+    clo = max(clo, nlo);
+    chi = max(chi, nhi);
+    if (clo == nlo && chi == nhi) break;
+    nlo = clo;
+    nhi = chi;
+  }
+  const int mm = M - nlo - nhi;
+  const float S = __fadd_rn(select_at(SL, nlo), select_at(SU, nhi));
+  o.median = __fmul_rn(__fadd_rn(a, b), 0.5f);
+  o.kept = mm;
+  o.mean = __fadd_rn(r, __fdiv_rn(S, (float)mm));
+  float lv = s[0], hv = s[M - 1];
+#pragma unroll
+  for (int j = 1; j <= KL; ++j) lv = (nlo == j) ? s[j] : lv;
+#pragma unroll
+  for (int k = 1; k <= KU; ++k) hv = (nhi == k) ? s[M - 1 - k] : hv;
+  o.lo_val = lv;
+  o.hi_val = hv;
+  return true;
+}
+
+// Largest gap N - m served by a fixed-count instantiation: the frame counts
+// that share register bucket N (up to 8 of them).
+template <int N>
+__host__ __device__ constexpr int clip_max_gap() {
+  constexpr int prev = N > 48 ? 48 : N > 40 ? 40 : N > 32 ? 32 : N > 24 ? 24 : N > 16 ? 16
+                     : N > 12 ? 12 : N > 10 ? 10 : N > 8 ? 8 : N > 6 ? 6 : N > 5 ? 5
+                     : N > 4 ? 4 : 0;
+  return clip_min(7, N - prev - 1);
+}
+
+template <int N, int G>
+__device__ __forceinline__ bool clip_fixed_dispatch(const float (&s)[N], int m, const ClipArgs& c,
+                                                    CombineOut& o) {
+  if constexpr (G > clip_max_gap<N>() || N - G < 3) {
+    return false;
+  } else {
+    if (m == N - G) return clip_fixed_count<N, N - G>(s, c, o);
+    return clip_fixed_dispatch<N, G + 1>(s, m, c, o);
+  }
+}
+
 // s: sorted samples, m valid.  Returns the sigma-clipped mean, the median of
 // all valid samples, the survivor count and the survivor value range.
 template <int N>
@@ -90,37 +208,7 @@ __device__ __forceinline__ CombineOut combine_sorted(const float (&s)[N], int m,
     o.hi_val = 0.0f;
     return o;
   }
-  if (m == N && c.center == 0 && c.max_iter > 0 && N - c.ddof > 0) {
-    // All N samples valid (the common case with an exact register bucket): the
-    // median and run ends have constant indices, and the first pass needs no
-    // range test.  It returns unless the first pass rejects something.
-    const float a = s[(N - 1) >> 1], b = s[N >> 1];
-    o.median = __fmul_rn(__fadd_rn(a, b), 0.5f);
-    const float r = a;
-    float S = 0.0f, C = 0.0f, Q = 0.0f;
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      const float d = __fsub_rn(s[j], r);
-      const float y = __fsub_rn(d, C);
-      const float t = __fadd_rn(S, y);
-      C = __fsub_rn(__fsub_rn(t, S), y);
-      S = t;
-      Q = __fmaf_rn(d, d, Q);
-    }
-    const float cd = __fdiv_rn(S, (float)N);
-    float ss = __fmaf_rn(cd, __fmaf_rn((float)N, cd, -2.0f * S), Q);
-    ss = fmaxf(ss, 0.0f);
-    const float sigma = sqrtf(__fdiv_rn(ss, (float)(N - c.ddof)));
-    const float elo = __fsub_rn(__fsub_rn(s[0], r), cd);
-    const float ehi = __fsub_rn(__fsub_rn(s[N - 1], r), cd);
-    if (!(sigma > 0.0f) || (!(-elo > c.kappa_lo * sigma) && !(ehi > c.kappa_hi * sigma))) {
-      o.kept = N;
-      o.mean = __fadd_rn(r, __fdiv_rn(S, (float)N));
-      o.lo_val = s[0];
-      o.hi_val = s[N - 1];
-      return o;
-    }
-  }
+  if (c.center == 0 && clip_fixed_dispatch<N, 0>(s, m, c, o)) return o;
   const float a = select_at(s, (m - 1) >> 1);
   const float b = select_at(s, m >> 1);
   o.median = __fmul_rn(__fadd_rn(a, b), 0.5f);
