@@ -173,14 +173,18 @@ __device__ __forceinline__ bool clip_fixed_count(const float (&s)[N], const Clip
   return true;
 }
 
+// The register bucket below N (frame counts 4, 5, 6, 8, 10, 12, 16, 24, 32,
+// 40, 48, 64): every set reduced with bucket N has more frames than this.
+__host__ __device__ constexpr int bucket_below(int N) {
+  return N > 48 ? 48 : N > 40 ? 40 : N > 32 ? 32 : N > 24 ? 24 : N > 16 ? 16 : N > 12 ? 12
+       : N > 10 ? 10 : N > 8 ? 8 : N > 6 ? 6 : N > 5 ? 5 : N > 4 ? 4 : 0;
+}
+
 // Largest gap N - m served by a fixed-count instantiation: the frame counts
 // that share register bucket N (up to 8 of them).
 template <int N>
 __host__ __device__ constexpr int clip_max_gap() {
-  constexpr int prev = N > 48 ? 48 : N > 40 ? 40 : N > 32 ? 32 : N > 24 ? 24 : N > 16 ? 16
-                     : N > 12 ? 12 : N > 10 ? 10 : N > 8 ? 8 : N > 6 ? 6 : N > 5 ? 5
-                     : N > 4 ? 4 : 0;
-  return clip_min(7, N - prev - 1);
+  return clip_min(7, N - bucket_below(N) - 1);
 }
 
 template <int N, int G>

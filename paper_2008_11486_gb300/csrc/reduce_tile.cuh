@@ -18,6 +18,8 @@
 // After the last frame each lane combines its PY pixels (combine.cuh).
 #pragma once
 
+#include <limits.h>
+
 #include "combine.cuh"
 #include "common.cuh"
 
@@ -115,19 +117,21 @@ __host__ __device__ inline size_t fused_smem_bytes(int src, int stencil, int py,
 
 // ------------------------------------------------------------------ staging
 // What the frame loop needs of one frame for the current tile, built once per
-// tile in shared memory (128 bytes).
+// tile in shared memory (128 bytes).  The fields the loop reads every frame
+// are grouped into 16-byte vectors, so each group is one broadcast load.
 struct FrameRec {
-  const uint8_t* base;   // staging source: element (ybase, xa) of the frame
-  const uint8_t* fbase;  // a valid address inside the frame (zero-byte copies)
-  int ybase, xa;         // first staged row / aligned first staged column
-  int off;               // tile's first source column inside the staged row
-  int mofs;              // union-window offset of the tile's first source pixel
-  int ox, oy;            // tap origin (masters read from global memory)
-  float fx, fy, t;
-  int vx0, vx1, vy0, vy1;
-  int flags;
-  float wx[4], wy[4];
-  int pad[6];
+  // compute: tile's first source column inside the staged row, union-window
+  // offset of the tile's first source pixel, and the column validity range
+  // as (first, width) for one unsigned compare (an empty range has first
+  // INT_MIN, which no column reaches)
+  int off, mofs, vx0, vxw;
+  float fx, fy, t, pad0;
+  int vy0, vyw, ox, oy;       // row validity; tap origin for global masters
+  float wx[4], wy[4];         // spline weights
+  const uint8_t* base;        // staging source: element (ybase, xa) of the frame
+  const uint8_t* fbase;       // a valid address inside the frame (zero-byte copies)
+  int ybase, xa, flags, pad1; // first staged row / aligned first staged column
+  int pad2[4];
 };
 static_assert(sizeof(FrameRec) == 128, "FrameRec layout");
 
@@ -155,16 +159,36 @@ __device__ __forceinline__ FrameRec make_rec(const FrameDesc& F, int tx0, int ty
   R.fx = F.fx;
   R.fy = F.fy;
   R.t = F.t;
-  R.vx0 = F.vx0;
-  R.vx1 = F.vx1;
-  R.vy0 = F.vy0;
-  R.vy1 = F.vy1;
+  R.pad0 = 0.0f;
+  const bool ex = F.vx1 < F.vx0, ey = F.vy1 < F.vy0;
+  R.vx0 = ex ? INT_MIN : F.vx0;
+  R.vxw = ex ? 0 : F.vx1 - F.vx0;
+  R.vy0 = ey ? INT_MIN : F.vy0;
+  R.vyw = ey ? 0 : F.vy1 - F.vy0;
   R.flags = F.flags;
+  R.pad1 = 0;
   for (int i = 0; i < 4; ++i) {
     R.wx[i] = F.wx[i];
     R.wy[i] = F.wy[i];
+    R.pad2[i] = 0;
   }
   return R;
+}
+
+// v in [lo, lo + w] with one unsigned compare (w >= 0; lo = INT_MIN: never)
+__device__ __forceinline__ bool in_range(int v, int lo, int w) {
+  return (unsigned)v - (unsigned)lo <= (unsigned)w;
+}
+
+// One 16-byte cp.async when p is set, zero-filling the bytes past src_bytes.
+__device__ __forceinline__ void cp_async16_if(bool p, void* smem, const void* gmem,
+                                              int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %3, 0;\n"
+      " @q cp.async.cg.shared.global [%0], [%1], 16, %2;\n}\n" ::"r"(s),
+      "l"(gmem), "r"(src_bytes), "r"((int)p)
+      : "memory");
 }
 
 // Copies the warp's window of one frame into one stage.  Each lane owns up
@@ -184,28 +208,27 @@ __device__ __forceinline__ void issue_stage(const FrameRec& R, const LaneChunks<
                                             int lane, int wrow) {
   using SS = StageShape<SRC, STENCIL, PY>;
   constexpr int kIt = (SS::rows * SS::chunks + 31) / 32;
-  if (SRC == SRC_RAW && !(R.flags & 1)) {
+  const int4 st = *(const int4*)&R.ybase;  // ybase, xa, flags
+  if (SRC == SRC_RAW && !(st.z & 1)) {
     uint16_t* dst = (uint16_t*)stage;
     const uint16_t* fb = (const uint16_t*)R.fbase;
     for (int e = lane; e < SS::rows * SS::elems; e += 32) {
       const int r = e / SS::elems, i = e - r * SS::elems;
-      const int y = R.ybase + wrow + r, xx = R.xa + i;
+      const int y = st.x + wrow + r, xx = st.y + i;
       dst[e] = ((unsigned)y < (unsigned)Hlim && (unsigned)xx < (unsigned)Wlim)
                    ? fb[(int64_t)y * pitch + xx] : (uint16_t)0;
     }
     return;
   }
+  const uint8_t* base = R.base;
+  const uint8_t* fbase = R.fbase;
 #pragma unroll
   for (int it = 0; it < kIt; ++it) {
-    if (L.soff[it] < 0) continue;
-    const int y = R.ybase + L.drow[it], xx = R.xa + L.dcol[it];
-    int bytes = 0;
-    const uint8_t* src = R.fbase;
-    if ((unsigned)y < (unsigned)Hlim && (unsigned)xx < (unsigned)Wlim) {
-      bytes = SRC == SRC_RAW ? min(16, 2 * (Wlim - xx)) : 16;
-      src = R.base + L.goff[it];
-    }
-    cp_async16(stage + L.soff[it], src, bytes);
+    const int y = st.x + L.drow[it], xx = st.y + L.dcol[it];
+    const bool in = ((unsigned)y < (unsigned)Hlim) & ((unsigned)xx < (unsigned)Wlim);
+    const int bytes = in ? (SRC == SRC_RAW ? min(16, 2 * (Wlim - xx)) : 16) : 0;
+    const uint8_t* src = in ? base + L.goff[it] : fbase;
+    cp_async16_if(L.soff[it] >= 0, stage + max(L.soff[it], 0), src, bytes);
   }
 }
 
@@ -228,11 +251,108 @@ __device__ __forceinline__ void stage_masters(const SetDesc& S, int tx0, int ty0
   }
 }
 
+// One frame of the warp's strip: calibrate the staged source rows, resample
+// them to the strip's PY output rows, store the samples (+inf when invalid)
+// and count the valid ones per row.
+template <int STENCIL, int SRC, int PY>
+__device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
+                                           const float4* s_mast_w, int mrow, const SetDesc& S,
+                                           float flat_norm, uint32_t* status, int lane, int x,
+                                           int tx0, int wy0, float* sk, int (&mq)[PY],
+                                           float* stack_out, int k, int W, int H,
+                                           int64_t out_pitch, bool stack_lane) {
+  using SS = StageShape<SRC, STENCIL, PY>;
+  const int4 g = *(const int4*)&F.off;      // off, mofs, vx0, vxw
+  const float4 w = *(const float4*)&F.fx;   // fx, fy, t
+  const int4 gy = *(const int4*)&F.vy0;     // vy0, vyw, ox, oy
+  float v[SS::rows];
+  if (SRC == SRC_RAW) {
+    const uint16_t* raw = (const uint16_t*)st + lane + g.x;
+    if (mrow > 0) {
+      const float4* mp = s_mast_w + g.y;
+#pragma unroll
+      for (int r = 0; r < SS::rows; ++r) {
+        const float4 m = mp[r * mrow];
+        v[r] = calibrate_px(raw[r * SS::elems], m.x, m.y, w.z, m.z);
+      }
+    } else {  // offsets too spread for a union window: masters from global memory
+      const int gx = tx0 + gy.z + lane;
+#pragma unroll
+      for (int r = 0; r < SS::rows; ++r) {
+        const int yy = wy0 + gy.w + r;
+        float b = 0.0f, d = 0.0f, rf = 0.0f;
+        if (gx >= 0 && gx < S.W && yy >= 0 && yy < S.H) {
+          const int64_t o = (int64_t)yy * S.master_pitch + gx;
+          b = __ldg(S.bias + o);
+          d = __ldg(S.dark + o);
+          rf = inv_flat(__ldg(S.flat + o), flat_norm, status);
+        }
+        v[r] = calibrate_px(raw[r * SS::elems], b, d, w.z, rf);
+      }
+    }
+  } else {
+    const float* cf = (const float*)st + lane + g.x;
+#pragma unroll
+    for (int r = 0; r < SS::rows; ++r) v[r] = cf[r * SS::elems];
+  }
+  float a[PY];
+  if (STENCIL == ST_NEAREST) {
+#pragma unroll
+    for (int q = 0; q < PY; ++q) a[q] = v[q];
+  } else if (STENCIL == ST_BILINEAR) {
+    float hrow[SS::rows];
+#pragma unroll
+    for (int r = 0; r < SS::rows; ++r) {
+      const float p1 = __shfl_down_sync(0xffffffffu, v[r], 1);
+      hrow[r] = __fmaf_rn(w.x, __fsub_rn(p1, v[r]), v[r]);
+    }
+#pragma unroll
+    for (int q = 0; q < PY; ++q) a[q] = __fmaf_rn(w.y, __fsub_rn(hrow[q + 1], hrow[q]), hrow[q]);
+  } else {
+    const float4 wx = *(const float4*)F.wx;
+    const float4 wy = *(const float4*)F.wy;
+    float hrow[SS::rows];
+#pragma unroll
+    for (int r = 0; r < SS::rows; ++r) {
+      const float p1 = __shfl_down_sync(0xffffffffu, v[r], 1);
+      const float p2 = __shfl_down_sync(0xffffffffu, v[r], 2);
+      const float p3 = __shfl_down_sync(0xffffffffu, v[r], 3);
+      float acc = wx.x * v[r];
+      acc = __fmaf_rn(wx.y, p1, acc);
+      acc = __fmaf_rn(wx.z, p2, acc);
+      hrow[r] = __fmaf_rn(wx.w, p3, acc);
+    }
+#pragma unroll
+    for (int q = 0; q < PY; ++q) {
+      float acc = wy.x * hrow[q];
+      acc = __fmaf_rn(wy.y, hrow[q + 1], acc);
+      acc = __fmaf_rn(wy.z, hrow[q + 2], acc);
+      a[q] = __fmaf_rn(wy.w, hrow[q + 3], acc);
+    }
+  }
+  const float kInf = __int_as_float(0x7f800000);
+  const bool xv = in_range(x, g.z, g.w);
+#pragma unroll
+  for (int q = 0; q < PY; ++q) {
+    const bool ok = xv & in_range(wy0 + q, gy.x, gy.y);
+    sk[q * 32] = ok ? a[q] : kInf;
+    mq[q] += ok ? 1 : 0;
+  }
+  if (stack_out) {
+#pragma unroll
+    for (int q = 0; q < PY; ++q) {
+      const int y = wy0 + q;
+      const bool ok = xv & in_range(y, gy.x, gy.y);
+      if (stack_lane && y < H)
+        stack_out[((int64_t)k * H + y) * out_pitch + x] = ok ? a[q] : __int_as_float(0x7fc00000);
+    }
+  }
+}
+
 template <int NMAX, int STENCIL, int SRC, int PY>
 __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* smem) {
   constexpr int TH = 8 * PY;
   constexpr int TW = StencilShape<STENCIL>::tw;
-  constexpr int T = StencilShape<STENCIL>::taps;
   using SS = StageShape<SRC, STENCIL, PY>;
   const PlanHeader& h = *P.h;
   const int si = find_set(P.sets, h.nsets, item);
@@ -294,106 +414,42 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
                                     lane, warp * PY);
     cp_async_commit();
   }
-  const float kInf = __int_as_float(0x7f800000);
-  const float qnan = __int_as_float(0x7fc00000);
-  for (int k = 0; k < n; ++k) {
-    cp_async_wait<kStages - 2>();
-    __syncwarp();
-    {
-      const int kn = k + kStages - 1;
-      if (kn < n)
-        issue_stage<SRC, STENCIL, PY>(frames[kn], LC, Hlim, Wlim, pitch,
-                                      s_stage + (kn % kStages) * SS::bytes, lane, warp * PY);
-      cp_async_commit();
-    }
-    const FrameRec& F = frames[k];
-    const uint8_t* st = s_stage + (k % kStages) * SS::bytes;
-    float v[SS::rows];
-    if (SRC == SRC_RAW) {
-      const int off = F.off;
-      const uint16_t* raw = (const uint16_t*)st;
-      const float t = F.t;
-      if (mwin_w > 0) {
-        const float4* mp = s_mast + F.mofs + warp * PY * mwin_w + lane;
+  const float4* s_mast_w = s_mast + warp * PY * mwin_w + lane;
+  const bool stack_lane = lane < TW && x < W;
+  int mq[PY];
 #pragma unroll
-        for (int r = 0; r < SS::rows; ++r) {
-          const float4 m = mp[r * mwin_w];
-          v[r] = calibrate_px(raw[r * SS::elems + lane + off], m.x, m.y, t, m.z);
-        }
-      } else {  // offsets too spread for a union window: masters from global memory
-        const int gx = tx0 + F.ox + lane;
+  for (int q = 0; q < PY; ++q) mq[q] = 0;
+  float* sk = s_samples + (size_t)warp * PY * 32 + lane;
+  // frames in groups of kStages, so that every stage slot is a constant
+  for (int k0 = 0; k0 < n; k0 += kStages) {
 #pragma unroll
-        for (int r = 0; r < SS::rows; ++r) {
-          const int gy = wy0 + F.oy + r;
-          float b = 0.0f, d = 0.0f, rf = 0.0f;
-          if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-            const int64_t o = (int64_t)gy * S.master_pitch + gx;
-            b = __ldg(S.bias + o);
-            d = __ldg(S.dark + o);
-            rf = inv_flat(__ldg(S.flat + o), flat_norm, h.status);
-          }
-          v[r] = calibrate_px(raw[r * SS::elems + lane + off], b, d, t, rf);
-        }
+    for (int u = 0; u < kStages; ++u) {
+      const int k = k0 + u;
+      if (k < n) {
+        cp_async_wait<kStages - 2>();
+        __syncwarp();
+        const int kn = k + kStages - 1;
+        if (kn < n)
+          issue_stage<SRC, STENCIL, PY>(frames[kn], LC, Hlim, Wlim, pitch,
+                                        s_stage + ((u + kStages - 1) % kStages) * SS::bytes, lane,
+                                        warp * PY);
+        cp_async_commit();
+        frame_step<STENCIL, SRC, PY>(frames[k], s_stage + u * SS::bytes, s_mast_w, mwin_w, S,
+                                     flat_norm, h.status, lane, x, tx0, wy0,
+                                     sk + (size_t)k * TH * 32, mq, stack_out, k, W, H, out_pitch,
+                                     stack_lane);
       }
-    } else {
-      const int off = F.off;
-      const float* cf = (const float*)st;
-#pragma unroll
-      for (int r = 0; r < SS::rows; ++r) v[r] = cf[r * SS::elems + lane + off];
-    }
-    float a[PY];
-    if (STENCIL == ST_NEAREST) {
-#pragma unroll
-      for (int q = 0; q < PY; ++q) a[q] = v[q];
-    } else if (STENCIL == ST_BILINEAR) {
-      float hrow[SS::rows];
-#pragma unroll
-      for (int r = 0; r < SS::rows; ++r) {
-        const float p1 = __shfl_down_sync(0xffffffffu, v[r], 1);
-        hrow[r] = __fmaf_rn(F.fx, __fsub_rn(p1, v[r]), v[r]);
-      }
-#pragma unroll
-      for (int q = 0; q < PY; ++q) a[q] = __fmaf_rn(F.fy, __fsub_rn(hrow[q + 1], hrow[q]), hrow[q]);
-    } else {
-      const float w0 = F.wx[0], w1 = F.wx[1], w2 = F.wx[2], w3 = F.wx[3];
-      float hrow[SS::rows];
-#pragma unroll
-      for (int r = 0; r < SS::rows; ++r) {
-        const float p1 = __shfl_down_sync(0xffffffffu, v[r], 1);
-        const float p2 = __shfl_down_sync(0xffffffffu, v[r], 2);
-        const float p3 = __shfl_down_sync(0xffffffffu, v[r], 3);
-        float acc = w0 * v[r];
-        acc = __fmaf_rn(w1, p1, acc);
-        acc = __fmaf_rn(w2, p2, acc);
-        hrow[r] = __fmaf_rn(w3, p3, acc);
-      }
-#pragma unroll
-      for (int q = 0; q < PY; ++q) {
-        float acc = F.wy[0] * hrow[q];
-        acc = __fmaf_rn(F.wy[1], hrow[q + 1], acc);
-        acc = __fmaf_rn(F.wy[2], hrow[q + 2], acc);
-        a[q] = __fmaf_rn(F.wy[3], hrow[q + 3], acc);
-      }
-    }
-    const bool xv = (x >= F.vx0) & (x <= F.vx1);
-    float* sk = s_samples + ((size_t)k * TH + warp * PY) * 32 + lane;
-#pragma unroll
-    for (int q = 0; q < PY; ++q) {
-      const int y = wy0 + q;
-      const bool ok = xv & (y >= F.vy0) & (y <= F.vy1);
-      sk[q * 32] = ok ? a[q] : kInf;
-      if (stack_out && lane < TW && x < W && y < H)
-        stack_out[((int64_t)k * H + y) * out_pitch + x] = ok ? a[q] : qnan;
     }
   }
   cp_async_wait<0>();
   __syncwarp();
-  (void)T;
 
   const ClipArgs ca{h.kappa_lo, h.kappa_hi, h.max_iter, h.center, h.ddof};
   float* const mean_out = S.mean_out;
   float* const median_out = S.median_out;
   uint16_t* const nkept_out = S.nkept_out;
+  constexpr int kSure = bucket_below(NMAX);  // every set of this bucket has more frames
+  const float kInf = __int_as_float(0x7f800000);
   if (lane < TW && x < W) {
 #pragma unroll 1
     for (int q = 0; q < PY; ++q) {
@@ -401,13 +457,13 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
       if (y >= H) break;
       const float* sp = s_samples + (size_t)(warp * PY + q) * 32 + lane;
       float s[NMAX];
-      int m = 0;
 #pragma unroll
-      for (int j = 0; j < NMAX; ++j) {
-        s[j] = (j < n) ? sp[(size_t)j * TH * 32] : kInf;
-        m += (s[j] < kInf) ? 1 : 0;
-      }
+      for (int j = 0; j < NMAX; ++j)
+        s[j] = (j < kSure || j < n) ? sp[(size_t)j * TH * 32] : kInf;
       sort_network<NMAX>(s);
+      int m = mq[0];
+#pragma unroll
+      for (int qq = 1; qq < PY; ++qq) m = (q == qq) ? mq[qq] : m;
       const CombineOut o = combine_sorted<NMAX>(s, m, ca);
       const int64_t oi = (int64_t)y * out_pitch + x;
       if (mean_out) mean_out[oi] = o.mean;
