@@ -20,6 +20,8 @@
 
 #include <limits.h>
 
+#include <type_traits>
+
 #include "combine.cuh"
 #include "common.cuh"
 
@@ -66,6 +68,12 @@ __device__ __forceinline__ float calibrate_px(uint16_t raw, float bias, float da
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem),
                "r"(src_bytes)
                : "memory");
 }
@@ -135,9 +143,13 @@ struct FrameRec {
 };
 static_assert(sizeof(FrameRec) == 128, "FrameRec layout");
 
+// flags: bit 0 = raw frame 16-byte aligned with a pitch of 8k elements;
+// bit 1 = the tile's whole staging window (rows x elems from (ybase, xa)) lies
+// inside the frame, so its chunks need no bounds checks.
 template <int SRC>
 __device__ __forceinline__ FrameRec make_rec(const FrameDesc& F, int tx0, int ty0, int64_t pitch,
-                                             int mox, int moy, int mwin_w) {
+                                             int mox, int moy, int mwin_w, int win_rows,
+                                             int win_elems, int Hlim, int Wlim) {
   FrameRec R;
   const int gx0 = tx0 + F.ox, gy0 = ty0 + F.oy;
   if (SRC == SRC_RAW) {
@@ -165,7 +177,10 @@ __device__ __forceinline__ FrameRec make_rec(const FrameDesc& F, int tx0, int ty
   R.vxw = ex ? 0 : F.vx1 - F.vx0;
   R.vy0 = ey ? INT_MIN : F.vy0;
   R.vyw = ey ? 0 : F.vy1 - F.vy0;
-  R.flags = F.flags;
+  const bool aligned_src = SRC != SRC_RAW || (F.flags & 1);
+  const bool interior = aligned_src && R.ybase >= 0 && R.ybase + win_rows <= Hlim && R.xa >= 0 &&
+                        R.xa + win_elems <= Wlim;
+  R.flags = (F.flags & 1) | (interior ? 2 : 0);
   R.pad1 = 0;
   for (int i = 0; i < 4; ++i) {
     R.wx[i] = F.wx[i];
@@ -198,7 +213,8 @@ __device__ __forceinline__ void cp_async16_if(bool p, void* smem, const void* gm
 // element by element instead.
 template <int SRC, int kIt>
 struct LaneChunks {
-  int drow[kIt], dcol[kIt], soff[kIt];
+  int drow[kIt], dcol[kIt], soff[kIt];  // soff: stage byte offset (0 when the lane has none)
+  bool has[kIt];                        // the lane owns chunk it
   int64_t goff[kIt];
 };
 
@@ -221,6 +237,11 @@ __device__ __forceinline__ void issue_stage(const FrameRec& R, const LaneChunks<
     return;
   }
   const uint8_t* base = R.base;
+  if (st.z & 2) {  // window inside the frame: no bounds checks
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) cp_async16_if(L.has[it], stage + L.soff[it], base + L.goff[it], 16);
+    return;
+  }
   const uint8_t* fbase = R.fbase;
 #pragma unroll
   for (int it = 0; it < kIt; ++it) {
@@ -228,33 +249,57 @@ __device__ __forceinline__ void issue_stage(const FrameRec& R, const LaneChunks<
     const bool in = ((unsigned)y < (unsigned)Hlim) & ((unsigned)xx < (unsigned)Wlim);
     const int bytes = in ? (SRC == SRC_RAW ? min(16, 2 * (Wlim - xx)) : 16) : 0;
     const uint8_t* src = in ? base + L.goff[it] : fbase;
-    cp_async16_if(L.soff[it] >= 0, stage + max(L.soff[it], 0), src, bytes);
+    cp_async16_if(L.has[it], stage + L.soff[it], src, bytes);
   }
 }
 
-// Loads the union window of the masters for this tile as {bias, dark, rf}.
-__device__ __forceinline__ void stage_masters(const SetDesc& S, int tx0, int ty0, float flat_norm,
-                                              float4* s_mast, uint32_t* status) {
+// The union window of the masters for this tile as {bias, dark, rf}: the
+// three masters are copied asynchronously into the float4 slots (zero outside
+// the frame), then finish_masters turns the flat into flat_norm/flat.
+__device__ __forceinline__ void issue_masters(const SetDesc& S, int tx0, int ty0,
+                                              float4* s_mast) {
   const int mw = S.mwin_w, mh = S.mwin_h;
   const int gx0 = tx0 + S.mox, gy0 = ty0 + S.moy;
-  for (int e = threadIdx.x; e < mw * mh; e += kThreads) {
-    const int r = e / mw, c = e - r * mw;
-    const int gx = gx0 + c, gy = gy0 + r;
-    float4 m = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (gx >= 0 && gx < S.W && gy >= 0 && gy < S.H) {
-      const int64_t o = (int64_t)gy * S.master_pitch + gx;
-      m.x = __ldg(S.bias + o);
-      m.y = __ldg(S.dark + o);
-      m.z = inv_flat(__ldg(S.flat + o), flat_norm, status);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < mh; r += kThreads / 32) {
+    const int gy = gy0 + r;
+    const bool yin = gy >= 0 && gy < S.H;
+    for (int c = lane; c < mw; c += 32) {
+      const int gx = gx0 + c;
+      const bool in = yin && gx >= 0 && gx < S.W;
+      const int64_t o = in ? (int64_t)gy * S.master_pitch + gx : 0;
+      const int nb = in ? 4 : 0;
+      float* d = (float*)(s_mast + r * mw + c);
+      cp_async4(d + 0, S.bias + o, nb);
+      cp_async4(d + 1, S.dark + o, nb);
+      cp_async4(d + 2, S.flat + o, nb);
     }
-    s_mast[e] = m;
+  }
+}
+
+__device__ __forceinline__ void finish_masters(const SetDesc& S, int tx0, int ty0,
+                                               float flat_norm, float4* s_mast,
+                                               uint32_t* status) {
+  const int mw = S.mwin_w, mh = S.mwin_h;
+  const int gx0 = tx0 + S.mox, gy0 = ty0 + S.moy;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < mh; r += kThreads / 32) {
+    const int gy = gy0 + r;
+    const bool yin = gy >= 0 && gy < S.H;
+    for (int c = lane; c < mw; c += 32) {
+      const int gx = gx0 + c;
+      float* d = (float*)(s_mast + r * mw + c);
+      if (yin && gx >= 0 && gx < S.W) d[2] = inv_flat(d[2], flat_norm, status);
+    }
   }
 }
 
 // One frame of the warp's strip: calibrate the staged source rows, resample
 // them to the strip's PY output rows, store the samples (+inf when invalid)
 // and count the valid ones per row.
-template <int STENCIL, int SRC, int PY>
+// GEN = false: masters from the union window and no stack output (the
+// common case, without those branches); GEN = true: both decided per call.
+template <int STENCIL, int SRC, int PY, bool GEN>
 __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
                                            const float4* s_mast_w, int mrow, const SetDesc& S,
                                            float flat_norm, uint32_t* status, int lane, int x,
@@ -268,7 +313,7 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
   float v[SS::rows];
   if (SRC == SRC_RAW) {
     const uint16_t* raw = (const uint16_t*)st + lane + g.x;
-    if (mrow > 0) {
+    if (!GEN || mrow > 0) {
       const float4* mp = s_mast_w + g.y;
 #pragma unroll
       for (int r = 0; r < SS::rows; ++r) {
@@ -338,7 +383,7 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
     sk[q * 32] = ok ? a[q] : kInf;
     mq[q] += ok ? 1 : 0;
   }
-  if (stack_out) {
+  if (GEN && stack_out) {
 #pragma unroll
     for (int q = 0; q < PY; ++q) {
       const int y = wy0 + q;
@@ -385,11 +430,16 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
     __syncthreads();
     if (!s_ok) return;  // status latched; this tile's outputs are left untouched
   }
+  // the masters' window first (one cp.async group), so that its latency
+  // overlaps the frame records and the first frames' staging
+  const bool uwin = SRC == SRC_RAW && mwin_w > 0;
+  if (uwin) issue_masters(S, tx0, ty0, s_mast);
+  cp_async_commit();
   for (int k = threadIdx.x; k < n; k += kThreads)
-    s_rec[k] = make_rec<SRC>(P.frames[S.frame0 + k], tx0, ty0, pitch, S.mox, S.moy, mwin_w);
+    s_rec[k] = make_rec<SRC>(P.frames[S.frame0 + k], tx0, ty0, pitch, S.mox, S.moy, mwin_w,
+                             TH + StencilShape<STENCIL>::taps - 1, SS::elems, Hlim, Wlim);
   float flat_norm = 1.0f;
   if (SRC == SRC_RAW && S.flat_sum) flat_norm = (float)(*S.flat_sum / ((double)S.W * S.H));
-  if (SRC == SRC_RAW && S.mwin_w > 0) stage_masters(S, tx0, ty0, flat_norm, s_mast, h.status);
   // this lane's staging chunks (frame-independent)
   constexpr int kIt = (SS::rows * SS::chunks + 31) / 32;
   LaneChunks<SRC, kIt> LC;
@@ -400,7 +450,8 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
     const int colw = SRC == SRC_RAW ? 8 : 4, esz = SRC == SRC_RAW ? 2 : 4;
     LC.drow[it] = warp * PY + r;
     LC.dcol[it] = colw * j;
-    LC.soff[it] = c < SS::rows * SS::chunks ? c * 16 : -1;
+    LC.has[it] = c < SS::rows * SS::chunks;
+    LC.soff[it] = LC.has[it] ? c * 16 : 0;
     LC.goff[it] = ((int64_t)LC.drow[it] * pitch + LC.dcol[it]) * esz;
   }
   __syncthreads();
@@ -414,6 +465,13 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
                                     lane, warp * PY);
     cp_async_commit();
   }
+  // the masters' group is the oldest: wait for it alone, then 1/flat in place
+  cp_async_wait<kStages - 1>();
+  __syncthreads();
+  if (uwin) {
+    finish_masters(S, tx0, ty0, flat_norm, s_mast, h.status);
+    __syncthreads();
+  }
   const float4* s_mast_w = s_mast + warp * PY * mwin_w + lane;
   const bool stack_lane = lane < TW && x < W;
   int mq[PY];
@@ -421,26 +479,33 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
   for (int q = 0; q < PY; ++q) mq[q] = 0;
   float* sk = s_samples + (size_t)warp * PY * 32 + lane;
   // frames in groups of kStages, so that every stage slot is a constant
-  for (int k0 = 0; k0 < n; k0 += kStages) {
+  auto frame_loop = [&](auto gen) {
+    constexpr bool GEN = decltype(gen)::value;
+    for (int k0 = 0; k0 < n; k0 += kStages) {
 #pragma unroll
-    for (int u = 0; u < kStages; ++u) {
-      const int k = k0 + u;
-      if (k < n) {
-        cp_async_wait<kStages - 2>();
-        __syncwarp();
-        const int kn = k + kStages - 1;
-        if (kn < n)
-          issue_stage<SRC, STENCIL, PY>(frames[kn], LC, Hlim, Wlim, pitch,
-                                        s_stage + ((u + kStages - 1) % kStages) * SS::bytes, lane,
-                                        warp * PY);
-        cp_async_commit();
-        frame_step<STENCIL, SRC, PY>(frames[k], s_stage + u * SS::bytes, s_mast_w, mwin_w, S,
-                                     flat_norm, h.status, lane, x, tx0, wy0,
-                                     sk + (size_t)k * TH * 32, mq, stack_out, k, W, H, out_pitch,
-                                     stack_lane);
+      for (int u = 0; u < kStages; ++u) {
+        const int k = k0 + u;
+        if (k < n) {
+          cp_async_wait<kStages - 2>();
+          __syncwarp();
+          const int kn = k + kStages - 1;
+          if (kn < n)
+            issue_stage<SRC, STENCIL, PY>(frames[kn], LC, Hlim, Wlim, pitch,
+                                          s_stage + ((u + kStages - 1) % kStages) * SS::bytes,
+                                          lane, warp * PY);
+          cp_async_commit();
+          frame_step<STENCIL, SRC, PY, GEN>(frames[k], s_stage + u * SS::bytes, s_mast_w, mwin_w,
+                                            S, flat_norm, h.status, lane, x, tx0, wy0,
+                                            sk + (size_t)k * TH * 32, mq, stack_out, k, W, H,
+                                            out_pitch, stack_lane);
+        }
       }
     }
-  }
+  };
+  if ((SRC != SRC_RAW || mwin_w > 0) && !stack_out)
+    frame_loop(std::integral_constant<bool, false>{});
+  else
+    frame_loop(std::integral_constant<bool, true>{});
   cp_async_wait<0>();
   __syncwarp();
 
