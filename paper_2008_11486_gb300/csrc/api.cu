@@ -376,6 +376,9 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     SetDesc* sd = (SetDesc*)(img + plan_sets_offset());
     FrameDesc* fd = (FrameDesc*)(img + plan_frames_offset((int)g.size()));
     int frame0 = 0, tile0 = 0, ptile0 = 0, nrows = 0, ncolsegs = 0, row_e = 32;
+    for (int si : g)  // row-pass width: 32 columns per lane, 64 when a frame is wider than 1024
+      if (stencil == ST_BSPLINE && spline_path(sets[si].W, sets[si].H) && sets[si].W > 1024)
+        row_e = 64;
     for (int si = 0; si < (int)g.size(); ++si) {
       const irp_set& s = sets[g[si]];
       SetDesc& S = sd[si];
@@ -416,9 +419,8 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
       S.row0 = nrows;
       S.colseg0 = ncolsegs;
       if (S.spath) {
-        nrows += ((s.n + kRowGroup - 1) / kRowGroup) * s.H;
+        nrows += ((s.n + kRowGroup - 1) / kRowGroup) * ((s.H + row_block(row_e) - 1) / row_block(row_e));
         ncolsegs += s.n * s.W * ((s.H + 31) / 32);
-        if (s.W > 1024) row_e = 64;
       }
       int oxmin = INT32_MAX, oxmax = INT32_MIN, oymin = INT32_MAX, oymax = INT32_MIN;
       for (int k = 0; k < s.n; ++k) {

@@ -73,7 +73,7 @@ struct SetDesc {
   int32_t pframes;               // frames per prefilter work item
   int64_t coef_pitch;            // padded spline-coefficient frames: (H+4) rows
   int64_t crow_pitch;            // row-pass coefficient frames (spath 1)
-  int32_t row0;                  // first row-pass work item (one warp per frame row)
+  int32_t row0;                  // first row-pass work item (row block x frame chunk)
   int32_t colseg0;               // first column-pass work item
   int32_t mflags;                // bit 0: masters 16-byte aligned, pitch of 4k elements
   int32_t spath;                 // spline prefilter: 0 tiled, 1 row + column passes

@@ -18,6 +18,8 @@
 // across the warp's columns, warm-up of 16 rows on each side read from the
 // mirror-extended rows; the result is written into the padded coefficient
 // frame together with its 2-sample mirrored border.
+#include <algorithm>
+
 #include "prefilter.cuh"
 #include "reduce_kernels.cuh"
 #include "spline.h"
@@ -53,76 +55,130 @@ __device__ __forceinline__ int find_by(const SetDesc* sets, int nsets, int item,
 template <int E>
 __global__ void __launch_bounds__(256, 2)
     k_spline_rows(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
-  // masters of the block's row, element x at [x % E][x / E] (stride 33): lane
-  // l reads column E l + j from word j*33 + l, one bank per lane
-  __shared__ float sm[3][E * 33];
+  constexpr int RB = row_block(E);   // rows per CTA
+  constexpr int MQ = E / 4;          // float4 master chunks per lane and row
+  constexpr int RQ = E / 8;          // 16-byte raw chunks per lane and row
+  extern __shared__ __align__(16) float4 smem4[];
+  // masters: [row][bias, dark, rf][MQ][32 lanes] float4 (lane l holds columns
+  // E l .. E l + E - 1, chunk i = columns E l + 4i .. + 3): conflict-free
+  float4* s_m = smem4;
+  // raw: per warp two stages of [RQ][32 lanes] uint4
+  uint4* s_raw = (uint4*)(smem4 + RB * 3 * MQ * 32);
   const PlanView P = make_view(inl, plan_dev);
   const int item = blockIdx.x;
   if (item >= P.h->nrows) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const SetDesc& S = P.sets[find_by(P.sets, P.h->nsets, item, 0)];
+  const int W = S.W, H = S.H;
+  const int nrb = (H + RB - 1) / RB;
   const int local = item - S.row0;
-  const int g = local / S.H, y = local - g * S.H;  // frame chunk, row
-  const int W = S.W;
+  const int g = local / nrb, rb = local - g * nrb;  // frame chunk, row block
+  const int y0 = rb * RB, nr = min(RB, H - y0);
+  const int k0 = g * kRowGroup, nk = min(kRowGroup, S.n - k0);
   const int x0 = lane * E;
+  // 1. the block's master rows, asynchronously (zero beyond the frame)
   {
-    const float flat_norm = S.flat_sum ? (float)(*S.flat_sum / ((double)W * S.H)) : 1.0f;
-    const int64_t mo = (int64_t)y * S.master_pitch;
-    for (int x = threadIdx.x; x < 32 * E; x += 256) {
-      const int si = (x % E) * 33 + x / E;
-      if (x < W) {
-        sm[0][si] = __ldg(S.bias + mo + x);
-        sm[1][si] = __ldg(S.dark + mo + x);
-        sm[2][si] = inv_flat(__ldg(S.flat + mo + x), flat_norm, P.h->status);
-      } else {
-        sm[0][si] = sm[1][si] = sm[2][si] = 0.0f;
+    const bool vec = S.mflags & 1;
+    if (vec) {
+      for (int c = threadIdx.x; c < RB * 3 * 8 * E; c += 256) {  // 16-byte chunks
+        const int rr = c / (3 * 8 * E), rem = c - rr * (3 * 8 * E);
+        const int a = rem / (8 * E), xc = rem - a * (8 * E);   // chunk xc: columns 4xc..
+        const int x = 4 * xc, l = x / E, i = (x - l * E) >> 2;
+        const int y = y0 + rr;
+        const int nb = (rr < nr && x < W) ? 4 * min(4, W - x) : 0;
+        const float* base = a == 0 ? S.bias : (a == 1 ? S.dark : S.flat);
+        const float* gp = nb ? base + (int64_t)y * S.master_pitch + x : S.bias;
+        cp_async16(s_m + ((rr * 3 + a) * MQ + i) * 32 + l, gp, nb);
       }
+    } else {
+      for (int c = threadIdx.x; c < RB * 3 * 32 * E; c += 256) {  // single floats
+        const int rr = c / (3 * 32 * E), rem = c - rr * (3 * 32 * E);
+        const int a = rem / (32 * E), x = rem - a * (32 * E);
+        const int l = x / E, j = x - l * E;
+        const int y = y0 + rr;
+        const int nb = (rr < nr && x < W) ? 4 : 0;
+        const float* base = a == 0 ? S.bias : (a == 1 ? S.dark : S.flat);
+        const float* gp = nb ? base + (int64_t)y * S.master_pitch + x : S.bias;
+        cp_async4((float*)(s_m + ((rr * 3 + a) * MQ + (j >> 2)) * 32 + l) + (j & 3), gp, nb);
+      }
+    }
+    cp_async_commit();
+  }
+  // 2. the warp's tasks: (row, frame) pairs of the block, t = warp + 8 m
+  const int ntask = nr * nk;
+  uint4* stage = s_raw + warp * 2 * RQ * 32;
+  auto issue = [&](int t, int slot) {
+    const int rr = t / nk, f = t - rr * nk;
+    const FrameDesc& F = P.frames[S.frame0 + k0 + f];
+    const bool vec = (F.flags & 1) && x0 + E <= W;
+    const uint16_t* raw = (const uint16_t*)F.src + (int64_t)(y0 + rr) * S.src_pitch + x0;
+#pragma unroll
+    for (int i = 0; i < RQ; ++i)
+      cp_async16_if(vec, stage + (slot * RQ + i) * 32 + lane, raw + 8 * i, 16);
+  };
+  if (warp < ntask) issue(warp, 0);
+  cp_async_commit();
+  // 3. masters landed: flat -> flat_norm / flat in place
+  cp_async_wait<1>();
+  __syncthreads();
+  {
+    const float flat_norm = S.flat_sum ? (float)(*S.flat_sum / ((double)W * H)) : 1.0f;
+    for (int c = threadIdx.x; c < RB * MQ * 32; c += 256) {
+      const int rr = c / (MQ * 32), rem = c - rr * (MQ * 32);
+      const int i = rem >> 5, l = rem & 31;
+      float* q = (float*)(s_m + ((rr * 3 + 2) * MQ + i) * 32 + l);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (rr < nr && l * E + 4 * i + e < W) q[e] = inv_flat(q[e], flat_norm, P.h->status);
     }
   }
   __syncthreads();
   constexpr ZPow<E> zp{};
-  // each warp reduces frames k and k + 8 of the chunk; both raw rows are
-  // requested before the first is used
-  constexpr int kQ = E / 8;  // 16-byte raw loads per lane and row
-  uint4 q[2][kQ];
-  int kf[2] = {g * kRowGroup + warp, g * kRowGroup + warp + 8};
-#pragma unroll
-  for (int f = 0; f < 2; ++f) {
-    if (kf[f] < S.n) {
-      const FrameDesc& F = P.frames[S.frame0 + kf[f]];
-      const uint16_t* raw = (const uint16_t*)F.src + (int64_t)y * S.src_pitch;
-      if ((F.flags & 1) && x0 + E <= W) {
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) q[f][i] = __ldg((const uint4*)(raw + x0) + i);
-      }
-    }
-  }
+  int m = 0;
 #pragma unroll 1
-  for (int f = 0; f < 2; ++f) {
-    const int k = kf[f];
-    if (k >= S.n) break;
-    const FrameDesc& F = P.frames[S.frame0 + k];
-    const uint16_t* raw = (const uint16_t*)F.src + (int64_t)y * S.src_pitch;
-    const float t = F.t;
+  for (int t = warp; t < ntask; t += 8, ++m) {
+    if (t + 8 < ntask) issue(t + 8, (m + 1) & 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+    const int rr = t / nk, f = t - rr * nk;
+    const int y = y0 + rr;
+    const FrameDesc& F = P.frames[S.frame0 + k0 + f];
+    const float tk = F.t;
+    const bool vec = (F.flags & 1) && x0 + E <= W;
+    const float4* mb = s_m + (rr * 3 + 0) * MQ * 32 + lane;
+    const float4* md = mb + MQ * 32;
+    const float4* mr = md + MQ * 32;
     float v[E];
-    if ((F.flags & 1) && x0 + E <= W) {
+    if (vec) {
+      const uint4* rs = stage + ((m & 1) * RQ) * 32 + lane;
 #pragma unroll
-      for (int j = 0; j < E; j += 8) {
-        const uint4 qq = f == 0 ? q[0][j / 8] : q[1][j / 8];
+      for (int i = 0; i < RQ; ++i) {
+        const uint4 qq = rs[i * 32];
         const uint32_t w[4] = {qq.x, qq.y, qq.z, qq.w};
+        const float4 b0 = mb[(2 * i) * 32], b1 = mb[(2 * i + 1) * 32];
+        const float4 d0 = md[(2 * i) * 32], d1 = md[(2 * i + 1) * 32];
+        const float4 r0 = mr[(2 * i) * 32], r1 = mr[(2 * i + 1) * 32];
+        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        const float dd[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+        const float rf[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int si = (j + i) * 33 + lane;
-          v[j + i] = calibrate_px((uint16_t)(w[i >> 1] >> (16 * (i & 1))), sm[0][si], sm[1][si],
-                                  t, sm[2][si]);
-        }
+        for (int e = 0; e < 8; ++e)
+          v[8 * i + e] = calibrate_px((uint16_t)(w[e >> 1] >> (16 * (e & 1))), bb[e], dd[e], tk,
+                                      rf[e]);
       }
     } else {
+      const uint16_t* raw = (const uint16_t*)F.src + (int64_t)y * S.src_pitch;
 #pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const int si = j * 33 + lane;
-        v[j] = x0 + j < W ? calibrate_px(__ldg(raw + x0 + j), sm[0][si], sm[1][si], t, sm[2][si])
-                          : 0.0f;
+      for (int i = 0; i < MQ; ++i) {
+        const float4 b = mb[i * 32], d = md[i * 32], r = mr[i * 32];
+        const float bb[4] = {b.x, b.y, b.z, b.w}, dd[4] = {d.x, d.y, d.z, d.w};
+        const float rf[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int x = x0 + 4 * i + e;
+          v[4 * i + e] = x < W ? calibrate_px(__ldg(raw + x), bb[e], dd[e], tk, rf[e]) : 0.0f;
+        }
       }
     }
     // causal recursion within the lane, then the carry from the left lane
@@ -136,10 +192,10 @@ __global__ void __launch_bounds__(256, 2)
       }
       float carry = __shfl_up_sync(0xffffffffu, yp[E - 1], 1);
       if (lane == 0) {  // y+[-1] = sum_k z1^k v[1+k] (mirror)
-        float m = 0.0f;
+        float mm = 0.0f;
 #pragma unroll
-        for (int j = E - 1; j >= 1; --j) m = __fmaf_rn(kZ1, m, v[j]);
-        carry = m;
+        for (int j = E - 1; j >= 1; --j) mm = __fmaf_rn(kZ1, mm, v[j]);
+        carry = mm;
       }
 #pragma unroll
       for (int j = 0; j < E; ++j) yp[j] = __fmaf_rn(zp.p[j + 1], carry, yp[j]);
@@ -175,16 +231,20 @@ __global__ void __launch_bounds__(256, 2)
         out[j] = c;
       }
     }
+    __syncwarp();  // this stage is refilled two tasks later
   }
+  cp_async_wait<0>();
 }
+
 
 constexpr int kColSeg = 32;  // output rows per column task
 
 __global__ void __launch_bounds__(256, 2)
     k_spline_cols(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
   const PlanView P = make_view(inl, plan_dev);
-  const int item = blockIdx.x * 256 + threadIdx.x;
-  if (item >= P.h->ncolsegs) return;
+#pragma unroll 1
+  for (int item = blockIdx.x * 256 + threadIdx.x; item < P.h->ncolsegs;
+       item += gridDim.x * 256) {
   const SetDesc& S = P.sets[find_by(P.sets, P.h->nsets, item, 1)];
   const int W = S.W, H = S.H;
   const int nseg = (H + kColSeg - 1) / kColSeg;
@@ -241,7 +301,7 @@ __global__ void __launch_bounds__(256, 2)
       *o = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], acc), vj));
       o -= cp;
     }
-    return;
+    continue;
   }
 #pragma unroll
   for (int j = kColSeg - 1; j >= 0; --j) {
@@ -261,21 +321,48 @@ __global__ void __launch_bounds__(256, 2)
             out[(int64_t)(ys[a] + 2) * cp + (xs[b] + 2)] = c;
     }
   }
+  }
 }
 
 cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_dev, int nrows,
-                               cudaStream_t s) {  // nrows: (row, frame group) work items
+                               cudaStream_t s) {  // nrows: (row block, frame group) work items
+  static bool opted[2] = {false, false};
   const int grid = nrows;
-  if (e == 32)
-    k_spline_rows<32><<<grid, 256, 0, s>>>(*inl, plan_dev);
-  else
-    k_spline_rows<64><<<grid, 256, 0, s>>>(*inl, plan_dev);
+  const size_t smem = rows_smem_bytes(e);
+  cudaError_t err = cudaSuccess;
+  if (e == 32) {
+    if (!opted[0]) {
+      err = cudaFuncSetAttribute(k_spline_rows<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+      if (err != cudaSuccess) return err;
+      opted[0] = true;
+    }
+    k_spline_rows<32><<<grid, 256, smem, s>>>(*inl, plan_dev);
+  } else {
+    if (!opted[1]) {
+      err = cudaFuncSetAttribute(k_spline_rows<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+      if (err != cudaSuccess) return err;
+      opted[1] = true;
+    }
+    k_spline_rows<64><<<grid, 256, smem, s>>>(*inl, plan_dev);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_spline_cols(const InlinePlan* inl, const void* plan_dev, int ncolsegs,
                                cudaStream_t s) {
-  k_spline_cols<<<(ncolsegs + 255) / 256, 256, 0, s>>>(*inl, plan_dev);
+  // a few resident waves that loop over the segments (short-lived threads
+  // spent most of their time fetching the kernel's instructions)
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 1;
+  }
+  const int grid = std::max(1, std::min((ncolsegs + 255) / 256, 8 * sms));
+  k_spline_cols<<<grid, 256, 0, s>>>(*inl, plan_dev);
   return cudaGetLastError();
 }
 

@@ -134,6 +134,38 @@ def test_persistent_and_batch_invariance():
                 mean_tolerance(ref["mean"]) + 8 * 2.0 ** -24 * 7e4, m)
 
 
+def _padded_device_set(fs, pad_raw, pad_master):
+    """Device set whose raw frames and masters are views into wider buffers
+    (row pitch W + pad), so that neither need be 16-byte aligned per row."""
+    n, H, W = fs.raw.shape
+    big = torch.zeros((n, H, W + pad_raw), dtype=torch.uint16, device="cuda")
+    big[..., :W] = torch.from_numpy(fs.raw.astype(np.int32)).to(torch.uint16).cuda()
+    ms = []
+    for a in (fs.bias, fs.dark, fs.flat):
+        m = torch.ones((H, W + pad_master), dtype=torch.float32, device="cuda")
+        m[:, :W] = torch.from_numpy(a).cuda()
+        ms.append(m[:, :W])
+    s = core.device_set(fs, raw=big[..., :W], masters=tuple(ms)).alloc_outputs(want_stack=True)
+    s._keep.append(big)
+    return s
+
+
+@pytest.mark.parametrize("W,H,n,pad_raw,pad_master", [
+    (1100, 37, 18, 0, 0),    # 64 columns per lane, two frame chunks, ragged row block
+    (1021, 35, 5, 3, 1),     # unaligned raw and master rows
+    (2048, 36, 3, 0, 0),     # widest row pass
+    (96, 34, 17, 8, 4),      # narrow: most lanes past the frame
+])
+def test_spline_row_pass_shapes(W, H, n, pad_raw, pad_master):
+    fs = synth.make_set(W, H, n, 6.0, 4100 + W + n, n_stars=30, n_cr=6)
+    s = _padded_device_set(fs, pad_raw, pad_master)
+    ws = core.reduce_sets([s], core.reduce_params("spline3", core.clip_params(3.0, 3)))
+    assert core.sync_status(ws) == 0
+    got = dict(mean=s.mean.cpu().numpy(), median=s.median.cpu().numpy(),
+               nkept=s.nkept.cpu().numpy().astype(np.int32), stack=s.stack.cpu().numpy())
+    check_against_oracle(fs, got, "spline3", 3.0, 3)
+
+
 def test_spline_batch_invariance_and_persistent():
     fss = [synth.make_set(80, 72, n, 6.0, 300 + n, n_stars=20, n_cr=4) for n in (4, 11)]
     alone = [run_fused([fs], "spline3", want_stack=False)[0] for fs in fss]
