@@ -5,19 +5,24 @@
 // prefilter.cuh the mirror-boundary solution is c = sqrt(3)(y+ + y- - v) with
 // y+[i] = v[i] + z1 y+[i-1] and y-[i] = v[i] + z1 y-[i+1], z1 = sqrt(3) - 2.
 //
-// Row pass: one CTA per frame row and chunk of kRowGroup = 16 frames; the
-// row's masters and 1/flat are staged in shared memory once for the chunk,
-// and each warp reduces two frames of the row (both rows loaded up front).  Lane l calibrates and holds the E
-// columns [E l, E l + E) in registers and runs both recursions over them from
-// zero; the value entering from the neighbouring lane is added afterwards,
-// y+[E l + j] = local+[j] + z1^(j+1) y+[E l - 1] (and likewise for y-), which
-// is exact up to z1^E (< 5e-19 for E >= 32).  The mirror boundary is exact:
-// y+[-1] is the sum of z1^k v[1+k], and y-[W-1] = y+[W-1].
+// Row pass: one CTA per block of rows (4, or 2 for frames wider than 1024)
+// and chunk of kRowGroup frames.  The block's master rows are copied into
+// shared memory asynchronously and 1/flat is formed in place; the warps take
+// the block's (row, frame) tasks round-robin and prefetch the next task's raw
+// row with cp.async while computing the current one.  Lane l calibrates and
+// holds the E columns [E l, E l + E) in registers and runs both recursions
+// over them from zero; the value entering from the neighbouring lane is added
+// afterwards, y+[E l + j] = local+[j] + z1^(j+1) y+[E l - 1] (and likewise for
+// y-), which is exact up to z1^E (< 5e-19 for E >= 32).  The mirror boundary
+// is exact: y+[-1] is the sum of z1^k v[1+k], and y-[W-1] = y+[W-1].
 //
-// Column pass: one thread per (frame, column, 32-row segment), coalesced
-// across the warp's columns, warm-up of 16 rows on each side read from the
-// mirror-extended rows; the result is written into the padded coefficient
-// frame together with its 2-sample mirrored border.
+// Column pass: one CTA per (frame, 32 columns, 256 rows); lane = column, warp
+// = 32 consecutive rows.  Each warp runs both recursions over its rows from
+// zero, the warps exchange their ends through shared memory (the carry from
+// the warp above / below, exact up to z1^32), and the CTA's first and last
+// warp take their outer carry from 16 warm-up rows of the mirror-extended
+// column.  The result is written into the padded coefficient frame together
+// with its 2-sample mirrored border.
 #include <algorithm>
 
 #include "prefilter.cuh"
@@ -237,52 +242,98 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 
-constexpr int kColSeg = 32;  // output rows per column task
+constexpr int kColRows = 256;  // rows per column-pass CTA: 8 warps x 32 rows
+constexpr int kColWarm = 16;   // warm-up rows above and below the CTA's rows
 
 __global__ void __launch_bounds__(256, 2)
     k_spline_cols(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
+  __shared__ float s_c[8][32], s_a[8][32];  // each warp's local recursion ends
   const PlanView P = make_view(inl, plan_dev);
-#pragma unroll 1
-  for (int item = blockIdx.x * 256 + threadIdx.x; item < P.h->ncolsegs;
-       item += gridDim.x * 256) {
+  const int item = blockIdx.x;
+  if (item >= P.h->ncolsegs) return;
   const SetDesc& S = P.sets[find_by(P.sets, P.h->nsets, item, 1)];
   const int W = S.W, H = S.H;
-  const int nseg = (H + kColSeg - 1) / kColSeg;
+  const int ncb = (W + 31) / 32, nrb = (H + kColRows - 1) / kColRows;
   const int local = item - S.colseg0;
-  const int k = local / (W * nseg);
-  const int rem = local - k * (W * nseg);
-  const int seg = rem / W, x = rem - seg * W;
+  const int k = local / (ncb * nrb);
+  const int rem = local - k * (ncb * nrb);
+  const int rbk = rem / ncb, cb = rem - rbk * ncb;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int x = cb * 32 + lane;
+  const bool xin = x < W;
   const FrameDesc& F = P.frames[S.frame0 + k];
-  const float* in = F.crow + x;
+  const float* in = F.crow + (xin ? x : W - 1);  // lanes past the frame only feed carries
   const int64_t ip = S.crow_pitch;
-  const int y0 = seg * kColSeg;
-  constexpr int L = kColSeg + 2 * kPrefHalo;
-  float v[L];
-  const bool inner = y0 - kPrefHalo >= 0 && y0 + kColSeg + kPrefHalo <= H;
-  if (inner) {
-    const float* p = in + (int64_t)(y0 - kPrefHalo) * ip;
+  const int y0 = rbk * kColRows + warp * 32;
+  // rows outside [0, H) read the mirror-extended column (period 2H - 2)
+  auto mirror = [&](int y) {
+    int a = y < 0 ? -y : y;
+    if (a >= H) {
+      const int p = 2 * H - 2;
+      a %= p;
+      if (a >= H) a = p - a;
+    }
+    return a;
+  };
+  // the warp's 32 rows and, for the CTA's first / last warp, the 16 warm-up
+  // rows above / below, all requested before the first is used
+  const bool edge_warp = warp == 0 || warp == 7;
+  const int yw = warp == 0 ? y0 - kColWarm : y0 + 32;
+  float v[32], w[kColWarm];
+  const int ylo = y0 - (warp == 0 ? kColWarm : 0), yhi = y0 + 32 + (warp == 7 ? kColWarm : 0);
+  if (ylo >= 0 && yhi <= H) {
+    const float* p = in + (int64_t)y0 * ip;
 #pragma unroll
-    for (int j = 0; j < L; ++j) v[j] = __ldg(p + (int64_t)j * ip);
+    for (int j = 0; j < 32; ++j) v[j] = __ldg(p + (int64_t)j * ip);
+    if (edge_warp) {
+      const float* q = in + (int64_t)yw * ip;
+#pragma unroll
+      for (int j = 0; j < kColWarm; ++j) w[j] = __ldg(q + (int64_t)j * ip);
+    }
   } else {
+    int iv[32], iw[kColWarm];
 #pragma unroll
-    for (int j = 0; j < L; ++j) {
-      int yy = y0 - kPrefHalo + j;  // one reflection suffices: H >= kSplineMinSide > kPrefHalo
-      yy = yy < 0 ? -yy : (yy >= H ? 2 * H - 2 - yy : yy);
-      v[j] = __ldg(in + (int64_t)yy * ip);
+    for (int j = 0; j < 32; ++j) iv[j] = mirror(y0 + j);
+#pragma unroll
+    for (int j = 0; j < kColWarm; ++j) iw[j] = mirror(yw + j);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __ldg(in + (int64_t)iv[j] * ip);
+    if (edge_warp) {
+#pragma unroll
+      for (int j = 0; j < kColWarm; ++j) w[j] = __ldg(in + (int64_t)iw[j] * ip);
     }
   }
-  float yp[kColSeg];
-  float acc = 0.0f;
+  // local recursions from zero: the causal end feeds the warp below, the
+  // anti-causal start feeds the warp above (anything older is damped by z1^32)
+  float yl[32];
+  {
+    float a = 0.0f;
 #pragma unroll
-  for (int j = 0; j < kPrefHalo; ++j) acc = __fmaf_rn(kZ1, acc, v[j]);
+    for (int j = 0; j < 32; ++j) {
+      a = __fmaf_rn(kZ1, a, v[j]);
+      yl[j] = a;
+    }
+    s_c[warp][lane] = a;
+    float b = 0.0f;
 #pragma unroll
-  for (int j = 0; j < kColSeg; ++j) {
-    acc = __fmaf_rn(kZ1, acc, v[kPrefHalo + j]);
-    yp[j] = acc;
+    for (int j = 31; j >= 0; --j) b = __fmaf_rn(kZ1, b, v[j]);
+    s_a[warp][lane] = b;
   }
-  acc = 0.0f;
+  // at the CTA's top and bottom the carries come from warm-up rows
+  float cin = 0.0f, ain = 0.0f;
+  if (warp == 0) {
 #pragma unroll
-  for (int j = L - 1; j >= kPrefHalo + kColSeg; --j) acc = __fmaf_rn(kZ1, acc, v[j]);
+    for (int j = 0; j < kColWarm; ++j) cin = __fmaf_rn(kZ1, cin, w[j]);
+  }
+  if (warp == 7) {
+#pragma unroll
+    for (int j = kColWarm - 1; j >= 0; --j) ain = __fmaf_rn(kZ1, ain, w[j]);
+  }
+  __syncthreads();
+  if (warp > 0) cin = s_c[warp - 1][lane];
+  if (warp < 7) ain = s_a[warp + 1][lane];
+  if (!xin || y0 >= H) return;
+  constexpr ZPow<32> zp{};
   // padded frame (x, y) at (y + 2) * pitch + x + 2; the 2-sample border
   // holds the mirrored coefficients: c[-1] = c[1], c[-2] = c[2],
   // c[W] = c[W-2], c[W+1] = c[W-3] (likewise for rows)
@@ -291,36 +342,36 @@ __global__ void __launch_bounds__(256, 2)
   const int bx1 = x == 1 ? -1 : (x == W - 2 ? W : -100);
   const int bx2 = x == 2 ? -2 : (x == W - 3 ? W + 1 : -100);
   const bool xedge = bx1 != -100 || bx2 != -100;
-  const bool yedge = y0 < 3 || y0 + kColSeg > H - 3;
-  if (!xedge && !yedge && y0 + kColSeg <= H) {
-    float* o = out + (int64_t)(y0 + kColSeg - 1 + 2) * cp + (x + 2);
+  const bool yedge = y0 < 3 || y0 + 32 > H - 3;
+  float acc = ain;
+  if (!xedge && !yedge) {
+    float* o = out + (int64_t)(y0 + 31 + 2) * cp + (x + 2);
 #pragma unroll
-    for (int j = kColSeg - 1; j >= 0; --j) {
-      const float vj = v[kPrefHalo + j];
-      acc = __fmaf_rn(kZ1, acc, vj);
-      *o = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], acc), vj));
+    for (int j = 31; j >= 0; --j) {
+      acc = __fmaf_rn(kZ1, acc, v[j]);
+      const float yp = __fmaf_rn(zp.p[j + 1], cin, yl[j]);
+      *o = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp, acc), v[j]));
       o -= cp;
     }
-    continue;
+    return;
   }
 #pragma unroll
-  for (int j = kColSeg - 1; j >= 0; --j) {
-    const float vj = v[kPrefHalo + j];
-    acc = __fmaf_rn(kZ1, acc, vj);
+  for (int j = 31; j >= 0; --j) {
+    acc = __fmaf_rn(kZ1, acc, v[j]);
     const int y = y0 + j;
     if (y >= H) continue;
-    const float c = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], acc), vj));
+    const float yp = __fmaf_rn(zp.p[j + 1], cin, yl[j]);
+    const float c = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp, acc), v[j]));
     out[(int64_t)(y + 2) * cp + (x + 2)] = c;
     const int by1 = y == 1 ? -1 : (y == H - 2 ? H : -100);
     const int by2 = y == 2 ? -2 : (y == H - 3 ? H + 1 : -100);
     if (xedge || by1 != -100 || by2 != -100) {
       const int ys[3] = {y, by1, by2}, xs[3] = {x, bx1, bx2};
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-          if ((a | b) && ys[a] != -100 && xs[b] != -100)
-            out[(int64_t)(ys[a] + 2) * cp + (xs[b] + 2)] = c;
+      for (int a2 = 0; a2 < 3; ++a2)
+        for (int b2 = 0; b2 < 3; ++b2)
+          if ((a2 | b2) && ys[a2] != -100 && xs[b2] != -100)
+            out[(int64_t)(ys[a2] + 2) * cp + (xs[b2] + 2)] = c;
     }
-  }
   }
 }
 
@@ -351,18 +402,8 @@ cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_de
 }
 
 cudaError_t launch_spline_cols(const InlinePlan* inl, const void* plan_dev, int ncolsegs,
-                               cudaStream_t s) {
-  // a few resident waves that loop over the segments (short-lived threads
-  // spent most of their time fetching the kernel's instructions)
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 1;
-  }
-  const int grid = std::max(1, std::min((ncolsegs + 255) / 256, 8 * sms));
-  k_spline_cols<<<grid, 256, 0, s>>>(*inl, plan_dev);
+                               cudaStream_t s) {  // ncolsegs: (frame, 32 columns, 256 rows) items
+  k_spline_cols<<<ncolsegs, 256, 0, s>>>(*inl, plan_dev);
   return cudaGetLastError();
 }
 

@@ -155,6 +155,8 @@ def _padded_device_set(fs, pad_raw, pad_master):
     (1021, 35, 5, 3, 1),     # unaligned raw and master rows
     (2048, 36, 3, 0, 0),     # widest row pass
     (96, 34, 17, 8, 4),      # narrow: most lanes past the frame
+    (64, 300, 3, 0, 0),      # two column-pass row blocks, the second mostly mirrored
+    (200, 513, 2, 4, 0),     # three row blocks with a one-row tail
 ])
 def test_spline_row_pass_shapes(W, H, n, pad_raw, pad_master):
     fs = synth.make_set(W, H, n, 6.0, 4100 + W + n, n_stars=30, n_cr=6)
