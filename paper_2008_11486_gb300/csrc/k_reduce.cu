@@ -31,19 +31,33 @@ size_t reduce_smem_bytes(int src, int stencil, int py, int max_n, int mwin_w, in
 
 cudaError_t launch_reduce(int bucket, int py, int stencil, const InlinePlan* inl,
                           const void* plan_dev, int grid, size_t smem, cudaStream_t s) {
-  switch (stencil) {
-    case ST_NEAREST: return launch_reduce_nearest(bucket, py, inl, plan_dev, grid, smem, s);
-    case ST_BILINEAR: return launch_reduce_bilinear(bucket, py, inl, plan_dev, grid, smem, s);
-    default: return launch_reduce_bspline(bucket, py, inl, plan_dev, grid, smem, s);
+#define IRP_PICK(ST)                                                                   \
+  switch (bucket_range(bucket)) {                                                      \
+    case 0: return launch_reduce_##ST##_lo(bucket, py, inl, plan_dev, grid, smem, s);  \
+    case 1: return launch_reduce_##ST##_mid(bucket, py, inl, plan_dev, grid, smem, s); \
+    default: return launch_reduce_##ST##_hi(bucket, py, inl, plan_dev, grid, smem, s); \
   }
+  switch (stencil) {
+    case ST_NEAREST: IRP_PICK(nearest)
+    case ST_BILINEAR: IRP_PICK(bilinear)
+    default: IRP_PICK(bspline)
+  }
+#undef IRP_PICK
 }
 
 int reduce_occupancy(int bucket, int py, int stencil, size_t smem) {
-  switch (stencil) {
-    case ST_NEAREST: return occupancy_reduce_nearest(bucket, py, smem);
-    case ST_BILINEAR: return occupancy_reduce_bilinear(bucket, py, smem);
-    default: return occupancy_reduce_bspline(bucket, py, smem);
+#define IRP_PICK(ST)                                                   \
+  switch (bucket_range(bucket)) {                                      \
+    case 0: return occupancy_reduce_##ST##_lo(bucket, py, smem);       \
+    case 1: return occupancy_reduce_##ST##_mid(bucket, py, smem);      \
+    default: return occupancy_reduce_##ST##_hi(bucket, py, smem);      \
   }
+  switch (stencil) {
+    case ST_NEAREST: IRP_PICK(nearest)
+    case ST_BILINEAR: IRP_PICK(bilinear)
+    default: IRP_PICK(bspline)
+  }
+#undef IRP_PICK
 }
 
 cudaError_t launch_prefilter_raw(const InlinePlan* inl, const void* plan_dev, int grid,

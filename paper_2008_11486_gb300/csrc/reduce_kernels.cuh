@@ -1,5 +1,5 @@
 // reduce_kernels.cuh -- the fused reduction kernel and its per-bucket launchers
-// (each stencil's instantiations live in their own translation unit).
+// (each stencil's instantiations live in three translation units by bucket).
 #pragma once
 
 #include "reduce_tile.cuh"
@@ -73,49 +73,60 @@ struct ReduceLauncher {
   }
 };
 
-#define IRP_FOR_BUCKETS(X) X(4) X(5) X(6) X(8) X(10) X(12) X(16) X(24) X(32) X(40) X(48) X(64)
+// Register buckets, in three ranges that are compiled in separate
+// translation units (k_reduce_<stencil>_<range>.cu) so that the build runs
+// in parallel.
+#define IRP_BUCKETS_LO(X) X(4) X(5) X(6) X(8) X(10) X(12)
+#define IRP_BUCKETS_MID(X) X(16) X(24) X(32)
+#define IRP_BUCKETS_HI(X) X(40) X(48) X(64)
+#define IRP_FOR_BUCKETS(X) IRP_BUCKETS_LO(X) IRP_BUCKETS_MID(X) IRP_BUCKETS_HI(X)
 
-// py: rows per warp, rows_per_warp_default(bucket) or rows_per_warp_alt(bucket)
-template <int ST, int SRC>
-cudaError_t launch_bucket_st(int bucket, int py, const InlinePlan* inl, const void* plan_dev,
-                             int grid, size_t smem, cudaStream_t s) {
-  const bool alt = py != rows_per_warp_default(bucket);
-  switch (bucket) {
-#define IRP_CASE(B)                                                                           \
+// The range of a bucket: 0 (4..12), 1 (16..32), 2 (40..64).
+inline int bucket_range(int bucket) { return bucket <= 12 ? 0 : (bucket <= 32 ? 1 : 2); }
+
+// Defines launch_reduce_<NAME> and occupancy_reduce_<NAME> over the buckets
+// of LIST; py: rows per warp, rows_per_warp_default(bucket) or
+// rows_per_warp_alt(bucket).
+#define IRP_CASE_LAUNCH(B)                                                                    \
   case B:                                                                                     \
     return alt ? ReduceLauncher<B, ST, SRC, rows_per_warp_alt(B)>::launch(inl, plan_dev, grid, \
                                                                           smem, s)            \
                : ReduceLauncher<B, ST, SRC, rows_per_warp_default(B)>::launch(inl, plan_dev,  \
                                                                               grid, smem, s);
-    IRP_FOR_BUCKETS(IRP_CASE)
-#undef IRP_CASE
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int ST, int SRC>
-int occupancy_bucket_st(int bucket, int py, size_t smem) {
-  const bool alt = py != rows_per_warp_default(bucket);
-  switch (bucket) {
-#define IRP_CASE(B)                                                               \
+#define IRP_CASE_OCC(B)                                                           \
   case B:                                                                         \
     return alt ? ReduceLauncher<B, ST, SRC, rows_per_warp_alt(B)>::occupancy(smem) \
                : ReduceLauncher<B, ST, SRC, rows_per_warp_default(B)>::occupancy(smem);
-    IRP_FOR_BUCKETS(IRP_CASE)
-#undef IRP_CASE
+#define IRP_REDUCE_PART(NAME, STENCIL, SOURCE, LIST)                                          \
+  cudaError_t launch_reduce_##NAME(int bucket, int py, const InlinePlan* inl,                 \
+                                   const void* plan_dev, int grid, size_t smem,                \
+                                   cudaStream_t s) {                                           \
+    constexpr int ST = STENCIL, SRC = SOURCE;                                                 \
+    const bool alt = py != rows_per_warp_default(bucket);                                     \
+    switch (bucket) { LIST(IRP_CASE_LAUNCH) }                                                 \
+    return cudaErrorInvalidValue;                                                             \
+  }                                                                                           \
+  int occupancy_reduce_##NAME(int bucket, int py, size_t smem) {                              \
+    constexpr int ST = STENCIL, SRC = SOURCE;                                                 \
+    const bool alt = py != rows_per_warp_default(bucket);                                     \
+    switch (bucket) { LIST(IRP_CASE_OCC) }                                                    \
+    return 1;                                                                                 \
   }
-  return 1;
-}
 
-// per-stencil entry points (k_reduce_<stencil>.cu)
-cudaError_t launch_reduce_nearest(int bucket, int py, const InlinePlan* inl, const void* plan_dev,
-                                  int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_reduce_bilinear(int bucket, int py, const InlinePlan* inl, const void* plan_dev,
-                                   int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_reduce_bspline(int bucket, int py, const InlinePlan* inl, const void* plan_dev,
-                                  int grid, size_t smem, cudaStream_t s);
-int occupancy_reduce_nearest(int bucket, int py, size_t smem);
-int occupancy_reduce_bilinear(int bucket, int py, size_t smem);
-int occupancy_reduce_bspline(int bucket, int py, size_t smem);
+#define IRP_DECLARE_PART(NAME)                                                                \
+  cudaError_t launch_reduce_##NAME(int bucket, int py, const InlinePlan* inl,                 \
+                                   const void* plan_dev, int grid, size_t smem,                \
+                                   cudaStream_t s);                                            \
+  int occupancy_reduce_##NAME(int bucket, int py, size_t smem);
+IRP_DECLARE_PART(nearest_lo)
+IRP_DECLARE_PART(nearest_mid)
+IRP_DECLARE_PART(nearest_hi)
+IRP_DECLARE_PART(bilinear_lo)
+IRP_DECLARE_PART(bilinear_mid)
+IRP_DECLARE_PART(bilinear_hi)
+IRP_DECLARE_PART(bspline_lo)
+IRP_DECLARE_PART(bspline_mid)
+IRP_DECLARE_PART(bspline_hi)
+#undef IRP_DECLARE_PART
 
 }  // namespace irp

@@ -145,11 +145,14 @@ static_assert(sizeof(FrameRec) == 128, "FrameRec layout");
 
 // flags: bit 0 = raw frame 16-byte aligned with a pitch of 8k elements;
 // bit 1 = the tile's whole staging window (rows x elems from (ybase, xa)) lies
-// inside the frame, so its chunks need no bounds checks.
+// inside the frame, so its chunks need no bounds checks; bit 2 = every output
+// pixel of the tile inside the frame, [tx0, tx1] x [ty0, ty1], has a valid
+// sample of this frame.
 template <int SRC>
 __device__ __forceinline__ FrameRec make_rec(const FrameDesc& F, int tx0, int ty0, int64_t pitch,
                                              int mox, int moy, int mwin_w, int win_rows,
-                                             int win_elems, int Hlim, int Wlim) {
+                                             int win_elems, int Hlim, int Wlim, int tx1,
+                                             int ty1) {
   FrameRec R;
   const int gx0 = tx0 + F.ox, gy0 = ty0 + F.oy;
   if (SRC == SRC_RAW) {
@@ -180,7 +183,8 @@ __device__ __forceinline__ FrameRec make_rec(const FrameDesc& F, int tx0, int ty
   const bool aligned_src = SRC != SRC_RAW || (F.flags & 1);
   const bool interior = aligned_src && R.ybase >= 0 && R.ybase + win_rows <= Hlim && R.xa >= 0 &&
                         R.xa + win_elems <= Wlim;
-  R.flags = (F.flags & 1) | (interior ? 2 : 0);
+  const bool all_valid = F.vx0 <= tx0 && F.vx1 >= tx1 && F.vy0 <= ty0 && F.vy1 >= ty1;
+  R.flags = (F.flags & 1) | (interior ? 2 : 0) | (all_valid ? 4 : 0);
   R.pad1 = 0;
   for (int i = 0; i < 4; ++i) {
     R.wx[i] = F.wx[i];
@@ -253,6 +257,17 @@ __device__ __forceinline__ void issue_stage(const FrameRec& R, const LaneChunks<
   }
 }
 
+// issue_stage for a frame whose window lies inside the frame and is aligned:
+// every owned chunk is one unconditional 16-byte copy.
+template <int SRC, int kIt>
+__device__ __forceinline__ void issue_stage_inside(const FrameRec& R,
+                                                   const LaneChunks<SRC, kIt>& L,
+                                                   uint8_t* stage) {
+  const uint8_t* base = R.base;
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) cp_async16_if(L.has[it], stage + L.soff[it], base + L.goff[it], 16);
+}
+
 // The union window of the masters for this tile as {bias, dark, rf}: the
 // three masters are copied asynchronously into the float4 slots (zero outside
 // the frame), then finish_masters turns the flat into flat_norm/flat.
@@ -297,9 +312,12 @@ __device__ __forceinline__ void finish_masters(const SetDesc& S, int tx0, int ty
 // One frame of the warp's strip: calibrate the staged source rows, resample
 // them to the strip's PY output rows, store the samples (+inf when invalid)
 // and count the valid ones per row.
-// GEN = false: masters from the union window and no stack output (the
-// common case, without those branches); GEN = true: both decided per call.
-template <int STENCIL, int SRC, int PY, bool GEN>
+// MODE kFast: every sample of the tile valid, masters from the union window,
+// no stack output (the interior of a set: no validity tests or counts);
+// MODE kGeneral: validity per sample, masters and stack output decided per call.
+constexpr int kFast = 0, kGeneral = 1;
+
+template <int STENCIL, int SRC, int PY, int MODE>
 __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
                                            const float4* s_mast_w, int mrow, const SetDesc& S,
                                            float flat_norm, uint32_t* status, int lane, int x,
@@ -313,7 +331,7 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
   float v[SS::rows];
   if (SRC == SRC_RAW) {
     const uint16_t* raw = (const uint16_t*)st + lane + g.x;
-    if (!GEN || mrow > 0) {
+    if (MODE == kFast || mrow > 0) {
       const float4* mp = s_mast_w + g.y;
 #pragma unroll
       for (int r = 0; r < SS::rows; ++r) {
@@ -375,6 +393,11 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
       a[q] = __fmaf_rn(wy.w, hrow[q + 3], acc);
     }
   }
+  if (MODE == kFast) {
+#pragma unroll
+    for (int q = 0; q < PY; ++q) sk[q * 32] = a[q];
+    return;
+  }
   const float kInf = __int_as_float(0x7f800000);
   const bool xv = in_range(x, g.z, g.w);
 #pragma unroll
@@ -383,7 +406,7 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
     sk[q * 32] = ok ? a[q] : kInf;
     mq[q] += ok ? 1 : 0;
   }
-  if (GEN && stack_out) {
+  if (stack_out) {
 #pragma unroll
     for (int q = 0; q < PY; ++q) {
       const int y = wy0 + q;
@@ -435,9 +458,14 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
   const bool uwin = SRC == SRC_RAW && mwin_w > 0;
   if (uwin) issue_masters(S, tx0, ty0, s_mast);
   cp_async_commit();
-  for (int k = threadIdx.x; k < n; k += kThreads)
-    s_rec[k] = make_rec<SRC>(P.frames[S.frame0 + k], tx0, ty0, pitch, S.mox, S.moy, mwin_w,
-                             TH + StencilShape<STENCIL>::taps - 1, SS::elems, Hlim, Wlim);
+  int rec_fast = 1;
+  for (int k = threadIdx.x; k < n; k += kThreads) {
+    const FrameRec R = make_rec<SRC>(P.frames[S.frame0 + k], tx0, ty0, pitch, S.mox, S.moy,
+                                     mwin_w, TH + StencilShape<STENCIL>::taps - 1, SS::elems,
+                                     Hlim, Wlim, min(tx0 + TW, W) - 1, min(ty0 + TH, H) - 1);
+    s_rec[k] = R;
+    rec_fast &= (R.flags & 6) == 6 && (SRC != SRC_RAW || (R.flags & 1));
+  }
   float flat_norm = 1.0f;
   if (SRC == SRC_RAW && S.flat_sum) flat_norm = (float)(*S.flat_sum / ((double)S.W * S.H));
   // this lane's staging chunks (frame-independent)
@@ -454,7 +482,10 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
     LC.soff[it] = LC.has[it] ? c * 16 : 0;
     LC.goff[it] = ((int64_t)LC.drow[it] * pitch + LC.dcol[it]) * esz;
   }
-  __syncthreads();
+  // the tile's class: interior tiles (every frame aligned, staged without
+  // bounds checks and valid at every pixel) take the branch-free loop
+  const bool tile_fast = __syncthreads_and(rec_fast) && (SRC != SRC_RAW || mwin_w > 0) &&
+                         !stack_out;
 
   const FrameRec* frames = s_rec;
   // prologue: frames 0 .. kStages-2 in flight
@@ -479,33 +510,41 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
   for (int q = 0; q < PY; ++q) mq[q] = 0;
   float* sk = s_samples + (size_t)warp * PY * 32 + lane;
   // frames in groups of kStages, so that every stage slot is a constant
-  auto frame_loop = [&](auto gen) {
-    constexpr bool GEN = decltype(gen)::value;
-    for (int k0 = 0; k0 < n; k0 += kStages) {
+  auto step = [&](auto mode, int k, int u, bool issue_next) {
+    constexpr int MODE = decltype(mode)::value;
+    cp_async_wait<kStages - 2>();
+    __syncwarp();
+    if (issue_next) {
+      uint8_t* dst = s_stage + ((u + kStages - 1) % kStages) * SS::bytes;
+      if (MODE == kFast)
+        issue_stage_inside<SRC, kIt>(frames[k + kStages - 1], LC, dst);
+      else
+        issue_stage<SRC, STENCIL, PY>(frames[k + kStages - 1], LC, Hlim, Wlim, pitch, dst, lane,
+                                      warp * PY);
+    }
+    cp_async_commit();
+    frame_step<STENCIL, SRC, PY, MODE>(frames[k], s_stage + u * SS::bytes, s_mast_w, mwin_w, S,
+                                       flat_norm, h.status, lane, x, tx0, wy0,
+                                       sk + (size_t)k * TH * 32, mq, stack_out, k, W, H,
+                                       out_pitch, stack_lane);
+  };
+  auto frame_loop = [&](auto mode) {
+    int k0 = 0;
+    // groups whose frames and whose successors' copies all exist: no tests
+    for (; k0 + 2 * kStages - 1 <= n; k0 += kStages) {
 #pragma unroll
-      for (int u = 0; u < kStages; ++u) {
-        const int k = k0 + u;
-        if (k < n) {
-          cp_async_wait<kStages - 2>();
-          __syncwarp();
-          const int kn = k + kStages - 1;
-          if (kn < n)
-            issue_stage<SRC, STENCIL, PY>(frames[kn], LC, Hlim, Wlim, pitch,
-                                          s_stage + ((u + kStages - 1) % kStages) * SS::bytes,
-                                          lane, warp * PY);
-          cp_async_commit();
-          frame_step<STENCIL, SRC, PY, GEN>(frames[k], s_stage + u * SS::bytes, s_mast_w, mwin_w,
-                                            S, flat_norm, h.status, lane, x, tx0, wy0,
-                                            sk + (size_t)k * TH * 32, mq, stack_out, k, W, H,
-                                            out_pitch, stack_lane);
-        }
-      }
+      for (int u = 0; u < kStages; ++u) step(mode, k0 + u, u, true);
+    }
+    for (; k0 < n; k0 += kStages) {
+#pragma unroll
+      for (int u = 0; u < kStages; ++u)
+        if (k0 + u < n) step(mode, k0 + u, u, k0 + u + kStages - 1 < n);
     }
   };
-  if ((SRC != SRC_RAW || mwin_w > 0) && !stack_out)
-    frame_loop(std::integral_constant<bool, false>{});
+  if (tile_fast)
+    frame_loop(std::integral_constant<int, kFast>{});
   else
-    frame_loop(std::integral_constant<bool, true>{});
+    frame_loop(std::integral_constant<int, kGeneral>{});
   cp_async_wait<0>();
   __syncwarp();
 
@@ -529,6 +568,7 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
       int m = mq[0];
 #pragma unroll
       for (int qq = 1; qq < PY; ++qq) m = (q == qq) ? mq[qq] : m;
+      if (tile_fast) m = n;
       const CombineOut o = combine_sorted<NMAX>(s, m, ca);
       const int64_t oi = (int64_t)y * out_pitch + x;
       if (mean_out) mean_out[oi] = o.mean;
