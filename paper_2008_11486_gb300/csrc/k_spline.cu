@@ -169,8 +169,9 @@ __global__ void __launch_bounds__(256, 2)
         const float rf[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
 #pragma unroll
         for (int e = 0; e < 8; ++e)
-          v[8 * i + e] = calibrate_px((uint16_t)(w[e >> 1] >> (16 * (e & 1))), bb[e], dd[e], tk,
-                                      rf[e]);
+          v[8 * i + e] = calibrate_pxf((e & 1) ? u16_hi_to_float(w[e >> 1])
+                                               : u16_lo_to_float(w[e >> 1]),
+                                       bb[e], dd[e], tk, rf[e]);
       }
     } else {
       const uint16_t* raw = (const uint16_t*)F.src + (int64_t)y * S.src_pitch;
@@ -205,35 +206,57 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
       for (int j = 0; j < E; ++j) yp[j] = __fmaf_rn(zp.p[j + 1], carry, yp[j]);
     }
-    // anti-causal recursion: starts at W-1 with y-[W-1] = y+[W-1] (mirror).  A
-    // first pass over the lane finds its local value at the left end, the carry
-    // into the left neighbour; the second pass starts from the carry of the
-    // right neighbour and emits the coefficients.
-    float carry;
-    {
-      float acc = 0.0f;
+    float* out = F.crow + (int64_t)y * S.crow_pitch + x0;
+    if (W % E == 0) {
+      // the frame ends at the end of lane `last`: y-[W-1] = y+[W-1] is set at a
+      // fixed position, and the lanes past it (zeros) pass no carry
+      const int last = W / E - 1;
+      const bool is_last = lane == last;
+      float acc = is_last ? yp[E - 1] : v[E - 1];
+#pragma unroll
+      for (int j = E - 2; j >= 0; --j) acc = __fmaf_rn(kZ1, acc, v[j]);
+      float carry = __shfl_down_sync(0xffffffffu, acc, 1);
+      if (lane >= last) carry = 0.0f;
+      if (lane <= last) {
+        acc = carry;
+        float c4[4];
+#pragma unroll
+        for (int j = E - 1; j >= 0; --j) {
+          acc = (j == E - 1 && is_last) ? yp[j] : __fmaf_rn(kZ1, acc, v[j]);
+          c4[j & 3] = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], acc), v[j]));
+          if ((j & 3) == 0) *(float4*)(out + j) = make_float4(c4[0], c4[1], c4[2], c4[3]);
+        }
+      }
+    } else {
+      // anti-causal recursion: starts at W-1 with y-[W-1] = y+[W-1] (mirror).
+      // A first pass over the lane finds its local value at the left end, the
+      // carry into the left neighbour; the second pass starts from the carry
+      // of the right neighbour and emits the coefficients.
+      float carry;
+      {
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = E - 1; j >= 0; --j) {
+          const int x = x0 + j;
+          acc = x > W - 1 ? 0.0f : (x == W - 1 ? yp[j] : __fmaf_rn(kZ1, acc, v[j]));
+        }
+        carry = __shfl_down_sync(0xffffffffu, acc, 1);
+        if (x0 + E - 1 >= W - 1) carry = 0.0f;
+      }
+      const bool vst = x0 + E <= W && (S.crow_pitch & 3) == 0;
+      float acc = carry;
+      float c4[4];
 #pragma unroll
       for (int j = E - 1; j >= 0; --j) {
         const int x = x0 + j;
         acc = x > W - 1 ? 0.0f : (x == W - 1 ? yp[j] : __fmaf_rn(kZ1, acc, v[j]));
-      }
-      carry = __shfl_down_sync(0xffffffffu, acc, 1);
-      if (x0 + E - 1 >= W - 1) carry = 0.0f;
-    }
-    float* out = F.crow + (int64_t)y * S.crow_pitch + x0;
-    const bool vst = x0 + E <= W && (S.crow_pitch & 3) == 0;
-    float acc = carry;
-    float c4[4];
-#pragma unroll
-    for (int j = E - 1; j >= 0; --j) {
-      const int x = x0 + j;
-      acc = x > W - 1 ? 0.0f : (x == W - 1 ? yp[j] : __fmaf_rn(kZ1, acc, v[j]));
-      const float c = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], acc), v[j]));
-      if (vst) {
-        c4[j & 3] = c;
-        if ((j & 3) == 0) *(float4*)(out + j) = make_float4(c4[0], c4[1], c4[2], c4[3]);
-      } else if (x < W) {
-        out[j] = c;
+        const float c = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], acc), v[j]));
+        if (vst) {
+          c4[j & 3] = c;
+          if ((j & 3) == 0) *(float4*)(out + j) = make_float4(c4[0], c4[1], c4[2], c4[3]);
+        } else if (x < W) {
+          out[j] = c;
+        }
       }
     }
     __syncwarp();  // this stage is refilled two tasks later
@@ -334,43 +357,55 @@ __global__ void __launch_bounds__(256, 2)
   if (warp < 7) ain = s_a[warp + 1][lane];
   if (!xin || y0 >= H) return;
   constexpr ZPow<32> zp{};
-  // padded frame (x, y) at (y + 2) * pitch + x + 2; the 2-sample border
-  // holds the mirrored coefficients: c[-1] = c[1], c[-2] = c[2],
-  // c[W] = c[W-2], c[W+1] = c[W-3] (likewise for rows)
-  float* out = F.coef;
-  const int64_t cp = S.coef_pitch;
-  const int bx1 = x == 1 ? -1 : (x == W - 2 ? W : -100);
-  const int bx2 = x == 2 ? -2 : (x == W - 3 ? W + 1 : -100);
-  const bool xedge = bx1 != -100 || bx2 != -100;
-  const bool yedge = y0 < 3 || y0 + 32 > H - 3;
+  // padded frame (x, y) at (y + 2) * pitch + x + 2
+  const int cpi = (int)S.coef_pitch;
+  float* const out = F.coef + (x + 2);
+  float* const o = out + (int64_t)(y0 + 2) * cpi;
+  const int ny = min(32, H - y0);
   float acc = ain;
-  if (!xedge && !yedge) {
-    float* o = out + (int64_t)(y0 + 31 + 2) * cp + (x + 2);
+  if (ny == 32) {
 #pragma unroll
     for (int j = 31; j >= 0; --j) {
       acc = __fmaf_rn(kZ1, acc, v[j]);
       const float yp = __fmaf_rn(zp.p[j + 1], cin, yl[j]);
-      *o = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp, acc), v[j]));
-      o -= cp;
+      yl[j] = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp, acc), v[j]));
+      o[j * cpi] = yl[j];
     }
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int j = 31; j >= 0; --j) {
-    acc = __fmaf_rn(kZ1, acc, v[j]);
-    const int y = y0 + j;
-    if (y >= H) continue;
-    const float yp = __fmaf_rn(zp.p[j + 1], cin, yl[j]);
-    const float c = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp, acc), v[j]));
-    out[(int64_t)(y + 2) * cp + (x + 2)] = c;
-    const int by1 = y == 1 ? -1 : (y == H - 2 ? H : -100);
-    const int by2 = y == 2 ? -2 : (y == H - 3 ? H + 1 : -100);
-    if (xedge || by1 != -100 || by2 != -100) {
-      const int ys[3] = {y, by1, by2}, xs[3] = {x, bx1, bx2};
-      for (int a2 = 0; a2 < 3; ++a2)
-        for (int b2 = 0; b2 < 3; ++b2)
-          if ((a2 | b2) && ys[a2] != -100 && xs[b2] != -100)
-            out[(int64_t)(ys[a2] + 2) * cp + (xs[b2] + 2)] = c;
+    for (int j = 31; j >= 0; --j) {
+      acc = __fmaf_rn(kZ1, acc, v[j]);
+      const float yp = __fmaf_rn(zp.p[j + 1], cin, yl[j]);
+      yl[j] = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp, acc), v[j]));
+      if (j < ny) o[j * cpi] = yl[j];
+    }
+  }
+  // the 2-sample mirrored border: c[-1] = c[1], c[-2] = c[2], c[W] = c[W-2],
+  // c[W+1] = c[W-3], likewise for rows (and the corners)
+  const int bx1 = x == 1 ? -1 : (x == W - 2 ? W : -100);
+  const int bx2 = x == 2 ? -2 : (x == W - 3 ? W + 1 : -100);
+  if (bx1 != -100 || bx2 != -100) {
+    float* ob1 = F.coef + (bx1 + 2) + (int64_t)(y0 + 2) * cpi;
+    float* ob2 = F.coef + (bx2 + 2) + (int64_t)(y0 + 2) * cpi;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j < ny) {
+        if (bx1 != -100) ob1[j * cpi] = yl[j];
+        if (bx2 != -100) ob2[j * cpi] = yl[j];
+      }
+    }
+  }
+  if (y0 < 3 || y0 + ny > H - 3) {
+    const int rows[4] = {1, 2, H - 2, H - 3}, mrow[4] = {-1, -2, H, H + 1};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int j = rows[r] - y0;
+      if (j < 0 || j >= ny) continue;
+      const float c = select_at(yl, j);
+      const int64_t yy = (int64_t)(mrow[r] + 2) * cpi;
+      out[yy] = c;
+      if (bx1 != -100) out[yy + bx1 - x] = c;
+      if (bx2 != -100) out[yy + bx2 - x] = c;
     }
   }
 }

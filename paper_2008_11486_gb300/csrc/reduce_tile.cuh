@@ -57,6 +57,21 @@ __device__ __forceinline__ float u16_to_float(uint32_t q) {
   return __fsub_rn(__int_as_float(0x4B000000u | q), 8388608.0f);
 }
 
+// The two uint16 halves of a 32-bit word as floats: one byte permute builds
+// the bits of 2^23 + q.
+__device__ __forceinline__ float u16_lo_to_float(uint32_t w) {
+  return __fsub_rn(__int_as_float(__byte_perm(w, 0x4B00u, 0x5410u)), 8388608.0f);
+}
+__device__ __forceinline__ float u16_hi_to_float(uint32_t w) {
+  return __fsub_rn(__int_as_float(__byte_perm(w, 0x4B00u, 0x5432u)), 8388608.0f);
+}
+
+__device__ __forceinline__ float calibrate_pxf(float rawf, float bias, float dark, float t,
+                                               float rf) {
+  const float s = __fmaf_rn(-dark, t, __fsub_rn(rawf, bias));
+  return __fmul_rn(s, rf);
+}
+
 __device__ __forceinline__ float calibrate_px(uint16_t raw, float bias, float dark, float t,
                                               float rf) {
   // (raw - bias) - dark*t, then times flat_norm/flat
