@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "libirp.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
 SOURCES = ["api.cu", "k_reduce.cu", "k_spline.cu", "k_unfused.cu"] + [
-    f"k_reduce_{st}_{r}.cu" for st in ("bilinear", "bspline", "nearest")
+    f"k_reduce_{st}_{r}.cu" for st in ("bilinear", "bsplinev", "bspline", "nearest")
     for r in ("mid", "lo", "hi")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

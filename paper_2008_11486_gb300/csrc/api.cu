@@ -21,7 +21,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr uint32_t kPlanMagic = 0x49525031u;  // "IRP1"
-constexpr int kMaxSub = 12;  // one sub-plan per frame-count bucket at most
+constexpr int kMaxSub = 24;  // one sub-plan per bucket (and spline path) at most
 constexpr int kDefaultSpin = 1 << 20;  // polls of 1 us: about one second
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -236,17 +236,28 @@ size_t coef_frame_bytes(int W, int H) {
   return align_up((size_t)(H + 4) * (size_t)coef_pitch(W) * sizeof(float), kAlign);
 }
 
-void group_sets(const irp_set* sets, int nsets, std::vector<std::vector<int>>& groups) {
+// Sets are grouped by register bucket and, for the cubic spline, by the way
+// their coefficients are formed (the two take different reduction kernels).
+int group_key(const irp_set& s, int interp) {
+  const int b = reduce_bucket(s.n);
+  return interp == IRP_INTERP_SPLINE3 ? 2 * b + spline_path(s.W, s.H) : 2 * b;
+}
+
+void group_sets(const irp_set* sets, int nsets, int interp,
+                std::vector<std::vector<int>>& groups) {
   std::vector<int> order(nsets);
   for (int i = 0; i < nsets; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sets[a].n > sets[b].n; });
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const int ka = group_key(sets[a], interp), kb = group_key(sets[b], interp);
+    return ka != kb ? ka > kb : sets[a].n > sets[b].n;
+  });
   groups.clear();
-  int cur_bucket = -1;
+  int cur = -1;
   for (int i : order) {
-    const int b = reduce_bucket(sets[i].n);
-    if (b != cur_bucket) {
+    const int key = group_key(sets[i], interp);
+    if (key != cur) {
       groups.emplace_back();
-      cur_bucket = b;
+      cur = key;
     }
     groups.back().push_back(i);
   }
@@ -291,7 +302,7 @@ irp_status check_params(const irp_set* sets, int nsets, const irp_reduce_params*
     if (st != IRP_OK) return st;
   }
   std::vector<std::vector<int>> groups;
-  group_sets(sets, nsets, groups);
+  group_sets(sets, nsets, p->interp, groups);
   if ((int)groups.size() > kMaxSub) return IRP_ERR_UNSUPPORTED;
   return IRP_OK;
 }
@@ -310,7 +321,7 @@ int sm_count() {
 
 size_t plan_file_bytes(const irp_set* sets, int nsets, const irp_reduce_params* p) {
   std::vector<std::vector<int>> groups;
-  group_sets(sets, nsets, groups);
+  group_sets(sets, nsets, p->interp, groups);
   size_t off = align_up(sizeof(PlanFile) + (size_t)nsets * sizeof(FlatJob), 64);
   for (const auto& g : groups) {
     int nf = 0;
@@ -326,7 +337,7 @@ size_t plan_file_bytes(const irp_set* sets, int nsets, const irp_reduce_params* 
 irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* p, uint8_t* buf,
                        size_t buf_bytes, uint8_t* ws, size_t ws_bytes) {
   std::vector<std::vector<int>> groups;
-  group_sets(sets, nsets, groups);
+  group_sets(sets, nsets, p->interp, groups);
   const Layout L = make_layout(sets, nsets, p, groups);
   if (!ws || !aligned(ws, kAlign)) return IRP_ERR_WORKSPACE;
   if (ws_bytes < L.total) return IRP_ERR_WORKSPACE;
@@ -362,7 +373,12 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     }
     const int bucket = reduce_bucket(max_n);
     const int py = rows_per_warp(bucket, p->rows_per_warp);
-    const int TWc = tile_cols(stencil), THr = tile_rows(bucket, py);
+    // the group's reduction stencil: spline sets on the row + column passes
+    // arrive horizontally filtered and take the vertical taps only
+    const bool spline = stencil == ST_BSPLINE;
+    const bool gpath = spline && spline_path(sets[g[0]].W, sets[g[0]].H);
+    const int gstencil = gpath ? ST_BSPLINE_V : stencil;
+    const int TWc = tile_cols(gstencil), THr = tile_rows(bucket, py);
     // prefilter work items: tiles x frame groups, enough groups to fill the GPU twice
     int pgroups = 1;
     if (stencil == ST_BSPLINE) {
@@ -420,7 +436,7 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
       S.colseg0 = ncolsegs;
       if (S.spath) {
         nrows += ((s.n + kRowGroup - 1) / kRowGroup) * ((s.H + row_block(row_e) - 1) / row_block(row_e));
-        ncolsegs += s.n * ((s.W + 31) / 32) * ((s.H + 255) / 256);
+        ncolsegs += s.n * ((s.W + 28) / 29) * ((s.H + 255) / 256);
       }
       int oxmin = INT32_MAX, oxmax = INT32_MIN, oymin = INT32_MAX, oymax = INT32_MIN;
       for (int k = 0; k < s.n; ++k) {
@@ -461,7 +477,7 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     h->npitems = ptile0;
     h->nrows = nrows;
     h->ncolsegs = ncolsegs;
-    h->stencil = stencil;
+    h->stencil = gstencil;
     h->max_n = max_n;
     h->persistent = p->persistent ? 1 : 0;
     h->spin_limit = p->wait_spin_limit > 0 ? p->wait_spin_limit : kDefaultSpin;
@@ -481,9 +497,8 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     si.bytes = plan_total_bytes((int)g.size(), nf);
     si.bucket = bucket;
     si.py = py;
-    si.stencil = stencil;
-    si.smem = reduce_smem_bytes(stencil == ST_BSPLINE ? SRC_F32 : SRC_RAW, stencil, py, max_n,
-                                mw_max, mh_max);
+    si.stencil = gstencil;
+    si.smem = reduce_smem_bytes(spline ? SRC_F32 : SRC_RAW, gstencil, py, max_n, mw_max, mh_max);
     si.nitems = tile0;
     si.counter = gi;
     si.nsets = (int)g.size();
@@ -494,7 +509,7 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     si.row_e = row_e;
     if (si.smem > 227 * 1024 - 1024) return IRP_ERR_UNSUPPORTED;  // opt-in limit less static smem
     if (p->persistent) {
-      const int occ = reduce_occupancy(si.bucket, si.py, stencil, si.smem);
+      const int occ = reduce_occupancy(si.bucket, si.py, gstencil, si.smem);
       int g_ctas = p->max_ctas > 0 ? p->max_ctas : occ * sm_count();
       si.grid = std::max(1, std::min(g_ctas, tile0));
     } else {
@@ -623,7 +638,7 @@ int irp_profile_read(double* ms_out, int64_t* launches_out, int max_kinds) {
 size_t irp_workspace_size(const irp_set* sets, int nsets, const irp_reduce_params* p) {
   if (check_params(sets, nsets, p) != IRP_OK) return 0;
   std::vector<std::vector<int>> groups;
-  group_sets(sets, nsets, groups);
+  group_sets(sets, nsets, p->interp, groups);
   return make_layout(sets, nsets, p, groups).total;
 }
 
@@ -937,7 +952,7 @@ extern "C" irp_status irp_reduce_set_noalloc(const irp_set* sets, int nsets,
   if (st != IRP_OK) return st;
   if (!aligned(status_out, 4)) return IRP_ERR_ALIGNMENT;
   std::vector<std::vector<int>> groups;
-  group_sets(sets, nsets, groups);
+  group_sets(sets, nsets, p->interp, groups);
   const size_t need = make_layout(sets, nsets, p, groups).total;
   const size_t plan_bytes = plan_file_bytes(sets, nsets, p);
   if (need > IRP_NOALLOC_SCRATCH_BYTES || plan_bytes > kNoallocPlanBytes) return IRP_ERR_WORKSPACE;

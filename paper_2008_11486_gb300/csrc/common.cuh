@@ -19,7 +19,9 @@ constexpr int kThreads = 256;  // 8 warps per CTA of the fused kernel
 constexpr int kMaxInlineSets = 4;
 constexpr int kMaxInlineFrames = 64;
 
-enum Stencil : int { ST_NEAREST = 0, ST_BILINEAR = 1, ST_BSPLINE = 2 };
+// ST_BSPLINE: 4x4 cubic B-spline on padded coefficient frames; ST_BSPLINE_V:
+// its vertical 4 taps on frames whose rows already carry the horizontal taps.
+enum Stencil : int { ST_NEAREST = 0, ST_BILINEAR = 1, ST_BSPLINE = 2, ST_BSPLINE_V = 3 };
 enum Source : int { SRC_RAW = 0, SRC_F32 = 1, SRC_F16 = 2 };
 
 // Cubic-spline prefilter (Sec. 3.2.1's per-line tridiagonal system, solved in
@@ -121,8 +123,8 @@ __host__ __device__ inline size_t plan_total_bytes(int nsets, int nframes) {
 // Workspace header (first 256 bytes of every workspace).
 struct WsHeader {
   uint32_t status;
-  uint32_t counters[15];
-  uint8_t pad[192];
+  uint32_t counters[31];  // persistent work counters, one per sub-plan
+  uint8_t pad[128];
 };
 static_assert(sizeof(WsHeader) == 256, "WsHeader layout");
 

@@ -13,9 +13,12 @@ int reduce_bucket(int n) {
 }
 
 int tile_cols(int stencil) {
-  return stencil == ST_BSPLINE ? StencilShape<ST_BSPLINE>::tw
-                               : (stencil == ST_BILINEAR ? StencilShape<ST_BILINEAR>::tw
-                                                         : StencilShape<ST_NEAREST>::tw);
+  switch (stencil) {
+    case ST_NEAREST: return StencilShape<ST_NEAREST>::tw;
+    case ST_BILINEAR: return StencilShape<ST_BILINEAR>::tw;
+    case ST_BSPLINE: return StencilShape<ST_BSPLINE>::tw;
+    default: return StencilShape<ST_BSPLINE_V>::tw;
+  }
 }
 
 int rows_per_warp(int bucket, int requested) {
@@ -40,7 +43,8 @@ cudaError_t launch_reduce(int bucket, int py, int stencil, const InlinePlan* inl
   switch (stencil) {
     case ST_NEAREST: IRP_PICK(nearest)
     case ST_BILINEAR: IRP_PICK(bilinear)
-    default: IRP_PICK(bspline)
+    case ST_BSPLINE: IRP_PICK(bspline)
+    default: IRP_PICK(bsplinev)
   }
 #undef IRP_PICK
 }
@@ -55,7 +59,8 @@ int reduce_occupancy(int bucket, int py, int stencil, size_t smem) {
   switch (stencil) {
     case ST_NEAREST: IRP_PICK(nearest)
     case ST_BILINEAR: IRP_PICK(bilinear)
-    default: IRP_PICK(bspline)
+    case ST_BSPLINE: IRP_PICK(bspline)
+    default: IRP_PICK(bsplinev)
   }
 #undef IRP_PICK
 }

@@ -1,5 +1,6 @@
 // k_spline.cu -- cubic-spline coefficients of calibrated raw frames, row pass
-// and column pass without tile halos.
+// and column pass without tile halos; the column pass also applies the
+// horizontal taps of each frame's resampling.
 //
 // Sec. 3.2.1: one tridiagonal system per row and per column.  As in
 // prefilter.cuh the mirror-boundary solution is c = sqrt(3)(y+ + y- - v) with
@@ -16,13 +17,16 @@
 // y-), which is exact up to z1^E (< 5e-19 for E >= 32).  The mirror boundary
 // is exact: y+[-1] is the sum of z1^k v[1+k], and y-[W-1] = y+[W-1].
 //
-// Column pass: one CTA per (frame, 32 columns, 256 rows); lane = column, warp
-// = 32 consecutive rows.  Each warp runs both recursions over its rows from
-// zero, the warps exchange their ends through shared memory (the carry from
-// the warp above / below, exact up to z1^32), and the CTA's first and last
-// warp take their outer carry from 16 warm-up rows of the mirror-extended
-// column.  The result is written into the padded coefficient frame together
-// with its 2-sample mirrored border.
+// Column pass: one CTA per (frame, 29 output columns, 256 rows); lane =
+// column, warp = 32 consecutive rows.  Lane l solves the source column the
+// frame's first horizontal tap of output column l falls on.  Each warp runs
+// both recursions over its rows from zero, the warps exchange their ends
+// through shared memory (the carry from the warp above / below, exact up to
+// z1^32), and the CTA's first and last warp take their outer carry from 16
+// warm-up rows of the mirror-extended column.  The coefficients then take the
+// frame's 4 horizontal B-spline taps from lanes l .. l + 3, so the frame
+// written is the coefficients filtered along x on the output grid, with a
+// 2-row mirrored border: the fused kernel only applies the vertical taps.
 #include <algorithm>
 
 #include "prefilter.cuh"
@@ -267,6 +271,7 @@ __global__ void __launch_bounds__(256, 2)
 
 constexpr int kColRows = 256;  // rows per column-pass CTA: 8 warps x 32 rows
 constexpr int kColWarm = 16;   // warm-up rows above and below the CTA's rows
+constexpr int kColOut = 29;    // output columns per CTA: lanes 0..28 (taps reach lane + 3)
 
 __global__ void __launch_bounds__(256, 2)
     k_spline_cols(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
@@ -276,16 +281,25 @@ __global__ void __launch_bounds__(256, 2)
   if (item >= P.h->ncolsegs) return;
   const SetDesc& S = P.sets[find_by(P.sets, P.h->nsets, item, 1)];
   const int W = S.W, H = S.H;
-  const int ncb = (W + 31) / 32, nrb = (H + kColRows - 1) / kColRows;
+  const int ncb = (W + kColOut - 1) / kColOut, nrb = (H + kColRows - 1) / kColRows;
   const int local = item - S.colseg0;
   const int k = local / (ncb * nrb);
   const int rem = local - k * (ncb * nrb);
   const int rbk = rem / ncb, cb = rem - rbk * ncb;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int x = cb * 32 + lane;
-  const bool xin = x < W;
   const FrameDesc& F = P.frames[S.frame0 + k];
-  const float* in = F.crow + (xin ? x : W - 1);  // lanes past the frame only feed carries
+  // lane l solves source column cx = kColOut cb + ox + l (mirror-extended:
+  // the coefficients of a mirrored column are the mirrored coefficients);
+  // output column x = kColOut cb + l takes its taps from lanes l .. l + 3
+  const int x = kColOut * cb + lane;
+  int cx = x + F.ox;
+  if ((unsigned)cx >= (unsigned)W) {
+    const int p = 2 * W - 2;
+    cx = cx < 0 ? -cx : cx;
+    cx %= p;
+    if (cx >= W) cx = p - cx;
+  }
+  const float* in = F.crow + cx;
   const int64_t ip = S.crow_pitch;
   const int y0 = rbk * kColRows + warp * 32;
   // rows outside [0, H) read the mirror-extended column (period 2H - 2)
@@ -355,57 +369,41 @@ __global__ void __launch_bounds__(256, 2)
   __syncthreads();
   if (warp > 0) cin = s_c[warp - 1][lane];
   if (warp < 7) ain = s_a[warp + 1][lane];
-  if (!xin || y0 >= H) return;
+  if (y0 >= H) return;  // (after the last shuffle partner has its data: none below)
   constexpr ZPow<32> zp{};
-  // padded frame (x, y) at (y + 2) * pitch + x + 2
-  const int cpi = (int)S.coef_pitch;
-  float* const out = F.coef + (x + 2);
-  float* const o = out + (int64_t)(y0 + 2) * cpi;
+  // coefficients, then the horizontal taps from lanes l .. l + 3:
+  // h(x, y) = sum_i wx_i c(x + ox + i, y), in the order the 4x4 evaluation uses
+  const float wx0 = F.wx[0], wx1 = F.wx[1], wx2 = F.wx[2], wx3 = F.wx[3];
+  const bool store = lane < kColOut && x < W;
+  const int hpi = (int)S.coef_pitch;
+  float* const out = F.coef + x;  // filtered frame (x, y) at (y + 2) * pitch + x
+  float* const o = out + (int64_t)(y0 + 2) * hpi;
   const int ny = min(32, H - y0);
   float acc = ain;
-  if (ny == 32) {
 #pragma unroll
-    for (int j = 31; j >= 0; --j) {
-      acc = __fmaf_rn(kZ1, acc, v[j]);
-      const float yp = __fmaf_rn(zp.p[j + 1], cin, yl[j]);
-      yl[j] = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp, acc), v[j]));
-      o[j * cpi] = yl[j];
-    }
-  } else {
-#pragma unroll
-    for (int j = 31; j >= 0; --j) {
-      acc = __fmaf_rn(kZ1, acc, v[j]);
-      const float yp = __fmaf_rn(zp.p[j + 1], cin, yl[j]);
-      yl[j] = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp, acc), v[j]));
-      if (j < ny) o[j * cpi] = yl[j];
-    }
+  for (int j = 31; j >= 0; --j) {
+    acc = __fmaf_rn(kZ1, acc, v[j]);
+    const float yp = __fmaf_rn(zp.p[j + 1], cin, yl[j]);
+    const float c = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp, acc), v[j]));
+    const float c1 = __shfl_down_sync(0xffffffffu, c, 1);
+    const float c2 = __shfl_down_sync(0xffffffffu, c, 2);
+    const float c3 = __shfl_down_sync(0xffffffffu, c, 3);
+    float hh = wx0 * c;
+    hh = __fmaf_rn(wx1, c1, hh);
+    hh = __fmaf_rn(wx2, c2, hh);
+    hh = __fmaf_rn(wx3, c3, hh);
+    yl[j] = hh;
+    if (store && j < ny) o[j * hpi] = hh;
   }
-  // the 2-sample mirrored border: c[-1] = c[1], c[-2] = c[2], c[W] = c[W-2],
-  // c[W+1] = c[W-3], likewise for rows (and the corners)
-  const int bx1 = x == 1 ? -1 : (x == W - 2 ? W : -100);
-  const int bx2 = x == 2 ? -2 : (x == W - 3 ? W + 1 : -100);
-  if (bx1 != -100 || bx2 != -100) {
-    float* ob1 = F.coef + (bx1 + 2) + (int64_t)(y0 + 2) * cpi;
-    float* ob2 = F.coef + (bx2 + 2) + (int64_t)(y0 + 2) * cpi;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j < ny) {
-        if (bx1 != -100) ob1[j * cpi] = yl[j];
-        if (bx2 != -100) ob2[j * cpi] = yl[j];
-      }
-    }
-  }
-  if (y0 < 3 || y0 + ny > H - 3) {
+  // the 2-row mirrored border: h[-1] = h[1], h[-2] = h[2], h[H] = h[H-2],
+  // h[H+1] = h[H-3] (the horizontal taps commute with the row mirror)
+  if (store && (y0 < 3 || y0 + ny > H - 3)) {
     const int rows[4] = {1, 2, H - 2, H - 3}, mrow[4] = {-1, -2, H, H + 1};
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int j = rows[r] - y0;
       if (j < 0 || j >= ny) continue;
-      const float c = select_at(yl, j);
-      const int64_t yy = (int64_t)(mrow[r] + 2) * cpi;
-      out[yy] = c;
-      if (bx1 != -100) out[yy + bx1 - x] = c;
-      if (bx2 != -100) out[yy + bx2 - x] = c;
+      out[(int64_t)(mrow[r] + 2) * hpi] = select_at(yl, j);
     }
   }
 }
@@ -437,7 +435,7 @@ cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_de
 }
 
 cudaError_t launch_spline_cols(const InlinePlan* inl, const void* plan_dev, int ncolsegs,
-                               cudaStream_t s) {  // ncolsegs: (frame, 32 columns, 256 rows) items
+                               cudaStream_t s) {  // ncolsegs: (frame, 29 columns, 256 rows) items
   k_spline_cols<<<ncolsegs, 256, 0, s>>>(*inl, plan_dev);
   return cudaGetLastError();
 }

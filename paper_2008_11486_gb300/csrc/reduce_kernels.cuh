@@ -127,6 +127,9 @@ IRP_DECLARE_PART(bilinear_hi)
 IRP_DECLARE_PART(bspline_lo)
 IRP_DECLARE_PART(bspline_mid)
 IRP_DECLARE_PART(bspline_hi)
+IRP_DECLARE_PART(bsplinev_lo)
+IRP_DECLARE_PART(bsplinev_mid)
+IRP_DECLARE_PART(bsplinev_hi)
 #undef IRP_DECLARE_PART
 
 }  // namespace irp

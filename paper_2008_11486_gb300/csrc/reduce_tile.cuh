@@ -103,9 +103,11 @@ __device__ __forceinline__ void cp_async_wait() {
 // ---------------------------------------------------------------- geometry
 template <int STENCIL>
 struct StencilShape {
-  static constexpr int taps = STENCIL == ST_BSPLINE ? 4 : (STENCIL == ST_BILINEAR ? 2 : 1);
-  // output columns per tile: lane l needs source columns l .. l + taps - 1
-  static constexpr int tw = 33 - taps;
+  static constexpr int taps_x = STENCIL == ST_BSPLINE ? 4 : (STENCIL == ST_BILINEAR ? 2 : 1);
+  static constexpr int taps_y = (STENCIL == ST_BSPLINE || STENCIL == ST_BSPLINE_V)
+                                    ? 4 : (STENCIL == ST_BILINEAR ? 2 : 1);
+  // output columns per tile: lane l needs source columns l .. l + taps_x - 1
+  static constexpr int tw = 33 - taps_x;
 };
 
 // Output rows per warp (tile height / 8): the two choices of each register
@@ -116,11 +118,16 @@ __host__ __device__ constexpr int rows_per_warp_alt(int nmax) { return nmax <= 1
 constexpr int kStages = 4;           // cp.async ring depth (frames in flight)
 constexpr int kRawChunks = 5;        // 16-byte chunks per staged raw row (40 uint16)
 constexpr int kCoefChunks = 9;       // 16-byte chunks per staged coefficient row (36 floats)
+constexpr int kRowChunks = 8;        // 16-byte chunks per staged filtered row (32 floats)
+
+__host__ __device__ constexpr int stage_chunks(int src, int stencil) {
+  return src == SRC_RAW ? kRawChunks : (stencil == ST_BSPLINE_V ? kRowChunks : kCoefChunks);
+}
 
 template <int SRC, int STENCIL, int PY>
 struct StageShape {
-  static constexpr int rows = PY + StencilShape<STENCIL>::taps - 1;
-  static constexpr int chunks = SRC == SRC_RAW ? kRawChunks : kCoefChunks;
+  static constexpr int rows = PY + StencilShape<STENCIL>::taps_y - 1;
+  static constexpr int chunks = stage_chunks(SRC, STENCIL);
   static constexpr int elems = chunks * (SRC == SRC_RAW ? 8 : 4);  // per row
   static constexpr int bytes = rows * chunks * 16;                  // per stage
 };
@@ -128,9 +135,10 @@ struct StageShape {
 // Shared memory per CTA of the fused kernel (host helper mirrors this).
 __host__ __device__ inline size_t fused_smem_bytes(int src, int stencil, int py, int max_n,
                                                    int mwin_w, int mwin_h) {
-  const int taps = stencil == ST_BSPLINE ? 4 : (stencil == ST_BILINEAR ? 2 : 1);
+  const int taps = (stencil == ST_BSPLINE || stencil == ST_BSPLINE_V)
+                       ? 4 : (stencil == ST_BILINEAR ? 2 : 1);
   const int rows = py + taps - 1;
-  const int chunks = src == SRC_RAW ? kRawChunks : kCoefChunks;
+  const int chunks = stage_chunks(src, stencil);
   const size_t stage = (size_t)kStages * rows * chunks * 16 * (kThreads / 32);
   const size_t samples = (size_t)max_n * (8 * py) * 32 * sizeof(float);
   const size_t masters = (size_t)mwin_w * mwin_h * sizeof(float4);
@@ -163,7 +171,7 @@ static_assert(sizeof(FrameRec) == 128, "FrameRec layout");
 // inside the frame, so its chunks need no bounds checks; bit 2 = every output
 // pixel of the tile inside the frame, [tx0, tx1] x [ty0, ty1], has a valid
 // sample of this frame.
-template <int SRC>
+template <int SRC, int STENCIL>
 __device__ __forceinline__ FrameRec make_rec(const FrameDesc& F, int tx0, int ty0, int64_t pitch,
                                              int mox, int moy, int mwin_w, int win_rows,
                                              int win_elems, int Hlim, int Wlim, int tx1,
@@ -176,6 +184,13 @@ __device__ __forceinline__ FrameRec make_rec(const FrameDesc& F, int tx0, int ty
     R.ybase = gy0;
     R.fbase = (const uint8_t*)F.src;
     R.base = R.fbase + ((int64_t)gy0 * pitch + R.xa) * 2;
+  } else if (STENCIL == ST_BSPLINE_V) {
+    // filtered rows on the output columns: element (x, y) at ((y + 2) * pitch + x)
+    R.xa = tx0;
+    R.off = 0;
+    R.ybase = gy0 + 2;
+    R.fbase = (const uint8_t*)F.coef;
+    R.base = R.fbase + ((int64_t)R.ybase * pitch + R.xa) * 4;
   } else {  // padded coefficient frame: element (x, y) at ((y + 2) * pitch + x + 2)
     R.xa = (gx0 + 2) & ~3;
     R.off = gx0 + 2 - R.xa;
@@ -386,6 +401,15 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
     }
 #pragma unroll
     for (int q = 0; q < PY; ++q) a[q] = __fmaf_rn(w.y, __fsub_rn(hrow[q + 1], hrow[q]), hrow[q]);
+  } else if (STENCIL == ST_BSPLINE_V) {
+    const float4 wy = *(const float4*)F.wy;
+#pragma unroll
+    for (int q = 0; q < PY; ++q) {
+      float acc = wy.x * v[q];
+      acc = __fmaf_rn(wy.y, v[q + 1], acc);
+      acc = __fmaf_rn(wy.z, v[q + 2], acc);
+      a[q] = __fmaf_rn(wy.w, v[q + 3], acc);
+    }
   } else {
     const float4 wx = *(const float4*)F.wx;
     const float4 wy = *(const float4*)F.wy;
@@ -475,8 +499,8 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
   cp_async_commit();
   int rec_fast = 1;
   for (int k = threadIdx.x; k < n; k += kThreads) {
-    const FrameRec R = make_rec<SRC>(P.frames[S.frame0 + k], tx0, ty0, pitch, S.mox, S.moy,
-                                     mwin_w, TH + StencilShape<STENCIL>::taps - 1, SS::elems,
+    const FrameRec R = make_rec<SRC, STENCIL>(P.frames[S.frame0 + k], tx0, ty0, pitch, S.mox,
+                                              S.moy, mwin_w, SS::rows + TH - PY, SS::elems,
                                      Hlim, Wlim, min(tx0 + TW, W) - 1, min(ty0 + TH, H) - 1);
     s_rec[k] = R;
     rec_fast &= (R.flags & 6) == 6 && (SRC != SRC_RAW || (R.flags & 1));

@@ -177,6 +177,25 @@ def test_spline_batch_invariance_and_persistent():
         assert np.array_equal(a["median"].view(np.uint32), b["median"].view(np.uint32))
 
 
+def test_spline_batch_mixing_coefficient_paths():
+    """One bucket holding sets on both spline paths (tiled prefilter for a
+    30-row frame, row + column passes for the others): each equals its
+    standalone reduction and the oracle."""
+    fss = [synth.make_set(70, 30, 5, 5.0, 510, n_stars=12, n_cr=3),
+           synth.make_set(70, 50, 5, 5.0, 511, n_stars=12, n_cr=3),
+           synth.make_set(40, 36, 6, 5.0, 512, n_stars=12, n_cr=3)]
+    alone = [run_fused([fs], "spline3", want_stack=False)[0] for fs in fss]
+    batch = run_fused(fss, "spline3", want_stack=False)
+    for fs, a, b in zip(fss, alone, batch):
+        assert np.array_equal(a["mean"].view(np.uint32), b["mean"].view(np.uint32))
+        assert np.array_equal(a["median"].view(np.uint32), b["median"].view(np.uint32))
+        ref = oracle.reduce_set(fs, interp="spline3")
+        m = (ref["margin"] >= 1e-3) & (b["nkept"] == ref["nkept"])
+        assert m.mean() > 0.99
+        samp = sample_tolerance(fs, "spline3", oracle).max(axis=0)
+        compare("mixed spline mean", b["mean"], ref["mean"], mean_tolerance(ref["mean"]) + samp, m)
+
+
 def test_normalize_flat():
     fs = synth.make_set(70, 50, 6, 3.0, 41, n_stars=20)
     fs.flat = (fs.flat * 1.7).astype(np.float32)   # not normalised to 1
