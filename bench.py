@@ -579,7 +579,11 @@ def run_served(args, cfg, dev, world, rank, local):
     # fill the rings so every measured request reduces a full stack
     serve.run_poisson(srv, make_requests(depth - 1, 0), rate_hz=1e6)
     sampler = ClockSampler(local)
-    lat, wall = serve.run_poisson(srv, make_requests(args.requests, 100), rate_hz=args.rate)
+    reqs = make_requests(args.requests, 100)
+    lat, wall = serve.run_poisson(srv, reqs, rate_hz=args.rate)
+    phase = {"queued_s": [r.admitted - r.arrival for r in reqs],
+             "upload_wait_s": [r.launched - r.admitted for r in reqs],
+             "device_s": [r.done - r.launched for r in reqs]}
     sat_n = max(8, args.requests)
     sat_lat, sat_wall = serve.run_poisson(srv, make_requests(sat_n, 1000), rate_hz=1e6)
     clocks = sampler.stop()
@@ -597,7 +601,9 @@ def run_served(args, cfg, dev, world, rank, local):
                        "parallelism": f"replicas x{world}"},
             "latency_s": {"p50": round(float(np.percentile(lat, 50)), 4),
                           "p99": round(float(np.percentile(lat, 99)), 4),
-                          "max": round(float(lat.max()), 4), "rate_hz": args.rate},
+                          "max": round(float(lat.max()), 4), "rate_hz": args.rate,
+                          "p50_phases": {k: round(float(np.percentile(v, 50)), 4)
+                                         for k, v in phase.items()}},
             "saturation": {"requests": sat_n, "wall_s": round(sat_wall, 3),
                            "p50_s": round(float(np.percentile(sat_lat, 50)), 4),
                            "p99_s": round(float(np.percentile(sat_lat, 99)), 4)},

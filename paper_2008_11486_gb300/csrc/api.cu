@@ -738,6 +738,11 @@ irp_status irp_calibrate(const uint16_t* raw, int64_t raw_pitch, int64_t raw_fra
   a.master_pitch = master_pitch;
   a.flat_sum = normalize_flat ? &flat_st->sum : nullptr;
   a.status = &wsh->status;
+  // four pixels per vector access when every row of every operand starts on it
+  a.vec = (W % 4 == 0 && raw_pitch % 4 == 0 && raw_frame_stride % 4 == 0 && aligned(raw, 8) &&
+           master_pitch % 4 == 0 && aligned(bias, 16) && aligned(dark_rate, 16) &&
+           aligned(flat, 16) && out_pitch % 4 == 0 && out_frame_stride % 4 == 0 &&
+           aligned(out, dt == IRP_F32 ? 16 : 8)) ? 1 : 0;
   for (int k0 = 0; k0 < n; k0 += kCalibChunk) {
     const int nk = std::min(kCalibChunk, n - k0);
     a.k0 = k0;

@@ -88,27 +88,92 @@ __global__ void k_stats_init(FrameStats* st, int n) {
   }
 }
 
+// A thread's partial sums over one row in FP32 with exact error terms: each
+// addition is split by TwoSum into its rounded sum and its rounding error,
+// and each square by one fused multiply-add into rn(v v) and its remainder;
+// the (small) error terms are summed in FP32.  A row's partials (at most
+// W / 256 values) are then added into FP64, so the frame sum carries FP64
+// accuracy at the FP32 arithmetic rate.
+struct RowPartial {
+  float s, es, q, eq;
+};
+
+__device__ __forceinline__ void two_sum_add(float& s, float& e, float v) {
+  const float t = __fadd_rn(s, v);
+  const float bp = __fsub_rn(t, s);
+  e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp)));
+  s = t;
+}
+
+__device__ __forceinline__ void row_add(RowPartial& r, float v) {
+  two_sum_add(r.s, r.es, v);
+  const float p = __fmul_rn(v, v);
+  two_sum_add(r.q, r.eq, p);
+  r.eq = __fadd_rn(r.eq, __fmaf_rn(v, v, -p));
+}
+
+__device__ __forceinline__ void row_flush(StatsAcc& acc, const RowPartial& r) {
+  acc.s += (double)r.s + (double)r.es;
+  acc.q += (double)r.q + (double)r.eq;
+}
+
+// Rows per stats block: about 16K pixels per block.
+__host__ __device__ inline int stats_rows(int W, int H) {
+  int r = 16384 / (W > 0 ? W : 1);
+  r = r < 1 ? 1 : r;
+  return r > H ? H : r;
+}
+
 // Sums of calibrated raw frames (FP16 scaling needs them before quantising).
+// Block b covers frame b % nk and the row block b / nk: consecutive blocks
+// share the row block's masters, which are then read from L2 for all frames
+// but the first.
 __global__ void __launch_bounds__(kThreads)
-    k_stats_raw(CalibArgs a, FrameStats* st) {
-  const int k = blockIdx.y + a.k0;
+    k_stats_raw(CalibArgs a, int nk, FrameStats* st) {
+  const int kl = blockIdx.x % nk, rb = blockIdx.x / nk;
+  const int k = kl + a.k0;
   const uint16_t* raw = a.raw + (int64_t)k * a.raw_frame_stride;
-  const float t = a.t[blockIdx.y];
+  const float t = a.t[kl];
   const float flat_norm = a.flat_sum ? (float)(*a.flat_sum / ((double)a.W * a.H)) : 1.0f;
   StatsAcc acc{0.0, 0.0, 0, FLT_MAX, -FLT_MAX};
-  const int64_t P = (int64_t)a.W * a.H;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < P;
-       i += (int64_t)gridDim.x * kThreads) {
-    const int y = (int)(i / a.W), x = (int)(i - (int64_t)y * a.W);
-    const int64_t m = (int64_t)y * a.master_pitch + x;
-    const float rf = inv_flat(__ldg(a.flat + m), flat_norm, a.status);
-    const float v = calibrate_px(__ldg(raw + (int64_t)y * a.raw_pitch + x), __ldg(a.bias + m),
-                                 __ldg(a.dark + m), t, rf);
-    acc.s += (double)v;
-    acc.q += (double)v * (double)v;
-    acc.c += 1;
-    acc.mn = fminf(acc.mn, v);
-    acc.mx = fmaxf(acc.mx, v);
+  const int R = stats_rows(a.W, a.H);
+  const int y1 = min(a.H, (rb + 1) * R);
+  for (int y = rb * R; y < y1; ++y) {
+    RowPartial r{0.0f, 0.0f, 0.0f, 0.0f};
+    const uint16_t* rr = raw + (int64_t)y * a.raw_pitch;
+    const int64_t mrow = (int64_t)y * a.master_pitch;
+    if (a.vec) {
+      for (int x = 4 * threadIdx.x; x < a.W; x += 4 * kThreads) {
+        const uint2 q = __ldg((const uint2*)(rr + x));
+        const float4 b = __ldg((const float4*)(a.bias + mrow + x));
+        const float4 d = __ldg((const float4*)(a.dark + mrow + x));
+        const float4 f = __ldg((const float4*)(a.flat + mrow + x));
+        const float v[4] = {
+            calibrate_pxf(u16_lo_to_float(q.x), b.x, d.x, t, inv_flat(f.x, flat_norm, a.status)),
+            calibrate_pxf(u16_hi_to_float(q.x), b.y, d.y, t, inv_flat(f.y, flat_norm, a.status)),
+            calibrate_pxf(u16_lo_to_float(q.y), b.z, d.z, t, inv_flat(f.z, flat_norm, a.status)),
+            calibrate_pxf(u16_hi_to_float(q.y), b.w, d.w, t, inv_flat(f.w, flat_norm, a.status))};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          row_add(r, v[e]);
+          acc.mn = fminf(acc.mn, v[e]);
+          acc.mx = fmaxf(acc.mx, v[e]);
+        }
+        acc.c += 4;
+      }
+      row_flush(acc, r);
+      continue;
+    }
+    for (int x = threadIdx.x; x < a.W; x += kThreads) {
+      const float rf = inv_flat(__ldg(a.flat + mrow + x), flat_norm, a.status);
+      const float v = calibrate_px(__ldg(rr + x), __ldg(a.bias + mrow + x),
+                                   __ldg(a.dark + mrow + x), t, rf);
+      row_add(r, v);
+      acc.c += 1;
+      acc.mn = fminf(acc.mn, v);
+      acc.mx = fmaxf(acc.mx, v);
+    }
+    row_flush(acc, r);
   }
   stats_commit(acc, &st[k].sum, &st[k].sumsq, &st[k].count, &st[k].min_key, &st[k].max_key);
 }
@@ -116,30 +181,32 @@ __global__ void __launch_bounds__(kThreads)
 // Sums of F32 / F16-scaled frames, NaN skipped (also the flat master).
 template <bool F16>
 __global__ void __launch_bounds__(kThreads)
-    k_stats_frames(const void* frames, int64_t pitch, int64_t fstride, int W, int H,
+    k_stats_frames(const void* frames, int64_t pitch, int64_t fstride, int W, int H, int n,
                    const float* scale, const float* offset, double* sum, double* sumsq,
                    long long* count, FrameStats* st) {
-  const int k = blockIdx.y;
+  const int k = blockIdx.x % n, rb = blockIdx.x / n;
   StatsAcc acc{0.0, 0.0, 0, FLT_MAX, -FLT_MAX};
-  const int64_t P = (int64_t)W * H;
   const float sc = (F16 && scale) ? scale[k] : 1.0f, of = (F16 && offset) ? offset[k] : 0.0f;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < P;
-       i += (int64_t)gridDim.x * kThreads) {
-    const int y = (int)(i / W), x = (int)(i - (int64_t)y * W);
-    const int64_t o = (int64_t)k * fstride + (int64_t)y * pitch + x;
-    float v;
-    if (F16) {
-      v = __fmaf_rn(__half2float(((const __half*)frames)[o]), sc, of);
-    } else {
-      v = __ldg((const float*)frames + o);
+  const int R = stats_rows(W, H);
+  const int y1 = min(H, (rb + 1) * R);
+  for (int y = rb * R; y < y1; ++y) {
+    RowPartial r{0.0f, 0.0f, 0.0f, 0.0f};
+    const int64_t o = (int64_t)k * fstride + (int64_t)y * pitch;
+    for (int x = threadIdx.x; x < W; x += kThreads) {
+      float v;
+      if (F16) {
+        v = __fmaf_rn(__half2float(((const __half*)frames)[o + x]), sc, of);
+      } else {
+        v = __ldg((const float*)frames + o + x);
+      }
+      if (v == v) {
+        row_add(r, v);
+        acc.c += 1;
+        acc.mn = fminf(acc.mn, v);
+        acc.mx = fmaxf(acc.mx, v);
+      }
     }
-    if (v == v) {
-      acc.s += (double)v;
-      acc.q += (double)v * (double)v;
-      acc.c += 1;
-      acc.mn = fminf(acc.mn, v);
-      acc.mx = fmaxf(acc.mx, v);
-    }
+    row_flush(acc, r);
   }
   if (st)
     stats_commit(acc, &st[k].sum, &st[k].sumsq, &st[k].count, &st[k].min_key, &st[k].max_key);
@@ -165,27 +232,69 @@ __global__ void k_f16_scaling(const FrameStats* st, int n, float* scale, float* 
 }
 
 // ---------------------------------------------------------------------------
-// Calibration (Sec. 2.1), one thread per pixel.
+// Calibration (Sec. 2.1).  Block b covers frame b % nk of one row segment of
+// 1024 pixels (four per thread, coalesced); consecutive blocks share the
+// segment's masters, read from L2 for all frames but the first.
 // ---------------------------------------------------------------------------
+constexpr int kCalibSeg = 4 * kThreads;
+
 template <bool F16>
-__global__ void __launch_bounds__(kThreads) k_calibrate(CalibArgs a, void* out, int64_t out_pitch,
-                                                        int64_t out_fstride, const float* scale,
+__global__ void __launch_bounds__(kThreads) k_calibrate(CalibArgs a, int nk, void* out,
+                                                        int64_t out_pitch, int64_t out_fstride,
+                                                        const float* scale,
                                                         const float* offset) {
-  const int x = blockIdx.x * kThreads + threadIdx.x;
-  const int y = blockIdx.y;
-  const int k = blockIdx.z + a.k0;
-  if (x >= a.W) return;
+  const int kl = blockIdx.x % nk;
+  const int64_t seg = blockIdx.x / nk;
+  const int nseg = (a.W + kCalibSeg - 1) / kCalibSeg;
+  const int y = (int)(seg / nseg);
+  const int xs = (int)(seg - (int64_t)y * nseg) * kCalibSeg;
+  const int k = kl + a.k0;
   const float flat_norm = a.flat_sum ? (float)(*a.flat_sum / ((double)a.W * a.H)) : 1.0f;
-  const int64_t m = (int64_t)y * a.master_pitch + x;
-  const float rf = inv_flat(__ldg(a.flat + m), flat_norm, a.status);
-  const uint16_t q = __ldg(a.raw + (int64_t)k * a.raw_frame_stride + (int64_t)y * a.raw_pitch + x);
-  const float v = calibrate_px(q, __ldg(a.bias + m), __ldg(a.dark + m), a.t[blockIdx.z], rf);
-  const int64_t o = (int64_t)k * out_fstride + (int64_t)y * out_pitch + x;
+  const float t = a.t[kl];
+  const uint16_t* rr = a.raw + (int64_t)k * a.raw_frame_stride + (int64_t)y * a.raw_pitch;
+  const int64_t mrow = (int64_t)y * a.master_pitch;
+  const int64_t orow = (int64_t)k * out_fstride + (int64_t)y * out_pitch;
+  float inv = 1.0f, off = 0.0f;
   if (F16) {
-    const float inv = 1.0f / scale[k];  // exact: the scale is a power of two
-    ((__half*)out)[o] = __float2half_rn(__fmul_rn(__fsub_rn(v, offset[k]), inv));
-  } else {
-    ((float*)out)[o] = v;
+    inv = 1.0f / scale[k];  // exact: the scale is a power of two
+    off = offset[k];
+  }
+  if (a.vec) {
+    const int x = xs + 4 * threadIdx.x;
+    if (x >= a.W) return;
+    const uint2 q = __ldg((const uint2*)(rr + x));
+    const float4 b = __ldg((const float4*)(a.bias + mrow + x));
+    const float4 d = __ldg((const float4*)(a.dark + mrow + x));
+    const float4 f = __ldg((const float4*)(a.flat + mrow + x));
+    float v[4] = {
+        calibrate_pxf(u16_lo_to_float(q.x), b.x, d.x, t, inv_flat(f.x, flat_norm, a.status)),
+        calibrate_pxf(u16_hi_to_float(q.x), b.y, d.y, t, inv_flat(f.y, flat_norm, a.status)),
+        calibrate_pxf(u16_lo_to_float(q.y), b.z, d.z, t, inv_flat(f.z, flat_norm, a.status)),
+        calibrate_pxf(u16_hi_to_float(q.y), b.w, d.w, t, inv_flat(f.w, flat_norm, a.status))};
+    if (F16) {
+      __half h[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) h[e] = __float2half_rn(__fmul_rn(__fsub_rn(v[e], off), inv));
+      uint2 pk;
+      pk.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
+      pk.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
+      *(uint2*)((__half*)out + orow + x) = pk;
+    } else {
+      *(float4*)((float*)out + orow + x) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int x = xs + j * kThreads + threadIdx.x;
+    if (x >= a.W) break;
+    const float rf = inv_flat(__ldg(a.flat + mrow + x), flat_norm, a.status);
+    const float v = calibrate_px(__ldg(rr + x), __ldg(a.bias + mrow + x),
+                                 __ldg(a.dark + mrow + x), t, rf);
+    if (F16)
+      ((__half*)out)[orow + x] = __float2half_rn(__fmul_rn(__fsub_rn(v, off), inv));
+    else
+      ((float*)out)[orow + x] = v;
   }
 }
 
@@ -258,6 +367,14 @@ template <int NMAX, bool F16>
 __global__ void __launch_bounds__(kThreads) k_combine(CombineArgs a) {
   const int x = blockIdx.x * kThreads + threadIdx.x;
   const int y = blockIdx.y;
+  __shared__ float s_sc[NMAX], s_of[NMAX];  // F16: per-frame scale and offset
+  if (F16) {
+    if (threadIdx.x < a.n) {
+      s_sc[threadIdx.x] = a.scale[threadIdx.x];
+      s_of[threadIdx.x] = a.offset[threadIdx.x];
+    }
+    __syncthreads();
+  }
   if (x >= a.W) return;
   const float kInf = __int_as_float(0x7f800000);
   auto load = [&](int k) -> float {
@@ -270,12 +387,33 @@ __global__ void __launch_bounds__(kThreads) k_combine(CombineArgs a) {
     if (a.valid && !a.valid[o]) v = kInf;
     return (v == v) ? v : kInf;
   };
+  // every frame's value and validity requested before any is used
+  const int64_t o0 = (int64_t)y * a.pitch + x;
   float s[NMAX];
+#pragma unroll
+  for (int j = 0; j < NMAX; ++j) {
+    if (j < a.n) {
+      const int64_t o = (int64_t)j * a.fstride + o0;
+      s[j] = F16 ? __half2float(((const __half*)a.stack)[o]) : __ldg((const float*)a.stack + o);
+    } else {
+      s[j] = kInf;
+    }
+  }
+  // validity as one bit per frame
+  uint64_t ok = ~0ull;
+  if (a.valid) {
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j)
+      if (j < a.n && !__ldg(a.valid + j * a.fstride + o0)) ok &= ~(1ull << j);
+  }
   int m = 0;
 #pragma unroll
   for (int j = 0; j < NMAX; ++j) {
-    s[j] = (j < a.n) ? load(j) : kInf;
-    m += (s[j] < kInf) ? 1 : 0;
+    float v = s[j];
+    if (F16 && j < a.n) v = __fmaf_rn(v, s_sc[j], s_of[j]);
+    v = (((ok >> j) & 1) && v == v) ? v : kInf;
+    s[j] = v;
+    m += (v < kInf) ? 1 : 0;
   }
   sort_network<NMAX>(s);
   const CombineOut o = combine_sorted<NMAX>(s, m, a.clip);
@@ -295,19 +433,14 @@ __global__ void __launch_bounds__(kThreads) k_combine(CombineArgs a) {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-static int stats_blocks(int64_t P) {
-  int64_t b = (P + kThreads * 8 - 1) / (kThreads * 8);
-  return (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
-}
-
 cudaError_t launch_stats_init(FrameStats* st, int n, cudaStream_t s) {
   k_stats_init<<<(n + 255) / 256, 256, 0, s>>>(st, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_stats_raw(const CalibArgs& a, int nk, FrameStats* st, cudaStream_t s) {
-  dim3 grid(stats_blocks((int64_t)a.W * a.H), nk);
-  k_stats_raw<<<grid, kThreads, 0, s>>>(a, st);
+  const int nrb = (a.H + stats_rows(a.W, a.H) - 1) / stats_rows(a.W, a.H);
+  k_stats_raw<<<(unsigned)((int64_t)nk * nrb), kThreads, 0, s>>>(a, nk, st);
   return cudaGetLastError();
 }
 
@@ -315,13 +448,14 @@ cudaError_t launch_stats_frames(const void* frames, int64_t pitch, int64_t fstri
                                 int n, bool f16, const float* scale, const float* offset,
                                 double* sum, double* sumsq, long long* count, FrameStats* st,
                                 cudaStream_t s) {
-  dim3 grid(stats_blocks((int64_t)W * H), n);
+  const int nrb = (H + stats_rows(W, H) - 1) / stats_rows(W, H);
+  const unsigned grid = (unsigned)((int64_t)n * nrb);
   if (f16)
-    k_stats_frames<true><<<grid, kThreads, 0, s>>>(frames, pitch, fstride, W, H, scale, offset,
+    k_stats_frames<true><<<grid, kThreads, 0, s>>>(frames, pitch, fstride, W, H, n, scale, offset,
                                                    sum, sumsq, count, st);
   else
-    k_stats_frames<false><<<grid, kThreads, 0, s>>>(frames, pitch, fstride, W, H, scale, offset,
-                                                    sum, sumsq, count, st);
+    k_stats_frames<false><<<grid, kThreads, 0, s>>>(frames, pitch, fstride, W, H, n, scale,
+                                                    offset, sum, sumsq, count, st);
   return cudaGetLastError();
 }
 
@@ -334,11 +468,15 @@ cudaError_t launch_f16_scaling(const FrameStats* st, int n, float* scale, float*
 cudaError_t launch_calibrate(const CalibArgs& a, int nk, bool f16, void* out, int64_t out_pitch,
                              int64_t out_fstride, const float* scale, const float* offset,
                              cudaStream_t s) {
-  dim3 grid((a.W + kThreads - 1) / kThreads, a.H, nk);
+  const int64_t nseg = (int64_t)((a.W + kCalibSeg - 1) / kCalibSeg) * a.H;
+  const int64_t grid = nseg * nk;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   if (f16)
-    k_calibrate<true><<<grid, kThreads, 0, s>>>(a, out, out_pitch, out_fstride, scale, offset);
+    k_calibrate<true><<<(unsigned)grid, kThreads, 0, s>>>(a, nk, out, out_pitch, out_fstride,
+                                                          scale, offset);
   else
-    k_calibrate<false><<<grid, kThreads, 0, s>>>(a, out, out_pitch, out_fstride, scale, offset);
+    k_calibrate<false><<<(unsigned)grid, kThreads, 0, s>>>(a, nk, out, out_pitch, out_fstride,
+                                                           scale, offset);
   return cudaGetLastError();
 }
 

@@ -19,7 +19,8 @@ struct FrameStats {  // 32 bytes per frame, workspace
 struct CalibArgs {
   const uint16_t* raw;
   int64_t raw_pitch, raw_frame_stride;
-  int W, H, k0, pad;
+  int W, H, k0;
+  int vec;                  // raw, masters (and outputs): 4-pixel vector loads and stores
   const float* bias;
   const float* dark;
   const float* flat;

@@ -8,7 +8,10 @@ ones (a rolling reference stack).
 
 Scheduling:
   * admission: a request is admitted when an in-flight slot is free and the
-    device has room for it (``torch.cuda.mem_get_info`` minus a reserve);
+    device keeps its reserve free (``torch.cuda.mem_get_info``); frames,
+    outputs and masters live in rings allocated once, so a request allocates
+    no device memory, and its outputs stay valid until ``out_slots`` newer
+    requests have been admitted;
     admitted requests copy their new frames into the chip rings on a copy
     stream (pinned host memory -> HBM);
   * batching: at every scheduler tick all admitted requests whose copies have
@@ -40,19 +43,27 @@ class Request:
     dy: np.ndarray
     exptime: float = 60.0
     arrival: float = 0.0
+    admitted: float = 0.0  # its frames' copies queued
+    launched: float = 0.0  # its reduction queued
     done: float = 0.0
-    outputs: list = None  # per chip (mean, median) device tensors
+    outputs: list = None  # per chip (mean, median) device tensors (views of the output ring)
+    out_slot: int = 0
     status: int = 0
 
 
 class Chip:
-    """Resident masters and the raw-frame ring of one detector chip."""
+    """Resident masters, the raw-frame ring and the output ring of one
+    detector chip (all allocated once)."""
 
-    def __init__(self, bias, dark, flat, depth: int, slots: int):
+    def __init__(self, bias, dark, flat, depth: int, slots: int, out_slots: int):
         self.bias, self.dark, self.flat = bias, dark, flat
         self.H, self.W = bias.shape
         self.depth = depth
         self.ring = torch.empty((slots, self.H, self.W), dtype=torch.uint16, device=bias.device)
+        # mean and median of the last out_slots requests
+        self.out = torch.empty((out_slots, 2, self.H, self.W), dtype=torch.float32,
+                               device=bias.device)
+        self.out_slots = out_slots
         self.slot_dx = np.zeros(slots)
         self.slot_dy = np.zeros(slots)
         self.slot_t = np.full(slots, 60.0, dtype=np.float32)
@@ -70,7 +81,7 @@ class Chip:
 
 class Server:
     def __init__(self, masters, depth=5, max_inflight=2, interp="bilinear", clip=None,
-                 hbm_reserve_bytes=2 << 30, device="cuda"):
+                 hbm_reserve_bytes=2 << 30, device="cuda", out_slots=None):
         self.device = torch.device(device)
         self.depth = depth
         self.max_inflight = max_inflight
@@ -79,7 +90,14 @@ class Server:
         self.reserve = hbm_reserve_bytes
         # ring slots: depth for the stack plus one per request that may still be
         # reading when the next one writes
-        self.chips = [Chip(b, d, f, depth, depth + max_inflight) for (b, d, f) in masters]
+        # output slots: a request's (mean, median) stay valid until out_slots
+        # newer requests have been admitted
+        self.out_slots = out_slots if out_slots is not None else max_inflight + 2
+        if self.out_slots < max_inflight:
+            raise ValueError("out_slots must cover the requests in flight")
+        self.chips = [Chip(b, d, f, depth, depth + max_inflight, self.out_slots)
+                      for (b, d, f) in masters]
+        self.admitted = 0
         self.copy_stream = torch.cuda.Stream(device=self.device)
         self.compute_stream = torch.cuda.Stream(device=self.device)
         self.pending = collections.deque()   # arrived, not admitted
@@ -98,8 +116,7 @@ class Server:
             self.pending.append(req)
 
     def _request_bytes(self, req) -> int:
-        out = sum(2 * c.H * c.W * 4 for c in self.chips)
-        return out
+        return 0  # frames, outputs and masters live in preallocated rings
 
     def _inflight(self) -> int:
         return len(self.uploading) + sum(len(r[0]) for r in self.running)
@@ -128,6 +145,9 @@ class Server:
                     chip.count += 1
                 ev = torch.cuda.Event()
                 ev.record(self.copy_stream)
+            req.admitted = time.perf_counter()
+            req.out_slot = self.admitted % self.out_slots
+            self.admitted += 1
             self.uploading.append((req, nums, ev))
 
     def _launch(self):
@@ -145,8 +165,9 @@ class Server:
                 slots = chip.stack_slots(num)
                 s = core.DeviceSet(frames=[chip.ring[k] for k in slots], bias=chip.bias,
                                    dark=chip.dark, flat=chip.flat, exptime=chip.slot_t[slots],
-                                   dx=chip.slot_dx[slots], dy=chip.slot_dy[slots])
-                s.alloc_outputs(want_nkept=False)
+                                   dx=chip.slot_dx[slots], dy=chip.slot_dy[slots],
+                                   mean=chip.out[req.out_slot, 0],
+                                   median=chip.out[req.out_slot, 1])
                 sets.append(s)
                 req.outputs.append((s.mean, s.median))
             reqs.append(req)
@@ -163,6 +184,9 @@ class Server:
             self.ws_all.append(ws)
         plan = core.Plan(sets, params, device=self.device, ws=ws)  # pinned plan: no host wait
         plan.launch(self.compute_stream)
+        t = time.perf_counter()
+        for r in reqs:
+            r.launched = t
         done_ev = torch.cuda.Event()
         done_ev.record(self.compute_stream)
         self.running.append((reqs, done_ev, plan, ws))

@@ -75,7 +75,7 @@ def test_server_results_equal_standalone_reductions():
     masters = [tuple(torch.from_numpy(a).cuda() for a in (fs.bias, fs.dark, fs.flat))
                for fs in chips]
     srv = serve.Server(masters, depth=depth, max_inflight=3, interp="bilinear",
-                       hbm_reserve_bytes=0)
+                       hbm_reserve_bytes=0, out_slots=nreq)
     reqs = []
     for r in range(nreq):
         frames = [torch.from_numpy(fs.raw[r]).pin_memory() for fs in chips]
@@ -122,3 +122,27 @@ def test_server_admission_waits_for_hbm():
     srv.reserve = 0
     srv.drain()
     assert len(srv.done) == 1 and srv.status() == 0
+
+
+def test_server_requests_allocate_no_outputs():
+    """Outputs come from the per-chip output ring: after the pools have warmed
+    up, further requests add no device allocation of output size."""
+    nchips, W, H = 2, 96, 80
+    chips = _chip_frames(nchips, W, H, 8, 91)
+    masters = [tuple(torch.from_numpy(a).cuda() for a in (fs.bias, fs.dark, fs.flat))
+               for fs in chips]
+    srv = serve.Server(masters, depth=3, max_inflight=2, hbm_reserve_bytes=0)
+
+    def reqs(lo, hi):
+        return [serve.Request(rid=r, frames=[torch.from_numpy(fs.raw[r]).pin_memory()
+                                             for fs in chips],
+                              dx=np.array([fs.dx[r] for fs in chips]),
+                              dy=np.array([fs.dy[r] for fs in chips])) for r in range(lo, hi)]
+
+    serve.run_poisson(srv, reqs(0, 4), rate_hz=2000.0)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    serve.run_poisson(srv, reqs(4, 8), rate_hz=2000.0)
+    torch.cuda.synchronize()
+    assert srv.status() == 0
+    assert torch.cuda.memory_allocated() - before < 2 * H * W * 4

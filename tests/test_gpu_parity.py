@@ -397,3 +397,17 @@ def test_frame_stats_f64():
     np.testing.assert_allclose(s.cpu().numpy(), h.reshape(4, -1).sum(1), rtol=1e-12)
     np.testing.assert_allclose(q.cpu().numpy(), (h ** 2).reshape(4, -1).sum(1), rtol=1e-12)
     assert (c.cpu().numpy() == 300 * 200).all()
+
+
+def test_frame_stats_f64_wide_rows():
+    """Rows of 4100 pixels (17 values per thread and row) with bright stars and
+    cosmic rays: the per-row FP32 partials with exact error terms keep the
+    FP64 accuracy of the frame sums."""
+    fs = synth.make_set(4100, 24, 3, 2.0, 126, n_stars=400, n_cr=200)
+    d = core.device_set(fs)
+    cal, _, _, _ = core.calibrate(torch.stack(d.frames), d.bias, d.dark, d.flat, fs.exptime)
+    s, q, c = core.frame_stats(cal)
+    h = cal.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(s.cpu().numpy(), h.reshape(3, -1).sum(1), rtol=1e-12)
+    np.testing.assert_allclose(q.cpu().numpy(), (h ** 2).reshape(3, -1).sum(1), rtol=1e-12)
+    assert (c.cpu().numpy() == 4100 * 24).all()
