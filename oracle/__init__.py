@@ -89,6 +89,11 @@ def lib():
             L.oracle_reduce_set.argtypes = [p, i64, i64, i, i, i, p, p, p, i64, p, p, p, i, i,
                                             ctypes.POINTER(ClipParams), i, i64, p, p,
                                             p, p, p, p, p, p]
+            L.oracle_reduce_set_masked.restype = i
+            L.oracle_reduce_set_masked.argtypes = [p, i64, i64, i, i, i, p, p, p, i64, p, p, p,
+                                                   i, i, p, i64, d,
+                                                   ctypes.POINTER(ClipParams), i, i64, p, p,
+                                                   p, p, p, p, p, p]
             _lib = L
     return _lib
 
@@ -197,8 +202,12 @@ def combine_stack(stack, valid, nthreads=1, **kw):
 
 def reduce_set(fs, interp="bilinear", kappa=3.0, max_iter=3, center="mean", ddof=0,
                normalize_flat=False, nthreads=1, pixels=None, want_stack=False,
-               kappa_lo=None, kappa_hi=None):
+               kappa_lo=None, kappa_hi=None, mask=None, saturation=None):
     """Whole frame set -> dict(mean, median, nkept, margin[, stack, valid]).
+
+    ``mask`` ([H,W] uint8, non-zero = bad) and ``saturation`` (raw ADU) mark
+    bad source pixels (Sec. 2.1 bad-pixel masking): a sample whose taps with
+    non-zero weight include a bad pixel is invalid.
 
     ``fs`` is a ``synth.FrameSet``-like object (raw [n,H,W] u16, masters [H,W]
     f32, exptime [n], dx/dy [n]).  ``pixels`` = (xs, ys) restricts the output
@@ -227,9 +236,12 @@ def reduce_set(fs, interp="bilinear", kappa=3.0, max_iter=3, center="mean", ddof
     margin = np.empty(shape)
     stack = np.empty((n, H, W)) if (want_stack and pixels is None) else None
     valid = np.empty((n, H, W), np.uint8) if (want_stack and pixels is None) else None
-    rc = lib().oracle_reduce_set(
+    mk = np.ascontiguousarray(mask, np.uint8) if mask is not None else None
+    rc = lib().oracle_reduce_set_masked(
         _ptr(raw), W, H * W, W, H, n, _ptr(bias), _ptr(dark), _ptr(flat), W, _ptr(t),
         _ptr(dx), _ptr(dy), INTERP.get(interp, interp), int(bool(normalize_flat)),
+        _ptr(mk) if mk is not None else None, W,
+        float(saturation) if saturation is not None else 0.0,
         ctypes.byref(cp), int(nthreads), int(npix), _ptr(px), _ptr(py),
         _ptr(mean), _ptr(med), _ptr(kept), _ptr(margin),
         _ptr(stack) if stack is not None else None,

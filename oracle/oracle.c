@@ -132,7 +132,10 @@ void oracle_spline_coeffs(const double* v, int W, int H, double* c) {
   free(col);
 }
 
-/* Frame data source: a full FP64 frame, or raw + masters calibrated on demand. */
+/* Frame data source: a full FP64 frame, or raw + masters calibrated on demand;
+ * plus the bad-pixel definition (Sec. 2.1 bad-pixel masking): a source pixel
+ * is bad when the mask master marks it or its raw value reaches the
+ * saturation level (mask NULL / saturation <= 0: no such test). */
 typedef struct {
   const double* f;
   const uint16_t* raw;
@@ -140,7 +143,17 @@ typedef struct {
   const float *bias, *dark, *flat;
   int64_t master_pitch;
   double t, flat_norm;
+  const uint8_t* mask;
+  int64_t mask_pitch;
+  double saturation;
 } frame_src;
+
+static int src_bad(const frame_src* s, int64_t i, int64_t j) {
+  if (s->mask && s->mask[j * s->mask_pitch + i]) return 1;
+  if (s->saturation > 0.0 && s->raw && (double)s->raw[j * s->raw_pitch + i] >= s->saturation)
+    return 1;
+  return 0;
+}
 
 static double src_value(const frame_src* s, int W, int64_t i, int64_t j) {
   if (s->f) return s->f[j * W + i];
@@ -174,6 +187,7 @@ static int sample_src(const frame_src* s, int W, int H, int x, int y, double dx,
   if (interp == ORACLE_NEAREST) {
     int64_t i = axis_nearest(i0, fx), j = axis_nearest(j0, fy);
     if (i < 0 || i > W - 1 || j < 0 || j > H - 1) return 0;
+    if (src_bad(s, i, j)) return 0;
     *a = src_value(s, W, i, j);
     return 1;
   }
@@ -185,13 +199,16 @@ static int sample_src(const frame_src* s, int W, int H, int x, int y, double dx,
       for (int p = 0; p < 2; ++p) {
         double w = wx[p] * wy[q];
         if (w == 0.0) continue; /* zero-weight taps are not read */
+        if (src_bad(s, i0 + p, j0 + q)) return 0;
         acc += w * src_value(s, W, i0 + p, j0 + q);
       }
     *a = acc;
     return 1;
   }
   /* cubic spline: a = sum_{i,j} c[i,j] beta3(xs - i) beta3(ys - j) over the
-   * four taps around the position, coefficients mirrored outside the frame */
+   * four taps around the position, coefficients mirrored outside the frame;
+   * a tap with non-zero weight on a bad pixel (after mirroring) invalidates
+   * the sample */
   double acc = 0.0;
   for (int q = 0; q < 4; ++q) {
     int64_t j = j0 - 1 + q;
@@ -199,6 +216,7 @@ static int sample_src(const frame_src* s, int W, int H, int x, int y, double dx,
     for (int p = 0; p < 4; ++p) {
       int64_t i = i0 - 1 + p;
       double w = oracle_bspline3(fx + 1.0 - p) * wyq;
+      if (w != 0.0 && src_bad(s, oracle_mirror(i, W), oracle_mirror(j, H))) return 0;
       acc += w * src_value(s, W, oracle_mirror(i, W), oracle_mirror(j, H));
     }
   }
@@ -328,6 +346,22 @@ int oracle_reduce_set(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stri
                       int64_t npix, const int32_t* px, const int32_t* py,
                       double* mean, double* median, int32_t* nkept, double* min_margin,
                       double* stack, uint8_t* valid) {
+  return oracle_reduce_set_masked(raw, raw_pitch, frame_stride, W, H, n, bias, dark, flat,
+                                  master_pitch, exptime, dx, dy, interp, normalize_flat, NULL, 0,
+                                  0.0, clip, nthreads, npix, px, py, mean, median, nkept,
+                                  min_margin, stack, valid);
+}
+
+int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stride,
+                             int W, int H, int n,
+                             const float* bias, const float* dark, const float* flat,
+                             int64_t master_pitch, const double* exptime,
+                             const double* dx, const double* dy, int interp, int normalize_flat,
+                             const uint8_t* mask, int64_t mask_pitch, double saturation,
+                             const oracle_clip_params* clip, int nthreads,
+                             int64_t npix, const int32_t* px, const int32_t* py,
+                             double* mean, double* median, int32_t* nkept, double* min_margin,
+                             double* stack, uint8_t* valid) {
   if (W < 1 || H < 1 || n < 1 || raw_pitch < W || master_pitch < W) return 1;
   if (interp < ORACLE_NEAREST || interp > ORACLE_SPLINE3) return 1;
 #ifdef _OPENMP
@@ -348,6 +382,9 @@ int oracle_reduce_set(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stri
     src[k].master_pitch = master_pitch;
     src[k].t = exptime[k];
     src[k].flat_norm = flat_norm;
+    src[k].mask = mask;
+    src[k].mask_pitch = mask_pitch;
+    src[k].saturation = saturation;
   }
   if (interp == ORACLE_SPLINE3) {
     /* the spline couples whole rows and columns: solve every frame fully */

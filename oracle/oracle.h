@@ -94,6 +94,21 @@ int oracle_reduce_set(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stri
                       double* mean, double* median, int32_t* nkept, double* min_margin,
                       double* stack, uint8_t* valid);
 
+/* oracle_reduce_set with bad-pixel masking (Sec. 2.1): a source pixel is bad
+ * when mask[j*mask_pitch + i] != 0 (mask may be NULL) or its raw value is at
+ * least `saturation` (<= 0: off); a sample whose taps with non-zero weight
+ * include a bad pixel is invalid and left out of the combine. */
+int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stride,
+                             int W, int H, int n,
+                             const float* bias, const float* dark, const float* flat,
+                             int64_t master_pitch, const double* exptime,
+                             const double* dx, const double* dy, int interp, int normalize_flat,
+                             const uint8_t* mask, int64_t mask_pitch, double saturation,
+                             const oracle_clip_params* clip, int nthreads,
+                             int64_t npix, const int32_t* px, const int32_t* py,
+                             double* mean, double* median, int32_t* nkept, double* min_margin,
+                             double* stack, uint8_t* valid);
+
 #ifdef __cplusplus
 }
 #endif

@@ -338,3 +338,83 @@ def test_reduce_set_aligns_dithered_stars():
     v0 = oracle.calibrate(fs.raw[0], fs.bias, fs.dark, fs.flat, 60.0)
     sl = np.s_[8:-8, 8:-8]
     assert np.std(out["median"][sl]) < np.std(v0[sl])
+
+
+# ------------------------------------------------- bad-pixel masking (Sec. 2.1)
+def _valid(fs, interp, **kw):
+    return oracle.reduce_set(fs, interp=interp, want_stack=True, **kw)["valid"][0]
+
+
+def _geometric(fs, interp):
+    return _valid(fs, interp)
+
+
+def test_mask_footprint_bilinear_by_hand():
+    """One bad pixel at (x=4, y=3) of a 9x7 frame: the invalid outputs are
+    exactly those whose taps with non-zero weight reach it."""
+    mask = np.zeros((7, 9), np.uint8)
+    mask[3, 4] = 1
+    cases = {
+        (0.5, 0.5): [(3, 2), (4, 2), (3, 3), (4, 3)],   # 2x2 taps
+        (0.0, 0.5): [(4, 2), (4, 3)],                   # fx = 0: one column
+        (2.0, -1.0): [(2, 4)],                          # integer move
+        (-0.25, 0.0): [(4, 3), (5, 3)],                 # floor(-0.25) = -1, fx = 0.75
+    }
+    for (dx, dy), bad in cases.items():
+        fs = synth.make_const_set(9, 7, 1, 1500, 1000.0, 0.05, 0.8, 60.0, dx=[dx], dy=[dy])
+        geo = _geometric(fs, "bilinear")
+        got = _valid(fs, "bilinear", mask=mask)
+        want = geo.copy()
+        for x, y in bad:
+            assert geo[y, x], (dx, dy, x, y)
+            want[y, x] = False
+        assert np.array_equal(got, want), (dx, dy)
+
+
+def test_mask_footprint_nearest_and_spline_by_hand():
+    mask = np.zeros((12, 12), np.uint8)
+    mask[6, 5] = 1
+    fs = synth.make_const_set(12, 12, 1, 1500, 1000.0, 0.05, 0.8, 60.0, dx=[0.75], dy=[0.0])
+    # nearest: 0.75 rounds to +1, so output x = 4 reads the bad pixel
+    got = _valid(fs, "nearest", mask=mask)
+    want = _geometric(fs, "nearest")
+    want[6, 4] = False
+    assert np.array_equal(got, want)
+    # spline, fx = 0.75, fy = 0: taps i0-1..i0+2 along x (all non-zero), and
+    # j0-1..j0+1 along y (beta3(2) = 0 drops the fourth): 4 columns x 3 rows
+    got = _valid(fs, "spline3", mask=mask)
+    want = _geometric(fs, "spline3")
+    for y in (5, 6, 7):
+        for x in (3, 4, 5, 6):
+            want[y, x] = False
+    assert np.array_equal(got, want)
+
+
+def test_saturation_level_marks_bad_pixels():
+    fs = synth.make_const_set(9, 7, 1, 1500, 1000.0, 0.05, 0.8, 60.0, dx=[0.5], dy=[0.5])
+    fs.raw[0, 3, 4] = 65535
+    geo = _geometric(fs, "bilinear")
+    got = _valid(fs, "bilinear", saturation=60000.0)
+    want = geo.copy()
+    for x, y in [(3, 2), (4, 2), (3, 3), (4, 3)]:
+        want[y, x] = False
+    assert np.array_equal(got, want)
+    # a level above every raw value, or off, masks nothing
+    assert np.array_equal(_valid(fs, "bilinear", saturation=70000.0), geo)
+    assert np.array_equal(_valid(fs, "bilinear", saturation=0.0), geo)
+
+
+def test_masked_sample_leaves_the_combine():
+    """Three constant frames calibrating to 1000, 2000 and 4000 ADU (flat 0.5,
+    no dark); the third is saturated at one pixel: that pixel combines the
+    first two only."""
+    fs = synth.make_const_set(6, 5, 3, 1500, 1000.0, 0.0, 0.5, 60.0)
+    fs.raw[1] = 2000
+    fs.raw[2] = 3000
+    fs.raw[2, 2, 3] = 3001   # the one saturated sample (level 3001)
+    out = oracle.reduce_set(fs, interp="nearest", saturation=3001.0)
+    assert out["nkept"][2, 3] == 2
+    assert out["median"][2, 3] == 1500.0
+    assert out["mean"][2, 3] == 1500.0
+    assert out["nkept"][0, 0] == 3
+    assert out["median"][0, 0] == 2000.0
