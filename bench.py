@@ -46,6 +46,11 @@ WORKLOADS = {
                            "choose the FP16 scaling; errors against the FP64 oracle",
                       sets=[(4096, 4096, 32)], offset=5.0, interp="bilinear", persistent=False,
                       seed=11486002),
+    "masked": dict(desc="32 frames of 4096x4096 uint16, offsets +-5 px, bilinear shift, a 1% "
+                        "bad-pixel mask master and a saturation level of 60000 ADU (samples "
+                        "touching a bad pixel leave the combine), 3-sigma clip + median",
+                   sets=[(4096, 4096, 32)], offset=5.0, interp="bilinear", persistent=False,
+                   seed=11486002, mask_frac=0.01, saturation=60000.0),
     "batch": dict(desc="64 frame sets, frame counts U{3..40}, sizes from {512^2, 1024^2, 2048^2, "
                        "4096^2}, bilinear: one autotuned persistent launch per frame-count bucket "
                        "replayed from a CUDA graph vs 64 plain per-set launches",
@@ -177,10 +182,15 @@ def cpu_baseline(workload, steps, warmup, nthreads, as_reference=False):
     fs = synth.make_set(Ws, Hs, n, cfg["offset"], cfg["seed"],
                         n_stars=max(1, 200 * Hs * Ws // (H * W)))
     oracle.build()
+    kw = {}
+    if cfg.get("mask_frac"):
+        rng = np.random.default_rng(cfg["seed"])
+        kw = dict(mask=(rng.random((Hs, Ws)) < cfg["mask_frac"]).astype(np.uint8),
+                  saturation=cfg["saturation"])
     times = []
     for i in range(warmup + steps):
         t0 = time.perf_counter()
-        oracle.reduce_set(fs, interp=cfg["interp"], nthreads=nthreads)
+        oracle.reduce_set(fs, interp=cfg["interp"], nthreads=nthreads, **kw)
         dt = time.perf_counter() - t0
         if i >= warmup:
             times.append(dt)
@@ -211,6 +221,7 @@ def run_reference(args, world, rank):
 
 
 def make_device_sets(shapes, cfg, dev, rank):
+    import torch
     from paper_2008_11486_gb300 import core, synth
     sets = []
     for i, (W, H, n) in enumerate(shapes):
@@ -221,6 +232,12 @@ def make_device_sets(shapes, cfg, dev, rank):
                            dy=d["dy"])
         s.alloc_outputs(want_nkept=False)
         s._keep.append(d["raw"])
+        if cfg.get("mask_frac"):
+            g = torch.Generator(device=dev)
+            g.manual_seed(cfg["seed"] + 17 * i + 104729 * rank)
+            s.mask = (torch.rand((H, W), generator=g, device=dev) < cfg["mask_frac"]).to(
+                torch.uint8)
+            s.saturation = cfg["saturation"]
         sets.append(s)
     return sets
 
@@ -374,7 +391,7 @@ def main():
     ap.add_argument("--requests", type=int, default=12, help="served: requests at the nominal rate")
     ap.add_argument("--rate", type=float, default=0.5, help="served: Poisson arrival rate (1/s)")
     args = ap.parse_args()
-    heavy = args.workload in ("deep", "precision", "batch", "served")
+    heavy = args.workload in ("deep", "precision", "batch", "served", "masked")
     if args.steps is None:
         args.steps = 10 if heavy else 2000
     if args.warmup is None:

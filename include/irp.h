@@ -175,6 +175,15 @@ typedef struct {
   const uint32_t* ready_flag;     /* device, nullable: the set's tiles wait until
                                      *ready_flag >= ready_value (bounded wait) */
   uint32_t ready_value;
+  /* Bad-pixel masking (Sec. 2.1, bad-pixel masking before alignment): a source
+   * pixel is bad when mask[y*mask_pitch + x] != 0 or its raw value is at least
+   * `saturation`; a sample whose taps with non-zero weight include a bad pixel
+   * is invalid (left out of the combine, NaN in stack_out).  Nearest and
+   * bilinear only: with the cubic spline a mask or level returns
+   * IRP_ERR_UNSUPPORTED. */
+  const uint8_t* mask;            /* device [H][mask_pitch] uint8, nullable */
+  int64_t mask_pitch;             /* elements (>= W when mask is set) */
+  float saturation;               /* raw ADU; 0 = no saturation test */
 } irp_set;
 
 typedef struct {

@@ -46,7 +46,8 @@ class IrpSet(ctypes.Structure):
                 ("exptime", ctypes.POINTER(ctypes.c_float)),
                 ("bias", c_p), ("dark_rate", c_p), ("flat", c_p), ("master_pitch", c_i64),
                 ("mean_out", c_p), ("median_out", c_p), ("nkept_out", c_p), ("out_pitch", c_i64),
-                ("stack_out", c_p), ("ready_flag", c_p), ("ready_value", ctypes.c_uint32)]
+                ("stack_out", c_p), ("ready_flag", c_p), ("ready_value", ctypes.c_uint32),
+                ("mask", c_p), ("mask_pitch", c_i64), ("saturation", ctypes.c_float)]
 
 
 class ReduceParams(ctypes.Structure):

@@ -137,6 +137,8 @@ class DeviceSet:
     stack: torch.Tensor | None = None
     ready_flag: torch.Tensor | None = None
     ready_value: int = 0
+    mask: torch.Tensor | None = None   # uint8 [H, W] bad-pixel mask (non-zero = bad)
+    saturation: float = 0.0            # raw ADU level marking a pixel bad; 0 = off
     _keep: list = field(default_factory=list)
 
     @property
@@ -164,18 +166,23 @@ class DeviceSet:
         return self
 
 
-def device_set(fs, device="cuda", raw=None, masters=None) -> DeviceSet:
-    """Uploads a synth.FrameSet (or uses the given device raw [n,H,W] / masters)."""
+def device_set(fs, device="cuda", raw=None, masters=None, mask=None,
+               saturation=0.0) -> DeviceSet:
+    """Uploads a synth.FrameSet (or uses the given device raw [n,H,W] / masters);
+    ``mask`` (host or device [H, W] uint8) and ``saturation`` mark bad pixels."""
     if raw is None:
         raw = torch.from_numpy(np.ascontiguousarray(fs.raw)).to(device)
     if masters is None:
         masters = tuple(torch.from_numpy(np.ascontiguousarray(a)).to(device)
                         for a in (fs.bias, fs.dark, fs.flat))
     frames = [raw[k] for k in range(raw.shape[0])]
+    if mask is not None and not isinstance(mask, torch.Tensor):
+        mask = torch.from_numpy(np.ascontiguousarray(mask, dtype=np.uint8)).to(device)
     return DeviceSet(frames=frames, bias=masters[0], dark=masters[1], flat=masters[2],
                      exptime=np.ascontiguousarray(fs.exptime, dtype=np.float32),
                      dx=np.ascontiguousarray(fs.dx, dtype=np.float64),
-                     dy=np.ascontiguousarray(fs.dy, dtype=np.float64))
+                     dy=np.ascontiguousarray(fs.dy, dtype=np.float64),
+                     mask=mask, saturation=float(saturation))
 
 
 def _irp_sets(sets):
@@ -205,6 +212,9 @@ def _irp_sets(sets):
         a.stack_out = s.stack.data_ptr() if s.stack is not None else None
         a.ready_flag = s.ready_flag.data_ptr() if s.ready_flag is not None else None
         a.ready_value = int(s.ready_value)
+        a.mask = s.mask.data_ptr() if s.mask is not None else None
+        a.mask_pitch = s.mask.stride(0) if s.mask is not None else 0
+        a.saturation = float(s.saturation)
     return arr, keep
 
 

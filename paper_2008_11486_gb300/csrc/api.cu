@@ -174,6 +174,8 @@ irp_status check_set(const irp_set& s) {
       !aligned(s.mean_out, 4) || !aligned(s.median_out, 4) || !aligned(s.nkept_out, 2) ||
       !aligned(s.stack_out, 4) || !aligned(s.ready_flag, 4))
     return IRP_ERR_ALIGNMENT;
+  if (s.mask && s.mask_pitch < s.W) return IRP_ERR_INVALID_ARG;
+  if (!(s.saturation >= 0.0f) || std::isinf(s.saturation)) return IRP_ERR_INVALID_ARG;
   for (int k = 0; k < s.n; ++k) {
     if (!s.frames[k]) return IRP_ERR_INVALID_ARG;
     if (!aligned(s.frames[k], 2)) return IRP_ERR_ALIGNMENT;
@@ -300,6 +302,9 @@ irp_status check_params(const irp_set* sets, int nsets, const irp_reduce_params*
   for (int i = 0; i < nsets; ++i) {
     irp_status st = check_set(sets[i]);
     if (st != IRP_OK) return st;
+    // bad-pixel masking is built for the nearest and bilinear stencils
+    if (p->interp == IRP_INTERP_SPLINE3 && (sets[i].mask || sets[i].saturation > 0.0f))
+      return IRP_ERR_UNSUPPORTED;
   }
   std::vector<std::vector<int>> groups;
   group_sets(sets, nsets, p->interp, groups);
@@ -431,6 +436,10 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
       S.mflags = (aligned(s.bias, 16) && aligned(s.dark_rate, 16) && aligned(s.flat, 16) &&
                   s.master_pitch % 4 == 0) ? 1 : 0;
       S.spath = stencil == ST_BSPLINE ? spline_path(s.W, s.H) : 0;
+      S.mask = s.mask;
+      S.mask_pitch = s.mask ? s.mask_pitch : 0;
+      S.saturation = s.saturation > 0.0f ? s.saturation : INFINITY;
+      S.masked = (s.mask || s.saturation > 0.0f) ? 1 : 0;
       S.crow_pitch = S.spath ? crow_pitch(s.W) : 0;
       S.row0 = nrows;
       S.colseg0 = ncolsegs;

@@ -198,6 +198,109 @@ __device__ __forceinline__ bool clip_fixed_dispatch(const float (&s)[N], int m, 
   }
 }
 
+// The same clip for any count m in [N - gap, N] in one code path (for warps
+// whose lanes hold different counts, e.g. under a bad-pixel mask, where the
+// per-count instantiations would run one after another).  Positions that
+// depend on m are picked from short candidate ranges, and the sums add zeros
+// at the positions outside this pixel's halves, so every sum, partial and
+// decision is the same FP32 sequence as in clip_fixed_count<N, m>.
+template <int N>
+__device__ __forceinline__ bool clip_window(const float (&s)[N], int m, const ClipArgs& c,
+                                            CombineOut& o) {
+  constexpr int K = kClipK;
+  constexpr int MLO = N - clip_max_gap<N>();  // smallest count handled
+  static_assert(MLO >= 9, "window clip needs at least 9 samples (constant K per side)");
+  if (m < MLO || m > N) return false;
+  constexpr int HLO = (MLO + 1) / 2, HHI = (N + 1) / 2;
+  static_assert(HHI <= MLO, "lower halves lie below every count");
+  const int h = (m + 1) / 2;
+  float a = s[(MLO - 1) / 2], b = s[MLO / 2];
+#pragma unroll
+  for (int i = (MLO - 1) / 2 + 1; i <= (N - 1) / 2; ++i) a = ((m - 1) / 2 == i) ? s[i] : a;
+#pragma unroll
+  for (int i = MLO / 2 + 1; i <= N / 2; ++i) b = (m / 2 == i) ? s[i] : b;
+  const float r = a;
+  float SL[K + 1], QL[K + 1], SU[K + 1], QU[K + 1], U[K + 1];
+  {
+    float S = 0.0f, Q = 0.0f;
+#pragma unroll
+    for (int j = HHI - 1; j >= 0; --j) {
+      float d = __fsub_rn(s[j], r);
+      if (j >= HLO) d = (j < h) ? d : 0.0f;
+      S = __fadd_rn(S, d);
+      Q = __fmaf_rn(d, d, Q);
+      if (j <= K) {
+        SL[j] = S;
+        QL[j] = Q;
+      }
+    }
+  }
+  {
+    float S = 0.0f, Q = 0.0f;
+#pragma unroll
+    for (int k = 0; k <= K; ++k) SU[k] = QU[k] = 0.0f;
+#pragma unroll
+    for (int j = HLO; j < N; ++j) {
+      float d = __fsub_rn(s[j], r);
+      const bool in = (j >= HHI || j >= h) && (j < MLO || j < m);
+      d = in ? d : 0.0f;
+      S = __fadd_rn(S, d);
+      Q = __fmaf_rn(d, d, Q);
+#pragma unroll
+      for (int k = 0; k <= K; ++k) {
+        if (j >= MLO - 1 - k && j <= N - 1 - k) {
+          const bool at = j == m - 1 - k;
+          SU[k] = at ? S : SU[k];
+          QU[k] = at ? Q : QU[k];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k <= K; ++k) {
+    float u = s[MLO - 1 - k];
+#pragma unroll
+    for (int j = MLO - k; j <= N - 1 - k; ++j) u = (j == m - 1 - k) ? s[j] : u;
+    U[k] = u;
+  }
+  int nlo = 0, nhi = 0;
+#pragma unroll 1
+  for (int it = 0; it < c.max_iter; ++it) {
+    const int mm = m - nlo - nhi;
+    if (mm - c.ddof <= 0) break;
+    const float S = __fadd_rn(select_at(SL, nlo), select_at(SU, nhi));
+    const float Q = __fadd_rn(select_at(QL, nlo), select_at(QU, nhi));
+    const float cd = __fdiv_rn(S, (float)mm);
+    float ss = __fmaf_rn(cd, __fmaf_rn((float)mm, cd, -2.0f * S), Q);
+    ss = fmaxf(ss, 0.0f);
+    const float sigma = sqrtf(__fdiv_rn(ss, (float)(mm - c.ddof)));
+    if (!(sigma > 0.0f)) break;
+    const float tlo = c.kappa_lo * sigma, thi = c.kappa_hi * sigma;
+    int clo = 0, chi = 0;
+#pragma unroll
+    for (int j = 0; j <= K; ++j) clo += (-__fsub_rn(__fsub_rn(s[j], r), cd) > tlo) ? 1 : 0;
+#pragma unroll
+    for (int k = 0; k <= K; ++k) chi += (__fsub_rn(__fsub_rn(U[k], r), cd) > thi) ? 1 : 0;
+    if (clo > K || chi > K) return false;
+    clo = max(clo, nlo);
+    chi = max(chi, nhi);
+    if (clo == nlo && chi == nhi) break;
+    nlo = clo;
+    nhi = chi;
+  }
+  const int mm = m - nlo - nhi;
+  const float S = __fadd_rn(select_at(SL, nlo), select_at(SU, nhi));
+  o.median = __fmul_rn(__fadd_rn(a, b), 0.5f);
+  o.kept = mm;
+  o.mean = __fadd_rn(r, __fdiv_rn(S, (float)mm));
+  float lv = s[0];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) lv = (nlo == j) ? s[j] : lv;
+  o.lo_val = lv;
+  o.hi_val = select_at(U, nhi);
+  return true;
+}
+
 // s: sorted samples, m valid.  Returns the sigma-clipped mean, the median of
 // all valid samples, the survivor count and the survivor value range.
 template <int N>
@@ -212,7 +315,22 @@ __device__ __forceinline__ CombineOut combine_sorted(const float (&s)[N], int m,
     o.hi_val = 0.0f;
     return o;
   }
-  if (c.center == 0 && clip_fixed_dispatch<N, 0>(s, m, c, o)) return o;
+  if (c.center == 0) {
+    if constexpr (N >= 16) {
+      // lanes of this warp holding different counts share one code path
+      const unsigned act = __activemask();
+      if (__match_any_sync(act, m) != act) {
+        float t[N];  // a copy for the count-generic path
+#pragma unroll
+        for (int j = 0; j < N; ++j) t[j] = s[j];
+        if (clip_window<N>(t, m, c, o)) return o;
+      } else if (clip_fixed_dispatch<N, 0>(s, m, c, o)) {
+        return o;
+      }
+    } else if (clip_fixed_dispatch<N, 0>(s, m, c, o)) {
+      return o;
+    }
+  }
   const float a = select_at(s, (m - 1) >> 1);
   const float b = select_at(s, m >> 1);
   o.median = __fmul_rn(__fadd_rn(a, b), 0.5f);

@@ -50,7 +50,7 @@ struct FrameDesc {
 };
 static_assert(sizeof(FrameDesc) == 128, "FrameDesc layout");
 
-// One frame set (192 bytes).
+// One frame set (224 bytes).
 struct SetDesc {
   int32_t W, H, n, frame0;       // frame0: index of frame 0 in the frame table
   int64_t src_pitch;             // elements of the frames' element type
@@ -79,8 +79,13 @@ struct SetDesc {
   int32_t colseg0;               // first column-pass work item
   int32_t mflags;                // bit 0: masters 16-byte aligned, pitch of 4k elements
   int32_t spath;                 // spline prefilter: 0 tiled, 1 row + column passes
+  const uint8_t* mask;           // bad-pixel mask master or null
+  int64_t mask_pitch;
+  float saturation;              // raw level marking a pixel bad (+inf: none)
+  int32_t masked;                // 1: mask or saturation level in use
+  int32_t pad[2];
 };
-static_assert(sizeof(SetDesc) == 192, "SetDesc layout");
+static_assert(sizeof(SetDesc) == 224, "SetDesc layout");
 
 struct PlanHeader {
   int32_t nsets, nframes, nitems, stencil;

@@ -334,7 +334,10 @@ __device__ __forceinline__ void finish_masters(const SetDesc& S, int tx0, int ty
     for (int c = lane; c < mw; c += 32) {
       const int gx = gx0 + c;
       float* d = (float*)(s_mast + r * mw + c);
-      if (yin && gx >= 0 && gx < S.W) d[2] = inv_flat(d[2], flat_norm, status);
+      const bool in = yin && gx >= 0 && gx < S.W;
+      if (in) d[2] = inv_flat(d[2], flat_norm, status);
+      // fourth component: 1 for a pixel the bad-pixel mask marks
+      d[3] = (in && S.mask && __ldg(S.mask + (int64_t)gy * S.mask_pitch + gx)) ? 1.0f : 0.0f;
     }
   }
 }
@@ -359,6 +362,10 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
   const float4 w = *(const float4*)&F.fx;   // fx, fy, t
   const int4 gy = *(const int4*)&F.vy0;     // vy0, vyw, ox, oy
   float v[SS::rows];
+  bool bad[SS::rows];  // bad source pixels (mask or saturation), general mode only
+#pragma unroll
+  for (int r = 0; r < SS::rows; ++r) bad[r] = false;
+  const bool masked = MODE == kGeneral && S.masked;
   if (SRC == SRC_RAW) {
     const uint16_t* raw = (const uint16_t*)st + lane + g.x;
     if (MODE == kFast || mrow > 0) {
@@ -366,7 +373,9 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
 #pragma unroll
       for (int r = 0; r < SS::rows; ++r) {
         const float4 m = mp[r * mrow];
-        v[r] = calibrate_px(raw[r * SS::elems], m.x, m.y, w.z, m.z);
+        const uint16_t q = raw[r * SS::elems];
+        v[r] = calibrate_px(q, m.x, m.y, w.z, m.z);
+        if (MODE == kGeneral) bad[r] = masked && (m.w != 0.0f || (float)q >= S.saturation);
       }
     } else {  // offsets too spread for a union window: masters from global memory
       const int gx = tx0 + gy.z + lane;
@@ -374,13 +383,17 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
       for (int r = 0; r < SS::rows; ++r) {
         const int yy = wy0 + gy.w + r;
         float b = 0.0f, d = 0.0f, rf = 0.0f;
+        bool mb = false;
         if (gx >= 0 && gx < S.W && yy >= 0 && yy < S.H) {
           const int64_t o = (int64_t)yy * S.master_pitch + gx;
           b = __ldg(S.bias + o);
           d = __ldg(S.dark + o);
           rf = inv_flat(__ldg(S.flat + o), flat_norm, status);
+          mb = S.mask && __ldg(S.mask + (int64_t)yy * S.mask_pitch + gx);
         }
-        v[r] = calibrate_px(raw[r * SS::elems], b, d, w.z, rf);
+        const uint16_t q = raw[r * SS::elems];
+        v[r] = calibrate_px(q, b, d, w.z, rf);
+        bad[r] = masked && (mb || (float)q >= S.saturation);
       }
     }
   } else {
@@ -439,9 +452,28 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
   }
   const float kInf = __int_as_float(0x7f800000);
   const bool xv = in_range(x, g.z, g.w);
+  // a sample is also invalid when a tap with non-zero weight is a bad pixel
+  bool badq[PY];
+#pragma unroll
+  for (int q = 0; q < PY; ++q) badq[q] = false;
+  if (SRC == SRC_RAW && masked) {
+    if (STENCIL == ST_NEAREST) {
+#pragma unroll
+      for (int q = 0; q < PY; ++q) badq[q] = bad[q];
+    } else {
+      bool bh[SS::rows];
+#pragma unroll
+      for (int r = 0; r < SS::rows; ++r) {
+        const int right = __shfl_down_sync(0xffffffffu, (int)bad[r], 1);
+        bh[r] = bad[r] | ((w.x > 0.0f) & (right != 0));
+      }
+#pragma unroll
+      for (int q = 0; q < PY; ++q) badq[q] = bh[q] | ((w.y > 0.0f) & bh[q + 1]);
+    }
+  }
 #pragma unroll
   for (int q = 0; q < PY; ++q) {
-    const bool ok = xv & in_range(wy0 + q, gy.x, gy.y);
+    const bool ok = xv & in_range(wy0 + q, gy.x, gy.y) & !badq[q];
     sk[q * 32] = ok ? a[q] : kInf;
     mq[q] += ok ? 1 : 0;
   }
@@ -449,7 +481,7 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
 #pragma unroll
     for (int q = 0; q < PY; ++q) {
       const int y = wy0 + q;
-      const bool ok = xv & in_range(y, gy.x, gy.y);
+      const bool ok = xv & in_range(y, gy.x, gy.y) & !badq[q];
       if (stack_lane && y < H)
         stack_out[((int64_t)k * H + y) * out_pitch + x] = ok ? a[q] : __int_as_float(0x7fc00000);
     }
@@ -524,7 +556,7 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
   // the tile's class: interior tiles (every frame aligned, staged without
   // bounds checks and valid at every pixel) take the branch-free loop
   const bool tile_fast = __syncthreads_and(rec_fast) && (SRC != SRC_RAW || mwin_w > 0) &&
-                         !stack_out;
+                         !stack_out && !S.masked;
 
   const FrameRec* frames = s_rec;
   // prologue: frames 0 .. kStages-2 in flight

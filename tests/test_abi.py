@@ -98,6 +98,10 @@ def test_reduce_set_validation_codes(L):
     s = _set()
     s._keep[1][1] = np.nan  # non-finite offset
     assert _reduce(L, [s], _params()) == 1
+    assert _reduce(L, [_set(mask=FAKE, mask_pitch=10)], _params()) == 1    # mask pitch < W
+    assert _reduce(L, [_set(saturation=-1.0)], _params()) == 1              # negative level
+    assert _reduce(L, [_set(mask=FAKE, mask_pitch=64)], _params(interp=2)) == 4  # spline
+    assert _reduce(L, [_set(saturation=6e4)], _params(interp=2)) == 4
 
 
 def test_workspace_size_accounts_for_spline_coefficients(L):

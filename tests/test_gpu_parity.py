@@ -411,3 +411,31 @@ def test_frame_stats_f64_wide_rows():
     np.testing.assert_allclose(s.cpu().numpy(), h.reshape(3, -1).sum(1), rtol=1e-12)
     np.testing.assert_allclose(q.cpu().numpy(), (h ** 2).reshape(3, -1).sum(1), rtol=1e-12)
     assert (c.cpu().numpy() == 4100 * 24).all()
+
+
+# ------------------------------------------------ bad-pixel masking (Sec. 2.1)
+@pytest.mark.parametrize("interp", ["nearest", "bilinear"])
+@pytest.mark.parametrize("offset", [4.0, 40.0])   # union master window / masters from HBM
+def test_masked_reduction_matches_oracle(interp, offset):
+    fs = synth.make_set(101, 77, 14, offset, 1313, n_stars=40, n_cr=10)
+    rng = np.random.default_rng(5)
+    mask = (rng.random((77, 101)) < 0.02).astype(np.uint8)
+    sat = 20000.0
+    s = core.device_set(fs, mask=mask, saturation=sat).alloc_outputs(want_stack=True)
+    ws = core.reduce_sets([s], core.reduce_params(interp, core.clip_params(2.5, 3)))
+    assert core.sync_status(ws) == 0
+    ref = oracle.reduce_set(fs, interp=interp, kappa=2.5, mask=mask, saturation=sat,
+                            want_stack=True)
+    st = s.stack.cpu().numpy()
+    gvalid = ~np.isnan(st)
+    assert np.array_equal(gvalid, ref["valid"]), "masked validity differs"
+    assert (~ref["valid"]).sum() > (~oracle.reduce_set(fs, interp=interp, want_stack=True)["valid"]).sum()
+    tol = sample_tolerance(fs, interp, oracle)
+    compare("masked stack", st, np.where(ref["valid"], ref["stack"], np.nan), tol)
+    kept = s.nkept.cpu().numpy().astype(np.int32)
+    m = (ref["margin"] >= 1e-3) & (kept == ref["nkept"])
+    assert m.mean() > 0.99
+    samp = np.max(np.where(ref["valid"], tol, 0.0), axis=0)
+    compare("masked mean", s.mean.cpu().numpy(), ref["mean"], mean_tolerance(ref["mean"]) + samp, m)
+    compare("masked median", s.median.cpu().numpy(), ref["median"],
+            mean_tolerance(ref["median"]) + samp)
