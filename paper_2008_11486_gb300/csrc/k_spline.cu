@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256, 2)
   // masters: [row][bias, dark, rf][MQ][32 lanes] float4 (lane l holds columns
   // E l .. E l + E - 1, chunk i = columns E l + 4i .. + 3): conflict-free
   float4* s_m = smem4;
-  // raw: per warp two stages of [RQ][32 lanes] uint4
+  // raw: per warp kRowStages stages of [RQ][32 lanes] uint4
   uint4* s_raw = (uint4*)(smem4 + RB * 3 * MQ * 32);
   const PlanView P = make_view(inl, plan_dev);
   const int item = blockIdx.x;
@@ -113,22 +113,37 @@ __global__ void __launch_bounds__(256, 2)
     }
     cp_async_commit();
   }
+  // the chunk's frame fields, read once per CTA instead of once per task
+  __shared__ const uint16_t* s_src[kRowGroup];
+  __shared__ float* s_crow[kRowGroup];
+  __shared__ float s_t[kRowGroup];
+  __shared__ int s_flags[kRowGroup];
+  if (threadIdx.x < nk) {
+    const FrameDesc& F = P.frames[S.frame0 + k0 + threadIdx.x];
+    s_src[threadIdx.x] = (const uint16_t*)F.src;
+    s_crow[threadIdx.x] = F.crow;
+    s_t[threadIdx.x] = F.t;
+    s_flags[threadIdx.x] = F.flags;
+  }
+  __syncthreads();
   // 2. the warp's tasks: (row, frame) pairs of the block, t = warp + 8 m
   const int ntask = nr * nk;
-  uint4* stage = s_raw + warp * 2 * RQ * 32;
+  uint4* stage = s_raw + warp * kRowStages * RQ * 32;
   auto issue = [&](int t, int slot) {
     const int rr = t / nk, f = t - rr * nk;
-    const FrameDesc& F = P.frames[S.frame0 + k0 + f];
-    const bool vec = (F.flags & 1) && x0 + E <= W;
-    const uint16_t* raw = (const uint16_t*)F.src + (int64_t)(y0 + rr) * S.src_pitch + x0;
+    const bool vec = (s_flags[f] & 1) && x0 + E <= W;
+    const uint16_t* raw = s_src[f] + (int64_t)(y0 + rr) * S.src_pitch + x0;
 #pragma unroll
     for (int i = 0; i < RQ; ++i)
       cp_async16_if(vec, stage + (slot * RQ + i) * 32 + lane, raw + 8 * i, 16);
   };
-  if (warp < ntask) issue(warp, 0);
-  cp_async_commit();
+#pragma unroll
+  for (int q = 0; q < kRowStages - 1; ++q) {
+    if (warp + 8 * q < ntask) issue(warp + 8 * q, q);
+    cp_async_commit();
+  }
   // 3. masters landed: flat -> flat_norm / flat in place
-  cp_async_wait<1>();
+  cp_async_wait<kRowStages - 1>();
   __syncthreads();
   {
     const float flat_norm = S.flat_sum ? (float)(*S.flat_sum / ((double)W * H)) : 1.0f;
@@ -146,21 +161,20 @@ __global__ void __launch_bounds__(256, 2)
   int m = 0;
 #pragma unroll 1
   for (int t = warp; t < ntask; t += 8, ++m) {
-    if (t + 8 < ntask) issue(t + 8, (m + 1) & 1);
+    if (t + 8 * (kRowStages - 1) < ntask) issue(t + 8 * (kRowStages - 1), (m + kRowStages - 1) % kRowStages);
     cp_async_commit();
-    cp_async_wait<1>();
+    cp_async_wait<kRowStages - 1>();
     __syncwarp();
     const int rr = t / nk, f = t - rr * nk;
     const int y = y0 + rr;
-    const FrameDesc& F = P.frames[S.frame0 + k0 + f];
-    const float tk = F.t;
-    const bool vec = (F.flags & 1) && x0 + E <= W;
+    const float tk = s_t[f];
+    const bool vec = (s_flags[f] & 1) && x0 + E <= W;
     const float4* mb = s_m + (rr * 3 + 0) * MQ * 32 + lane;
     const float4* md = mb + MQ * 32;
     const float4* mr = md + MQ * 32;
     float v[E];
     if (vec) {
-      const uint4* rs = stage + ((m & 1) * RQ) * 32 + lane;
+      const uint4* rs = stage + ((m % kRowStages) * RQ) * 32 + lane;
 #pragma unroll
       for (int i = 0; i < RQ; ++i) {
         const uint4 qq = rs[i * 32];
@@ -178,7 +192,7 @@ __global__ void __launch_bounds__(256, 2)
                                        bb[e], dd[e], tk, rf[e]);
       }
     } else {
-      const uint16_t* raw = (const uint16_t*)F.src + (int64_t)y * S.src_pitch;
+      const uint16_t* raw = s_src[f] + (int64_t)y * S.src_pitch;
 #pragma unroll
       for (int i = 0; i < MQ; ++i) {
         const float4 b = mb[i * 32], d = md[i * 32], r = mr[i * 32];
@@ -191,43 +205,66 @@ __global__ void __launch_bounds__(256, 2)
         }
       }
     }
-    // causal recursion within the lane, then the carry from the left lane
+    // causal recursion within the lane, as two independent half-lane chains
+    // joined exactly (y+[h + j] gets z1^(j+1) y+[h - 1]), then the carry
+    // from the left lane
+    constexpr int Hh = E / 2;
     float yp[E];
     {
-      float acc = 0.0f;
+      float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
-      for (int j = 0; j < E; ++j) {
-        acc = __fmaf_rn(kZ1, acc, v[j]);
-        yp[j] = acc;
+      for (int j = 0; j < Hh; ++j) {
+        a0 = __fmaf_rn(kZ1, a0, v[j]);
+        a1 = __fmaf_rn(kZ1, a1, v[Hh + j]);
+        yp[j] = a0;
+        yp[Hh + j] = a1;
       }
-      float carry = __shfl_up_sync(0xffffffffu, yp[E - 1], 1);
-      if (lane == 0) {  // y+[-1] = sum_k z1^k v[1+k] (mirror)
-        float mm = 0.0f;
 #pragma unroll
-        for (int j = E - 1; j >= 1; --j) mm = __fmaf_rn(kZ1, mm, v[j]);
-        carry = mm;
+      for (int j = 0; j < Hh; ++j) yp[Hh + j] = __fmaf_rn(zp.p[j + 1], a0, yp[Hh + j]);
+      float carry = __shfl_up_sync(0xffffffffu, yp[E - 1], 1);
+      if (lane == 0) {  // y+[-1] = sum_k z1^k v[1+k] (mirror), as two chains
+        float lo = 0.0f, hi = 0.0f;
+#pragma unroll
+        for (int j = Hh - 1; j >= 1; --j) lo = __fmaf_rn(kZ1, lo, v[j]);
+#pragma unroll
+        for (int j = E - 1; j >= Hh; --j) hi = __fmaf_rn(kZ1, hi, v[j]);
+        carry = __fmaf_rn(zp.p[Hh - 1], hi, lo);
       }
 #pragma unroll
       for (int j = 0; j < E; ++j) yp[j] = __fmaf_rn(zp.p[j + 1], carry, yp[j]);
     }
-    float* out = F.crow + (int64_t)y * S.crow_pitch + x0;
+    float* out = s_crow[f] + (int64_t)y * S.crow_pitch + x0;
     if (W % E == 0) {
       // the frame ends at the end of lane `last`: y-[W-1] = y+[W-1] is set at a
       // fixed position, and the lanes past it (zeros) pass no carry
       const int last = W / E - 1;
       const bool is_last = lane == last;
-      float acc = is_last ? yp[E - 1] : v[E - 1];
+      // the lane's value at its left end, as two half-lane chains
+      float hi = is_last ? yp[E - 1] : v[E - 1], lo = 0.0f;
 #pragma unroll
-      for (int j = E - 2; j >= 0; --j) acc = __fmaf_rn(kZ1, acc, v[j]);
-      float carry = __shfl_down_sync(0xffffffffu, acc, 1);
+      for (int t = 1; t < Hh; ++t) hi = __fmaf_rn(kZ1, hi, v[E - 1 - t]);
+#pragma unroll
+      for (int j = Hh - 1; j >= 0; --j) lo = __fmaf_rn(kZ1, lo, v[j]);
+      float carry = __shfl_down_sync(0xffffffffu, __fmaf_rn(zp.p[Hh], hi, lo), 1);
       if (lane >= last) carry = 0.0f;
       if (lane <= last) {
-        acc = carry;
+        // upper half from the carry (emitting its coefficients) and lower half
+        // from zero, side by side; then the lower half gets z1^(h-j) y-[h]
+        float ah = carry, al = 0.0f, ml[Hh];
         float c4[4];
 #pragma unroll
-        for (int j = E - 1; j >= 0; --j) {
-          acc = (j == E - 1 && is_last) ? yp[j] : __fmaf_rn(kZ1, acc, v[j]);
-          c4[j & 3] = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], acc), v[j]));
+        for (int t = 0; t < Hh; ++t) {
+          const int j = E - 1 - t;
+          ah = (j == E - 1 && is_last) ? yp[j] : __fmaf_rn(kZ1, ah, v[j]);
+          al = __fmaf_rn(kZ1, al, v[Hh - 1 - t]);
+          ml[Hh - 1 - t] = al;
+          c4[j & 3] = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], ah), v[j]));
+          if ((j & 3) == 0) *(float4*)(out + j) = make_float4(c4[0], c4[1], c4[2], c4[3]);
+        }
+#pragma unroll
+        for (int j = Hh - 1; j >= 0; --j) {
+          const float m = __fmaf_rn(zp.p[Hh - j], ah, ml[j]);
+          c4[j & 3] = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], m), v[j]));
           if ((j & 3) == 0) *(float4*)(out + j) = make_float4(c4[0], c4[1], c4[2], c4[3]);
         }
       }
@@ -263,7 +300,7 @@ __global__ void __launch_bounds__(256, 2)
         }
       }
     }
-    __syncwarp();  // this stage is refilled two tasks later
+    __syncwarp();  // this stage is refilled kRowStages tasks later
   }
   cp_async_wait<0>();
 }
