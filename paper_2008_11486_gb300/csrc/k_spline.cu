@@ -73,6 +73,9 @@ __global__ void __launch_bounds__(256, 2)
   float4* s_m = smem4;
   // raw: per warp kRowStages stages of [RQ][32 lanes] uint4
   uint4* s_raw = (uint4*)(smem4 + RB * 3 * MQ * 32);
+  // E = 32: per-warp output row, chunk c = 8 l + i of lane l at 8 l + (i ^ (l & 7))
+  // (conflict-free for the lane-wise writes and the row-order reads)
+  float4* s_out = (float4*)(s_raw + 8 * kRowStages * RQ * 32) + (threadIdx.x >> 5) * 256;
   const PlanView P = make_view(inl, plan_dev);
   const int item = blockIdx.x;
   if (item >= P.h->nrows) return;
@@ -247,6 +250,13 @@ __global__ void __launch_bounds__(256, 2)
       for (int j = Hh - 1; j >= 0; --j) lo = __fmaf_rn(kZ1, lo, v[j]);
       float carry = __shfl_down_sync(0xffffffffu, __fmaf_rn(zp.p[Hh], hi, lo), 1);
       if (lane >= last) carry = 0.0f;
+      // the lane's coefficients go to the row buffer (E = 32) or straight out
+      auto put = [&](int j, float4 c) {
+        if (E == 32)
+          s_out[8 * lane + ((j >> 2) ^ (lane & 7))] = c;
+        else
+          *(float4*)(out + j) = c;
+      };
       if (lane <= last) {
         // upper half from the carry (emitting its coefficients) and lower half
         // from zero, side by side; then the lower half gets z1^(h-j) y-[h]
@@ -259,14 +269,27 @@ __global__ void __launch_bounds__(256, 2)
           al = __fmaf_rn(kZ1, al, v[Hh - 1 - t]);
           ml[Hh - 1 - t] = al;
           c4[j & 3] = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], ah), v[j]));
-          if ((j & 3) == 0) *(float4*)(out + j) = make_float4(c4[0], c4[1], c4[2], c4[3]);
+          if ((j & 3) == 0) put(j, make_float4(c4[0], c4[1], c4[2], c4[3]));
         }
 #pragma unroll
         for (int j = Hh - 1; j >= 0; --j) {
           const float m = __fmaf_rn(zp.p[Hh - j], ah, ml[j]);
           c4[j & 3] = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], m), v[j]));
-          if ((j & 3) == 0) *(float4*)(out + j) = make_float4(c4[0], c4[1], c4[2], c4[3]);
+          if ((j & 3) == 0) put(j, make_float4(c4[0], c4[1], c4[2], c4[3]));
         }
+      }
+      if (E == 32) {
+        // the row in order: chunk g = 32 k + lane, contiguous per instruction
+        __syncwarp();
+        float* row = s_crow[f] + (int64_t)y * S.crow_pitch;
+        const int nchunk = W / 4;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int g = 32 * k + lane;
+          const int l = g >> 3, i = g & 7;
+          if (g < nchunk) *(float4*)(row + 4 * g) = s_out[8 * l + (i ^ (l & 7))];
+        }
+        __syncwarp();
       }
     } else {
       // anti-causal recursion: starts at W-1 with y-[W-1] = y+[W-1] (mirror).

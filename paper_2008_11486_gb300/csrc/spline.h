@@ -13,9 +13,11 @@ constexpr int kRowGroup = 16;       // frames per row-pass CTA
 // block's master rows as float4 plus two raw stages per warp).
 constexpr int kRowStages = 2;       // raw-row ring per warp (tasks in flight + 1)
 __host__ __device__ constexpr int row_block(int E) { return E == 32 ? 4 : 2; }
+// E = 32 also stages each output row per warp, so that it leaves in
+// contiguous 512-byte stores.
 __host__ __device__ constexpr size_t rows_smem_bytes(int E) {
   return (size_t)row_block(E) * 3 * (E / 4) * 32 * 16 +
-         (size_t)8 * kRowStages * (E / 8) * 32 * 16;
+         (size_t)8 * kRowStages * (E / 8) * 32 * 16 + (E == 32 ? (size_t)8 * 8 * 32 * 16 : 0);
 }
 
 cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_dev, int nrows,
