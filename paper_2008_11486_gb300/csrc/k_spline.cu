@@ -132,13 +132,18 @@ __global__ void __launch_bounds__(256, 2)
   // 2. the warp's tasks: (row, frame) pairs of the block, t = warp + 8 m
   const int ntask = nr * nk;
   uint4* stage = s_raw + warp * kRowStages * RQ * 32;
+  // the row's 16-byte chunks in order (contiguous per instruction), each put
+  // where its owner lane reads it: chunk c of lane c / RQ at (c % RQ) * 32 + c / RQ
   auto issue = [&](int t, int slot) {
     const int rr = t / nk, f = t - rr * nk;
-    const bool vec = (s_flags[f] & 1) && x0 + E <= W;
-    const uint16_t* raw = s_src[f] + (int64_t)(y0 + rr) * S.src_pitch + x0;
+    const bool aligned_f = s_flags[f] & 1;
+    const uint16_t* raw = s_src[f] + (int64_t)(y0 + rr) * S.src_pitch;
 #pragma unroll
-    for (int i = 0; i < RQ; ++i)
-      cp_async16_if(vec, stage + (slot * RQ + i) * 32 + lane, raw + 8 * i, 16);
+    for (int k = 0; k < RQ; ++k) {
+      const int c = 32 * k + lane, lc = c / RQ, ic = c - lc * RQ;
+      cp_async16_if(aligned_f && (lc + 1) * E <= W, stage + (slot * RQ + ic) * 32 + lc,
+                    raw + 8 * c, 16);
+    }
   };
 #pragma unroll
   for (int q = 0; q < kRowStages - 1; ++q) {
