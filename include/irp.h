@@ -17,7 +17,8 @@
  *     in ELEMENTS of the buffer's own type.
  *   - Every device buffer is allocated and owned by the caller.  Host arrays
  *     (offsets, exposure times, frame pointer tables) are read during the call
- *     only.  No entry point allocates device or host memory.
+ *     only.  No entry point allocates device memory; irp_reduce_set builds its
+ *     launch plan in a temporary host buffer, irp_plan_encode in the caller's.
  *   - Offsets: output pixel (x, y) samples frame k at (x + dx[k], y + dy[k]).
  *     The offset is split as dx = ix + fx, ix = floor(dx), fx in [0, 1).
  *   - A sample is valid iff every tap with non-zero weight lies inside the
