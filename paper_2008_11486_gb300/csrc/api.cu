@@ -445,7 +445,7 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
       S.colseg0 = ncolsegs;
       if (S.spath) {
         nrows += ((s.n + kRowGroup - 1) / kRowGroup) * ((s.H + row_block(row_e) - 1) / row_block(row_e));
-        ncolsegs += s.n * ((s.W + 28) / 29) * ((s.H + 255) / 256);
+        ncolsegs += s.n * ((s.W + 28) / 29) * ((s.H + kColRows - 1) / kColRows);
       }
       int oxmin = INT32_MAX, oxmax = INT32_MIN, oymin = INT32_MAX, oymax = INT32_MIN;
       for (int k = 0; k < s.n; ++k) {

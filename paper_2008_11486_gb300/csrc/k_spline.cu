@@ -17,7 +17,7 @@
 // y-), which is exact up to z1^E (< 5e-19 for E >= 32).  The mirror boundary
 // is exact: y+[-1] is the sum of z1^k v[1+k], and y-[W-1] = y+[W-1].
 //
-// Column pass: one CTA per (frame, 29 output columns, 256 rows); lane =
+// Column pass: one CTA per (frame, 29 output columns, kColRows rows); lane =
 // column, warp = 32 consecutive rows.  Lane l solves the source column the
 // frame's first horizontal tap of output column l falls on.  Each warp runs
 // both recursions over its rows from zero, the warps exchange their ends
@@ -334,13 +334,13 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 
-constexpr int kColRows = 256;  // rows per column-pass CTA: 8 warps x 32 rows
+constexpr int kColWarps = kColRows / 32;  // one warp per 32 rows
 constexpr int kColWarm = 16;   // warm-up rows above and below the CTA's rows
 constexpr int kColOut = 29;    // output columns per CTA: lanes 0..28 (taps reach lane + 3)
 
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(kColRows, kColRows < 512 ? 512 / kColRows : 1)
     k_spline_cols(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
-  __shared__ float s_c[8][32], s_a[8][32];  // each warp's local recursion ends
+  __shared__ float s_c[kColWarps][32], s_a[kColWarps][32];  // each warp's recursion ends
   const PlanView P = make_view(inl, plan_dev);
   const int item = blockIdx.x;
   if (item >= P.h->ncolsegs) return;
@@ -379,10 +379,11 @@ __global__ void __launch_bounds__(256, 2)
   };
   // the warp's 32 rows and, for the CTA's first / last warp, the 16 warm-up
   // rows above / below, all requested before the first is used
-  const bool edge_warp = warp == 0 || warp == 7;
+  const bool edge_warp = warp == 0 || warp == kColWarps - 1;
   const int yw = warp == 0 ? y0 - kColWarm : y0 + 32;
   float v[32], w[kColWarm];
-  const int ylo = y0 - (warp == 0 ? kColWarm : 0), yhi = y0 + 32 + (warp == 7 ? kColWarm : 0);
+  const int ylo = y0 - (warp == 0 ? kColWarm : 0),
+            yhi = y0 + 32 + (warp == kColWarps - 1 ? kColWarm : 0);
   if (ylo >= 0 && yhi <= H) {
     const float* p = in + (int64_t)y0 * ip;
 #pragma unroll
@@ -427,13 +428,13 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
     for (int j = 0; j < kColWarm; ++j) cin = __fmaf_rn(kZ1, cin, w[j]);
   }
-  if (warp == 7) {
+  if (warp == kColWarps - 1) {
 #pragma unroll
     for (int j = kColWarm - 1; j >= 0; --j) ain = __fmaf_rn(kZ1, ain, w[j]);
   }
   __syncthreads();
   if (warp > 0) cin = s_c[warp - 1][lane];
-  if (warp < 7) ain = s_a[warp + 1][lane];
+  if (warp < kColWarps - 1) ain = s_a[warp + 1][lane];
   if (y0 >= H) return;  // (after the last shuffle partner has its data: none below)
   constexpr ZPow<32> zp{};
   // coefficients, then the horizontal taps from lanes l .. l + 3:
@@ -500,8 +501,8 @@ cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_de
 }
 
 cudaError_t launch_spline_cols(const InlinePlan* inl, const void* plan_dev, int ncolsegs,
-                               cudaStream_t s) {  // ncolsegs: (frame, 29 columns, 256 rows) items
-  k_spline_cols<<<ncolsegs, 256, 0, s>>>(*inl, plan_dev);
+                               cudaStream_t s) {  // ncolsegs: (frame, 29 columns, kColRows rows) items
+  k_spline_cols<<<ncolsegs, kColRows, 0, s>>>(*inl, plan_dev);
   return cudaGetLastError();
 }
 

@@ -11,13 +11,15 @@ namespace irp {
 // frame count, so the longest items are handed out first.
 // Resident CTAs per SM the register allocation must allow (2 up to 32
 // samples per pixel: at most 128 registers per thread).
-template <int NMAX>
+// The vertical spline taps on filtered rows stage no master window, so up to
+// 12 samples per pixel three CTAs fit per SM (at most 85 registers per thread).
+template <int NMAX, int STENCIL>
 struct MinBlocks {
-  static constexpr int value = NMAX <= 32 ? 2 : 1;
+  static constexpr int value = (STENCIL == ST_BSPLINE_V && NMAX <= 12) ? 3 : (NMAX <= 32 ? 2 : 1);
 };
 
 template <int NMAX, int STENCIL, int SRC, int PY>
-__global__ void __launch_bounds__(kThreads, MinBlocks<NMAX>::value)
+__global__ void __launch_bounds__(kThreads, MinBlocks<NMAX, STENCIL>::value)
     k_reduce(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);

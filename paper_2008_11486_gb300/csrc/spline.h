@@ -12,6 +12,7 @@ constexpr int kRowGroup = 16;       // frames per row-pass CTA
 // Row pass: rows per CTA for E columns per lane, and its shared memory (the
 // block's master rows as float4 plus two raw stages per warp).
 constexpr int kRowStages = 2;       // raw-row ring per warp (tasks in flight + 1)
+constexpr int kColRows = 64;        // rows per column-pass CTA (32 per warp)
 __host__ __device__ constexpr int row_block(int E) { return E == 32 ? 4 : 2; }
 // E = 32 also stages each output row per warp, so that it leaves in
 // contiguous 512-byte stores.
