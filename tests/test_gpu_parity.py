@@ -4,6 +4,7 @@ Every case runs the C ABI through the ctypes binding on seeded synthetic
 frame sets and compares element by element with the oracle on the same
 inputs, at sizes that span several tiles and ragged tile tails."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -438,4 +439,40 @@ def test_masked_reduction_matches_oracle(interp, offset):
     samp = np.max(np.where(ref["valid"], tol, 0.0), axis=0)
     compare("masked mean", s.mean.cpu().numpy(), ref["mean"], mean_tolerance(ref["mean"]) + samp, m)
     compare("masked median", s.median.cpu().numpy(), ref["median"],
+            mean_tolerance(ref["median"]) + samp)
+
+
+# ------------------------------------------- overscan cutout (Sec. 2.1 geometry)
+@pytest.mark.parametrize("interp", ["bilinear", "spline3"])
+def test_overscan_cutout_roi_of_1074x1024_frames(interp):
+    """Raw frames of 1074x1024 with a 50-column overscan and 2 px trimmed on
+    every side leave 1020x1020 (Sec. 2.1): the cutout is a region of the raw
+    and master buffers (pointer offset, pitch 1074), reduced in place; it must
+    equal the reduction of the same region copied out."""
+    full = synth.make_set(1074, 1024, 4, 5.0, 10741024, n_stars=120, n_cr=10)
+    x0, y0, W, H = 52, 2, 1020, 1020
+    fs = synth.FrameSet(raw=np.ascontiguousarray(full.raw[:, y0:y0 + H, x0:x0 + W]),
+                        bias=np.ascontiguousarray(full.bias[y0:y0 + H, x0:x0 + W]),
+                        dark=np.ascontiguousarray(full.dark[y0:y0 + H, x0:x0 + W]),
+                        flat=np.ascontiguousarray(full.flat[y0:y0 + H, x0:x0 + W]),
+                        exptime=full.exptime, dx=full.dx, dy=full.dy)
+    raw_dev = torch.from_numpy(full.raw.astype(np.int32)).to(torch.uint16).cuda()
+    masters = [torch.from_numpy(a).cuda()[y0:y0 + H, x0:x0 + W]
+               for a in (full.bias, full.dark, full.flat)]
+    s = core.device_set(fs, raw=raw_dev[:, y0:y0 + H, x0:x0 + W], masters=tuple(masters))
+    assert s.frames[0].stride(0) == 1074 and s.bias.stride(0) == 1074
+    s.alloc_outputs(want_stack=False)
+    ws = core.reduce_sets([s], core.reduce_params(interp))
+    assert core.sync_status(ws) == 0
+    copied = run_fused([fs], interp, want_stack=False)[0]
+    assert np.array_equal(s.mean.cpu().numpy().view(np.uint32), copied["mean"].view(np.uint32))
+    assert np.array_equal(s.median.cpu().numpy().view(np.uint32), copied["median"].view(np.uint32))
+    rng = np.random.default_rng(7)
+    xs, ys = rng.integers(0, W, 3000), rng.integers(0, H, 3000)
+    ref = oracle.reduce_set(fs, interp=interp, pixels=(xs, ys), nthreads=os.cpu_count() or 1)
+    m = ref["margin"] >= 1e-3
+    samp = sample_tolerance(fs, interp, oracle).max(axis=0)[ys, xs]
+    compare("cutout mean", s.mean.cpu().numpy()[ys, xs], ref["mean"],
+            mean_tolerance(ref["mean"]) + samp, m)
+    compare("cutout median", s.median.cpu().numpy()[ys, xs], ref["median"],
             mean_tolerance(ref["median"]) + samp)
