@@ -55,6 +55,11 @@ WORKLOADS = {
                        "4096^2}, bilinear: one autotuned persistent launch per frame-count bucket "
                        "replayed from a CUDA graph vs 64 plain per-set launches",
                   sets=None, offset=5.0, interp="bilinear", persistent=True, seed=11486003),
+    "paper": dict(desc="the paper's timed run: 3 bands x 180 frames of 1020x1020 uint16 (n = 540), "
+                       "offsets +-10 px, cubic-spline shift, 3-sigma clipped mean (3 passes) + "
+                       "median; 180-frame sets: aligned stack in chunks, then one warp per pixel",
+                  sets=[(1020, 1020, 180)] * 3, offset=10.0, interp="spline3", persistent=False,
+                  seed=11486005),
     "served": dict(desc="Poisson arrivals (0.5/s), each request 16 chips of 6144x6160 uint16 "
                         "reduced against a 5-frame rolling stack per chip (raw ring, resident "
                         "masters), admission by free HBM, continuous batching; p50/p99 latency "
@@ -146,19 +151,28 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+DEEP = 64  # sets of more frames combine from an aligned stack, one warp per pixel
+
+
 def algorithmic_bytes(kind, sets, interp, want_nkept=False):
     """Bytes one launch of ``kind`` must move, per the path's data flow:
     reduce from raw: n*P*2 (raw) + P*12 (bias, dark, flat) + P*8 (mean, median)
     reduce from spline coefficients: n*P*4 + P*8
-    prefilter: n*P*2 (raw) + P*12 (masters) + n*P*4 (coefficients)."""
+    prefilter: n*P*2 (raw) + P*12 (masters) + n*P*4 (coefficients)
+    sets of more than 64 frames: reduce writes the aligned FP32 stack (n*P*4)
+    in place of the outputs, and combine reads it back: n*P*4 + P*8."""
     tot = 0
     for (W, H, n) in sets:
         P = W * H
         out = P * (8 + (2 if want_nkept else 0))
+        deep = n > DEEP
         if kind == "reduce":
-            tot += (n * P * 4 + out) if interp == "spline3" else (n * P * 2 + P * 12 + out)
+            src = n * P * 4 if interp == "spline3" else n * P * 2 + P * 12
+            tot += src + (n * P * 4 if deep else out)
         elif kind == "prefilter":
             tot += n * P * 2 + P * 12 + n * P * 4
+        elif kind == "combine" and deep:
+            tot += n * P * 4 + out
     return tot
 
 
@@ -355,6 +369,8 @@ def step_bytes(shapes, interp):
     by = {"reduce": algorithmic_bytes("reduce", shapes, interp)}
     if interp == "spline3":
         by["prefilter"] = algorithmic_bytes("prefilter", shapes, interp)
+    if any(n > DEEP for (_, _, n) in shapes):
+        by["combine"] = algorithmic_bytes("combine", shapes, interp)
     return by
 
 
@@ -391,7 +407,7 @@ def main():
     ap.add_argument("--requests", type=int, default=12, help="served: requests at the nominal rate")
     ap.add_argument("--rate", type=float, default=0.5, help="served: Poisson arrival rate (1/s)")
     args = ap.parse_args()
-    heavy = args.workload in ("deep", "precision", "batch", "served", "masked")
+    heavy = args.workload in ("deep", "precision", "batch", "served", "masked", "paper")
     if args.steps is None:
         args.steps = 10 if heavy else 2000
     if args.warmup is None:
@@ -457,6 +473,11 @@ def main():
         extra["autotuned"] = bcfg
     if args.workload == "precision":
         extra["unfused"] = run_unfused(sets, interp, stream, world, local)
+    if args.workload == "paper":
+        # the paper's own GPU timing of the same run shape (Sec. 3.2.1, table
+        # "Breakdown of t", n = 540 on one TITAN X Pascal); context only
+        extra["paper_context"] = {"gpu": "TITAN X (Pascal)", "alignment_s": 0.48,
+                                  "combining_s": 0.14, "bias_dark_flat_s": 1.0e-3}
 
     total_ms, wall, prof, clocks = timed_steps(step, args.steps, args.warmup, stream,
                                                None if heavy else flush, world, local)
@@ -519,6 +540,8 @@ def main():
                                            f"disjoint set shards x{world}")},
                 "roofline": rf, "e2e": e2e, "gpu_launches": gpu_launches,
                 "wall_s": round(wall, 3), "clocks": clocks, "cpu_baseline": cpu}
+        if "paper_context" in extra:
+            extra["paper_context"]["this_step_s"] = round(ms_per_step * 1e-3, 6)
         line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:

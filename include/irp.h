@@ -58,7 +58,10 @@ extern "C" {
 #endif
 
 #define IRP_VERSION 10000      /* 1.0.0 */
-#define IRP_MAX_FRAMES 64      /* frames per set on the register/shared-memory combine */
+#define IRP_MAX_FRAMES 64      /* frames per set on the per-thread register combine */
+#define IRP_MAX_WIDE_FRAMES 1024 /* frames per set; from IRP_MAX_FRAMES + 1 on, one
+                                    warp combines each pixel (the paper's bands hold
+                                    180 frames, Sec. 3.2.1) */
 
 typedef enum {
   IRP_OK = 0,
@@ -141,7 +144,9 @@ size_t irp_shift_workspace_size(int W, int H, int n, irp_interp interp);
  *   nkept_out  nullable [H][out_pitch] uint16 survivors of the clip.
  *   reject_out nullable [n][H][out_pitch] uint8, 1 where a valid sample was
  *              rejected by the clip (debug output).
- *   n <= IRP_MAX_FRAMES.
+ *   n <= IRP_MAX_WIDE_FRAMES: up to IRP_MAX_FRAMES one thread sorts a pixel's
+ *   samples in registers; deeper stacks take one warp per pixel (bitonic sort
+ *   over the lanes, the same clip), with identical semantics.
  * ------------------------------------------------------------------------- */
 irp_status irp_combine(const void* stack, int64_t pitch, int64_t frame_stride,
                        int W, int H, int n, irp_stack_dtype dt,
@@ -155,6 +160,11 @@ irp_status irp_combine(const void* stack, int64_t pitch, int64_t frame_stride,
  * one or more frame sets, each raw pixel read from HBM once (bilinear and
  * nearest; cubic spline computes the spline coefficients of every calibrated
  * frame into the workspace first and then resamples and combines them).
+ * A set of more than IRP_MAX_FRAMES frames (up to IRP_MAX_WIDE_FRAMES) is
+ * resampled in chunks of at most 16 frames into its aligned FP32 stack
+ * [n][H][pitch] -- stack_out when given (pitch out_pitch), else the workspace
+ * (pitch W rounded up to 32) -- and the stack is then combined one warp per
+ * pixel; irp_workspace_size accounts for it.
  * ------------------------------------------------------------------------- */
 typedef struct {
   const uint16_t* const* frames;  /* host array of n device pointers           */

@@ -163,7 +163,7 @@ bool clip_ok(const irp_clip_params& c) {
 
 irp_status check_set(const irp_set& s) {
   if (!s.frames || s.W < 1 || s.H < 1 || s.n < 1) return IRP_ERR_INVALID_ARG;
-  if (s.n > IRP_MAX_FRAMES) return IRP_ERR_UNSUPPORTED;
+  if (s.n > IRP_MAX_WIDE_FRAMES) return IRP_ERR_UNSUPPORTED;
   if ((int64_t)s.W * s.H > (int64_t)1 << 31) return IRP_ERR_UNSUPPORTED;
   if (s.raw_pitch < s.W || s.master_pitch < s.W) return IRP_ERR_INVALID_ARG;
   if (!s.dx || !s.dy || !s.exptime || !s.bias || !s.dark_rate || !s.flat) return IRP_ERR_INVALID_ARG;
@@ -205,9 +205,10 @@ struct SubInfo {
 struct PlanFile {
   uint32_t magic;
   int32_t nsub, interp, normalize_flat;
-  int32_t nflat, persistent, pad[2];
+  int32_t nflat, persistent, nsets, ndeep;
   uint64_t ws_required;
   uint64_t flat_off;    // FrameStats[nflat] in the workspace
+  uint64_t deep_off;    // CombineArgs[ndeep] in the plan file: the deep sets' combines
   SubInfo sub[kMaxSub];
 };
 
@@ -221,7 +222,71 @@ struct Layout {
   size_t flat_off, plan_off, coef_off, total;
   std::vector<size_t> coef_frame_off;  // per set: offset of its first coefficient frame
   std::vector<size_t> crow_frame_off;  // per set: offset of its first row-pass frame
+  std::vector<size_t> stack_off;       // per deep set: its aligned stack (0: caller's)
 };
+
+// Sets deeper than the register buckets (IRP_MAX_FRAMES < n <=
+// IRP_MAX_WIDE_FRAMES) are reduced in two steps.  Chunks of at most
+// kDeepChunk frames go through the fused kernel as sets of their own that
+// write the aligned FP32 stack and combine nothing; then one warp per pixel
+// combines the whole stack.  Chunks of 13 to 16 frames share one register
+// bucket, so a call adds one sub-plan per spline path at most.
+constexpr int kDeepChunk = 16;
+
+struct DeepSet {
+  int user;         // index in the caller's array
+  int64_t spitch;   // stack row pitch (elements)
+  bool own_stack;   // the stack lives in the workspace (no caller stack_out)
+};
+
+struct PlanSets {
+  std::vector<irp_set> sets;  // plain sets and the chunks of deep sets, in call order
+  std::vector<int> deep_of;   // per entry: its deep set, or -1
+  std::vector<int> k0;        // per entry: first frame of the chunk in its deep set
+  std::vector<DeepSet> deep;
+  const irp_set* user;
+  int nsets() const { return (int)sets.size(); }
+};
+
+int64_t deep_stack_pitch(int W) { return (int64_t)align_up((size_t)W, 32); }
+
+PlanSets expand_sets(const irp_set* sets, int nsets) {
+  PlanSets ps;
+  ps.user = sets;
+  for (int i = 0; i < nsets; ++i) {
+    const irp_set& s = sets[i];
+    if (s.n <= IRP_MAX_FRAMES) {
+      ps.sets.push_back(s);
+      ps.deep_of.push_back(-1);
+      ps.k0.push_back(0);
+      continue;
+    }
+    DeepSet d;
+    d.user = i;
+    d.own_stack = s.stack_out == nullptr;
+    d.spitch = d.own_stack ? deep_stack_pitch(s.W) : s.out_pitch;
+    const int nch = (s.n + kDeepChunk - 1) / kDeepChunk;
+    for (int c = 0; c < nch; ++c) {
+      const int a = (int)((int64_t)c * s.n / nch), b = (int)((int64_t)(c + 1) * s.n / nch);
+      irp_set cs = s;
+      cs.frames = s.frames + a;
+      cs.dx = s.dx + a;
+      cs.dy = s.dy + a;
+      cs.exptime = s.exptime + a;
+      cs.n = b - a;
+      cs.mean_out = nullptr;
+      cs.median_out = nullptr;
+      cs.nkept_out = nullptr;
+      cs.stack_out = nullptr;  // placed in the stack by encode_plan
+      cs.out_pitch = d.spitch;
+      ps.sets.push_back(cs);
+      ps.deep_of.push_back((int)ps.deep.size());
+      ps.k0.push_back(a);
+    }
+    ps.deep.push_back(d);
+  }
+  return ps;
+}
 
 // Spline prefilter of a set: row + column passes (1) or tiled (0).
 int spline_path(int W, int H) {
@@ -240,23 +305,27 @@ size_t coef_frame_bytes(int W, int H) {
 
 // Sets are grouped by register bucket and, for the cubic spline, by the way
 // their coefficients are formed (the two take different reduction kernels).
-int group_key(const irp_set& s, int interp) {
+// Chunks of deep sets form groups of their own (no shared memory for samples).
+int group_key(const PlanSets& ps, int i, int interp) {
+  const irp_set& s = ps.sets[i];
   const int b = reduce_bucket(s.n);
-  return interp == IRP_INTERP_SPLINE3 ? 2 * b + spline_path(s.W, s.H) : 2 * b;
+  const int key = interp == IRP_INTERP_SPLINE3 ? 2 * b + spline_path(s.W, s.H) : 2 * b;
+  return ps.deep_of[i] >= 0 ? key + 1000 : key;
 }
 
-void group_sets(const irp_set* sets, int nsets, int interp,
-                std::vector<std::vector<int>>& groups) {
+void group_sets(const PlanSets& ps, int interp, std::vector<std::vector<int>>& groups) {
+  const int nsets = ps.nsets();
+  const irp_set* sets = ps.sets.data();
   std::vector<int> order(nsets);
   for (int i = 0; i < nsets; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    const int ka = group_key(sets[a], interp), kb = group_key(sets[b], interp);
+    const int ka = group_key(ps, a, interp), kb = group_key(ps, b, interp);
     return ka != kb ? ka > kb : sets[a].n > sets[b].n;
   });
   groups.clear();
   int cur = -1;
   for (int i : order) {
-    const int key = group_key(sets[i], interp);
+    const int key = group_key(ps, i, interp);
     if (key != cur) {
       groups.emplace_back();
       cur = key;
@@ -265,8 +334,10 @@ void group_sets(const irp_set* sets, int nsets, int interp,
   }
 }
 
-Layout make_layout(const irp_set* sets, int nsets, const irp_reduce_params* p,
+Layout make_layout(const PlanSets& ps, const irp_reduce_params* p,
                    const std::vector<std::vector<int>>& groups) {
+  const irp_set* sets = ps.sets.data();
+  const int nsets = ps.nsets();
   Layout L;
   size_t off = sizeof(WsHeader);
   L.flat_off = off;
@@ -290,6 +361,13 @@ Layout make_layout(const irp_set* sets, int nsets, const irp_reduce_params* p,
       }
     }
   }
+  L.stack_off.assign(ps.deep.size(), 0);
+  for (size_t d = 0; d < ps.deep.size(); ++d) {
+    if (!ps.deep[d].own_stack) continue;
+    const irp_set& u = ps.user[ps.deep[d].user];
+    L.stack_off[d] = off;
+    off += align_up((size_t)u.n * u.H * ps.deep[d].spitch * sizeof(float), kAlign);
+  }
   L.total = off;
   return L;
 }
@@ -307,7 +385,7 @@ irp_status check_params(const irp_set* sets, int nsets, const irp_reduce_params*
       return IRP_ERR_UNSUPPORTED;
   }
   std::vector<std::vector<int>> groups;
-  group_sets(sets, nsets, p->interp, groups);
+  group_sets(expand_sets(sets, nsets), p->interp, groups);
   if ((int)groups.size() > kMaxSub) return IRP_ERR_UNSUPPORTED;
   return IRP_OK;
 }
@@ -324,10 +402,19 @@ int sm_count() {
   return sms;
 }
 
-size_t plan_file_bytes(const irp_set* sets, int nsets, const irp_reduce_params* p) {
+size_t deep_jobs_offset(int nsets) {
+  return align_up(sizeof(PlanFile) + (size_t)nsets * sizeof(FlatJob), 64);
+}
+
+size_t plan_images_offset(const PlanSets& ps) {
+  return align_up(deep_jobs_offset(ps.nsets()) + ps.deep.size() * sizeof(CombineArgs), 64);
+}
+
+size_t plan_file_bytes(const PlanSets& ps, const irp_reduce_params* p) {
+  const irp_set* sets = ps.sets.data();
   std::vector<std::vector<int>> groups;
-  group_sets(sets, nsets, p->interp, groups);
-  size_t off = align_up(sizeof(PlanFile) + (size_t)nsets * sizeof(FlatJob), 64);
+  group_sets(ps, p->interp, groups);
+  size_t off = plan_images_offset(ps);
   for (const auto& g : groups) {
     int nf = 0;
     for (int i : g) nf += sets[i].n;
@@ -339,15 +426,18 @@ size_t plan_file_bytes(const irp_set* sets, int nsets, const irp_reduce_params* 
 
 // Encodes the plan file.  Needs the workspace address (descriptors point into
 // it) but touches neither the device nor the workspace contents.
-irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* p, uint8_t* buf,
+irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* buf,
                        size_t buf_bytes, uint8_t* ws, size_t ws_bytes) {
+  const irp_set* sets = ps.sets.data();
+  const int nsets = ps.nsets();
   std::vector<std::vector<int>> groups;
-  group_sets(sets, nsets, p->interp, groups);
-  const Layout L = make_layout(sets, nsets, p, groups);
+  group_sets(ps, p->interp, groups);
+  const Layout L = make_layout(ps, p, groups);
   if (!ws || !aligned(ws, kAlign)) return IRP_ERR_WORKSPACE;
   if (ws_bytes < L.total) return IRP_ERR_WORKSPACE;
-  if (buf_bytes < plan_file_bytes(sets, nsets, p)) return IRP_ERR_INVALID_ARG;
-  std::memset(buf, 0, plan_file_bytes(sets, nsets, p));
+  const size_t file_bytes = plan_file_bytes(ps, p);
+  if (buf_bytes < file_bytes) return IRP_ERR_INVALID_ARG;
+  std::memset(buf, 0, file_bytes);
   PlanFile* pf = (PlanFile*)buf;
   pf->magic = kPlanMagic;
   pf->nsub = (int)groups.size();
@@ -357,6 +447,29 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
   pf->persistent = p->persistent ? 1 : 0;
   pf->ws_required = L.total;
   pf->flat_off = L.flat_off;
+  pf->nsets = nsets;
+  pf->ndeep = (int)ps.deep.size();
+  pf->deep_off = deep_jobs_offset(nsets);
+  // the deep sets' stacks and their warp-per-pixel combines
+  std::vector<float*> stack_base(ps.deep.size());
+  CombineArgs* dj = (CombineArgs*)(buf + pf->deep_off);
+  for (size_t d = 0; d < ps.deep.size(); ++d) {
+    const irp_set& u = ps.user[ps.deep[d].user];
+    stack_base[d] = ps.deep[d].own_stack ? (float*)(ws + L.stack_off[d]) : u.stack_out;
+    CombineArgs& a = dj[d];
+    a.stack = stack_base[d];
+    a.pitch = ps.deep[d].spitch;
+    a.fstride = (int64_t)u.H * ps.deep[d].spitch;
+    a.W = u.W;
+    a.H = u.H;
+    a.n = u.n;
+    a.clip = ClipArgs{p->clip.kappa_lo, p->clip.kappa_hi, p->clip.max_iter, p->clip.center,
+                      p->clip.ddof};
+    a.mean_out = u.mean_out;
+    a.median_out = u.median_out;
+    a.nkept_out = u.nkept_out;
+    a.out_pitch = u.out_pitch;
+  }
   FlatJob* fj = (FlatJob*)(buf + sizeof(PlanFile));
   for (int i = 0; i < nsets; ++i) {
     fj[i].flat = sets[i].flat;
@@ -367,7 +480,7 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
   const int stencil = stencil_of(p->interp);
   const int taps = stencil == ST_BSPLINE ? 4 : (stencil == ST_BILINEAR ? 2 : 1);
   WsHeader* wsh = (WsHeader*)ws;
-  size_t img_off = align_up(sizeof(PlanFile) + (size_t)nsets * sizeof(FlatJob), 64);
+  size_t img_off = plan_images_offset(ps);
   size_t dev_off = L.plan_off;
   for (int gi = 0; gi < (int)groups.size(); ++gi) {
     const auto& g = groups[gi];
@@ -378,6 +491,7 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     }
     const int bucket = reduce_bucket(max_n);
     const int py = rows_per_warp(bucket, p->rows_per_warp);
+    const bool stack_only = ps.deep_of[g[0]] >= 0;  // the group holds deep-set chunks
     // the group's reduction stencil: spline sets on the row + column passes
     // arrive horizontally filtered and take the vertical taps only
     const bool spline = stencil == ST_BSPLINE;
@@ -421,6 +535,11 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
       S.nkept_out = s.nkept_out;
       S.stack_out = s.stack_out;
       S.out_pitch = s.out_pitch;
+      if (ps.deep_of[g[si]] >= 0) {
+        const int d = ps.deep_of[g[si]];
+        S.stack_only = 1;
+        S.stack_out = stack_base[d] + (int64_t)ps.k0[g[si]] * s.H * ps.deep[d].spitch;
+      }
       S.tiles_x = (s.W + TWc - 1) / TWc;
       S.tiles_y = (s.H + THr - 1) / THr;
       S.tile0 = tile0;
@@ -496,7 +615,7 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     h->max_iter = p->clip.max_iter;
     h->center = p->clip.center;
     h->ddof = p->clip.ddof;
-    h->smem_samples = max_n * THr * 32;
+    h->smem_samples = stack_only ? 0 : max_n * THr * 32;
     h->smem_master = mw_max * mh_max;  // float4 entries
     h->status = &wsh->status;
     h->counter = &wsh->counters[gi];
@@ -507,7 +626,8 @@ irp_status encode_plan(const irp_set* sets, int nsets, const irp_reduce_params* 
     si.bucket = bucket;
     si.py = py;
     si.stencil = gstencil;
-    si.smem = reduce_smem_bytes(spline ? SRC_F32 : SRC_RAW, gstencil, py, max_n, mw_max, mh_max);
+    si.smem = reduce_smem_bytes(spline ? SRC_F32 : SRC_RAW, gstencil, py, max_n, mw_max, mh_max) -
+              (stack_only ? (size_t)max_n * THr * 32 * sizeof(float) : 0);
     si.nitems = tile0;
     si.counter = gi;
     si.nsets = (int)g.size();
@@ -587,6 +707,13 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
     }
     if (e != cudaSuccess) return note_cuda(e);
   }
+  // deep sets: their stacks are complete in stream order
+  const CombineArgs* dj = (const CombineArgs*)(buf + pf->deep_off);
+  for (int d = 0; d < pf->ndeep; ++d) {
+    TraceScope tr(IRP_KERNEL_COMBINE, s);
+    e = launch_combine_wide(dj[d], false, s);
+    if (e != cudaSuccess) return note_cuda(e);
+  }
   return IRP_OK;
 }
 
@@ -646,14 +773,15 @@ int irp_profile_read(double* ms_out, int64_t* launches_out, int max_kinds) {
 
 size_t irp_workspace_size(const irp_set* sets, int nsets, const irp_reduce_params* p) {
   if (check_params(sets, nsets, p) != IRP_OK) return 0;
+  const PlanSets ps = expand_sets(sets, nsets);
   std::vector<std::vector<int>> groups;
-  group_sets(sets, nsets, p->interp, groups);
-  return make_layout(sets, nsets, p, groups).total;
+  group_sets(ps, p->interp, groups);
+  return make_layout(ps, p, groups).total;
 }
 
 size_t irp_plan_bytes(const irp_set* sets, int nsets, const irp_reduce_params* p) {
   if (check_params(sets, nsets, p) != IRP_OK) return 0;
-  return plan_file_bytes(sets, nsets, p);
+  return plan_file_bytes(expand_sets(sets, nsets), p);
 }
 
 irp_status irp_plan_encode(const irp_set* sets, int nsets, const irp_reduce_params* p,
@@ -661,7 +789,8 @@ irp_status irp_plan_encode(const irp_set* sets, int nsets, const irp_reduce_para
   irp_status st = check_params(sets, nsets, p);
   if (st != IRP_OK) return st;
   if (!plan_host) return IRP_ERR_INVALID_ARG;
-  return encode_plan(sets, nsets, p, (uint8_t*)plan_host, plan_bytes, (uint8_t*)workspace, ws_bytes);
+  return encode_plan(expand_sets(sets, nsets), p, (uint8_t*)plan_host, plan_bytes,
+                     (uint8_t*)workspace, ws_bytes);
 }
 
 irp_status irp_plan_launch(const void* plan_host, size_t plan_bytes, void* workspace,
@@ -675,8 +804,9 @@ irp_status irp_reduce_set(const irp_set* sets, int nsets, const irp_reduce_param
                           void* workspace, size_t ws_bytes, void* stream) {
   irp_status st = check_params(sets, nsets, p);
   if (st != IRP_OK) return st;
-  std::vector<uint8_t> buf(plan_file_bytes(sets, nsets, p));
-  st = encode_plan(sets, nsets, p, buf.data(), buf.size(), (uint8_t*)workspace, ws_bytes);
+  const PlanSets ps = expand_sets(sets, nsets);
+  std::vector<uint8_t> buf(plan_file_bytes(ps, p));
+  st = encode_plan(ps, p, buf.data(), buf.size(), (uint8_t*)workspace, ws_bytes);
   if (st != IRP_OK) return st;
   // Small plans travel as kernel parameters; larger ones are copied from this
   // pageable buffer (cudaMemcpyAsync then returns after staging the data).
@@ -891,7 +1021,7 @@ irp_status irp_combine(const void* stack, int64_t pitch, int64_t frame_stride, i
     return IRP_ERR_INVALID_ARG;
   if (!mean_out && !median_out && !nkept_out && !reject_out) return IRP_ERR_INVALID_ARG;
   if (n > 1 && frame_stride < pitch * H) return IRP_ERR_INVALID_ARG;
-  if (n > IRP_MAX_FRAMES) return IRP_ERR_UNSUPPORTED;
+  if (n > IRP_MAX_WIDE_FRAMES) return IRP_ERR_UNSUPPORTED;
   if (dt != IRP_F32 && dt != IRP_F16_SCALED) return IRP_ERR_INVALID_ARG;
   if (dt == IRP_F16_SCALED && (!scale || !offset)) return IRP_ERR_INVALID_ARG;
   if (!clip_ok(*clip)) return IRP_ERR_INVALID_ARG;
@@ -917,7 +1047,9 @@ irp_status irp_combine(const void* stack, int64_t pitch, int64_t frame_stride, i
   a.reject_out = reject_out;
   a.out_pitch = out_pitch;
   TraceScope tr(IRP_KERNEL_COMBINE, (cudaStream_t)stream);
-  return cuda_status(launch_combine(a, dt == IRP_F16_SCALED, (cudaStream_t)stream));
+  const bool f16 = dt == IRP_F16_SCALED;
+  return cuda_status(n > IRP_MAX_FRAMES ? launch_combine_wide(a, f16, (cudaStream_t)stream)
+                                        : launch_combine(a, f16, (cudaStream_t)stream));
 }
 
 }  // extern "C"
@@ -965,16 +1097,17 @@ extern "C" irp_status irp_reduce_set_noalloc(const irp_set* sets, int nsets,
   irp_status st = check_params(sets, nsets, p);
   if (st != IRP_OK) return st;
   if (!aligned(status_out, 4)) return IRP_ERR_ALIGNMENT;
+  const PlanSets ps = expand_sets(sets, nsets);
   std::vector<std::vector<int>> groups;
-  group_sets(sets, nsets, p->interp, groups);
-  const size_t need = make_layout(sets, nsets, p, groups).total;
-  const size_t plan_bytes = plan_file_bytes(sets, nsets, p);
+  group_sets(ps, p->interp, groups);
+  const size_t need = make_layout(ps, p, groups).total;
+  const size_t plan_bytes = plan_file_bytes(ps, p);
   if (need > IRP_NOALLOC_SCRATCH_BYTES || plan_bytes > kNoallocPlanBytes) return IRP_ERR_WORKSPACE;
   uint8_t* ws = nullptr;
   cudaError_t e = noalloc_scratch(&ws);
   if (e != cudaSuccess) return note_cuda(e);
   alignas(64) uint8_t buf[kNoallocPlanBytes];  // on the stack: no allocation
-  st = encode_plan(sets, nsets, p, buf, plan_bytes, ws, IRP_NOALLOC_SCRATCH_BYTES);
+  st = encode_plan(ps, p, buf, plan_bytes, ws, IRP_NOALLOC_SCRATCH_BYTES);
   if (st != IRP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   // the status word and work counters must start at zero for every call

@@ -83,7 +83,8 @@ struct SetDesc {
   int64_t mask_pitch;
   float saturation;              // raw level marking a pixel bad (+inf: none)
   int32_t masked;                // 1: mask or saturation level in use
-  int32_t pad[2];
+  int32_t stack_only;            // 1: write stack_out only (a chunk of a deeper set)
+  int32_t pad;
 };
 static_assert(sizeof(SetDesc) == 224, "SetDesc layout");
 

@@ -471,11 +471,13 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
       for (int q = 0; q < PY; ++q) badq[q] = bh[q] | ((w.y > 0.0f) & bh[q + 1]);
     }
   }
+  if (sk) {  // null for a stack-only set
 #pragma unroll
-  for (int q = 0; q < PY; ++q) {
-    const bool ok = xv & in_range(wy0 + q, gy.x, gy.y) & !badq[q];
-    sk[q * 32] = ok ? a[q] : kInf;
-    mq[q] += ok ? 1 : 0;
+    for (int q = 0; q < PY; ++q) {
+      const bool ok = xv & in_range(wy0 + q, gy.x, gy.y) & !badq[q];
+      sk[q * 32] = ok ? a[q] : kInf;
+      mq[q] += ok ? 1 : 0;
+    }
   }
   if (stack_out) {
 #pragma unroll
@@ -579,7 +581,9 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
   int mq[PY];
 #pragma unroll
   for (int q = 0; q < PY; ++q) mq[q] = 0;
-  float* sk = s_samples + (size_t)warp * PY * 32 + lane;
+  // a stack-only set (a chunk of a set deeper than the register buckets) keeps
+  // no samples: its group reserves no shared memory for them
+  float* sk = S.stack_only ? nullptr : s_samples + (size_t)warp * PY * 32 + lane;
   // frames in groups of kStages, so that every stage slot is a constant
   auto step = [&](auto mode, int k, int u, bool issue_next) {
     constexpr int MODE = decltype(mode)::value;
@@ -596,7 +600,8 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
     cp_async_commit();
     frame_step<STENCIL, SRC, PY, MODE>(frames[k], s_stage + u * SS::bytes, s_mast_w, mwin_w, S,
                                        flat_norm, h.status, lane, x, tx0, wy0,
-                                       sk + (size_t)k * TH * 32, mq, stack_out, k, W, H,
+                                       sk ? sk + (size_t)k * TH * 32 : nullptr, mq,
+                                       stack_out, k, W, H,
                                        out_pitch, stack_lane);
   };
   auto frame_loop = [&](auto mode) {
@@ -625,7 +630,7 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
   uint16_t* const nkept_out = S.nkept_out;
   constexpr int kSure = bucket_below(NMAX);  // every set of this bucket has more frames
   const float kInf = __int_as_float(0x7f800000);
-  if (lane < TW && x < W) {
+  if (!S.stack_only && lane < TW && x < W) {
 #pragma unroll 1
     for (int q = 0; q < PY; ++q) {
       const int y = wy0 + q;

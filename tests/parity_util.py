@@ -1,7 +1,7 @@
 """Shared helpers of the GPU parity tests: uploads, oracle runs and the
 tolerances derived from the FP32 arithmetic of the kernels.
 
-Tolerances (reasoning in DESIGN.md, "Parity tolerances"):
+Tolerances, each derived from the rounding steps of the FP32 arithmetic:
   * clipped mean / median end to end:  |gpu - ref| <= max(1e-3 ADU, 1e-6 |ref|)
     plus the per-sample bound below (the mean of samples is off by at most
     the largest sample error);
@@ -25,12 +25,16 @@ def maxfilter(a, size):
     return maximum_filter(np.abs(a), size=size, mode="nearest")
 
 
-def sample_tolerance(fs, interp, oracle_mod):
-    """Per-sample tolerance [n,H,W] of the aligned stack on the output grid."""
+def sample_tolerance(fs, interp, oracle_mod, pixels=None):
+    """Per-sample tolerance [n,H,W] of the aligned stack on the output grid,
+    or [n, len(xs)] at the output pixels ``pixels`` = (xs, ys)."""
     n, H, W = fs.raw.shape
-    tol = np.empty((n, H, W))
     size, coef, floor_ = (9, 64.0, 1e-4) if interp == "spline3" else (3, 8.0, 1e-5)
-    yy, xx = np.mgrid[0:H, 0:W]
+    if pixels is None:
+        yy, xx = np.mgrid[0:H, 0:W]
+    else:
+        xx, yy = (np.asarray(a) for a in pixels)
+    tol = np.empty((n,) + xx.shape)
     for k in range(n):
         v = oracle_mod.calibrate(fs.raw[k], fs.bias, fs.dark, fs.flat, fs.exptime[k])
         M = maxfilter(v, size)

@@ -80,7 +80,7 @@ def _reduce(L, sets, p, ws=FAKE, ws_bytes=1 << 30):
 def test_reduce_set_validation_codes(L):
     assert _reduce(L, [_set()], _params(), ws_bytes=0) == 3            # workspace too small
     assert _reduce(L, [_set()], _params(), ws=FAKE + 8) == 3           # workspace misaligned
-    assert _reduce(L, [_set(n=65)], _params()) == 4                    # too many frames
+    assert _reduce(L, [_set(n=1025)], _params()) == 4                  # too many frames
     assert _reduce(L, [_set()], _params(interp=7)) == 1                # bad interpolation
     assert _reduce(L, [_set(W=0)], _params()) == 1                     # empty frame
     assert _reduce(L, [_set(raw_pitch=10)], _params()) == 1            # pitch < W
@@ -129,11 +129,30 @@ def test_plan_accepts_a_batch_spanning_every_frame_count_bucket(L):
         assert L.irp_workspace_size(arr, len(sets), ctypes.byref(p)) > 0
 
 
+def test_deep_sets_plan_and_stack_workspace(L):
+    # a set deeper than the register buckets adds its aligned FP32 stack to
+    # the workspace, [n][H][W rounded up to 32] floats, unless the caller
+    # passes stack_out; its chunks form one extra sub-plan
+    assert L.irp_workspace_size((B.IrpSet * 1)(_set(n=1024)), 1, ctypes.byref(_params())) > 0
+    plain = _set(n=64, W=50, H=48)
+    deep = _set(n=100, W=50, H=48)
+    deep_own = _set(n=100, W=50, H=48, stack_out=FAKE + 32768)
+    ws = {k: L.irp_workspace_size((B.IrpSet * 1)(s), 1, ctypes.byref(_params()))
+          for k, s in (("deep", deep), ("own", deep_own))}
+    assert ws["deep"] - ws["own"] == -(-100 * 48 * 64 * 4 // 256) * 256
+    arr = (B.IrpSet * 3)(plain, deep, _set(n=300, W=40, H=40))
+    for interp in (0, 1, 2):
+        for persistent in (0, 1):
+            p = _params(interp=interp, persistent=persistent)
+            assert L.irp_plan_bytes(arr, 3, ctypes.byref(p)) > 0
+            assert L.irp_workspace_size(arr, 3, ctypes.byref(p)) > 0
+
+
 def test_unfused_validation_codes(L):
     clip = B.ClipParams(3.0, 3.0, 3, 0, 0)
     f = ctypes.c_void_p(FAKE)
-    # combine: n above the register combine limit, null clip, bad dtype
-    assert L.irp_combine(f, 64, 64 * 64, 64, 64, 65, 0, None, None, None, ctypes.byref(clip),
+    # combine: n above the warp-per-pixel limit, null clip, bad dtype
+    assert L.irp_combine(f, 64, 64 * 64, 64, 64, 1025, 0, None, None, None, ctypes.byref(clip),
                          f, f, None, None, 64, None) == 4
     assert L.irp_combine(f, 64, 64 * 64, 64, 64, 5, 0, None, None, None, None,
                          f, f, None, None, 64, None) == 1
