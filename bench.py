@@ -60,6 +60,10 @@ WORKLOADS = {
                        "median; 180-frame sets: aligned stack in chunks, then one warp per pixel",
                   sets=[(1020, 1020, 180)] * 3, offset=10.0, interp="spline3", persistent=False,
                   seed=11486005),
+    "paper_band": dict(desc="one band of the paper's run: 180 frames of 1020x1020 uint16, offsets "
+                            "+-10 px, cubic-spline shift, 3-sigma clipped mean (3 passes) + median",
+                       sets=[(1020, 1020, 180)], offset=10.0, interp="spline3", persistent=False,
+                       seed=11486005),
     "served": dict(desc="Poisson arrivals (0.5/s), each request 16 chips of 6144x6160 uint16 "
                         "reduced against a 5-frame rolling stack per chip (raw ring, resident "
                         "masters), admission by free HBM, continuous batching; p50/p99 latency "
@@ -407,7 +411,8 @@ def main():
     ap.add_argument("--requests", type=int, default=12, help="served: requests at the nominal rate")
     ap.add_argument("--rate", type=float, default=0.5, help="served: Poisson arrival rate (1/s)")
     args = ap.parse_args()
-    heavy = args.workload in ("deep", "precision", "batch", "served", "masked", "paper")
+    heavy = args.workload in ("deep", "precision", "batch", "served", "masked", "paper",
+                              "paper_band")
     if args.steps is None:
         args.steps = 10 if heavy else 2000
     if args.warmup is None:
@@ -473,7 +478,7 @@ def main():
         extra["autotuned"] = bcfg
     if args.workload == "precision":
         extra["unfused"] = run_unfused(sets, interp, stream, world, local)
-    if args.workload == "paper":
+    if args.workload in ("paper", "paper_band"):
         # the paper's own GPU timing of the same run shape (Sec. 3.2.1, table
         # "Breakdown of t", n = 540 on one TITAN X Pascal); context only
         extra["paper_context"] = {"gpu": "TITAN X (Pascal)", "alignment_s": 0.48,

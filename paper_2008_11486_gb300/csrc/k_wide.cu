@@ -9,7 +9,9 @@ namespace irp {
 
 // The CTA copies its [n][32] slab of the stack into shared memory (each
 // frame's 32 pixels are one 128-byte row segment), then its 8 warps take the
-// 32 pixels in turn: load, sort, clip, and write the results as one row.
+// 32 pixels in turn: load, sort (the sorted run replaces the samples in
+// shared memory, where the order statistics are read), clip, and write the
+// results as one row.
 template <int J, bool F16>
 __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs a, int tiles_x) {
   extern __shared__ float s_wide[];
@@ -22,58 +24,68 @@ __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs a, in
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const float kInf = __int_as_float(0x7f800000);
   const int n = a.n;
+  // sample of frame k at stack offset o: +inf when invalid (NaN or masked)
+  auto load = [&](int k, int64_t o) -> float {
+    float v;
+    if (F16)
+      v = __fmaf_rn(__half2float(((const __half*)a.stack)[o]), __ldg(a.scale + k),
+                    __ldg(a.offset + k));
+    else
+      v = __ldg((const float*)a.stack + o);
+    if (a.valid && !__ldg(a.valid + o)) v = kInf;
+    return (v == v) ? v : kInf;
+  };
   {
     // staging: thread (warp, lane) copies frames warp, warp + 8, ... of pixel lane
     const int x = x0 + lane;
     const bool xin = x < a.W;
     const int64_t o0 = (int64_t)y * a.pitch + x;
-    constexpr int kBatch = 4;  // loads in flight per thread
+    constexpr int kBatch = 16;  // loads in flight per thread
     for (int k0 = warp; k0 < n; k0 += 8 * kBatch) {
       float v[kBatch];
 #pragma unroll
       for (int b = 0; b < kBatch; ++b) {
         const int k = k0 + 8 * b;
-        v[b] = kInf;
-        if (xin && k < n) {
-          const int64_t o = (int64_t)k * a.fstride + o0;
-          if (F16)
-            v[b] = __fmaf_rn(__half2float(((const __half*)a.stack)[o]), __ldg(a.scale + k),
-                             __ldg(a.offset + k));
-          else
-            v[b] = __ldg((const float*)a.stack + o);
-          if (a.valid && !__ldg(a.valid + o)) v[b] = kInf;
-        }
+        v[b] = (xin && k < n) ? load(k, (int64_t)k * a.fstride + o0) : kInf;
       }
 #pragma unroll
       for (int b = 0; b < kBatch; ++b) {
         const int k = k0 + 8 * b;
-        if (k < n) s_wide[SM::at(lane, k)] = (v[b] == v[b]) ? v[b] : kInf;  // NaN: invalid
+        if (k < n) s_wide[SM::at(lane, k)] = v[b];
       }
     }
   }
   __syncthreads();
+#pragma unroll 1
   for (int p = warp; p < 32; p += 8) {
     if (x0 + p >= a.W) break;
+    float* const col = s_wide + SM::at(p, 0);  // this pixel's samples
     float v[J];
     int cnt = 0;
 #pragma unroll
     for (int i = 0; i < J; ++i) {
       const int e = lane * J + i;
-      v[i] = e < n ? s_wide[SM::at(p, e)] : kInf;
+      v[i] = e < n ? col[lane * (J + 1) + i] : kInf;
       cnt += v[i] < kInf ? 1 : 0;
     }
     const int m = __reduce_add_sync(0xffffffffu, cnt);
     if (m > 0) warp_bitonic_sort<J>(v, lane);
-    const WideOut o = wide_combine<J>(v, m, a.clip, lane);
+    // the sorted run replaces the pixel's samples (sample e at col[e + e / J])
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < J; ++i) col[lane * (J + 1) + i] = v[i];
+    __syncwarp();
+    const WideOut o = wide_combine<J>(v, col, m, a.clip, lane);
     if (lane == 0) {
       s_mean[p] = o.mean;
       s_median[p] = o.median;
       s_kept[p] = o.kept;
     }
-    if (a.reject_out) {
+    if (a.reject_out) {  // debug output: the frames' samples again, in frame order
       const int x = x0 + p;
+      const int64_t o0 = (int64_t)y * a.pitch + x;
       for (int k = lane; k < n; k += 32) {
-        const float val = s_wide[SM::at(p, k)];
+        const float val = load(k, (int64_t)k * a.fstride + o0);
         const bool rej = (val < kInf) & ((val < o.lo_val) | (val > o.hi_val));
         a.reject_out[((int64_t)k * a.H + y) * a.out_pitch + x] = rej ? 1 : 0;
       }

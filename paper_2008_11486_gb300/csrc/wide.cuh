@@ -35,49 +35,56 @@ struct WideSmem {
   __device__ static __forceinline__ int at(int p, int e) { return p * kPixStride + e + e / J; }
 };
 
-// Ascending bitonic sort of the warp's 32 J values (lane-major blocks).
+// Ascending bitonic sort of the warp's 32 J values (lane-major blocks), in
+// the form whose merges start with a mirrored compare (element e against
+// e ^ (s - 1)) and continue with ascending half-cleaners: every compare keeps
+// the minimum at the lower index, so the in-lane ones need no direction test.
 template <int J>
 __device__ __forceinline__ void warp_bitonic_sort(float (&v)[J], int lane) {
   constexpr int L = 32 * J;
 #pragma unroll
   for (int s = 2; s <= L; s <<= 1) {
+    if (s <= J) {
+      // mirrored compare inside the lane: i against i ^ (s - 1)
 #pragma unroll
-    for (int d = s >> 1; d > 0; d >>= 1) {
+      for (int i = 0; i < J; ++i) {
+        if (i & (s >> 1)) continue;
+        const int j = i ^ (s - 1);
+        const float a = v[i], b = v[j];
+        v[i] = fminf(a, b);
+        v[j] = fmaxf(a, b);
+      }
+    } else {
+      // mirrored compare across lanes: (lane, i) against (lane ^ (s/J - 1), J-1-i)
+      const int lm = s / J - 1;
+      const bool lower = (lane & ((s >> 1) / J)) == 0;
+      float p[J];
+#pragma unroll
+      for (int i = 0; i < J; ++i) p[i] = __shfl_xor_sync(0xffffffffu, v[J - 1 - i], lm);
+#pragma unroll
+      for (int i = 0; i < J; ++i) v[i] = lower ? fminf(v[i], p[i]) : fmaxf(v[i], p[i]);
+    }
+#pragma unroll
+    for (int d = s >> 2; d > 0; d >>= 1) {
       if (d >= J) {
-        // partner: the same register of lane ^ (d / J); the lower element of
-        // the pair keeps the minimum when its run of length s ascends
         const int ld = d / J;
-        const bool asc = ((lane * J) & s) == 0;
-        const bool keep_min = asc != ((lane & ld) != 0);
+        const bool lower = (lane & ld) == 0;
 #pragma unroll
         for (int i = 0; i < J; ++i) {
           const float p = __shfl_xor_sync(0xffffffffu, v[i], ld);
-          v[i] = keep_min ? fminf(v[i], p) : fmaxf(v[i], p);
+          v[i] = lower ? fminf(v[i], p) : fmaxf(v[i], p);
         }
       } else {
 #pragma unroll
         for (int i = 0; i < J; ++i) {
           if (i & d) continue;
-          // runs shorter than a block: direction fixed by i; longer: by the lane
-          const bool asc = s < J ? (i & s) == 0 : ((lane * J) & s) == 0;
           const float a = v[i], b = v[i ^ d];
-          const float lo = fminf(a, b), hi = fmaxf(a, b);
-          v[i] = asc ? lo : hi;
-          v[i ^ d] = asc ? hi : lo;
+          v[i] = fminf(a, b);
+          v[i ^ d] = fmaxf(a, b);
         }
       }
     }
   }
-}
-
-// Sorted sample e (warp-uniform e).
-template <int J>
-__device__ __forceinline__ float wide_at(const float (&v)[J], int e) {
-  const int r = e % J;
-  float sel = v[0];
-#pragma unroll
-  for (int i = 1; i < J; ++i) sel = (i == r) ? v[i] : sel;
-  return __shfl_sync(0xffffffffu, sel, e / J);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -108,17 +115,16 @@ struct WideOut {
   int kept;
 };
 
-// Kahan-compensated sum over the warp of (v[e] - r) for e in [lo, lo + mm),
-// and (optionally) the plain sum of their squares.
+// Kahan-compensated sum over the warp of the deviations dv[e] for e in
+// [lo, lo + mm), and (optionally) the plain sum of their squares.
 template <int J, bool SQ>
-__device__ __forceinline__ float wide_run_sums(const float (&v)[J], int lane, int lo, int mm,
-                                               float r, float* q_out) {
+__device__ __forceinline__ float wide_run_sums(const float (&dv)[J], int lane, int lo, int mm,
+                                               float* q_out) {
   float S = 0.0f, C = 0.0f, Q = 0.0f;
 #pragma unroll
   for (int i = 0; i < J; ++i) {
-    const int e = lane * J + i;
-    const bool in = (unsigned)(e - lo) < (unsigned)mm;
-    const float d = in ? __fsub_rn(v[i], r) : 0.0f;
+    const bool in = (unsigned)(lane * J + i - lo) < (unsigned)mm;
+    const float d = in ? dv[i] : 0.0f;
     const float y = __fsub_rn(d, C);
     const float t = __fadd_rn(S, y);
     C = __fsub_rn(__fsub_rn(t, S), y);
@@ -130,12 +136,15 @@ __device__ __forceinline__ float wide_run_sums(const float (&v)[J], int lane, in
 }
 
 // Sigma-clipped mean (cumulative rejection, at most max_iter passes) and
-// median of the m valid samples, sorted to the front of v.
+// median of the m valid samples, sorted to the front of v.  `run` holds the
+// same sorted values in shared memory (sample e at run[e + e / J]), from which
+// the order statistics are read.
 template <int J>
-__device__ __forceinline__ WideOut wide_combine(const float (&v)[J], int m, const ClipArgs& c,
-                                                int lane) {
+__device__ __forceinline__ WideOut wide_combine(const float (&v)[J], const float* run, int m,
+                                                const ClipArgs& c, int lane) {
   WideOut o;
   const float kNaN = __int_as_float(0x7fffffff);
+  auto at = [&](int e) { return run[e + e / J]; };
   if (m <= 0) {
     o.mean = kNaN;
     o.median = kNaN;
@@ -144,10 +153,13 @@ __device__ __forceinline__ WideOut wide_combine(const float (&v)[J], int m, cons
     o.hi_val = 0.0f;
     return o;
   }
-  const float a = wide_at<J>(v, (m - 1) >> 1);
-  const float b = wide_at<J>(v, m >> 1);
+  const float a = at((m - 1) >> 1);
+  const float b = at(m >> 1);
   o.median = __fmul_rn(__fadd_rn(a, b), 0.5f);
   const float r = a;  // reference of the shifted sums: no cancellation in the squares
+  float dv[J];        // deviations from r (+inf for invalid samples)
+#pragma unroll
+  for (int i = 0; i < J; ++i) dv[i] = __fsub_rn(v[i], r);
   int lo = 0, hi = m;
   float S = 0.0f;
   bool have = false;
@@ -155,12 +167,12 @@ __device__ __forceinline__ WideOut wide_combine(const float (&v)[J], int m, cons
     const int mm = hi - lo;
     if (mm - c.ddof <= 0) break;
     float Q;
-    S = wide_run_sums<J, true>(v, lane, lo, mm, r, &Q);
+    S = wide_run_sums<J, true>(dv, lane, lo, mm, &Q);
     have = true;
     float cd;  // centre - r
     if (c.center == 1) {
-      const float qa = wide_at<J>(v, lo + ((mm - 1) >> 1));
-      const float qb = wide_at<J>(v, lo + (mm >> 1));
+      const float qa = at(lo + ((mm - 1) >> 1));
+      const float qb = at(lo + (mm >> 1));
       cd = __fsub_rn(__fmul_rn(__fadd_rn(qa, qb), 0.5f), r);
     } else {
       cd = __fdiv_rn(S, (float)mm);
@@ -172,31 +184,31 @@ __device__ __forceinline__ WideOut wide_combine(const float (&v)[J], int m, cons
     if (!(sigma > 0.0f)) break;
     const float tlo = c.kappa_lo * sigma, thi = c.kappa_hi * sigma;
     // the rejected samples are a prefix and a suffix of the run
-    const float elo = __fsub_rn(__fsub_rn(wide_at<J>(v, lo), r), cd);
-    const float ehi = __fsub_rn(__fsub_rn(wide_at<J>(v, hi - 1), r), cd);
-    if (!(-elo > tlo) && !(ehi > thi)) break;
-    int nlo = 0, nhi = 0;
+    const bool rlo = -__fsub_rn(__fsub_rn(at(lo), r), cd) > tlo;
+    const bool rhi = __fsub_rn(__fsub_rn(at(hi - 1), r), cd) > thi;
+    if (!rlo && !rhi) break;
+    // Both tests are monotone in the sample value and the run is sorted: when
+    // the run's lowest sample is rejected, so is every sample below the run,
+    // and no sample above it; likewise at the top, where the invalid samples
+    // (+inf) and those already rejected all pass the test.
+    int clo = 0, chi = 0;
 #pragma unroll
     for (int i = 0; i < J; ++i) {
-      const int e = lane * J + i;
-      const bool in = (unsigned)(e - lo) < (unsigned)mm;
-      const float d = __fsub_rn(__fsub_rn(v[i], r), cd);
-      nlo += (in & (-d > tlo)) ? 1 : 0;
-      nhi += (in & (d > thi)) ? 1 : 0;
+      const float d = __fsub_rn(dv[i], cd);
+      clo += (-d > tlo) ? 1 : 0;
+      chi += (d > thi) ? 1 : 0;
     }
-    nlo = __reduce_add_sync(0xffffffffu, nlo);
-    nhi = __reduce_add_sync(0xffffffffu, nhi);
-    if (nlo + nhi == 0) break;
+    const int nlo = rlo ? min(__reduce_add_sync(0xffffffffu, clo) - lo, mm) : 0;
+    const int nhi = rhi ? min(__reduce_add_sync(0xffffffffu, chi) - (32 * J - hi), mm - nlo) : 0;
     lo += nlo;
     hi -= nhi;
-    if (hi < lo) hi = lo;
     have = false;
   }
-  if (!have) S = wide_run_sums<J, false>(v, lane, lo, hi - lo, r, nullptr);
+  if (!have) S = wide_run_sums<J, false>(dv, lane, lo, hi - lo, nullptr);
   o.kept = hi - lo;
   o.mean = o.kept > 0 ? __fadd_rn(r, __fdiv_rn(S, (float)o.kept)) : kNaN;
-  o.lo_val = o.kept > 0 ? wide_at<J>(v, lo) : 1.0f;
-  o.hi_val = o.kept > 0 ? wide_at<J>(v, hi - 1) : 0.0f;
+  o.lo_val = o.kept > 0 ? at(lo) : 1.0f;
+  o.hi_val = o.kept > 0 ? at(hi - 1) : 0.0f;
   return o;
 }
 
