@@ -226,17 +226,24 @@ struct Layout {
 };
 
 // Sets deeper than the register buckets (IRP_MAX_FRAMES < n <=
-// IRP_MAX_WIDE_FRAMES) are reduced in two steps.  Chunks of at most
-// kDeepChunk frames go through the fused kernel as sets of their own that
-// write the aligned FP32 stack and combine nothing; then one warp per pixel
-// combines the whole stack.  Chunks of 13 to 16 frames share one register
-// bucket, so a call adds one sub-plan per spline path at most.
+// IRP_MAX_WIDE_FRAMES) are reduced in two steps, and one warp per pixel
+// combines them.
+// * Cubic spline on the row + column passes, without a caller stack: the
+//   column pass already leaves each frame's rows filtered along x on the
+//   output grid, so the set only runs its prefilter, and the combine applies
+//   the four vertical taps itself while it gathers the samples.
+// * Otherwise chunks of at most kDeepChunk frames go through the fused kernel
+//   as sets of their own that write the aligned FP32 stack and combine
+//   nothing; the combine then reads the stack.  Chunks of 13 to 16 frames
+//   share one register bucket, so a call adds one sub-plan per spline path
+//   at most.
 constexpr int kDeepChunk = 16;
 
 struct DeepSet {
   int user;         // index in the caller's array
   int64_t spitch;   // stack row pitch (elements)
   bool own_stack;   // the stack lives in the workspace (no caller stack_out)
+  bool rows;        // combined from the filtered spline rows (no stack)
 };
 
 struct PlanSets {
@@ -250,7 +257,9 @@ struct PlanSets {
 
 int64_t deep_stack_pitch(int W) { return (int64_t)align_up((size_t)W, 32); }
 
-PlanSets expand_sets(const irp_set* sets, int nsets) {
+int spline_path(int W, int H);
+
+PlanSets expand_sets(const irp_set* sets, int nsets, int interp) {
   PlanSets ps;
   ps.user = sets;
   for (int i = 0; i < nsets; ++i) {
@@ -263,6 +272,20 @@ PlanSets expand_sets(const irp_set* sets, int nsets) {
     }
     DeepSet d;
     d.user = i;
+    d.rows = interp == IRP_INTERP_SPLINE3 && spline_path(s.W, s.H) && !s.stack_out;
+    if (d.rows) {  // the whole set, prefilter only
+      d.own_stack = false;
+      d.spitch = 0;
+      irp_set cs = s;
+      cs.mean_out = nullptr;
+      cs.median_out = nullptr;
+      cs.nkept_out = nullptr;
+      ps.sets.push_back(cs);
+      ps.deep_of.push_back((int)ps.deep.size());
+      ps.k0.push_back(0);
+      ps.deep.push_back(d);
+      continue;
+    }
     d.own_stack = s.stack_out == nullptr;
     d.spitch = d.own_stack ? deep_stack_pitch(s.W) : s.out_pitch;
     const int nch = (s.n + kDeepChunk - 1) / kDeepChunk;
@@ -305,12 +328,14 @@ size_t coef_frame_bytes(int W, int H) {
 
 // Sets are grouped by register bucket and, for the cubic spline, by the way
 // their coefficients are formed (the two take different reduction kernels).
-// Chunks of deep sets form groups of their own (no shared memory for samples).
+// Chunks of deep sets form groups of their own (no shared memory for
+// samples), and whole deep sets that only run their prefilter another.
 int group_key(const PlanSets& ps, int i, int interp) {
   const irp_set& s = ps.sets[i];
   const int b = reduce_bucket(s.n);
   const int key = interp == IRP_INTERP_SPLINE3 ? 2 * b + spline_path(s.W, s.H) : 2 * b;
-  return ps.deep_of[i] >= 0 ? key + 1000 : key;
+  if (ps.deep_of[i] < 0) return key;
+  return ps.deep[ps.deep_of[i]].rows ? 2000 : key + 1000;
 }
 
 void group_sets(const PlanSets& ps, int interp, std::vector<std::vector<int>>& groups) {
@@ -385,7 +410,7 @@ irp_status check_params(const irp_set* sets, int nsets, const irp_reduce_params*
       return IRP_ERR_UNSUPPORTED;
   }
   std::vector<std::vector<int>> groups;
-  group_sets(expand_sets(sets, nsets), p->interp, groups);
+  group_sets(expand_sets(sets, nsets, p->interp), p->interp, groups);
   if ((int)groups.size() > kMaxSub) return IRP_ERR_UNSUPPORTED;
   return IRP_OK;
 }
@@ -457,7 +482,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     const irp_set& u = ps.user[ps.deep[d].user];
     stack_base[d] = ps.deep[d].own_stack ? (float*)(ws + L.stack_off[d]) : u.stack_out;
     CombineArgs& a = dj[d];
-    a.stack = stack_base[d];
+    a.stack = ps.deep[d].rows ? nullptr : stack_base[d];  // rows: frames set below
     a.pitch = ps.deep[d].spitch;
     a.fstride = (int64_t)u.H * ps.deep[d].spitch;
     a.W = u.W;
@@ -492,6 +517,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     const int bucket = reduce_bucket(max_n);
     const int py = rows_per_warp(bucket, p->rows_per_warp);
     const bool stack_only = ps.deep_of[g[0]] >= 0;  // the group holds deep-set chunks
+    const bool pre_only = stack_only && ps.deep[ps.deep_of[g[0]]].rows;  // ... or whole sets
     // the group's reduction stencil: spline sets on the row + column passes
     // arrive horizontally filtered and take the vertical taps only
     const bool spline = stencil == ST_BSPLINE;
@@ -538,12 +564,20 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
       if (ps.deep_of[g[si]] >= 0) {
         const int d = ps.deep_of[g[si]];
         S.stack_only = 1;
-        S.stack_out = stack_base[d] + (int64_t)ps.k0[g[si]] * s.H * ps.deep[d].spitch;
+        if (ps.deep[d].rows) {
+          // the combine reads the set's frame table from this sub-plan's image
+          CombineArgs& a = dj[d];
+          a.frames = (const FrameDesc*)(ws + dev_off + plan_frames_offset((int)g.size())) +
+                     frame0;
+          a.coef_pitch = coef_pitch(s.W);
+        } else {
+          S.stack_out = stack_base[d] + (int64_t)ps.k0[g[si]] * s.H * ps.deep[d].spitch;
+        }
       }
       S.tiles_x = (s.W + TWc - 1) / TWc;
       S.tiles_y = (s.H + THr - 1) / THr;
       S.tile0 = tile0;
-      tile0 += S.tiles_x * S.tiles_y;
+      if (!pre_only) tile0 += S.tiles_x * S.tiles_y;  // prefilter-only sets have no tiles
       S.ptiles_x = (s.W + kPrefTile - 1) / kPrefTile;
       S.ptiles_y = (s.H + kPrefTile - 1) / kPrefTile;
       S.ptile0 = ptile0;
@@ -697,6 +731,7 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
       if (e == cudaSuccess && si.ncolsegs > 0) e = launch_spline_cols(&inl, dev_plan, si.ncolsegs, s);
       if (e != cudaSuccess) return note_cuda(e);
     }
+    if (si.nitems == 0) continue;  // prefilter-only sub-plan (deep spline sets)
     if (pf->persistent) {
       e = cudaMemsetAsync(&wsh->counters[si.counter], 0, sizeof(uint32_t), s);
       if (e != cudaSuccess) return note_cuda(e);
@@ -719,6 +754,7 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
 
 bool plan_fits_inline(const uint8_t* buf) {
   const PlanFile* pf = (const PlanFile*)buf;
+  if (pf->ndeep > 0) return false;  // deep combines read frame tables in the workspace
   for (int i = 0; i < pf->nsub; ++i)
     if (pf->sub[i].nsets > kMaxInlineSets || pf->sub[i].nframes > kMaxInlineFrames) return false;
   return true;
@@ -773,7 +809,7 @@ int irp_profile_read(double* ms_out, int64_t* launches_out, int max_kinds) {
 
 size_t irp_workspace_size(const irp_set* sets, int nsets, const irp_reduce_params* p) {
   if (check_params(sets, nsets, p) != IRP_OK) return 0;
-  const PlanSets ps = expand_sets(sets, nsets);
+  const PlanSets ps = expand_sets(sets, nsets, p->interp);
   std::vector<std::vector<int>> groups;
   group_sets(ps, p->interp, groups);
   return make_layout(ps, p, groups).total;
@@ -781,7 +817,7 @@ size_t irp_workspace_size(const irp_set* sets, int nsets, const irp_reduce_param
 
 size_t irp_plan_bytes(const irp_set* sets, int nsets, const irp_reduce_params* p) {
   if (check_params(sets, nsets, p) != IRP_OK) return 0;
-  return plan_file_bytes(expand_sets(sets, nsets), p);
+  return plan_file_bytes(expand_sets(sets, nsets, p->interp), p);
 }
 
 irp_status irp_plan_encode(const irp_set* sets, int nsets, const irp_reduce_params* p,
@@ -789,7 +825,7 @@ irp_status irp_plan_encode(const irp_set* sets, int nsets, const irp_reduce_para
   irp_status st = check_params(sets, nsets, p);
   if (st != IRP_OK) return st;
   if (!plan_host) return IRP_ERR_INVALID_ARG;
-  return encode_plan(expand_sets(sets, nsets), p, (uint8_t*)plan_host, plan_bytes,
+  return encode_plan(expand_sets(sets, nsets, p->interp), p, (uint8_t*)plan_host, plan_bytes,
                      (uint8_t*)workspace, ws_bytes);
 }
 
@@ -804,7 +840,7 @@ irp_status irp_reduce_set(const irp_set* sets, int nsets, const irp_reduce_param
                           void* workspace, size_t ws_bytes, void* stream) {
   irp_status st = check_params(sets, nsets, p);
   if (st != IRP_OK) return st;
-  const PlanSets ps = expand_sets(sets, nsets);
+  const PlanSets ps = expand_sets(sets, nsets, p->interp);
   std::vector<uint8_t> buf(plan_file_bytes(ps, p));
   st = encode_plan(ps, p, buf.data(), buf.size(), (uint8_t*)workspace, ws_bytes);
   if (st != IRP_OK) return st;
@@ -1097,7 +1133,7 @@ extern "C" irp_status irp_reduce_set_noalloc(const irp_set* sets, int nsets,
   irp_status st = check_params(sets, nsets, p);
   if (st != IRP_OK) return st;
   if (!aligned(status_out, 4)) return IRP_ERR_ALIGNMENT;
-  const PlanSets ps = expand_sets(sets, nsets);
+  const PlanSets ps = expand_sets(sets, nsets, p->interp);
   std::vector<std::vector<int>> groups;
   group_sets(ps, p->interp, groups);
   const size_t need = make_layout(ps, p, groups).total;

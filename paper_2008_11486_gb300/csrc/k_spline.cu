@@ -81,6 +81,13 @@ __global__ void __launch_bounds__(256, 2)
   if (item >= P.h->nrows) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const SetDesc& S = P.sets[find_by(P.sets, P.h->nsets, item, 0)];
+  if (S.ready_flag) {  // the set's raw frames may still be arriving
+    __shared__ int s_ok;
+    if (threadIdx.x == 0)
+      s_ok = wait_ready(S.ready_flag, S.ready_value, P.h->spin_limit, P.h->status);
+    __syncthreads();
+    if (!s_ok) return;  // status latched
+  }
   const int W = S.W, H = S.H;
   const int nrb = (H + RB - 1) / RB;
   const int local = item - S.row0;

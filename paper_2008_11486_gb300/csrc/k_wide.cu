@@ -7,12 +7,22 @@
 
 namespace irp {
 
-// The CTA copies its [n][32] slab of the stack into shared memory (each
-// frame's 32 pixels are one 128-byte row segment), then its 8 warps take the
-// 32 pixels in turn: load, sort (the sorted run replaces the samples in
-// shared memory, where the order statistics are read), clip, and write the
-// results as one row.
-template <int J, bool F16>
+// One frame's source for the CTA's output row when the samples come from
+// horizontally filtered spline rows (32 bytes, shared memory).
+struct RowTap {
+  const float* row;  // filtered row of the first vertical tap, null if the row is invalid
+  int vx0, vx1;      // valid output columns
+  float wy[4];       // vertical cubic B-spline weights
+};
+
+// The CTA gathers its [n][32] slab of samples into shared memory, then its 8
+// warps take the 32 pixels in turn: load, sort (the sorted run replaces the
+// samples in shared memory, where the order statistics are read), clip, and
+// write the results as one row.  The samples are read from an aligned stack
+// (each frame's 32 pixels one 128-byte row segment), or (ROWS) formed from a
+// cubic-spline frame whose rows already carry the horizontal taps: the four
+// vertical taps, in the fused kernel's order, so that the samples are the same.
+template <int J, bool F16, bool ROWS>
 __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs a, int tiles_x) {
   extern __shared__ float s_wide[];
   __shared__ float s_mean[32], s_median[32];
@@ -35,7 +45,50 @@ __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs a, in
     if (a.valid && !__ldg(a.valid + o)) v = kInf;
     return (v == v) ? v : kInf;
   };
-  {
+  if (ROWS) {
+    // the frames' sources for this output row, after the sample slab
+    RowTap* tab = (RowTap*)(s_wide + SM::kBytes / sizeof(float));
+    for (int k = t; k < n; k += kWideThreads) {
+      const FrameDesc* F = a.frames + k;
+      RowTap r;
+      const int vy0 = __ldg(&F->vy0), vy1 = __ldg(&F->vy1);
+      const float* coef = (const float*)__ldg((const unsigned long long*)&F->coef);
+      r.row = (y >= vy0 && y <= vy1) ? coef + (int64_t)(y + __ldg(&F->oy) + 2) * a.coef_pitch
+                                     : nullptr;
+      r.vx0 = __ldg(&F->vx0);
+      r.vx1 = __ldg(&F->vx1);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) r.wy[j] = __ldg(&F->wy[j]);
+      tab[k] = r;
+    }
+    __syncthreads();
+    const int x = x0 + lane;
+    const int64_t p1 = a.coef_pitch;
+    constexpr int kBatch = 4;  // samples (4 loads each) in flight per thread
+    for (int k0 = warp; k0 < n; k0 += 8 * kBatch) {
+      float h[kBatch][4];
+      float4 w[kBatch];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        const int k = k0 + 8 * b;
+        const RowTap r = k < n ? tab[k] : RowTap{nullptr, 0, -1, {0.0f, 0.0f, 0.0f, 0.0f}};
+        const bool ok = r.row && x >= r.vx0 && x <= r.vx1;
+        w[b] = make_float4(r.wy[0], r.wy[1], r.wy[2], r.wy[3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[b][j] = ok ? __ldg(r.row + x + j * p1) : kInf;
+      }
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        const int k = k0 + 8 * b;
+        if (k >= n) continue;
+        float acc = w[b].x * h[b][0];
+        acc = __fmaf_rn(w[b].y, h[b][1], acc);
+        acc = __fmaf_rn(w[b].z, h[b][2], acc);
+        acc = __fmaf_rn(w[b].w, h[b][3], acc);
+        s_wide[SM::at(lane, k)] = h[b][0] < kInf ? acc : kInf;
+      }
+    }
+  } else {
     // staging: thread (warp, lane) copies frames warp, warp + 8, ... of pixel lane
     const int x = x0 + lane;
     const bool xin = x < a.W;
@@ -81,7 +134,7 @@ __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs a, in
       s_median[p] = o.median;
       s_kept[p] = o.kept;
     }
-    if (a.reject_out) {  // debug output: the frames' samples again, in frame order
+    if (!ROWS && a.reject_out) {  // debug output: the frames' samples again, in frame order
       const int x = x0 + p;
       const int64_t o0 = (int64_t)y * a.pitch + x;
       for (int k = lane; k < n; k += 32) {
@@ -100,11 +153,11 @@ __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs a, in
   }
 }
 
-template <int J, bool F16>
+template <int J, bool F16, bool ROWS>
 static cudaError_t combine_wide_j(const CombineArgs& a, cudaStream_t s) {
   static size_t granted = 0;
-  const size_t smem = WideSmem<J>::kBytes;
-  auto fn = k_combine_wide<J, F16>;
+  const size_t smem = WideSmem<J>::kBytes + (ROWS ? (size_t)a.n * sizeof(RowTap) : 0);
+  auto fn = k_combine_wide<J, F16, ROWS>;
   if (smem > granted && smem > 47 * 1024) {
     const cudaError_t e =
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -118,19 +171,20 @@ static cudaError_t combine_wide_j(const CombineArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <bool F16>
+template <bool F16, bool ROWS>
 static cudaError_t combine_wide_f(const CombineArgs& a, cudaStream_t s) {
   switch (wide_j(a.n)) {
-    case 4: return combine_wide_j<4, F16>(a, s);
-    case 8: return combine_wide_j<8, F16>(a, s);
-    case 16: return combine_wide_j<16, F16>(a, s);
-    default: return combine_wide_j<32, F16>(a, s);
+    case 4: return combine_wide_j<4, F16, ROWS>(a, s);
+    case 8: return combine_wide_j<8, F16, ROWS>(a, s);
+    case 16: return combine_wide_j<16, F16, ROWS>(a, s);
+    default: return combine_wide_j<32, F16, ROWS>(a, s);
   }
 }
 
 cudaError_t launch_combine_wide(const CombineArgs& a, bool f16, cudaStream_t s) {
   if (a.n < 1 || a.n > kWideMaxFrames) return cudaErrorInvalidValue;
-  return f16 ? combine_wide_f<true>(a, s) : combine_wide_f<false>(a, s);
+  if (!a.stack) return a.frames ? combine_wide_f<false, true>(a, s) : cudaErrorInvalidValue;
+  return f16 ? combine_wide_f<true, false>(a, s) : combine_wide_f<false, false>(a, s);
 }
 
 }  // namespace irp

@@ -59,6 +59,13 @@ __global__ void __launch_bounds__(kPrefThreads, 1)
     si = lo;
   }
   const SetDesc& S = P.sets[si];
+  if (SRC == SRC_RAW && S.ready_flag) {  // the set's raw frames may still be arriving
+    __shared__ int s_ok;
+    if (threadIdx.x == 0)
+      s_ok = wait_ready(S.ready_flag, S.ready_value, P.h->spin_limit, P.h->status);
+    __syncthreads();
+    if (!s_ok) return;  // status latched
+  }
   const int ntiles = S.ptiles_x * S.ptiles_y;
   const int local = item - S.ptile0;
   const int grp = local / ntiles;

@@ -42,7 +42,9 @@ struct ShiftArgs {
 };
 
 struct CombineArgs {
-  const void* stack;
+  const void* stack;         // null: samples from horizontally filtered spline rows
+  const FrameDesc* frames;   // ... of these frames (device), when stack is null
+  int64_t coef_pitch;        // ... with this row pitch
   int64_t pitch, fstride;
   int W, H, n, pad;
   const float* scale;

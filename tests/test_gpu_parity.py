@@ -278,19 +278,21 @@ def test_bad_flat_master_is_latched():
     assert core.sync_status(ws) == 0  # cleared after reading
 
 
-def test_bounded_wait_gives_up_with_timeout():
-    """A set whose ready flag nothing sets: the kernel's bounded wait ends,
-    IRP_ERR_TIMEOUT is latched, and the context stays usable."""
-    fs = synth.make_set(64, 32, 3, 1.0, 11, n_stars=3)
+@pytest.mark.parametrize("interp,H", [("bilinear", 32), ("spline3", 32), ("spline3", 40)])
+def test_bounded_wait_gives_up_with_timeout(interp, H):
+    """A set whose ready flag nothing sets: the kernels' bounded waits end
+    (the spline prefilter's too: 32 rows take the tiled prefilter, 40 the
+    row pass), IRP_ERR_TIMEOUT is latched, and the context stays usable."""
+    fs = synth.make_set(64, H, 3, 1.0, 11, n_stars=3)
     s = core.device_set(fs).alloc_outputs()
     s.ready_flag = torch.zeros(1, dtype=torch.int32, device="cuda")
     s.ready_value = 1
-    ws = core.reduce_sets([s], core.reduce_params("bilinear", wait_spin_limit=2000))
+    ws = core.reduce_sets([s], core.reduce_params(interp, wait_spin_limit=2000))
     assert core.sync_status(ws) == 7
     s.ready_flag.fill_(1)
-    ws = core.reduce_sets([s], core.reduce_params("bilinear", wait_spin_limit=2000), ws=ws)
+    ws = core.reduce_sets([s], core.reduce_params(interp, wait_spin_limit=2000), ws=ws)
     assert core.sync_status(ws) == 0
-    ref = oracle.reduce_set(fs, interp="bilinear")
+    ref = oracle.reduce_set(fs, interp=interp)
     compare("after timeout", s.mean.cpu().numpy(), ref["mean"],
             mean_tolerance(ref["mean"]) + 1e-2)
 

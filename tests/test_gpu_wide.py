@@ -121,6 +121,26 @@ def test_deep_set_fused_matches_oracle(interp, W, H, n):
     check_against_oracle(fs, got, interp, 3.0, 3)
 
 
+@pytest.mark.parametrize("W,H,n", [(40, 36, 80), (100, 50, 200), (70, 34, 65)])
+def test_deep_spline_from_filtered_rows_equals_stack_path(W, H, n):
+    """Without a caller stack, a deep spline set is combined straight from its
+    horizontally filtered rows (vertical taps inside the combine); with one,
+    its chunks write the stack first.  The samples are formed by the same
+    FP32 operations, so the two results are bit-identical."""
+    fs = synth.make_set(W, H, n, 5.0, 7350 + n, n_stars=15, n_cr=4)
+    rows = run_fused([fs], "spline3", want_stack=False)[0]
+    stack = run_fused([fs], "spline3", want_stack=True)[0]
+    for k in ("mean", "median"):
+        assert np.array_equal(rows[k].view(np.uint32), stack[k].view(np.uint32)), k
+    assert np.array_equal(rows["nkept"], stack["nkept"])
+    ref = oracle.reduce_set(fs, interp="spline3")
+    m = (ref["margin"] >= 1e-3) & (rows["nkept"] == ref["nkept"])
+    assert m.mean() > 0.99
+    samp = sample_tolerance(fs, "spline3", oracle).max(axis=0)
+    compare("deep spline rows mean", rows["mean"], ref["mean"],
+            mean_tolerance(ref["mean"]) + samp, m)
+
+
 def test_deep_set_in_a_batch_and_persistent():
     """A deep set (workspace stack) beside plain sets: each result equals its
     standalone reduction, in both launch forms."""
@@ -137,6 +157,20 @@ def test_deep_set_in_a_batch_and_persistent():
     # the workspace-stack form equals the caller-stack form
     with_stack = run_fused(fss[:1], "bilinear", want_stack=True)[0]
     assert np.array_equal(with_stack["mean"].view(np.uint32), alone[0]["mean"].view(np.uint32))
+
+
+def test_deep_spline_sets_in_a_batch():
+    """Two deep spline sets (filtered-row path, and the tiled path's stack
+    chunks for a 30-row frame) beside a plain one, in both launch forms."""
+    fss = [synth.make_set(64, 40, 90, 4.0, 7410, n_stars=10, n_cr=3),
+           synth.make_set(50, 30, 70, 4.0, 7411, n_stars=10, n_cr=3),
+           synth.make_set(48, 48, 9, 4.0, 7412, n_stars=10, n_cr=3)]
+    alone = [run_fused([fs], "spline3", want_stack=False)[0] for fs in fss]
+    for persistent in (False, True):
+        batch = run_fused(fss, "spline3", persistent=persistent, want_stack=False)
+        for a, b in zip(alone, batch):
+            for k in ("mean", "median"):
+                assert np.array_equal(a[k].view(np.uint32), b[k].view(np.uint32))
 
 
 def test_deep_set_masked():
