@@ -606,6 +606,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
         if (!fill_geometry(F, s.dx[k], s.dy[k], s.W, s.H, p->interp)) return IRP_ERR_INVALID_ARG;
         F.src = s.frames[k];
         F.flags = (aligned(s.frames[k], 16) && s.raw_pitch % 8 == 0) ? 1 : 0;
+        F.flags |= (aligned(s.frames[k], 8) && s.raw_pitch % 4 == 0) ? 2 : 0;
         F.t = s.exptime[k];
         F.scale = 1.0f;
         F.offset = 0.0f;

@@ -44,7 +44,8 @@ struct FrameDesc {
   int32_t vx0, vx1;    // sample valid iff vx0 <= x <= vx1 ...
   int32_t vy0, vy1;    //              ... and vy0 <= y <= vy1
   float wx[4], wy[4];  // stencil weights (bilinear: 1-f, f; spline: beta3)
-  int32_t flags;       // bit 0: raw frame 16-byte aligned with a pitch of 8k elements
+  int32_t flags;       // bit 0: raw frame 16-byte aligned with a pitch of 8k elements;
+                       // bit 1: 8-byte aligned with a pitch of 4k elements
   float* crow;         // row-pass spline coefficients (workspace) or null
   int32_t pad[6];
 };

@@ -140,16 +140,24 @@ __global__ void __launch_bounds__(256, 2)
   const int ntask = nr * nk;
   uint4* stage = s_raw + warp * kRowStages * RQ * 32;
   // the row's 16-byte chunks in order (contiguous per instruction), each put
-  // where its owner lane reads it: chunk c of lane c / RQ at (c % RQ) * 32 + c / RQ
+  // where its owner lane reads it: chunk c of lane c / RQ at (c % RQ) * 32 + c / RQ.
+  // Rows 16-byte aligned take one copy per chunk, rows 8-byte aligned (pitch
+  // 4k, e.g. 1020 columns) two; the columns past the row are zero-filled.
   auto issue = [&](int t, int slot) {
     const int rr = t / nk, f = t - rr * nk;
-    const bool aligned_f = s_flags[f] & 1;
+    const int fl = s_flags[f];
     const uint16_t* raw = s_src[f] + (int64_t)(y0 + rr) * S.src_pitch;
 #pragma unroll
     for (int k = 0; k < RQ; ++k) {
       const int c = 32 * k + lane, lc = c / RQ, ic = c - lc * RQ;
-      cp_async16_if(aligned_f && (lc + 1) * E <= W, stage + (slot * RQ + ic) * 32 + lc,
-                    raw + 8 * c, 16);
+      const int nb = max(0, min(16, 2 * (W - 8 * c)));  // bytes inside the row
+      uint4* dst = stage + (slot * RQ + ic) * 32 + lc;
+      if (fl & 1) {
+        cp_async16(dst, nb ? raw + 8 * c : raw, nb);
+      } else if (fl & 2) {
+        cp_async8(dst, nb ? raw + 8 * c : raw, min(nb, 8));
+        cp_async8((uint8_t*)dst + 8, nb > 8 ? raw + 8 * c + 4 : raw, max(nb - 8, 0));
+      }
     }
   };
 #pragma unroll
@@ -183,7 +191,7 @@ __global__ void __launch_bounds__(256, 2)
     const int rr = t / nk, f = t - rr * nk;
     const int y = y0 + rr;
     const float tk = s_t[f];
-    const bool vec = (s_flags[f] & 1) && x0 + E <= W;
+    const bool vec = (s_flags[f] & 3) != 0;  // staged (zero past the row)
     const float4* mb = s_m + (rr * 3 + 0) * MQ * 32 + lane;
     const float4* md = mb + MQ * 32;
     const float4* mr = md + MQ * 32;

@@ -158,6 +158,9 @@ def _padded_device_set(fs, pad_raw, pad_master):
     (96, 34, 17, 8, 4),      # narrow: most lanes past the frame
     (64, 300, 3, 0, 0),      # two column-pass row blocks, the second mostly mirrored
     (200, 513, 2, 4, 0),     # three row blocks with a one-row tail
+    (1020, 40, 4, 0, 0),     # the paper's 1020 columns: 8-byte rows, partial last lane
+    (1000, 36, 3, 0, 0),     # 16-byte rows, the last lane's chunks partly past the row
+    (1018, 36, 3, 2, 0),     # 8-byte rows, a chunk cut inside its first half
 ])
 def test_spline_row_pass_shapes(W, H, n, pad_raw, pad_master):
     fs = synth.make_set(W, H, n, 6.0, 4100 + W + n, n_stars=30, n_cr=6)
