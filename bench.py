@@ -72,6 +72,20 @@ WORKLOADS = {
                    seed=11486004),
 }
 
+# Scans of the paper's Sec. 3.2.2 (execution time against the frame size at
+# 100 frames per band, and against the frame count at 1020 x 1020), 3 bands
+# each: one JSON line with the time per point and a straight-line fit.
+SWEEPS = {
+    "sweep_size": dict(desc="3 bands x 100 frames of N x N uint16 (n = 300), N = 256 .. 4096, "
+                            "offsets +-10 px, cubic-spline shift, 3-sigma clip + median",
+                       points=[(N, N, 100) for N in (256, 512, 1020, 2048, 4096)],
+                       offset=10.0, interp="spline3", persistent=False, seed=11486006),
+    "sweep_frames": dict(desc="3 bands of 1020 x 1020 uint16, 10 .. 333 frames per band (n = 30 "
+                              ".. 999), offsets +-10 px, cubic-spline shift, 3-sigma clip + median",
+                         points=[(1020, 1020, nb) for nb in (10, 30, 60, 100, 180, 333)],
+                         offset=10.0, interp="spline3", persistent=False, seed=11486007),
+}
+
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -181,7 +195,9 @@ def algorithmic_bytes(kind, sets, interp, want_nkept=False):
 
 
 def workload_shapes(workload):
-    """(W, H, n) of every set of one step."""
+    """(W, H, n) of every set of one step (of a scan: every point's 3 bands)."""
+    if workload in SWEEPS:
+        return [p for p in SWEEPS[workload]["points"] for _ in range(3)]
     cfg = WORKLOADS[workload]
     if cfg["sets"] is not None:
         return list(cfg["sets"])
@@ -194,7 +210,7 @@ def cpu_baseline(workload, steps, warmup, nthreads, as_reference=False):
     workload, cropped to at most 256 rows (and 2048 columns), per step."""
     import oracle
     from paper_2008_11486_gb300 import synth
-    cfg = WORKLOADS[workload]
+    cfg = WORKLOADS[workload] if workload in WORKLOADS else SWEEPS[workload]
     W, H, n = max(workload_shapes(workload), key=lambda t: t[2])
     Hs, Ws = min(H, 256), min(W, 2048)
     fs = synth.make_set(Ws, Hs, n, cfg["offset"], cfg["seed"],
@@ -225,7 +241,7 @@ def run_reference(args, world, rank):
         return
     nthreads = os.cpu_count() or 1
     cb = cpu_baseline(args.workload, args.steps, args.warmup, nthreads, as_reference=True)
-    cfg = WORKLOADS[args.workload]
+    cfg = WORKLOADS[args.workload] if args.workload in WORKLOADS else SWEEPS[args.workload]
     line = {"impl": "reference", "metric": "reduced Mpix/s", "value": cb["value"],
             "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": cb["seconds_per_sample"] * 1e3, "higher_is_better": True,
@@ -405,14 +421,14 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bands", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="bands", choices=sorted(WORKLOADS) + sorted(SWEEPS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--requests", type=int, default=12, help="served: requests at the nominal rate")
     ap.add_argument("--rate", type=float, default=0.5, help="served: Poisson arrival rate (1/s)")
     args = ap.parse_args()
     heavy = args.workload in ("deep", "precision", "batch", "served", "masked", "paper",
-                              "paper_band")
+                              "paper_band") or args.workload in SWEEPS
     if args.steps is None:
         args.steps = 10 if heavy else 2000
     if args.warmup is None:
@@ -431,12 +447,18 @@ def main():
     irp_build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = WORKLOADS[args.workload]
+    cfg = WORKLOADS[args.workload] if args.workload in WORKLOADS else SWEEPS[args.workload]
     interp = cfg["interp"]
     stream = torch.cuda.Stream(dev)   # non-default stream: graph capture needs one
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     extra = {}
+
+    if args.workload in SWEEPS:
+        line = run_sweep(args, dev, stream, world, rank, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
 
     if args.workload == "served":
         line = run_served(args, cfg, dev, world, rank, local)
@@ -552,6 +574,51 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_sweep(args, dev, stream, world, rank, local):
+    """Times one call over the 3 bands of every point of a scan (inputs larger
+    than L2 at all but the smallest points; L2 flushed before each step)."""
+    import torch
+    from paper_2008_11486_gb300 import core
+    cfg = SWEEPS[args.workload]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    params = core.reduce_params(cfg["interp"], core.clip_params(3.0, 3), persistent=False)
+    points, t_ms, px_all, clocks = [], 0.0, 0, None
+    for (W, H, nb) in cfg["points"]:
+        shapes = [(W, H, nb)] * 3
+        sets = make_device_sets(shapes, cfg, dev, rank)
+        ws = core.workspace(core.workspace_size(sets, params), dev)
+        total, _, prof, clocks = timed_steps(lambda: core.reduce_sets(sets, params, ws=ws),
+                                             args.steps, args.warmup, stream, flush, world, local)
+        assert core.sync_status(ws) == 0
+        ms = total / args.steps
+        px = 3 * nb * W * H
+        points.append({"W": W, "H": H, "frames_per_band": nb, "raw_mpix": px / 1e6,
+                       "ms_per_step": round(ms, 4), "mpix_s": round(world * px / (ms * 1e-3) / 1e6, 1),
+                       "kernel_ms": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]}})
+        t_ms += ms
+        px_all += px
+        del sets, ws
+        torch.cuda.empty_cache()
+    # t = a + b * pixels: the largest relative residual shows how straight the scan is
+    x = np.array([p["raw_mpix"] for p in points])
+    y = np.array([p["ms_per_step"] for p in points])
+    b, a = np.polyfit(x, y, 1)
+    resid = float(np.max(np.abs(a + b * x - y) / y))
+    return {"metric": "reduced Mpix/s", "value": round(world * px_all / (t_ms * 1e-3) / 1e6, 1),
+            "unit": "Mpix/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded device generator, paper-shaped frames)",
+            "config": {"workload": args.workload, "desc": cfg["desc"],
+                       "value": "all points' pixels over the sum of their step times",
+                       "l2": "flushed by a 256 MB write before every timed step",
+                       "parallelism": f"replicas x{world} (sets independent per GPU)"},
+            "points": points,
+            "linear_fit": {"ms_offset": round(float(a), 4), "ms_per_mpix": round(float(b), 6),
+                           "max_rel_residual": round(resid, 4)},
+            "clocks": clocks}
 
 
 def host_frameset(s):
