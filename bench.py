@@ -313,8 +313,11 @@ def timed_steps(step, steps, warmup, stream, flush, world, local):
 # the kernel sources it was taken on, identified by their hash; otherwise the
 # line reports null.
 TRAFFIC = {
-    "bands": ("2b434fda97051f45", "prefilter", 373_607_322),  # row + column pass
-    "deep": ("2b434fda97051f45", "reduce", 1_416_998_229),
+    "bands": ("880627b9fa83fe0f", "prefilter", 374_658_918),  # row + column pass
+    "deep": ("880627b9fa83fe0f", "reduce", 1_417_006_250),
+    "paper_band": ("880627b9fa83fe0f", "combine", 758_094_592),
+    # three bands of the paper_band shape: three launches of the same traffic
+    "paper": ("880627b9fa83fe0f", "combine", 3 * 758_094_592),
 }
 
 
