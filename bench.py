@@ -354,10 +354,13 @@ def roofline(prof, steps, bytes_per_step_by_kind, ms_per_step, path_bytes_per_st
             "path_frac": round(path_bytes_per_step / (ms_per_step * 1e-3) / 1e9 / peak, 4)}
 
 
-def e2e_run(sets, step, e2e_steps, stream, world):
-    """Same metric through the public API with pinned host buffers: every step
-    copies its raw frames in and its mean/median out inside the timed region."""
+def e2e_run(sets, params, ws, e2e_steps, stream, world):
+    """Same metric through the public host-buffer entry point
+    (irp_reduce_set_host): every step copies its raw frames in from pinned
+    host memory and its mean/median out, inside the timed region; each set's
+    copies overlap its neighbours' reduction."""
     import torch
+    from paper_2008_11486_gb300 import core
     host_raw = [torch.empty((s.n, s.H, s.W), dtype=torch.uint16, pin_memory=True) for s in sets]
     for h, s in zip(host_raw, sets):
         h.copy_(s._keep[0])
@@ -365,12 +368,7 @@ def e2e_run(sets, step, e2e_steps, stream, world):
                  torch.empty((s.H, s.W), dtype=torch.float32, pin_memory=True)) for s in sets]
 
     def e2e_step():
-        for h, s in zip(host_raw, sets):
-            s._keep[0].copy_(h, non_blocking=True)
-        step()
-        for (m, d), s in zip(host_out, sets):
-            m.copy_(s.mean, non_blocking=True)
-            d.copy_(s.median, non_blocking=True)
+        core.reduce_sets_host(sets, host_raw, host_out, params, ws=ws, stream=stream)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -381,9 +379,11 @@ def e2e_run(sets, step, e2e_steps, stream, world):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
+    assert core.sync_status(ws) == 0
     ms = max_over_ranks(e0.elapsed_time(e1), world) / e2e_steps
     px = sum(s.n * s.W * s.H for s in sets)
     return {"value": round(world * px / (ms * 1e-3) / 1e6, 1), "unit": "Mpix/s",
+            "api": "irp_reduce_set_host (per set: upload, reduce, download, overlapped)",
             "h2d_bytes_per_step": sum(h.numel() * 2 for h in host_raw),
             "d2h_bytes_per_step": sum(2 * s.H * s.W * 4 for s in sets)}
 
@@ -539,7 +539,7 @@ def main():
     rf = roofline(prof, args.steps, step_bytes(shapes, interp), ms_per_step,
                   algorithmic_bytes("reduce", shapes, "bilinear"), args.workload)
     gpu_launches = int(sum(v[1] for v in prof.values()))
-    e2e = e2e_run(sets, step, args.e2e_steps, stream, world)
+    e2e = e2e_run(sets, params, ws, args.e2e_steps, stream, world)
 
     if args.workload == "precision" and rank == 0:
         fs_host = host_frameset(sets[0])

@@ -260,6 +260,39 @@ irp_status irp_plan_launch(const void* plan_host, size_t plan_bytes, void* works
 irp_status irp_reduce_set_noalloc(const irp_set* sets, int nsets, const irp_reduce_params* p,
                                   uint32_t* status_out, void* stream);
 
+/* irp_reduce_set_host -- irp_reduce_set with the raw frames and the results
+ * in host memory (Sec. 2.2: the frames are read into host memory and sent to
+ * the GPU; the results come back to be written out).
+ *   sets  as for irp_reduce_set: the device buffers that receive the frames
+ *         (sets[i].frames) and the results (mean_out, median_out, nkept_out).
+ *   io    [nsets] host side of each set:
+ *           frames  host array of n host pointers, raw uint16 [H][pitch]
+ *                   (page-locked memory lets the copies overlap the work);
+ *           mean, median, nkept  host [H][out_pitch] destinations, each
+ *                   nullable, and only with the matching device output set.
+ *   workspace  >= irp_workspace_size(&sets[i], 1, p) for every i.
+ * For each set in turn: its frames are copied to the device on an upload
+ * stream, the set is reduced on `stream` once they have landed, and its
+ * results are copied back on a download stream.  Set i+1 is uploaded while
+ * set i is reduced, and set i's results return while set i+1 is reduced.
+ * Both copy streams are the library's own (one pair per device, created on
+ * first use); they fork from and join back into `stream` through events, so
+ * the call is ordered on `stream` like any other, and the results are in
+ * host memory once `stream` has reached the call's end.  No device memory
+ * is allocated.  Validation errors return before anything is enqueued. */
+typedef struct {
+  const uint16_t* const* frames;  /* host array of n host pointers            */
+  int64_t pitch;                  /* elements, shared by the set's frames     */
+  float* mean;                    /* host, nullable */
+  float* median;                  /* host, nullable */
+  uint16_t* nkept;                /* host, nullable */
+  int64_t out_pitch;              /* elements (>= W when an output is set)   */
+} irp_host_io;
+
+irp_status irp_reduce_set_host(const irp_set* sets, int nsets, const irp_host_io* io,
+                               const irp_reduce_params* p, void* workspace, size_t ws_bytes,
+                               void* stream);
+
 /* Synchronises the stream, returns and clears the device status latched in
  * the workspace's status word. */
 irp_status irp_sync_status(void* workspace, void* stream);

@@ -50,6 +50,11 @@ class IrpSet(ctypes.Structure):
                 ("mask", c_p), ("mask_pitch", c_i64), ("saturation", ctypes.c_float)]
 
 
+class IrpHostIo(ctypes.Structure):
+    _fields_ = [("frames", ctypes.POINTER(c_p)), ("pitch", c_i64), ("mean", c_p),
+                ("median", c_p), ("nkept", c_p), ("out_pitch", c_i64)]
+
+
 class ReduceParams(ctypes.Structure):
     _fields_ = [("interp", c_i), ("clip", ClipParams), ("normalize_flat", c_i),
                 ("persistent", c_i), ("max_ctas", c_i), ("wait_spin_limit", c_i),
@@ -99,6 +104,9 @@ def lib() -> ctypes.CDLL:
             L.irp_workspace_size.argtypes = [P(IrpSet), c_i, P(ReduceParams)]
             L.irp_reduce_set.restype = c_i
             L.irp_reduce_set.argtypes = [P(IrpSet), c_i, P(ReduceParams), PP, c_sz, PP]
+            L.irp_reduce_set_host.restype = c_i
+            L.irp_reduce_set_host.argtypes = [P(IrpSet), c_i, P(IrpHostIo), P(ReduceParams),
+                                              PP, c_sz, PP]
             L.irp_plan_bytes.restype = c_sz
             L.irp_plan_bytes.argtypes = [P(IrpSet), c_i, P(ReduceParams)]
             L.irp_plan_encode.restype = c_i

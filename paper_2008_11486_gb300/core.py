@@ -12,8 +12,8 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from ._binding import (DTYPE, INTERP, KERNEL_KINDS, ClipParams, IrpSet, ReduceParams, check,
-                       lib)
+from ._binding import (DTYPE, INTERP, KERNEL_KINDS, ClipParams, IrpHostIo, IrpSet, ReduceParams,
+                       check, lib)
 
 
 def _vp(t):
@@ -244,6 +244,35 @@ def reduce_sets(sets, params: ReduceParams, ws=None, stream=None):
         ws = workspace(need, sets[0].frames[0].device)
     check(L.irp_reduce_set(arr, len(sets), ctypes.byref(params), _vp(ws), ws.numel(),
                            _stream(stream)), "irp_reduce_set")
+    del keep
+    return ws
+
+
+def reduce_sets_host(sets, host_raw, host_out, params: ReduceParams, ws=None, stream=None):
+    """irp_reduce_set_host: ``host_raw`` [i] is a host uint16 tensor [n, H, W]
+    (pinned for overlap) copied into ``sets[i]``'s device frames, and
+    ``host_out`` [i] a (mean, median) pair of host float32 [H, W] tensors (or
+    None) that receive its results; each set is uploaded, reduced and
+    downloaded in turn, the copies overlapping the neighbouring sets' work."""
+    arr, keep = _irp_sets(sets)
+    L = lib()
+    need = max(L.irp_workspace_size(ctypes.byref(a), 1, ctypes.byref(params)) for a in arr)
+    if need == 0:
+        raise ValueError("irp_workspace_size rejected the sets/params")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, sets[0].frames[0].device)
+    io = (IrpHostIo * len(sets))()
+    for i, (h, out) in enumerate(zip(host_raw, host_out)):
+        n, H, W = h.shape
+        ptrs = (ctypes.c_void_p * n)(*[h[k].data_ptr() for k in range(n)])
+        keep.append(ptrs)
+        io[i].frames = ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p))
+        io[i].pitch = h.stride(1)
+        if out is not None:
+            io[i].mean, io[i].median = out[0].data_ptr(), out[1].data_ptr()
+            io[i].out_pitch = out[0].stride(0)
+    check(L.irp_reduce_set_host(arr, len(sets), io, ctypes.byref(params), _vp(ws), ws.numel(),
+                                _stream(stream)), "irp_reduce_set_host")
     del keep
     return ws
 

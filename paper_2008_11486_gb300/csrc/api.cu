@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -753,6 +754,41 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
   return IRP_OK;
 }
 
+// Copy streams of irp_reduce_set_host, one pair per device (created on first
+// use and kept for the process), and the events that order them.
+struct HostPipe {
+  std::mutex mu;
+  cudaStream_t up = nullptr, down = nullptr;
+  std::vector<cudaEvent_t> ev;
+};
+
+cudaError_t host_pipe(HostPipe** out) {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static HostPipe pipes[kMaxDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  HostPipe& hp = pipes[dev];
+  if (!hp.up) e = cudaStreamCreateWithFlags(&hp.up, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !hp.down) e = cudaStreamCreateWithFlags(&hp.down, cudaStreamNonBlocking);
+  *out = &hp;
+  return e;
+}
+
+// At least `count` events in the pipe (caller holds hp->mu).
+cudaError_t host_pipe_events(HostPipe* hp, int count) {
+  while ((int)hp->ev.size() < count) {
+    cudaEvent_t ev = nullptr;
+    const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    hp->ev.push_back(ev);
+  }
+  return cudaSuccess;
+}
+
 bool plan_fits_inline(const uint8_t* buf) {
   const PlanFile* pf = (const PlanFile*)buf;
   if (pf->ndeep > 0) return false;  // deep combines read frame tables in the workspace
@@ -849,6 +885,84 @@ irp_status irp_reduce_set(const irp_set* sets, int nsets, const irp_reduce_param
   // pageable buffer (cudaMemcpyAsync then returns after staging the data).
   return run_plan(buf.data(), (uint8_t*)workspace, ws_bytes, (cudaStream_t)stream,
                   !plan_fits_inline(buf.data()));
+}
+
+irp_status irp_reduce_set_host(const irp_set* sets, int nsets, const irp_host_io* io,
+                               const irp_reduce_params* p, void* workspace, size_t ws_bytes,
+                               void* stream) {
+  irp_status st = check_params(sets, nsets, p);
+  if (st != IRP_OK) return st;
+  if (!io) return IRP_ERR_INVALID_ARG;
+  for (int i = 0; i < nsets; ++i) {
+    const irp_set& s = sets[i];
+    const irp_host_io& h = io[i];
+    if (!h.frames || h.pitch < s.W) return IRP_ERR_INVALID_ARG;
+    for (int k = 0; k < s.n; ++k)
+      if (!h.frames[k]) return IRP_ERR_INVALID_ARG;
+    if ((h.mean && !s.mean_out) || (h.median && !s.median_out) || (h.nkept && !s.nkept_out))
+      return IRP_ERR_INVALID_ARG;
+    if ((h.mean || h.median || h.nkept) && h.out_pitch < s.W) return IRP_ERR_INVALID_ARG;
+    if (irp_workspace_size(&s, 1, p) > ws_bytes) return IRP_ERR_WORKSPACE;
+  }
+  if (!workspace || !aligned(workspace, kAlign)) return IRP_ERR_WORKSPACE;
+  HostPipe* hp = nullptr;
+  cudaError_t e = host_pipe(&hp);
+  if (e != cudaSuccess) return note_cuda(e);
+  std::lock_guard<std::mutex> lock(hp->mu);  // the pipe's streams and events
+  e = host_pipe_events(hp, 2 * nsets + 1);
+  if (e != cudaSuccess) return note_cuda(e);
+  cudaStream_t s0 = (cudaStream_t)stream;
+  cudaEvent_t* ev = hp->ev.data();
+  // fork: both copy streams start after the work already on the caller's stream
+  e = cudaEventRecord(ev[0], s0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->up, ev[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->down, ev[0], 0);
+  for (int i = 0; i < nsets && e == cudaSuccess; ++i) {
+    const irp_set& s = sets[i];
+    const irp_host_io& h = io[i];
+    if (h.pitch == s.W && s.raw_pitch == s.W) {
+      // dense frames: one copy per run of frames contiguous on both sides
+      const size_t fb = (size_t)s.W * s.H * 2;
+      for (int k0 = 0; k0 < s.n && e == cudaSuccess;) {
+        const uint8_t* hs = (const uint8_t*)h.frames[k0];
+        const uint8_t* ds = (const uint8_t*)s.frames[k0];
+        int k1 = k0 + 1;
+        while (k1 < s.n && (const uint8_t*)h.frames[k1] == hs + (size_t)(k1 - k0) * fb &&
+               (const uint8_t*)s.frames[k1] == ds + (size_t)(k1 - k0) * fb)
+          ++k1;
+        e = cudaMemcpyAsync((void*)ds, hs, (size_t)(k1 - k0) * fb, cudaMemcpyHostToDevice,
+                            hp->up);
+        k0 = k1;
+      }
+    } else {
+      for (int k = 0; k < s.n && e == cudaSuccess; ++k)
+        e = cudaMemcpy2DAsync((void*)s.frames[k], (size_t)s.raw_pitch * 2, h.frames[k],
+                              (size_t)h.pitch * 2, (size_t)s.W * 2, (size_t)s.H,
+                              cudaMemcpyHostToDevice, hp->up);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1 + 2 * i], hp->up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, ev[1 + 2 * i], 0);
+    if (e != cudaSuccess) break;
+    st = irp_reduce_set(&s, 1, p, workspace, ws_bytes, stream);
+    if (st != IRP_OK) return st;
+    e = cudaEventRecord(ev[2 + 2 * i], s0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->down, ev[2 + 2 * i], 0);
+    auto down = [&](void* dst, const void* src, size_t es) {
+      if (e != cudaSuccess || !dst) return;
+      if (h.out_pitch == s.W && s.out_pitch == s.W)  // dense: one plain copy
+        e = cudaMemcpyAsync(dst, src, (size_t)s.W * s.H * es, cudaMemcpyDeviceToHost, hp->down);
+      else
+        e = cudaMemcpy2DAsync(dst, (size_t)h.out_pitch * es, src, (size_t)s.out_pitch * es,
+                              (size_t)s.W * es, (size_t)s.H, cudaMemcpyDeviceToHost, hp->down);
+    };
+    down(h.mean, s.mean_out, sizeof(float));
+    down(h.median, s.median_out, sizeof(float));
+    down(h.nkept, s.nkept_out, sizeof(uint16_t));
+  }
+  // join: the caller's stream continues after the last download
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], hp->down);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, ev[0], 0);
+  return cuda_status(e);
 }
 
 irp_status irp_sync_status(void* workspace, void* stream) {
@@ -1095,7 +1209,6 @@ irp_status irp_combine(const void* stack, int64_t pitch, int64_t frame_stride, i
 // irp_reduce_set_noalloc: the fused reduction with its scratch in a static
 // device array instead of a caller-provided workspace (see include/irp.h).
 // ---------------------------------------------------------------------------
-#include <mutex>
 
 namespace {
 

@@ -148,6 +148,34 @@ def test_deep_sets_plan_and_stack_workspace(L):
             assert L.irp_workspace_size(arr, 3, ctypes.byref(p)) > 0
 
 
+def test_reduce_set_host_validation_codes(L):
+    n, W, H = 3, 64, 48
+    hp = (ctypes.c_void_p * n)(*[FAKE + 65536 * k for k in range(n)])
+    io = (B.IrpHostIo * 1)()
+    io[0].frames = ctypes.cast(hp, ctypes.POINTER(ctypes.c_void_p))
+    io[0].pitch = W
+    arr = (B.IrpSet * 1)(_set(n=n, W=W, H=H))
+    p = _params()
+
+    def call(io_arg, ws_bytes=1 << 30):
+        return L.irp_reduce_set_host(arr, 1, io_arg, ctypes.byref(p), ctypes.c_void_p(FAKE),
+                                     ws_bytes, None)
+    assert call(None) == 1                      # no host side
+    io[0].pitch = W - 1
+    assert call(io) == 1                        # host pitch < W
+    io[0].pitch = W
+    io[0].nkept, io[0].out_pitch = FAKE, W     # host kept count without a device one
+    assert call(io) == 1
+    io[0].nkept = None
+    io[0].mean, io[0].out_pitch = FAKE, W - 2  # output pitch < W
+    assert call(io) == 1
+    io[0].out_pitch = W
+    assert call(io, ws_bytes=256) == 3          # workspace smaller than one set's
+    bad = (ctypes.c_void_p * n)(FAKE, None, FAKE)
+    io[0].frames = ctypes.cast(bad, ctypes.POINTER(ctypes.c_void_p))
+    assert call(io) == 1                        # null host frame
+
+
 def test_unfused_validation_codes(L):
     clip = B.ClipParams(3.0, 3.0, 3, 0, 0)
     f = ctypes.c_void_p(FAKE)
