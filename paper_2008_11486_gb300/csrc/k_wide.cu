@@ -15,19 +15,20 @@ struct RowTap {
   float wy[4];       // vertical cubic B-spline weights
 };
 
-// The CTA gathers its [n][32] slab of samples into shared memory, then its 8
-// warps take the 32 pixels in turn: load, sort (the sorted run replaces the
-// samples in shared memory, where the order statistics are read), clip, and
-// write the results as one row.  The samples are read from an aligned stack
+// The CTA gathers its [n][32] slab of samples into shared memory, then each
+// of its 8 warps takes 32 / G pixels at a time, one per group of G lanes:
+// load, sort (the sorted run replaces the samples in shared memory, where the
+// order statistics are read), clip, and the CTA writes the results as one row.  The samples are read from an aligned stack
 // (each frame's 32 pixels one 128-byte row segment), or (ROWS) formed from a
 // cubic-spline frame whose rows already carry the horizontal taps: the four
 // vertical taps, in the fused kernel's order, so that the samples are the same.
-template <int J, bool F16, bool ROWS>
+template <int G, int J, bool F16, bool ROWS>
 __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs a, int tiles_x) {
   extern __shared__ float s_wide[];
   __shared__ float s_mean[32], s_median[32];
   __shared__ int s_kept[32];
-  using SM = WideSmem<J>;
+  using SM = WideSmem<G, J>;
+  constexpr int P = 32 / G;  // pixels per warp at a time
   const int tx = blockIdx.x % tiles_x;
   const int y = blockIdx.x / tiles_x;
   const int x0 = tx * 32;
@@ -109,35 +110,38 @@ __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs a, in
     }
   }
   __syncthreads();
+  const int g = lane / G, tg = lane % G;  // the lane's group and its index in it
 #pragma unroll 1
-  for (int p = warp; p < 32; p += 8) {
-    if (x0 + p >= a.W) break;
+  for (int q = warp; q < 32 / P; q += 8) {
+    // the warp's groups take pixels 32 / P apart (conflict-free shared memory);
+    // pixels past the frame were staged as invalid and give no output
+    const int p = q + g * (32 / P);
     float* const col = s_wide + SM::at(p, 0);  // this pixel's samples
     float v[J];
     int cnt = 0;
 #pragma unroll
     for (int i = 0; i < J; ++i) {
-      const int e = lane * J + i;
-      v[i] = e < n ? col[lane * (J + 1) + i] : kInf;
+      const int e = tg * J + i;
+      v[i] = e < n ? col[tg * (J + 1) + i] : kInf;
       cnt += v[i] < kInf ? 1 : 0;
     }
-    const int m = __reduce_add_sync(0xffffffffu, cnt);
-    if (m > 0) warp_bitonic_sort<J>(v, lane);
+    const int m = group_sum_i<G>(cnt);
+    group_bitonic_sort<G, J>(v, tg);
     // the sorted run replaces the pixel's samples (sample e at col[e + e / J])
     __syncwarp();
 #pragma unroll
-    for (int i = 0; i < J; ++i) col[lane * (J + 1) + i] = v[i];
+    for (int i = 0; i < J; ++i) col[tg * (J + 1) + i] = v[i];
     __syncwarp();
-    const WideOut o = wide_combine<J>(v, col, m, a.clip, lane);
-    if (lane == 0) {
+    const WideOut o = group_combine<G, J>(v, col, m, a.clip, tg);
+    if (tg == 0) {
       s_mean[p] = o.mean;
       s_median[p] = o.median;
       s_kept[p] = o.kept;
     }
-    if (!ROWS && a.reject_out) {  // debug output: the frames' samples again, in frame order
-      const int x = x0 + p;
+    const int x = x0 + p;
+    if (!ROWS && a.reject_out && x < a.W) {  // debug output: the samples again, in frame order
       const int64_t o0 = (int64_t)y * a.pitch + x;
-      for (int k = lane; k < n; k += 32) {
+      for (int k = tg; k < n; k += G) {
         const float val = load(k, (int64_t)k * a.fstride + o0);
         const bool rej = (val < kInf) & ((val < o.lo_val) | (val > o.hi_val));
         a.reject_out[((int64_t)k * a.H + y) * a.out_pitch + x] = rej ? 1 : 0;
@@ -153,11 +157,11 @@ __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs a, in
   }
 }
 
-template <int J, bool F16, bool ROWS>
+template <int G, int J, bool F16, bool ROWS>
 static cudaError_t combine_wide_j(const CombineArgs& a, cudaStream_t s) {
   static size_t granted = 0;
-  const size_t smem = WideSmem<J>::kBytes + (ROWS ? (size_t)a.n * sizeof(RowTap) : 0);
-  auto fn = k_combine_wide<J, F16, ROWS>;
+  const size_t smem = WideSmem<G, J>::kBytes + (ROWS ? (size_t)a.n * sizeof(RowTap) : 0);
+  auto fn = k_combine_wide<G, J, F16, ROWS>;
   if (smem > granted && smem > 47 * 1024) {
     const cudaError_t e =
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -173,11 +177,11 @@ static cudaError_t combine_wide_j(const CombineArgs& a, cudaStream_t s) {
 
 template <bool F16, bool ROWS>
 static cudaError_t combine_wide_f(const CombineArgs& a, cudaStream_t s) {
-  switch (wide_j(a.n)) {
-    case 4: return combine_wide_j<4, F16, ROWS>(a, s);
-    case 8: return combine_wide_j<8, F16, ROWS>(a, s);
-    case 16: return combine_wide_j<16, F16, ROWS>(a, s);
-    default: return combine_wide_j<32, F16, ROWS>(a, s);
+  switch (wide_g(a.n) * 100 + wide_j(a.n)) {
+    case 816: return combine_wide_j<8, 16, F16, ROWS>(a, s);
+    case 1616: return combine_wide_j<16, 16, F16, ROWS>(a, s);
+    case 3216: return combine_wide_j<32, 16, F16, ROWS>(a, s);
+    default: return combine_wide_j<32, 32, F16, ROWS>(a, s);
   }
 }
 
