@@ -59,9 +59,9 @@ extern "C" {
 
 #define IRP_VERSION 10000      /* 1.0.0 */
 #define IRP_MAX_FRAMES 64      /* frames per set on the per-thread register combine */
-#define IRP_MAX_WIDE_FRAMES 1024 /* frames per set; from IRP_MAX_FRAMES + 1 on, one
-                                    warp combines each pixel (the paper's bands hold
-                                    180 frames, Sec. 3.2.1) */
+#define IRP_MAX_WIDE_FRAMES 1024 /* frames per set; from IRP_MAX_FRAMES + 1 on, a
+                                    group of lanes combines each pixel (the paper's
+                                    bands hold 180 frames, Sec. 3.2.1) */
 
 typedef enum {
   IRP_OK = 0,
@@ -145,8 +145,8 @@ size_t irp_shift_workspace_size(int W, int H, int n, irp_interp interp);
  *   reject_out nullable [n][H][out_pitch] uint8, 1 where a valid sample was
  *              rejected by the clip (debug output).
  *   n <= IRP_MAX_WIDE_FRAMES: up to IRP_MAX_FRAMES one thread sorts a pixel's
- *   samples in registers; deeper stacks take one warp per pixel (bitonic sort
- *   over the lanes, the same clip), with identical semantics.
+ *   samples in registers; deeper stacks take 4 to 32 lanes per pixel
+ *   (bitonic sort over the lanes, the same clip), with identical semantics.
  * ------------------------------------------------------------------------- */
 irp_status irp_combine(const void* stack, int64_t pitch, int64_t frame_stride,
                        int W, int H, int n, irp_stack_dtype dt,

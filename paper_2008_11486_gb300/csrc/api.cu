@@ -227,8 +227,8 @@ struct Layout {
 };
 
 // Sets deeper than the register buckets (IRP_MAX_FRAMES < n <=
-// IRP_MAX_WIDE_FRAMES) are reduced in two steps, and one warp per pixel
-// combines them.
+// IRP_MAX_WIDE_FRAMES) are reduced in two steps, and groups of lanes
+// combine them.
 // * Cubic spline on the row + column passes, without a caller stack: the
 //   column pass already leaves each frame's rows filtered along x on the
 //   output grid, so the set only runs its prefilter, and the combine applies
@@ -476,7 +476,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
   pf->nsets = nsets;
   pf->ndeep = (int)ps.deep.size();
   pf->deep_off = deep_jobs_offset(nsets);
-  // the deep sets' stacks and their warp-per-pixel combines
+  // the deep sets' stacks and their lane-group combines
   std::vector<float*> stack_base(ps.deep.size());
   CombineArgs* dj = (CombineArgs*)(buf + pf->deep_off);
   for (size_t d = 0; d < ps.deep.size(); ++d) {

@@ -177,10 +177,11 @@ static cudaError_t combine_wide_j(const CombineArgs& a, cudaStream_t s) {
 
 template <bool F16, bool ROWS>
 static cudaError_t combine_wide_f(const CombineArgs& a, cudaStream_t s) {
-  switch (wide_g(a.n) * 100 + wide_j(a.n)) {
-    case 816: return combine_wide_j<8, 16, F16, ROWS>(a, s);
-    case 1616: return combine_wide_j<16, 16, F16, ROWS>(a, s);
-    case 3216: return combine_wide_j<32, 16, F16, ROWS>(a, s);
+  static_assert(wide_j(1) == 32, "one sample count per lane");
+  switch (wide_g(a.n)) {
+    case 4: return combine_wide_j<4, 32, F16, ROWS>(a, s);
+    case 8: return combine_wide_j<8, 32, F16, ROWS>(a, s);
+    case 16: return combine_wide_j<16, 32, F16, ROWS>(a, s);
     default: return combine_wide_j<32, 32, F16, ROWS>(a, s);
   }
 }

@@ -22,13 +22,16 @@ constexpr int kWideThreads = 256;  // 8 warps, 32 pixels of one output row per C
 constexpr int kWideMaxFrames = IRP_MAX_WIDE_FRAMES;
 
 // Lanes per pixel (G) and samples per lane (J) for n frames: the sort length
-// G J is the power of two >= n, with J = 16 up to 512 frames.
-__host__ __device__ constexpr int wide_g(int n) { return n <= 128 ? 8 : (n <= 256 ? 16 : 32); }
-__host__ __device__ constexpr int wide_j(int n) { return n <= 512 ? 16 : 32; }
+// G J is the power of two >= n, with 32 samples per lane, so that only the
+// sort stages of stride 32 or more cross lanes.
+__host__ __device__ constexpr int wide_g(int n) {
+  return n <= 128 ? 4 : (n <= 256 ? 8 : (n <= 512 ? 16 : 32));
+}
+__host__ __device__ constexpr int wide_j(int n) { return 32; }
 
 // Shared-memory position of sample e of pixel p.  A pixel's samples are
 // contiguous with one pad word after every J of them, and the pixel stride
-// G (J + 1) + 1 is 1 mod 4.  The staging stores (one frame, 32 pixels) then
+// G (J + 1) + 1 is odd.  The staging stores (one frame, 32 pixels) then
 // touch 32 distinct banks, and so do the sort's loads, where the warp's
 // 32 / G groups read pixels 32 / (32 / G) apart in lane-major blocks of J.
 template <int G, int J>
