@@ -313,11 +313,11 @@ def timed_steps(step, steps, warmup, stream, flush, world, local):
 # the kernel sources it was taken on, identified by their hash; otherwise the
 # line reports null.
 TRAFFIC = {
-    "bands": ("880627b9fa83fe0f", "prefilter", 374_658_918),  # row + column pass
-    "deep": ("880627b9fa83fe0f", "reduce", 1_417_006_250),
-    "paper_band": ("880627b9fa83fe0f", "combine", 758_094_592),
+    "bands": ("7d03a8604e4f95fd", "prefilter", 374_298_316),  # row + column pass
+    "deep": ("7d03a8604e4f95fd", "reduce", 1_417_629_525),
+    "paper_band": ("7d03a8604e4f95fd", "combine", 758_102_912),
     # three bands of the paper_band shape: three launches of the same traffic
-    "paper": ("880627b9fa83fe0f", "combine", 3 * 758_094_592),
+    "paper": ("7d03a8604e4f95fd", "combine", 3 * 758_102_912),
 }
 
 
