@@ -57,7 +57,7 @@ WORKLOADS = {
                   sets=None, offset=5.0, interp="bilinear", persistent=True, seed=11486003),
     "paper": dict(desc="the paper's timed run: 3 bands x 180 frames of 1020x1020 uint16 (n = 540), "
                        "offsets +-10 px, cubic-spline shift, 3-sigma clipped mean (3 passes) + "
-                       "median; 180-frame sets: aligned stack in chunks, then one warp per pixel",
+                       "median; 180-frame sets: prefilter, then 8 lanes per pixel from the filtered rows",
                   sets=[(1020, 1020, 180)] * 3, offset=10.0, interp="spline3", persistent=False,
                   seed=11486005),
     "paper_band": dict(desc="one band of the paper's run: 180 frames of 1020x1020 uint16, offsets "
@@ -169,7 +169,7 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-DEEP = 64  # sets of more frames combine from an aligned stack, one warp per pixel
+DEEP = 64  # sets of more frames are combined by groups of lanes, not one thread per pixel
 
 
 def algorithmic_bytes(kind, sets, interp, want_nkept=False):
@@ -178,7 +178,9 @@ def algorithmic_bytes(kind, sets, interp, want_nkept=False):
     reduce from spline coefficients: n*P*4 + P*8
     prefilter: n*P*2 (raw) + P*12 (masters) + n*P*4 (coefficients)
     sets of more than 64 frames: reduce writes the aligned FP32 stack (n*P*4)
-    in place of the outputs, and combine reads it back: n*P*4 + P*8."""
+    in place of the outputs, and combine reads it back, or reads the filtered
+    rows of a spline set on the row/column passes (no reduce launch then):
+    n*P*4 + P*8."""
     tot = 0
     for (W, H, n) in sets:
         P = W * H

@@ -73,7 +73,7 @@ cudaError_t launch_calibrate(const CalibArgs& a, int nk, bool f16, void* out, in
 cudaError_t launch_shift(const ShiftArgs& a, int nk, int stencil, bool f16, cudaStream_t s);
 cudaError_t launch_prefilter_frames(const InlinePlan* inl, int grid, bool f16, cudaStream_t s);
 cudaError_t launch_combine(const CombineArgs& a, bool f16, cudaStream_t s);
-// More than IRP_MAX_FRAMES frames (up to IRP_MAX_WIDE_FRAMES): one warp per pixel.
+// More than IRP_MAX_FRAMES frames (up to IRP_MAX_WIDE_FRAMES): a group of lanes per pixel.
 cudaError_t launch_combine_wide(const CombineArgs& a, bool f16, cudaStream_t s);
 
 }  // namespace irp
