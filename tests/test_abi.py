@@ -133,14 +133,17 @@ def test_deep_sets_plan_and_stack_workspace(L):
     # a set deeper than the register buckets adds its aligned FP32 stack to
     # the workspace, [n][H][W rounded up to 32] floats, unless the caller
     # passes stack_out; its chunks form one extra sub-plan
-    assert L.irp_workspace_size((B.IrpSet * 1)(_set(n=1024)), 1, ctypes.byref(_params())) > 0
+    # the IrpSet objects own the host arrays the structs point at: keep them
+    big = _set(n=1024)
+    assert L.irp_workspace_size((B.IrpSet * 1)(big), 1, ctypes.byref(_params())) > 0
     plain = _set(n=64, W=50, H=48)
     deep = _set(n=100, W=50, H=48)
     deep_own = _set(n=100, W=50, H=48, stack_out=FAKE + 32768)
     ws = {k: L.irp_workspace_size((B.IrpSet * 1)(s), 1, ctypes.byref(_params()))
           for k, s in (("deep", deep), ("own", deep_own))}
     assert ws["deep"] - ws["own"] == -(-100 * 48 * 64 * 4 // 256) * 256
-    arr = (B.IrpSet * 3)(plain, deep, _set(n=300, W=40, H=40))
+    deeper = _set(n=300, W=40, H=40)
+    arr = (B.IrpSet * 3)(plain, deep, deeper)
     for interp in (0, 1, 2):
         for persistent in (0, 1):
             p = _params(interp=interp, persistent=persistent)
@@ -154,7 +157,8 @@ def test_reduce_set_host_validation_codes(L):
     io = (B.IrpHostIo * 1)()
     io[0].frames = ctypes.cast(hp, ctypes.POINTER(ctypes.c_void_p))
     io[0].pitch = W
-    arr = (B.IrpSet * 1)(_set(n=n, W=W, H=H))
+    s = _set(n=n, W=W, H=H)  # owns the host arrays the struct points at
+    arr = (B.IrpSet * 1)(s)
     p = _params()
 
     def call(io_arg, ws_bytes=1 << 30):
