@@ -206,9 +206,11 @@ typedef struct {
   int max_ctas;                   /* persistent grid size; 0 = SMs x occupancy  */
   int wait_spin_limit;            /* bounded-wait polls before IRP_ERR_TIMEOUT; 0 = default */
   int rows_per_warp;              /* tile height / 8: 0 = default of the frame-count
-                                     bucket (4 up to 16 frames, else 2); the other
-                                     accepted value is 2 (resp. 1); anything else
-                                     falls back to the default */
+                                     bucket (4 up to 16 frames, else 2), or the
+                                     bucket's other value when the default tiles
+                                     of a group would give fewer than two CTAs per
+                                     SM; the other accepted value is 2 (resp. 1);
+                                     anything else falls back to the default */
 } irp_reduce_params;
 
 size_t irp_workspace_size(const irp_set* sets, int nsets, const irp_reduce_params* p);

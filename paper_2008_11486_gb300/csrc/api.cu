@@ -516,7 +516,6 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
       max_n = std::max(max_n, sets[i].n);
     }
     const int bucket = reduce_bucket(max_n);
-    const int py = rows_per_warp(bucket, p->rows_per_warp);
     const bool stack_only = ps.deep_of[g[0]] >= 0;  // the group holds deep-set chunks
     const bool pre_only = stack_only && ps.deep[ps.deep_of[g[0]]].rows;  // ... or whole sets
     // the group's reduction stencil: spline sets on the row + column passes
@@ -524,7 +523,19 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     const bool spline = stencil == ST_BSPLINE;
     const bool gpath = spline && spline_path(sets[g[0]].W, sets[g[0]].H);
     const int gstencil = gpath ? ST_BSPLINE_V : stencil;
-    const int TWc = tile_cols(gstencil), THr = tile_rows(bucket, py);
+    const int TWc = tile_cols(gstencil);
+    // rows per warp: the caller's choice, else the bucket's default, unless the
+    // group's tiles at the default would give fewer than two CTAs per SM; the
+    // bucket's shorter tiles then spread the group further
+    int py = rows_per_warp(bucket, p->rows_per_warp);
+    if (p->rows_per_warp == 0) {
+      int64_t tiles = 0;
+      for (int i : g)
+        tiles += (int64_t)((sets[i].W + TWc - 1) / TWc) *
+                 ((sets[i].H + tile_rows(bucket, py) - 1) / tile_rows(bucket, py));
+      if (tiles < 2 * (int64_t)sm_count()) py = rows_per_warp(bucket, rows_per_warp_alt(bucket));
+    }
+    const int THr = tile_rows(bucket, py);
     // prefilter work items: tiles x frame groups, enough groups to fill the GPU twice
     int pgroups = 1;
     if (stencil == ST_BSPLINE) {
