@@ -68,7 +68,7 @@ typedef enum {
   IRP_ERR_INVALID_ARG = 1,   /* null required pointer, bad size, bad enum */
   IRP_ERR_ALIGNMENT = 2,     /* a buffer is not aligned to its element size */
   IRP_ERR_WORKSPACE = 3,     /* workspace missing or smaller than required */
-  IRP_ERR_UNSUPPORTED = 4,   /* a valid request this build does not implement */
+  IRP_ERR_UNSUPPORTED = 4,   /* a valid request the library does not implement */
   IRP_ERR_BAD_MASTER = 5,    /* device: flat value <= 0 or not finite */
   IRP_ERR_CUDA = 6,          /* a CUDA runtime call failed */
   IRP_ERR_TIMEOUT = 7        /* device: a bounded wait gave up */
