@@ -39,62 +39,74 @@ def clip_params(kappa=3.0, max_iter=3, center="mean", ddof=0, kappa_lo=None, kap
                       1 if center == "median" else 0, int(ddof))
 
 
-def build(force: bool = False) -> str:
-    """Compiles liboracle.so with gcc (OpenMP when available)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
-        return _LIB
-    tmp = _LIB + f".{os.getpid()}.tmp"
+def compile_library(src: str, out: str) -> str:
+    """Compiles one oracle source file into a shared library at ``out`` with
+    gcc (OpenMP when available).  The test suite also compiles deliberately
+    broken copies of the source this way to check that its pins fail."""
+    tmp = out + f".{os.getpid()}.tmp"
     base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-            _SRC, "-o", tmp, "-lm"]
+            "-I" + _HERE, src, "-o", tmp, "-lm"]
     try:
         subprocess.run(base[:6] + ["-fopenmp"] + base[6:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
         subprocess.run(base, check=True, capture_output=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compiles liboracle.so from oracle.c unless it is up to date."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        return _LIB
+    return compile_library(_SRC, _LIB)
+
+
+def load(path: str):
+    """Loads an oracle shared library and declares its function signatures."""
+    L = ctypes.CDLL(path)
+    d, i, i64, p = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+    L.oracle_bspline3.restype = d
+    L.oracle_bspline3.argtypes = [d]
+    L.oracle_mirror.restype = i64
+    L.oracle_mirror.argtypes = [i64, i64]
+    L.oracle_mean_f32.restype = d
+    L.oracle_mean_f32.argtypes = [p, i64, i, i]
+    L.oracle_calibrate.restype = None
+    L.oracle_calibrate.argtypes = [p, i64, i, i, p, p, p, i64, d, d, p]
+    L.oracle_spline_solve_line.restype = None
+    L.oracle_spline_solve_line.argtypes = [p, i64, p, i64, i, p]
+    L.oracle_spline_coeffs.restype = None
+    L.oracle_spline_coeffs.argtypes = [p, i, i, p]
+    L.oracle_sample.restype = i
+    L.oracle_sample.argtypes = [p, i, i, i, i, d, d, i, p]
+    L.oracle_shift.restype = None
+    L.oracle_shift.argtypes = [p, i, i, d, d, i, p, p]
+    L.oracle_clip.restype = None
+    L.oracle_clip.argtypes = [p, p, i, ctypes.POINTER(ClipParams), p, p, p, p]
+    L.oracle_median.restype = d
+    L.oracle_median.argtypes = [p, p, i]
+    L.oracle_combine_stack.restype = None
+    L.oracle_combine_stack.argtypes = [p, p, i, i64, ctypes.POINTER(ClipParams), i,
+                                       p, p, p, p, p]
+    L.oracle_reduce_set.restype = i
+    L.oracle_reduce_set.argtypes = [p, i64, i64, i, i, i, p, p, p, i64, p, p, p, i, i,
+                                    ctypes.POINTER(ClipParams), i, i64, p, p,
+                                    p, p, p, p, p, p]
+    L.oracle_reduce_set_masked.restype = i
+    L.oracle_reduce_set_masked.argtypes = [p, i64, i64, i, i, i, p, p, p, i64, p, p, p,
+                                           i, i, p, i64, d,
+                                           ctypes.POINTER(ClipParams), i, i64, p, p,
+                                           p, p, p, p, p, p]
+    return L
 
 
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
-            d, i, i64, p = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
-            L.oracle_bspline3.restype = d
-            L.oracle_bspline3.argtypes = [d]
-            L.oracle_mirror.restype = i64
-            L.oracle_mirror.argtypes = [i64, i64]
-            L.oracle_mean_f32.restype = d
-            L.oracle_mean_f32.argtypes = [p, i64, i, i]
-            L.oracle_calibrate.restype = None
-            L.oracle_calibrate.argtypes = [p, i64, i, i, p, p, p, i64, d, d, p]
-            L.oracle_spline_solve_line.restype = None
-            L.oracle_spline_solve_line.argtypes = [p, i64, p, i64, i, p]
-            L.oracle_spline_coeffs.restype = None
-            L.oracle_spline_coeffs.argtypes = [p, i, i, p]
-            L.oracle_sample.restype = i
-            L.oracle_sample.argtypes = [p, i, i, i, i, d, d, i, p]
-            L.oracle_shift.restype = None
-            L.oracle_shift.argtypes = [p, i, i, d, d, i, p, p]
-            L.oracle_clip.restype = None
-            L.oracle_clip.argtypes = [p, p, i, ctypes.POINTER(ClipParams), p, p, p, p]
-            L.oracle_median.restype = d
-            L.oracle_median.argtypes = [p, p, i]
-            L.oracle_combine_stack.restype = None
-            L.oracle_combine_stack.argtypes = [p, p, i, i64, ctypes.POINTER(ClipParams), i,
-                                               p, p, p, p, p]
-            L.oracle_reduce_set.restype = i
-            L.oracle_reduce_set.argtypes = [p, i64, i64, i, i, i, p, p, p, i64, p, p, p, i, i,
-                                            ctypes.POINTER(ClipParams), i, i64, p, p,
-                                            p, p, p, p, p, p]
-            L.oracle_reduce_set_masked.restype = i
-            L.oracle_reduce_set_masked.argtypes = [p, i64, i64, i, i, i, p, p, p, i64, p, p, p,
-                                                   i, i, p, i64, d,
-                                                   ctypes.POINTER(ClipParams), i, i64, p, p,
-                                                   p, p, p, p, p, p]
-            _lib = L
+            _lib = load(build())
     return _lib
 
 

@@ -309,6 +309,41 @@ def test_reduce_set_constant_frames(interp):
     assert (out["nkept"][inner] == 6).all()
 
 
+@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3"])
+def test_reduce_set_per_frame_exposure_and_flat_normalisation(interp):
+    """Worked by hand.  Three constant frames of raw 1500, 1600, 1700 ADU with
+    exposures 10, 60 and 100 s, bias 1000 ADU, dark rate 0.5 ADU/s, zero
+    offsets (every interpolation is the identity).  Each frame's dark is its
+    own exposure times the rate (Sec. 2.1 dark subtraction): raw - bias - dark
+    = 495, 570, 650 ADU.  Three samples cannot be clipped at kappa 3
+    (Samuelson), so the mean is 1715 / 3 and the median 570, each divided by
+    the pixel's flat."""
+    W, H = 6, 5
+    raw = np.empty((3, H, W), np.uint16)
+    raw[0], raw[1], raw[2] = 1500, 1600, 1700
+    bias = np.full((H, W), 1000.0, np.float32)
+    dark = np.full((H, W), 0.5, np.float32)
+    t = np.array([10.0, 60.0, 100.0], np.float32)
+    zero = np.zeros(3)
+    # flat 0.5 everywhere: 990, 1140, 1300 -> median 1140, mean 3430 / 3
+    fs = synth.FrameSet(raw=raw, bias=bias, dark=dark, flat=np.full((H, W), 0.5, np.float32),
+                        exptime=t, dx=zero, dy=zero)
+    out = oracle.reduce_set(fs, interp=interp)
+    np.testing.assert_allclose(out["median"], 1140.0, rtol=1e-12)
+    np.testing.assert_allclose(out["mean"], 1143.3333333333333, rtol=1e-12)
+    # flat 0.5 and 1.0 in alternate columns, normalised by its mean 0.75: the
+    # flat becomes 2/3 and 4/3, so the values are 1.5x and 0.75x the
+    # differences: median 855 and 427.5, mean 857.5 and 428.75
+    flat = np.tile(np.array([0.5, 1.0], np.float32), (H, W // 2))
+    fs = synth.FrameSet(raw=raw, bias=bias, dark=dark, flat=flat, exptime=t, dx=zero, dy=zero)
+    out = oracle.reduce_set(fs, interp=interp, normalize_flat=True)
+    np.testing.assert_allclose(out["median"][:, 0::2], 855.0, rtol=1e-12)
+    np.testing.assert_allclose(out["median"][:, 1::2], 427.5, rtol=1e-12)
+    np.testing.assert_allclose(out["mean"][:, 0::2], 857.5, rtol=1e-12)
+    np.testing.assert_allclose(out["mean"][:, 1::2], 428.75, rtol=1e-12)
+    assert (out["nkept"] == 3).all()
+
+
 def test_reduce_set_composes_calibrate_shift_clip_median():
     fs = synth.make_set(40, 36, 7, 3.0, 9)
     full = oracle.reduce_set(fs, interp="bilinear", kappa=2.0, want_stack=True)
