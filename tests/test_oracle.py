@@ -282,6 +282,10 @@ def test_clip_margin_reports_distance_to_threshold():
     assert mg == 0.0
     _, _, _, mg = oracle.clip(np.array([5.0, 5.0]))
     assert mg == np.inf
+    # 0 0 0 0 10 at kappa 3: mean 2, sigma^2 = (4*4 + 64)/5 = 16, threshold 12;
+    # the 10 lies 8 from the mean, one sigma inside it (the zeros 2.5 sigma)
+    _, kept, _, mg = oracle.clip(np.array([0.0, 0.0, 0.0, 0.0, 10.0]))
+    assert kept == 5 and mg == pytest.approx(1.0, abs=1e-15)
 
 
 @pytest.mark.parametrize("m", [1, 2, 3, 4, 7, 10, 31, 40])

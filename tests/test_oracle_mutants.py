@@ -96,6 +96,16 @@ MUTANTS = [
     ("each frame sampled at the first frame's offset",
      "sample_src(&src[k], W, H, x, y, dx[k], dy[k], interp, &a);",
      "sample_src(&src[k], W, H, x, y, dx[0], dy[k], interp, &a);"),
+    # validity and masks
+    ("clip counts invalid samples", "alive[k] = valid[k] ? 1 : 0;", "alive[k] = 1;"),
+    ("median counts invalid samples", "    if (valid[k]) buf[m++] = x[k];\n",
+     "    buf[m++] = x[k];\n"),
+    ("stack combine ignores validity", "ok[k] = valid[(int64_t)k * P + o];", "ok[k] = 1;"),
+    ("nearest ignores bad pixels", "    if (src_bad(s, i, j)) return 0;\n", ""),
+    ("spline ignores bad pixels",
+     "if (w != 0.0 && src_bad(s, oracle_mirror(i, W), oracle_mirror(j, H))) return 0;", ""),
+    ("clip margin not in units of sigma", "double mg = fabs(fabs(d) - thr) / sigma;",
+     "double mg = fabs(fabs(d) - thr);"),
 ]
 
 
