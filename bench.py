@@ -315,15 +315,15 @@ def timed_steps(step, steps, warmup, stream, flush, world, local):
 # the kernel sources it was taken on, identified by their hash; otherwise the
 # line reports null.
 # The figures were captured on sources 7d03a8604e4f95fd.  The current sources
-# differ from those by one comment and by the plan's choice of shorter tiles
-# for groups of fewer than two tiles per SM, which none of these workloads
-# forms: their kernels and launches are the ones captured.
+# differ from those in comments and in the plan's choice of shorter tiles for
+# groups of fewer than two tiles per SM, which none of these workloads forms:
+# their kernels and launches are the ones captured.
 TRAFFIC = {
-    "bands": ("6fd564cb6364fb53", "prefilter", 374_298_316),  # row + column pass
-    "deep": ("6fd564cb6364fb53", "reduce", 1_417_629_525),
-    "paper_band": ("6fd564cb6364fb53", "combine", 758_102_912),
+    "bands": ("01544d57caae0ba5", "prefilter", 374_298_316),  # row + column pass
+    "deep": ("01544d57caae0ba5", "reduce", 1_417_629_525),
+    "paper_band": ("01544d57caae0ba5", "combine", 758_102_912),
     # three bands of the paper_band shape: three launches of the same traffic
-    "paper": ("6fd564cb6364fb53", "combine", 3 * 758_102_912),
+    "paper": ("01544d57caae0ba5", "combine", 3 * 758_102_912),
 }
 
 

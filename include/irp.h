@@ -163,8 +163,11 @@ irp_status irp_combine(const void* stack, int64_t pitch, int64_t frame_stride,
  * A set of more than IRP_MAX_FRAMES frames (up to IRP_MAX_WIDE_FRAMES) is
  * resampled in chunks of at most 16 frames into its aligned FP32 stack
  * [n][H][pitch] -- stack_out when given (pitch out_pitch), else the workspace
- * (pitch W rounded up to 32) -- and the stack is then combined one warp per
- * pixel; irp_workspace_size accounts for it.
+ * (pitch W rounded up to 32) -- and the stack is then combined by a group of
+ * lanes per pixel.  A cubic-spline set whose frames take the row and column
+ * passes (W from 34 to 2048, H at least 34) writes no stack unless stack_out
+ * is given: its combine forms each sample from the horizontally filtered
+ * rows.  irp_workspace_size accounts for what each set needs.
  * ------------------------------------------------------------------------- */
 typedef struct {
   const uint16_t* const* frames;  /* host array of n device pointers           */

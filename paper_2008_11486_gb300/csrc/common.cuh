@@ -1,7 +1,7 @@
 // common.cuh -- descriptors and device helpers shared by the sm_103a kernels.
 //
-// The fused path reduces frame sets tile by tile: one CTA owns an output tile
-// tile of the output grid of one set, walks the set's frames, calibrates and
+// The fused path reduces frame sets tile by tile: one CTA owns one tile of
+// the output grid of one set, walks the set's frames, calibrates and
 // resamples each frame's source window into shared memory, and finally
 // combines the per-pixel samples (sigma-clipped mean, median).
 #pragma once

@@ -1,7 +1,7 @@
 // k_wide.cu -- combination of an aligned stack of more frames than the
 // register buckets hold (Sec. 2.1 co-adding; the paper's sets reach 180
-// frames per band): one CTA per 32 pixels of an output row, one warp per
-// pixel.
+// frames per band): one CTA per 32 pixels of an output row, a group of
+// lanes per pixel (wide.cuh).
 #include "unfused.h"
 #include "wide.cuh"
 
