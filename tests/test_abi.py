@@ -83,6 +83,13 @@ def test_reduce_set_validation_codes(L):
     assert _reduce(L, [_set(n=1025)], _params()) == 4                  # too many frames
     assert _reduce(L, [_set()], _params(interp=7)) == 1                # bad interpolation
     assert _reduce(L, [_set(W=0)], _params()) == 1                     # empty frame
+    assert _reduce(L, [_set(H=0)], _params()) == 1
+    assert _reduce(L, [_set(n=0)], _params()) == 1                     # empty set
+    s0 = _set()  # owns the host arrays the struct points at
+    empty = (B.IrpSet * 1)(s0)
+    assert L.irp_reduce_set(empty, 0, ctypes.byref(_params()), ctypes.c_void_p(FAKE), 1 << 30,
+                            None) == 1                                  # no sets
+    assert L.irp_workspace_size(empty, 0, ctypes.byref(_params())) == 0
     assert _reduce(L, [_set(raw_pitch=10)], _params()) == 1            # pitch < W
     assert _reduce(L, [_set(bias=FAKE + 2)], _params()) == 2           # misaligned master
     assert _reduce(L, [_set(frames=[FAKE, 0, FAKE])], _params()) == 1  # null frame
