@@ -218,3 +218,25 @@ def test_unfused_validation_codes(L):
                            None, f, 4096, None) == 1
     assert L.irp_calibrate(f, 64, 4096, 64, 64, 2, f, f, f, 64, tp, 0, g, 64, 4096, 0, None,
                            None, f, 16, None) == 3
+
+
+def test_noalloc_validation_before_any_device_call(L):
+    # a separate prototype: the shared binding object stays as the tests that
+    # run on a GPU declare it
+    proto = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(B.IrpSet), ctypes.c_int,
+                             ctypes.POINTER(B.ReduceParams), ctypes.c_void_p, ctypes.c_void_p)
+    noalloc = proto(("irp_reduce_set_noalloc", L))
+
+    def call(sets, p, status=None):
+        arr = (B.IrpSet * max(len(sets), 1))(*sets)
+        return noalloc(arr, len(sets), ctypes.byref(p), status, None)
+
+    assert call([], _params()) == 1                                  # no sets
+    assert call([_set(W=0)], _params()) == 1                         # empty frame
+    assert call([_set(n=1025)], _params()) == 4                      # too many frames
+    assert call([_set()], _params(), status=FAKE + 2) == 2           # misaligned status word
+    # the spline workspace of 8 frames of 1024x512 (32 MiB) exceeds the 8 MiB scratch
+    assert call([_set(n=8, W=1024, H=512)], _params(interp=2)) == 3
+    # 64 sets of 40 frames: the plan outgrows the call's fixed host buffer
+    many = [_set(n=40, W=64, H=48) for _ in range(64)]
+    assert call(many, _params()) == 3

@@ -68,7 +68,7 @@ def test_noalloc_matches_workspace_entry_point_twice(L, interp):
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch(L):
-    # spline coefficients of 8 frames of 1024x512 need 16 MiB > 8 MiB of scratch
+    # the spline workspace of 8 frames of 1024x512 (32 MiB) exceeds the 8 MiB scratch
     fs = synth.make_const_set(1024, 512, 8, 1500, 1000.0, 0.05, 0.8, 60.0)
     s = core.device_set(fs).alloc_outputs()
     arr, keep = core._irp_sets([s])
