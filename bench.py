@@ -327,6 +327,42 @@ TRAFFIC = {
 }
 
 
+# Warp instructions executed per step by the dominant kernel kind (ncu
+# smsp__inst_executed, summed over the kind's launches in one step; the same
+# captures and source hash as TRAFFIC).  Against the issue peak -- one warp
+# instruction per cycle in each of an SM's 4 schedulers at the maximum SM
+# clock -- they bound the kernels that issue, not HBM, limits.
+ISSUE = {
+    "bands": ("01544d57caae0ba5", "prefilter", 35_221_760 + 38_887_200),  # rows + columns
+    "deep": ("01544d57caae0ba5", "reduce", 1_292_075_776),
+    "paper_band": ("01544d57caae0ba5", "combine", 1_195_229_264),
+    "paper": ("01544d57caae0ba5", "combine", 3 * 1_195_229_264),
+}
+
+
+def issue_roofline(workload, dom, dom_ms, sm_count, sm_max_mhz):
+    """Issue-rate roofline of the dominant kernel kind, or None without an ncu
+    instruction count for the current sources."""
+    rec = ISSUE.get(workload)
+    if not rec or rec[1] != dom or rec[0] != kernel_source_hash() or dom_ms <= 0:
+        return None
+    peak = sm_count * 4 * sm_max_mhz * 1e6 / 1e9  # G warp instructions / s
+    achieved = rec[2] / (dom_ms * 1e-3) / 1e9
+    return {"bound": "issue", "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G warp instructions/s", "frac": round(achieved / peak, 4),
+            "warp_instructions": rec[2],
+            "peak_basis": f"{sm_count} SMs x 4 schedulers x 1 warp instruction/cycle at "
+                          f"{sm_max_mhz:.0f} MHz"}
+
+
+def sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0  # GB300 maximum SM clock
+
+
 def kernel_source_hash():
     import hashlib
     d = os.path.join(ROOT, "paper_2008_11486_gb300", "csrc")
@@ -339,7 +375,7 @@ def kernel_source_hash():
 
 
 def roofline(prof, steps, bytes_per_step_by_kind, ms_per_step, path_bytes_per_step,
-             workload=None):
+             workload=None, sm_count=None):
     """HBM roofline of the dominant kernel: its algorithmic bytes per step over
     its device time per step (both summed over its launches in a step)."""
     kinds = {k: v for k, v in prof.items() if v[1] > 0 and k in bytes_per_step_by_kind}
@@ -357,7 +393,9 @@ def roofline(prof, steps, bytes_per_step_by_kind, ms_per_step, path_bytes_per_st
             "peak_source": peak_src,
             "launches_per_step": round(kinds[dom][1] / steps, 3),
             "kernel_ms": {k: round(v[0] / steps, 5) for k, v in prof.items() if v[1]},
-            "path_frac": round(path_bytes_per_step / (ms_per_step * 1e-3) / 1e9 / peak, 4)}
+            "path_frac": round(path_bytes_per_step / (ms_per_step * 1e-3) / 1e9 / peak, 4),
+            "issue": (issue_roofline(workload, dom, dom_ms, sm_count, sm_max_mhz())
+                      if sm_count else None)}
 
 
 def e2e_run(sets, params, ws, e2e_steps, stream, world):
@@ -543,7 +581,8 @@ def main():
         extra["plain_mpix_s"] = round(px_local / (extra["plain_ms_per_step"] * 1e-3) / 1e6, 1)
         extra["batched_over_plain"] = round(extra["plain_ms_per_step"] / ms_per_step, 3)
     rf = roofline(prof, args.steps, step_bytes(shapes, interp), ms_per_step,
-                  algorithmic_bytes("reduce", shapes, "bilinear"), args.workload)
+                  algorithmic_bytes("reduce", shapes, "bilinear"), args.workload,
+                  sm_count=core.lib().irp_device_sm_count())
     gpu_launches = int(sum(v[1] for v in prof.values()))
     e2e = e2e_run(sets, params, ws, args.e2e_steps, stream, world)
 
