@@ -144,12 +144,14 @@ class ClockSampler:
 
 
 def dist_init():
+    """One rank per GPU from the torchrun environment.  The collectives run
+    over NCCL; IRP_DIST_BACKEND=gloo runs them on the CPU instead (tests)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(os.environ.get("IRP_DIST_BACKEND", "nccl"))
     return world, rank, local
 
 
@@ -159,14 +161,29 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def _reduce_over_ranks(x, world, op):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    return _reduce_over_ranks(x, world, dist.ReduceOp.MAX)
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    return _reduce_over_ranks(x, world, dist.ReduceOp.SUM)
 
 
 DEEP = 64  # sets of more frames are combined by groups of lanes, not one thread per pixel
@@ -573,10 +590,7 @@ def main():
     px_local = sum(n * W * H for (W, H, n) in shapes)
     value = (world if scaling == "weak" else 1) * px_local * args.steps / (total_ms * 1e-3) / 1e6
     if scaling == "strong" and world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([float(px_local)], dtype=torch.float64, device=dev)
-        dist.all_reduce(t)
-        value = float(t.item()) * args.steps / (total_ms * 1e-3) / 1e6
+        value = sum_over_ranks(float(px_local), world) * args.steps / (total_ms * 1e-3) / 1e6
     if args.workload == "batch":
         extra["plain_mpix_s"] = round(px_local / (extra["plain_ms_per_step"] * 1e-3) / 1e6, 1)
         extra["batched_over_plain"] = round(extra["plain_ms_per_step"] / ms_per_step, 3)
