@@ -106,6 +106,12 @@ MUTANTS = [
      "if (w != 0.0 && src_bad(s, oracle_mirror(i, W), oracle_mirror(j, H))) return 0;", ""),
     ("clip margin not in units of sigma", "double mg = fabs(fabs(d) - thr) / sigma;",
      "double mg = fabs(fabs(d) - thr);"),
+    ("shift marks every sample valid", "valid[(int64_t)y * W + x] = (uint8_t)ok;",
+     "valid[(int64_t)y * W + x] = 1;"),
+    ("every spline frame takes the first frame's coefficients",
+     "src[k].f = coef + (int64_t)k * P;", "src[k].f = coef;"),
+    ("median leaves out samples far from the clipped mean", "        if (ok[k]) tmp[m++] = s[k];\n",
+     "        if (ok[k] && fabs(s[k] - mu) <= 3.0 * fabs(mu)) tmp[m++] = s[k];\n"),
 ]
 
 
