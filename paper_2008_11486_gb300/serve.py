@@ -18,7 +18,12 @@ Scheduling:
     landed are reduced together in one persistent launch (all their chip sets
     in one plan), on the compute stream, while newer requests keep uploading;
   * completion: an event per batch; a request's latency is the time from its
-    arrival to the host seeing its outputs ready.
+    arrival to the host seeing its outputs ready;
+  * errors: each batch's device status word is cleared before its launch and
+    copied back to pinned host memory behind it.  A batch that reports an
+    error (a bad flat, a timed-out wait) has its requests reduced again one by
+    one, so that only the failing ones carry the error in ``Request.status``
+    and the others complete normally.
 Each result depends only on its own frames and masters, so it is the same
 alone and inside any batch.
 """
@@ -48,7 +53,7 @@ class Request:
     done: float = 0.0
     outputs: list = None  # per chip (mean, median) device tensors (views of the output ring)
     out_slot: int = 0
-    status: int = 0
+    status: int = 0       # device status of its reduction (0 = IRP_OK), set on completion
 
 
 class Chip:
@@ -108,6 +113,12 @@ class Server:
         self.ws_free = []                    # workspaces of completed batches
         self.ws_all = []
         self.batches = 0
+        # one host status word per batch in flight (a batch holds at least one
+        # request, so at most max_inflight batches run at once)
+        self.status_host = torch.zeros(max_inflight, dtype=torch.int32,
+                                       pin_memory=torch.cuda.is_available())
+        self.status_free = list(range(max_inflight))
+        self.failed = []                     # completed requests whose status is not OK
 
     # ---------------------------------------------------------------- intake
     def submit(self, req: Request):
@@ -157,10 +168,11 @@ class Server:
         if not ready:
             return
         self.uploading = waiting
-        sets, reqs = [], []
+        sets, reqs, per_req = [], [], []
         for req, nums, ev in ready:
             self.compute_stream.wait_event(ev)
             req.outputs = []
+            per_req.append([])
             for chip, num in zip(self.chips, nums):
                 slots = chip.stack_slots(num)
                 s = core.DeviceSet(frames=[chip.ring[k] for k in slots], bias=chip.bias,
@@ -169,6 +181,7 @@ class Server:
                                    mean=chip.out[req.out_slot, 0],
                                    median=chip.out[req.out_slot, 1])
                 sets.append(s)
+                per_req[-1].append(s)
                 req.outputs.append((s.mean, s.median))
             reqs.append(req)
         params = core.reduce_params(self.interp, self.clip, persistent=True)
@@ -183,26 +196,50 @@ class Server:
                 ws = core.workspace(need, self.device)
             self.ws_all.append(ws)
         plan = core.Plan(sets, params, device=self.device, ws=ws)  # pinned plan: no host wait
+        slot = self.status_free.pop()
+        with torch.cuda.stream(self.compute_stream):
+            status = ws[:4].view(torch.int32)
+            status.zero_()  # this batch's status word starts clear
         plan.launch(self.compute_stream)
+        with torch.cuda.stream(self.compute_stream):
+            self.status_host[slot:slot + 1].copy_(status, non_blocking=True)
         t = time.perf_counter()
         for r in reqs:
             r.launched = t
         done_ev = torch.cuda.Event()
         done_ev.record(self.compute_stream)
-        self.running.append((reqs, done_ev, plan, ws))
+        self.running.append((reqs, done_ev, plan, ws, slot, per_req))
         self.batches += 1
+
+    def _isolate(self, reqs, per_req, ws):
+        """A batch reported a device error: each of its requests is reduced
+        again alone (its ring slots are still intact: it is still in flight),
+        and only the failing ones keep the error.  The others' outputs are
+        recomputed, with the same values."""
+        params = core.reduce_params(self.interp, self.clip, persistent=True)
+        core.sync_status(ws, self.compute_stream)  # clears the batch's latched status
+        for req, sets in zip(reqs, per_req):
+            core.reduce_sets(sets, params, ws=ws, stream=self.compute_stream)
+            req.status = core.sync_status(ws, self.compute_stream)
+            if req.status != 0:
+                self.failed.append(req)
 
     def _complete(self):
         still = []
-        for reqs, ev, plan, ws in self.running:
+        for entry in self.running:
+            reqs, ev, plan, ws, slot, per_req = entry
             if ev.query():
+                st = int(self.status_host[slot])
+                self.status_free.append(slot)
+                if st != 0:
+                    self._isolate(reqs, per_req, ws)
                 t = time.perf_counter()
                 for r in reqs:
                     r.done = t
                     self.done.append(r)
                 self.ws_free.append(ws)
             else:
-                still.append((reqs, ev, plan, ws))
+                still.append(entry)
         self.running = still
 
     def tick(self):
@@ -224,8 +261,9 @@ class Server:
         self._complete()
 
     def status(self) -> int:
-        """Synchronises and returns the first non-OK device status of any batch."""
-        st = 0
+        """Synchronises and returns the first non-OK device status of any
+        completed request, or of any batch's workspace."""
+        st = next((r.status for r in self.done if r.status), 0)
         for ws in self.ws_all:
             s = core.sync_status(ws, self.compute_stream)
             st = st or s
