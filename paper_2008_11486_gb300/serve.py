@@ -19,7 +19,9 @@ Scheduling:
     in one plan), on the compute stream, while newer requests keep uploading;
   * completion: an event per batch; a request's latency is the time from its
     arrival to the host seeing its outputs ready;
-  * errors: each batch's device status word is cleared before its launch and
+  * errors: a request the rings cannot take (a frame of the wrong shape or
+    type, a non-finite offset) completes at submission with its own status;
+    each batch's device status word is cleared before its launch and
     copied back to pinned host memory behind it.  A batch that reports an
     error (a bad flat, a timed-out wait) has its requests reduced again one by
     one, so that only the failing ones carry the error in ``Request.status``
@@ -122,9 +124,37 @@ class Server:
 
     # ---------------------------------------------------------------- intake
     def submit(self, req: Request):
+        """Queues a request, or completes it at once with IRP_ERR_INVALID_ARG
+        (1) in ``status`` when the rings cannot take it: the other requests
+        are not affected."""
         req.arrival = time.perf_counter()
+        st = self._validate(req)
         with self.lock:
-            self.pending.append(req)
+            if st:
+                req.status = st
+                req.done = req.arrival
+                self.done.append(req)
+                self.failed.append(req)
+            else:
+                self.pending.append(req)
+
+    def _validate(self, req) -> int:
+        """One uint16 frame of its chip's shape per chip, finite offsets and a
+        finite, non-negative exposure time."""
+        if len(req.frames) != len(self.chips):
+            return 1
+        for chip, f in zip(self.chips, req.frames):
+            if not isinstance(f, torch.Tensor) or f.dtype != torch.uint16 or \
+                    tuple(f.shape) != (chip.H, chip.W):
+                return 1
+        dx = np.asarray(req.dx, dtype=np.float64)
+        dy = np.asarray(req.dy, dtype=np.float64)
+        if dx.shape != (len(self.chips),) or dy.shape != dx.shape or \
+                not (np.isfinite(dx).all() and np.isfinite(dy).all()):
+            return 1
+        if not (np.isfinite(req.exptime) and req.exptime >= 0):
+            return 1
+        return 0
 
     def _request_bytes(self, req) -> int:
         return 0  # frames, outputs and masters live in preallocated rings

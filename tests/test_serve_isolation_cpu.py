@@ -112,3 +112,26 @@ def test_only_the_failing_request_carries_the_error(host_server):
     assert srv.status() == ERR
     # every status slot is free again once nothing is in flight
     assert sorted(srv.status_free) == [0, 1]
+
+
+def test_invalid_requests_are_rejected_alone(host_server):
+    H, W, nchips = 4, 6, 2
+    masters = [(torch.zeros(H, W), torch.zeros(H, W), torch.ones(H, W)) for _ in range(nchips)]
+    srv = serve.Server(masters, depth=3, max_inflight=2, device="cpu")
+
+    def request(r, shape=(H, W), dtype=torch.uint16, dx=0.0, frames=nchips):
+        return serve.Request(r, [torch.full(shape, 100, dtype=dtype) for _ in range(frames)],
+                             np.full(nchips, dx), np.zeros(nchips))
+
+    bad = [request(1, dx=float("nan")), request(2, shape=(H + 1, W)),
+           request(3, dtype=torch.int32), request(4, frames=nchips - 1)]
+    good = [request(0), request(5)]
+    for r in (good[0], *bad, good[1]):
+        srv.submit(r)
+    assert [r.rid for r in srv.failed] == [1, 2, 3, 4]
+    assert all(r.status == 1 and r.done > 0 for r in bad)
+    assert [r.rid for r in srv.pending] == [0, 5]
+    for _ in range(6):
+        srv.tick()
+    assert srv.idle() and all(r.status == 0 and r.done > 0 for r in good)
+    assert float(good[1].outputs[0][0][0, 0]) == 100.0
