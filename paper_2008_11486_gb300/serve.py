@@ -290,6 +290,42 @@ class Server:
             time.sleep(50e-6)
         self._complete()
 
+    # ------------------------------------------------------ checkpoint / resume
+    def snapshot(self) -> dict:
+        """Host copy of the state a restarted server needs to continue the
+        rolling stacks: each chip's raw-frame ring with its slots' offsets and
+        exposure times, the frame counters and the admission count.  The
+        masters are the caller's and are not copied.  Needs an idle server
+        (``drain()`` first)."""
+        if not self.idle():
+            raise RuntimeError("snapshot needs an idle server: drain() first")
+        if self.device.type == "cuda":
+            torch.cuda.synchronize(self.device)
+        return {"depth": self.depth, "admitted": self.admitted,
+                "chips": [{"ring": c.ring.cpu().clone(), "dx": c.slot_dx.copy(),
+                           "dy": c.slot_dy.copy(), "t": c.slot_t.copy(), "count": c.count}
+                          for c in self.chips]}
+
+    def restore(self, snap: dict) -> None:
+        """Loads a snapshot into an idle server with the same chips, stack
+        depth and ring size; the next request continues the stacks where the
+        snapshot's server stopped."""
+        if not self.idle():
+            raise RuntimeError("restore needs an idle server")
+        if snap["depth"] != self.depth or len(snap["chips"]) != len(self.chips) or any(
+                tuple(s["ring"].shape) != tuple(c.ring.shape)
+                for s, c in zip(snap["chips"], self.chips)):
+            raise ValueError("snapshot of a server with other chips, depth or ring size")
+        for c, s in zip(self.chips, snap["chips"]):
+            c.ring.copy_(s["ring"])
+            c.slot_dx[:] = s["dx"]
+            c.slot_dy[:] = s["dy"]
+            c.slot_t[:] = s["t"]
+            c.count = int(s["count"])
+        self.admitted = int(snap["admitted"])
+        if self.device.type == "cuda":
+            torch.cuda.synchronize(self.device)
+
     def status(self) -> int:
         """Synchronises and returns the first non-OK device status of any
         completed request, or of any batch's workspace."""
