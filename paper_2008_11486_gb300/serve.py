@@ -109,7 +109,8 @@ class Server:
         self.compute_stream = torch.cuda.Stream(device=self.device)
         self.pending = collections.deque()   # arrived, not admitted
         self.uploading = []                  # (request, frame numbers, copy event)
-        self.running = []                    # (requests, completion event, plan, ws)
+        self.running = []                    # (requests, completion event, plan, ws,
+                                             #  status slot, each request's sets)
         self.done = []
         self.lock = threading.Lock()
         self.ws_free = []                    # workspaces of completed batches
