@@ -6,7 +6,9 @@ it and shares no code with it.  The arithmetic lives in ``oracle.c`` (plain C,
 double precision); this module only compiles and marshals.
 
 Function pins (what checks the oracle against something other than itself)
-are listed in ``tests/test_oracle.py``.
+are listed in ``tests/test_oracle.py``; ``tests/test_oracle_mutants.py``
+compiles copies of ``oracle.c`` with planted mistakes (``compile_library``,
+``load``) and checks that every one of them fails a pin.
 """
 from __future__ import annotations
 
