@@ -363,6 +363,8 @@ def issue_roofline(workload, dom, dom_ms, sm_count, sm_max_mhz):
     rec = ISSUE.get(workload)
     if not rec or rec[1] != dom or rec[0] != kernel_source_hash() or dom_ms <= 0:
         return None
+    if sm_count < 2:  # the device's SM count could not be read
+        return None
     peak = sm_count * 4 * sm_max_mhz * 1e6 / 1e9  # G warp instructions / s
     achieved = rec[2] / (dom_ms * 1e-3) / 1e9
     return {"bound": "issue", "achieved": round(achieved, 1), "peak": round(peak, 1),
