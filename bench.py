@@ -348,7 +348,8 @@ TRAFFIC = {
 # smsp__inst_executed, summed over the kind's launches in one step; the same
 # captures and source hash as TRAFFIC).  Against the issue peak -- one warp
 # instruction per cycle in each of an SM's 4 schedulers at the maximum SM
-# clock -- they bound the kernels that issue, not HBM, limits.
+# clock -- they give the roofline of kernels that instruction issue, rather
+# than HBM, limits.
 ISSUE = {
     "bands": ("01544d57caae0ba5", "prefilter", 35_221_760 + 38_887_200),  # rows + columns
     "deep": ("01544d57caae0ba5", "reduce", 1_292_075_776),
