@@ -47,8 +47,13 @@ class Autotuner:
         self._lock = threading.Lock()
         self.cache = {}
         if cache_path and os.path.exists(cache_path):
-            with open(cache_path) as f:
-                self.cache = json.load(f)
+            try:
+                with open(cache_path) as f:
+                    cache = json.load(f)
+                if isinstance(cache, dict):
+                    self.cache = cache
+            except (OSError, ValueError):
+                pass  # an unreadable cache is re-tuned, not fatal
 
     @staticmethod
     def candidates(sets, persistent: bool):

@@ -48,6 +48,13 @@ def test_autotuner_caches_per_signature(tmp_path, monkeypatch):
     assert calls == [2]
 
 
+def test_autotuner_ignores_an_unreadable_cache(tmp_path):
+    for text in ("{not json", "[1, 2]", ""):
+        path = tmp_path / "tune.json"
+        path.write_text(text)
+        assert batch.Autotuner(str(path)).cache == {}
+
+
 def test_shard_sets_partition_and_balance():
     shapes = batch_shapes = [(n, s, s) for n, s in
                              zip([3, 40, 17, 8, 25, 31, 5, 12, 39, 22, 6, 14],
