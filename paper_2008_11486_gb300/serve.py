@@ -42,6 +42,9 @@ import torch
 from . import core
 
 
+CANCELLED = -1  # Request.status of a withdrawn request (not a library status)
+
+
 @dataclasses.dataclass
 class Request:
     rid: int
@@ -138,6 +141,20 @@ class Server:
                 self.failed.append(req)
             else:
                 self.pending.append(req)
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraws a request that has not been admitted yet: it completes at
+        once with ``status = CANCELLED`` and takes no ring slot.  An admitted
+        request runs to completion.  Returns whether the request was withdrawn."""
+        with self.lock:
+            for i, r in enumerate(self.pending):
+                if r.rid == rid:
+                    del self.pending[i]
+                    r.status = CANCELLED
+                    r.done = time.perf_counter()
+                    self.done.append(r)
+                    return True
+        return False
 
     def _validate(self, req) -> int:
         """One uint16 frame of its chip's shape per chip, finite offsets and a
@@ -328,9 +345,9 @@ class Server:
             torch.cuda.synchronize(self.device)
 
     def status(self) -> int:
-        """Synchronises and returns the first non-OK device status of any
-        completed request, or of any batch's workspace."""
-        st = next((r.status for r in self.done if r.status), 0)
+        """Synchronises and returns the first non-OK status of any completed
+        request (withdrawn ones aside), or of any batch's workspace."""
+        st = next((r.status for r in self.done if r.status not in (0, CANCELLED)), 0)
         for ws in self.ws_all:
             s = core.sync_status(ws, self.compute_stream)
             st = st or s

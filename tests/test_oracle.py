@@ -288,6 +288,29 @@ def test_clip_margin_reports_distance_to_threshold():
     assert kept == 5 and mg == pytest.approx(1.0, abs=1e-15)
 
 
+def test_clip_result_is_a_fixed_point_of_the_rule():
+    """Properties any correct run of the iteration has, checked on random small
+    stacks with outliers (mean centre, ddof 0, passes until nothing changes):
+    the survivors S reject nothing more (|x - mean(S)| <= kappa sigma(S), or
+    sigma(S) = 0); every rejected sample lies outside [min S, max S], since
+    each pass cuts both tails of the current survivors; the output is mean(S)
+    and the count |S|."""
+    rng = np.random.default_rng(20081)
+    for trial in range(400):
+        n = int(rng.integers(1, 9))
+        x = rng.normal(0.0, 1.0, n)
+        x[rng.random(n) < 0.25] += rng.choice([-1, 1]) * rng.uniform(3, 30)
+        kappa = float(rng.choice([1.0, 1.5, 2.0, 2.5]))
+        mean, kept, rej, _ = oracle.clip(x, kappa=kappa, max_iter=100)
+        S = x[~rej]
+        assert kept == S.size >= 1
+        mu, sd = S.mean(), S.std()
+        if sd > 0:
+            assert np.all(np.abs(S - mu) <= kappa * sd * (1 + 1e-12)), (trial, x, kappa)
+        assert np.all((x[rej] < S.min()) | (x[rej] > S.max())), (trial, x, kappa)
+        assert mean == pytest.approx(mu, rel=1e-12, abs=1e-12)
+
+
 @pytest.mark.parametrize("m", [1, 2, 3, 4, 7, 10, 31, 40])
 def test_median_matches_numpy(m):
     rng = np.random.default_rng(100 + m)

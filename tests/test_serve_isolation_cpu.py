@@ -135,3 +135,25 @@ def test_invalid_requests_are_rejected_alone(host_server):
         srv.tick()
     assert srv.idle() and all(r.status == 0 and r.done > 0 for r in good)
     assert float(good[1].outputs[0][0][0, 0]) == 100.0
+
+
+def test_pending_requests_can_be_withdrawn(host_server):
+    H, W, nchips = 4, 6, 2
+    masters = [(torch.zeros(H, W), torch.zeros(H, W), torch.ones(H, W)) for _ in range(nchips)]
+    srv = serve.Server(masters, depth=3, max_inflight=1, device="cpu")
+    reqs = [serve.Request(r, [torch.full((H, W), 100 + r, dtype=torch.uint16)] * nchips,
+                          np.zeros(nchips), np.zeros(nchips)) for r in range(3)]
+    for q in reqs:
+        srv.submit(q)
+    srv.tick()                      # request 0 admitted and reduced (one slot)
+    assert not srv.cancel(0)        # too late: admitted
+    assert srv.cancel(1) and not srv.cancel(1)
+    for _ in range(4):
+        srv.tick()
+    assert srv.idle()
+    assert reqs[1].status == serve.CANCELLED and reqs[1].outputs is None
+    assert reqs[0].status == reqs[2].status == 0
+    # request 2's stack holds frames 0 and 2 only: the withdrawn frame never
+    # entered the ring
+    assert float(reqs[2].outputs[0][0][0, 0]) == pytest.approx((100 + 102) / 2)
+    assert srv.status() == 0
