@@ -56,3 +56,23 @@ def test_roofline_reports_no_counters_for_changed_sources(monkeypatch):
     # workloads without a capture, or without a device, carry none either
     rf = bench.roofline(prof, 10, by, 0.235, by["reduce"], "small", sm_count=152)
     assert rf["traffic"] is None and rf["issue"] is None
+
+
+def test_sampled_errors_report_the_relative_difference_ranges():
+    import numpy as np
+
+    import oracle
+    from paper_2008_11486_gb300 import synth
+    fs = synth.make_set(48, 40, 6, 3.0, 77, n_stars=10, n_cr=3)
+    full = oracle.reduce_set(fs, interp="bilinear")
+    # the oracle's own result, rounded to FP32 and scaled by (1 + 1e-6)
+    mean = (full["mean"] * (1 + 1e-6)).astype(np.float32)
+    med = full["median"].astype(np.float32)
+    res = bench.sampled_errors(fs, {"scaled": (mean, med)}, "bilinear", npix=500)
+    r = res["scaled"]
+    lo90, hi90 = r["mean_dI_90"]
+    lo95, hi95 = r["mean_dI_95"]
+    assert lo95 <= lo90 <= hi90 <= hi95
+    # dI is 1e-6 up to the FP32 rounding of the outputs (about 6e-8)
+    assert abs(lo95 - 1e-6) < 1e-7 and abs(hi95 - 1e-6) < 1e-7
+    assert r["median_max_rel"] < 1e-7 and res["pixels"] > 400
