@@ -8,10 +8,13 @@ ones (a rolling reference stack).
 
 Scheduling:
   * admission: a request is admitted when an in-flight slot is free and the
-    device keeps its reserve free (``torch.cuda.mem_get_info``); frames,
-    outputs and masters live in rings allocated once, so a request allocates
-    no device memory, and its outputs stay valid until ``out_slots`` newer
-    requests have been admitted;
+    device keeps its reserve free after the request's own device bytes
+    (``torch.cuda.mem_get_info``).  Frames, outputs and masters live in rings
+    allocated once; what a request may still allocate is the workspace of the
+    batch it joins, unless a free workspace of a completed batch is large
+    enough.  A request held back for memory waits at the head of the queue
+    until a batch completes.  Its outputs stay valid until ``out_slots``
+    newer requests have been admitted;
     admitted requests copy their new frames into the chip rings on a copy
     stream (pinned host memory -> HBM);
   * batching: at every scheduler tick all admitted requests whose copies have
@@ -125,6 +128,8 @@ class Server:
                                        pin_memory=torch.cuda.is_available())
         self.status_free = list(range(max_inflight))
         self.failed = []                     # completed requests whose status is not OK
+        self._ws_per_req = None              # workspace bytes of one request's sets
+        self.held_for_memory = 0             # admissions deferred for lack of free HBM
 
     # ---------------------------------------------------------------- intake
     def submit(self, req: Request):
@@ -174,8 +179,30 @@ class Server:
             return 1
         return 0
 
+    def _ws_bytes_per_request(self) -> int:
+        """Workspace bytes of one request's chip sets (every request has the
+        same shapes, so this is computed once, from the chips' first ring
+        slots)."""
+        if self._ws_per_req is None:
+            params = core.reduce_params(self.interp, self.clip, persistent=True)
+            sets = [core.DeviceSet(frames=[chip.ring[k] for k in range(self.depth)],
+                                   bias=chip.bias, dark=chip.dark, flat=chip.flat,
+                                   exptime=chip.slot_t[:self.depth],
+                                   dx=chip.slot_dx[:self.depth], dy=chip.slot_dy[:self.depth],
+                                   mean=chip.out[0, 0], median=chip.out[0, 1])
+                    for chip in self.chips]
+            self._ws_per_req = int(core.workspace_size(sets, params))
+        return self._ws_per_req
+
     def _request_bytes(self, req) -> int:
-        return 0  # frames, outputs and masters live in preallocated rings
+        """Device bytes that admitting ``req`` may allocate.  Its frames and
+        outputs go to rings allocated once, so only the workspace of the batch
+        it joins counts: that batch holds it and the requests uploading now,
+        and a free workspace of that size from an earlier batch is reused."""
+        need = self._ws_bytes_per_request() * (len(self.uploading) + 1)
+        if any(w.numel() >= need for w in self.ws_free):
+            return 0
+        return need
 
     def _inflight(self) -> int:
         return len(self.uploading) + sum(len(r[0]) for r in self.running)
@@ -189,8 +216,12 @@ class Server:
                 req = self.pending[0]
             free, _ = torch.cuda.mem_get_info(self.device)
             if free - self._request_bytes(req) < self.reserve:
+                self.held_for_memory += 1
                 return
             with self.lock:
+                # cancel() may have withdrawn the head while the lock was free
+                if not self.pending or self.pending[0] is not req:
+                    continue
                 self.pending.popleft()
             nums = []
             with torch.cuda.stream(self.copy_stream):
