@@ -254,6 +254,11 @@ irp_status irp_plan_launch(const void* plan_host, size_t plan_bytes, void* works
  *     IRP_NOALLOC_SCRATCH_BYTES, or whose plan exceeds the call's fixed host
  *     plan buffer, return IRP_ERR_WORKSPACE with nothing enqueued; use
  *     irp_reduce_set for those.
+ *   - A plan of more than 4 sets or 64 frames in one frame-count group, or
+ *     with a set deeper than IRP_MAX_FRAMES, is copied to the device from a
+ *     buffer on the call's own stack.  While `stream` is being captured such
+ *     a request returns IRP_ERR_UNSUPPORTED with nothing enqueued, since the
+ *     recorded copy would read that buffer after the call has returned.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture on the device.

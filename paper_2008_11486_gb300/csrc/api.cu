@@ -1271,10 +1271,19 @@ extern "C" irp_status irp_reduce_set_noalloc(const irp_set* sets, int nsets,
   st = encode_plan(ps, p, buf, plan_bytes, ws, IRP_NOALLOC_SCRATCH_BYTES);
   if (st != IRP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  const bool upload = !plan_fits_inline(buf);
+  if (upload) {
+    // the plan would be copied from `buf`, which lives on this call's stack:
+    // a copy recorded into a graph would read it after the call has returned
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return note_cuda(e);
+    if (cs != cudaStreamCaptureStatusNone) return IRP_ERR_UNSUPPORTED;
+  }
   // the status word and work counters must start at zero for every call
   e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), s);
   if (e != cudaSuccess) return note_cuda(e);
-  st = run_plan(buf, ws, IRP_NOALLOC_SCRATCH_BYTES, s, !plan_fits_inline(buf));
+  st = run_plan(buf, ws, IRP_NOALLOC_SCRATCH_BYTES, s, upload);
   if (st != IRP_OK) return st;
   if (status_out) {
     e = cudaMemcpyAsync(status_out, ws, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
