@@ -86,21 +86,21 @@ def load(path: str):
     L.oracle_shift.restype = None
     L.oracle_shift.argtypes = [p, i, i, d, d, i, p, p]
     L.oracle_clip.restype = None
-    L.oracle_clip.argtypes = [p, p, i, ctypes.POINTER(ClipParams), p, p, p, p]
+    L.oracle_clip.argtypes = [p, p, i, ctypes.POINTER(ClipParams), p, p, p, p, p]
     L.oracle_median.restype = d
     L.oracle_median.argtypes = [p, p, i]
     L.oracle_combine_stack.restype = None
     L.oracle_combine_stack.argtypes = [p, p, i, i64, ctypes.POINTER(ClipParams), i,
-                                       p, p, p, p, p]
+                                       p, p, p, p, p, p]
     L.oracle_reduce_set.restype = i
     L.oracle_reduce_set.argtypes = [p, i64, i64, i, i, i, p, p, p, i64, p, p, p, i, i,
                                     ctypes.POINTER(ClipParams), i, i64, p, p,
-                                    p, p, p, p, p, p]
+                                    p, p, p, p, p, p, p]
     L.oracle_reduce_set_masked.restype = i
     L.oracle_reduce_set_masked.argtypes = [p, i64, i64, i, i, i, p, p, p, i64, p, p, p,
                                            i, i, p, i64, d,
                                            ctypes.POINTER(ClipParams), i, i64, p, p,
-                                           p, p, p, p, p, p]
+                                           p, p, p, p, p, p, p]
     return L
 
 
@@ -175,7 +175,9 @@ def shift(v, dx, dy, interp):
     return a, valid.astype(bool)
 
 
-def clip(x, valid=None, **kw):
+def clip(x, valid=None, adu=False, **kw):
+    """(mean, kept, rejected, margin); with ``adu`` also the margin in the
+    data's units (the smallest | |x - centre| - kappa sigma | of any pass)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     n = x.shape[0]
     valid = np.ones(n, np.uint8) if valid is None else np.ascontiguousarray(valid, np.uint8)
@@ -183,10 +185,12 @@ def clip(x, valid=None, **kw):
     kept = np.zeros(1, dtype=np.int32)
     rej = np.zeros(n, dtype=np.uint8)
     mg = np.zeros(1)
+    mga = np.zeros(1)
     cp = clip_params(**kw)
     lib().oracle_clip(_ptr(x), _ptr(valid), n, ctypes.byref(cp), _ptr(mean), _ptr(kept),
-                      _ptr(rej), _ptr(mg))
-    return float(mean[0]), int(kept[0]), rej.astype(bool), float(mg[0])
+                      _ptr(rej), _ptr(mg), _ptr(mga))
+    out = (float(mean[0]), int(kept[0]), rej.astype(bool), float(mg[0]))
+    return out + (float(mga[0]),) if adu else out
 
 
 def median(x, valid=None):
@@ -207,17 +211,20 @@ def combine_stack(stack, valid, nthreads=1, **kw):
     med = np.empty(shape)
     kept = np.empty(shape, dtype=np.int32)
     margin = np.empty(shape)
+    margin_adu = np.empty(shape)
     rej = np.empty(stack.shape, dtype=np.uint8)
     cp = clip_params(**kw)
     lib().oracle_combine_stack(_ptr(stack), _ptr(valid), n, P, ctypes.byref(cp), int(nthreads),
-                               _ptr(mean), _ptr(med), _ptr(kept), _ptr(margin), _ptr(rej))
-    return dict(mean=mean, median=med, nkept=kept, margin=margin, rejected=rej.astype(bool))
+                               _ptr(mean), _ptr(med), _ptr(kept), _ptr(margin),
+                               _ptr(margin_adu), _ptr(rej))
+    return dict(mean=mean, median=med, nkept=kept, margin=margin, margin_adu=margin_adu,
+                rejected=rej.astype(bool))
 
 
 def reduce_set(fs, interp="bilinear", kappa=3.0, max_iter=3, center="mean", ddof=0,
                normalize_flat=False, nthreads=1, pixels=None, want_stack=False,
                kappa_lo=None, kappa_hi=None, mask=None, saturation=None):
-    """Whole frame set -> dict(mean, median, nkept, margin[, stack, valid]).
+    """Whole frame set -> dict(mean, median, nkept, margin, margin_adu[, stack, valid]).
 
     ``mask`` ([H,W] uint8, non-zero = bad) and ``saturation`` (raw ADU) mark
     bad source pixels (Sec. 2.1 bad-pixel masking): a sample whose taps with
@@ -248,6 +255,7 @@ def reduce_set(fs, interp="bilinear", kappa=3.0, max_iter=3, center="mean", ddof
     med = np.empty(shape)
     kept = np.empty(shape, np.int32)
     margin = np.empty(shape)
+    margin_adu = np.empty(shape)
     stack = np.empty((n, H, W)) if (want_stack and pixels is None) else None
     valid = np.empty((n, H, W), np.uint8) if (want_stack and pixels is None) else None
     mk = np.ascontiguousarray(mask, np.uint8) if mask is not None else None
@@ -257,12 +265,12 @@ def reduce_set(fs, interp="bilinear", kappa=3.0, max_iter=3, center="mean", ddof
         _ptr(mk) if mk is not None else None, W,
         float(saturation) if saturation is not None else 0.0,
         ctypes.byref(cp), int(nthreads), int(npix), _ptr(px), _ptr(py),
-        _ptr(mean), _ptr(med), _ptr(kept), _ptr(margin),
+        _ptr(mean), _ptr(med), _ptr(kept), _ptr(margin), _ptr(margin_adu),
         _ptr(stack) if stack is not None else None,
         _ptr(valid) if valid is not None else None)
     if rc != 0:
         raise ValueError("oracle_reduce_set rejected its arguments")
-    out = dict(mean=mean, median=med, nkept=kept, margin=margin)
+    out = dict(mean=mean, median=med, nkept=kept, margin=margin, margin_adu=margin_adu)
     if stack is not None:
         out["stack"] = stack
         out["valid"] = valid.astype(bool)

@@ -272,11 +272,12 @@ double oracle_median(const double* x, const uint8_t* valid, int n) {
 }
 
 void oracle_clip(const double* x, const uint8_t* valid, int n, const oracle_clip_params* p,
-                 double* mean, int* nkept, uint8_t* rejected, double* min_margin) {
+                 double* mean, int* nkept, uint8_t* rejected, double* min_margin,
+                 double* min_margin_adu) {
   uint8_t* alive = (uint8_t*)malloc((size_t)(n > 0 ? n : 1));
   uint8_t* rej = (uint8_t*)malloc((size_t)(n > 0 ? n : 1));
   double* buf = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-  double margin = INFINITY;
+  double margin = INFINITY, margin_adu = INFINITY;
   for (int k = 0; k < n; ++k) {
     alive[k] = valid[k] ? 1 : 0;
     if (rejected) rejected[k] = 0;
@@ -308,7 +309,9 @@ void oracle_clip(const double* x, const uint8_t* valid, int n, const oracle_clip
       if (!alive[k]) continue;
       double d = x[k] - mu;
       double thr = (d < 0.0 ? p->kappa_lo : p->kappa_hi) * sigma;
-      double mg = fabs(fabs(d) - thr) / sigma;
+      double dist = fabs(fabs(d) - thr);  /* distance to the threshold, data units */
+      if (dist < margin_adu) margin_adu = dist;
+      double mg = dist / sigma;
       if (mg < margin) margin = mg;
       if (fabs(d) > thr) {
         rej[k] = 1;
@@ -332,6 +335,7 @@ void oracle_clip(const double* x, const uint8_t* valid, int n, const oracle_clip
   *mean = (m == 0) ? NAN : s / m;
   *nkept = m;
   if (min_margin) *min_margin = margin;
+  if (min_margin_adu) *min_margin_adu = margin_adu;
   free(alive);
   free(rej);
   free(buf);
@@ -345,11 +349,11 @@ int oracle_reduce_set(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stri
                       const oracle_clip_params* clip, int nthreads,
                       int64_t npix, const int32_t* px, const int32_t* py,
                       double* mean, double* median, int32_t* nkept, double* min_margin,
-                      double* stack, uint8_t* valid) {
+                      double* min_margin_adu, double* stack, uint8_t* valid) {
   return oracle_reduce_set_masked(raw, raw_pitch, frame_stride, W, H, n, bias, dark, flat,
                                   master_pitch, exptime, dx, dy, interp, normalize_flat, NULL, 0,
                                   0.0, clip, nthreads, npix, px, py, mean, median, nkept,
-                                  min_margin, stack, valid);
+                                  min_margin, min_margin_adu, stack, valid);
 }
 
 int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stride,
@@ -361,7 +365,7 @@ int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t fra
                              const oracle_clip_params* clip, int nthreads,
                              int64_t npix, const int32_t* px, const int32_t* py,
                              double* mean, double* median, int32_t* nkept, double* min_margin,
-                             double* stack, uint8_t* valid) {
+                             double* min_margin_adu, double* stack, uint8_t* valid) {
   if (W < 1 || H < 1 || n < 1 || raw_pitch < W || master_pitch < W) return 1;
   if (interp < ORACLE_NEAREST || interp > ORACLE_SPLINE3) return 1;
 #ifdef _OPENMP
@@ -417,11 +421,12 @@ int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t fra
         if (valid && npix <= 0) valid[(int64_t)k * P + o] = ok[k];
       }
       int kept = 0;
-      double mg = INFINITY, mu = 0.0;
-      oracle_clip(s, ok, n, clip, &mu, &kept, NULL, &mg);
+      double mg = INFINITY, mga = INFINITY, mu = 0.0;
+      oracle_clip(s, ok, n, clip, &mu, &kept, NULL, &mg, &mga);
       mean[o] = mu;
       if (nkept) nkept[o] = kept;
       if (min_margin) min_margin[o] = mg;
+      if (min_margin_adu) min_margin_adu[o] = mga;
       int m = 0;
       for (int k = 0; k < n; ++k)
         if (ok[k]) tmp[m++] = s[k];
@@ -439,7 +444,7 @@ int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t fra
 void oracle_combine_stack(const double* stack, const uint8_t* valid, int n, int64_t P,
                           const oracle_clip_params* clip, int nthreads, double* mean,
                           double* median, int32_t* nkept, double* min_margin,
-                          uint8_t* rejected) {
+                          double* min_margin_adu, uint8_t* rejected) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -457,11 +462,12 @@ void oracle_combine_stack(const double* stack, const uint8_t* valid, int n, int6
         ok[k] = valid[(int64_t)k * P + o];
       }
       int kept = 0;
-      double mg = INFINITY, mu = 0.0;
-      oracle_clip(x, ok, n, clip, &mu, &kept, rej, &mg);
+      double mg = INFINITY, mga = INFINITY, mu = 0.0;
+      oracle_clip(x, ok, n, clip, &mu, &kept, rej, &mg, &mga);
       mean[o] = mu;
       nkept[o] = kept;
       min_margin[o] = mg;
+      if (min_margin_adu) min_margin_adu[o] = mga;
       median[o] = oracle_median(x, ok, n);
       if (rejected)
         for (int k = 0; k < n; ++k) rejected[(int64_t)k * P + o] = rej[k];

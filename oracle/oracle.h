@@ -64,11 +64,13 @@ void oracle_shift(const double* v, int W, int H, double dx, double dy, int inter
                   double* a, uint8_t* valid);
 
 /* Sigma-clipped mean of the valid entries of x[0..n).  Writes the mean (NaN if
- * nothing is valid), the kept count, the rejected flags (nullable) and the
+ * nothing is valid), the kept count, the rejected flags (nullable), the
  * smallest distance of any tested sample to its threshold in units of sigma
- * (+inf if no pass had sigma > 0). */
+ * (+inf if no pass had sigma > 0) and, nullable, the smallest such distance in
+ * the data's own units (| |x - centre| - kappa sigma |, over every pass). */
 void oracle_clip(const double* x, const uint8_t* valid, int n, const oracle_clip_params* p,
-                 double* mean, int* nkept, uint8_t* rejected, double* min_margin);
+                 double* mean, int* nkept, uint8_t* rejected, double* min_margin,
+                 double* min_margin_adu);
 
 /* Median of the valid entries (mean of the two middle values for even counts). */
 double oracle_median(const double* x, const uint8_t* valid, int n);
@@ -77,7 +79,7 @@ double oracle_median(const double* x, const uint8_t* valid, int n);
 void oracle_combine_stack(const double* stack, const uint8_t* valid, int n, int64_t P,
                           const oracle_clip_params* clip, int nthreads, double* mean,
                           double* median, int32_t* nkept, double* min_margin,
-                          uint8_t* rejected);
+                          double* min_margin_adu, uint8_t* rejected);
 
 /* Whole frame set.  raw frame k starts at raw + k*frame_stride (elements).
  * If npix > 0 only the output pixels (px[i], py[i]) are computed and written at
@@ -92,7 +94,7 @@ int oracle_reduce_set(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stri
                       const oracle_clip_params* clip, int nthreads,
                       int64_t npix, const int32_t* px, const int32_t* py,
                       double* mean, double* median, int32_t* nkept, double* min_margin,
-                      double* stack, uint8_t* valid);
+                      double* min_margin_adu, double* stack, uint8_t* valid);
 
 /* oracle_reduce_set with bad-pixel masking (Sec. 2.1): a source pixel is bad
  * when mask[j*mask_pitch + i] != 0 (mask may be NULL) or its raw value is at
@@ -107,7 +109,7 @@ int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t fra
                              const oracle_clip_params* clip, int nthreads,
                              int64_t npix, const int32_t* px, const int32_t* py,
                              double* mean, double* median, int32_t* nkept, double* min_margin,
-                             double* stack, uint8_t* valid);
+                             double* min_margin_adu, double* stack, uint8_t* valid);
 
 #ifdef __cplusplus
 }

@@ -288,6 +288,34 @@ def test_clip_margin_reports_distance_to_threshold():
     assert kept == 5 and mg == pytest.approx(1.0, abs=1e-15)
 
 
+def test_clip_margin_in_data_units_worked_by_hand():
+    """The threshold distance in the data's units, | |x - centre| - kappa sigma |,
+    the smallest over every sample of every pass (cases of the golden file)."""
+    # A: 1..5, kappa 3: sigma = sqrt(2); the outer samples sit 3 sqrt(2) - 2 inside
+    *_, mga = oracle.clip(np.arange(1.0, 6.0), adu=True)
+    assert mga == pytest.approx(3 * np.sqrt(2) - 2, abs=1e-13)
+    # C: ten 0 and one 11: pass 1 has mu 1, sigma sqrt(10); the 11 lies
+    # 10 - 3 sqrt(10) beyond the threshold; pass 2 has sigma 0 and tests nothing
+    *_, mg, mga = oracle.clip(np.array([0.0] * 10 + [11.0]), adu=True)
+    assert mga == pytest.approx(10 - 3 * np.sqrt(10), abs=1e-13)
+    assert mga == pytest.approx(mg * np.sqrt(10), abs=1e-13)
+    # D: eight 0, 3, 100 at kappa 2.  Pass 1: mu 10.3, 2 sigma = 59.83, the
+    # closest sample (100, |d| = 89.7) is 29.87 away.  Pass 2: eight 0 and 3,
+    # mu 1/3, sigma sqrt(8)/3: the 3 lies 8/3 - 2 sqrt(8)/3 beyond 2 sigma, the
+    # smallest distance of all (a zero lies 2 sqrt(8)/3 - 1/3 inside).
+    x = np.array([0.0] * 8 + [3.0, 100.0])
+    *_, mga = oracle.clip(x, adu=True, kappa=2.0)
+    assert mga == pytest.approx(8 / 3 - 2 * np.sqrt(8) / 3, abs=1e-13)
+    # asymmetric thresholds: F, nine 0 and 10 with kappa_hi 2: mu 1, sigma 3,
+    # the 10 is 9 - 6 = 3 beyond, the zeros 9 - 1 = 8 inside kappa_lo 3
+    *_, mga = oracle.clip(np.array([0.0] * 9 + [10.0]), adu=True, kappa_lo=3.0, kappa_hi=2.0)
+    assert mga == pytest.approx(3.0, abs=1e-13)
+    # G, the mirror image: nine 0 and -10 with kappa_lo 2: the -10 lies 9 below
+    # the mean, 3 beyond 2 sigma (the zeros lie 8 inside kappa_hi 3)
+    *_, mga = oracle.clip(np.array([0.0] * 9 + [-10.0]), adu=True, kappa_lo=2.0, kappa_hi=3.0)
+    assert mga == pytest.approx(3.0, abs=1e-13)
+
+
 def test_clip_result_is_a_fixed_point_of_the_rule():
     """Properties any correct run of the iteration has, checked on random small
     stacks with outliers (mean centre, ddof 0, passes until nothing changes):

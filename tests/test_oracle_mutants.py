@@ -104,8 +104,11 @@ MUTANTS = [
     ("nearest ignores bad pixels", "    if (src_bad(s, i, j)) return 0;\n", ""),
     ("spline ignores bad pixels",
      "if (w != 0.0 && src_bad(s, oracle_mirror(i, W), oracle_mirror(j, H))) return 0;", ""),
-    ("clip margin not in units of sigma", "double mg = fabs(fabs(d) - thr) / sigma;",
-     "double mg = fabs(fabs(d) - thr);"),
+    ("clip margin not in units of sigma", "double mg = dist / sigma;", "double mg = dist;"),
+    ("clip margin in data units divided by sigma",
+     "if (dist < margin_adu) margin_adu = dist;", "if (dist / sigma < margin_adu) margin_adu = dist / sigma;"),
+    ("clip margin in data units from the signed deviation",
+     "double dist = fabs(fabs(d) - thr);", "double dist = fabs(d - thr);"),
     ("shift marks every sample valid", "valid[(int64_t)y * W + x] = (uint8_t)ok;",
      "valid[(int64_t)y * W + x] = 1;"),
     ("every spline frame takes the first frame's coefficients",
