@@ -3,11 +3,19 @@
 
 A step is one pass of the whole path -- calibration, alignment, sigma-clipped
 mean and median -- over one batch of synthetic frames resident in HBM.
-Default workload: 3 bands x 10 frames of 1024x1024 uint16 with offsets of up
-to +-10 px, cubic-spline alignment, 3-sigma clipping with 3 passes plus the
-median, all three bands in one call.  The metric is reduced raw megapixels per second
-(sum of n*W*H over the step's sets).  L2 is flushed (256 MB write) before
-every timed step; each step is timed with CUDA events on the launch stream.
+
+Default (``--workload headline``): the metric's own configuration.  The line's
+value is the batched form: 64 frame sets of uneven shape (3 to 40 frames of
+512^2 to 4096^2 uint16, bilinear, 3-sigma clip with 3 passes plus the median)
+reduced by autotuned persistent launches replayed from a CUDA graph, beside
+the same sets reduced by 64 plain per-set launches (``plain_mpix_s``,
+``batched_over_plain``).  Sub-records: the largest plain set (32 frames of
+4096^2, its HBM roofline fraction and its FP16/FP32 stack forms with errors
+against the FP64 oracle), the three 10-frame bands of 1024^2 with the cubic
+spline, and the served form (16-chip exposures at Poisson arrivals, p50/p99
+latency).  The metric is reduced raw megapixels per second (sum of n*W*H over
+a step's sets); each step is timed with CUDA events on the launch stream, L2
+flushed (256 MB write) before every step whose data fit in L2.
 
 --impl reference times the FP64 CPU oracle on the same workload (a bounded
 sample per step) on this machine's cores.
@@ -108,7 +116,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "100", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -186,33 +194,6 @@ def sum_over_ranks(x, world):
     return _reduce_over_ranks(x, world, dist.ReduceOp.SUM)
 
 
-DEEP = 64  # sets of more frames are combined by groups of lanes, not one thread per pixel
-
-
-def algorithmic_bytes(kind, sets, interp, want_nkept=False):
-    """Bytes one launch of ``kind`` must move, per the path's data flow:
-    reduce from raw: n*P*2 (raw) + P*12 (bias, dark, flat) + P*8 (mean, median)
-    reduce from spline coefficients: n*P*4 + P*8
-    prefilter: n*P*2 (raw) + P*12 (masters) + n*P*4 (coefficients)
-    sets of more than 64 frames: reduce writes the aligned FP32 stack (n*P*4)
-    in place of the outputs, and combine reads it back, or reads the filtered
-    rows of a spline set on the row/column passes (no reduce launch then):
-    n*P*4 + P*8."""
-    tot = 0
-    for (W, H, n) in sets:
-        P = W * H
-        out = P * (8 + (2 if want_nkept else 0))
-        deep = n > DEEP
-        if kind == "reduce":
-            src = n * P * 4 if interp == "spline3" else n * P * 2 + P * 12
-            tot += src + (n * P * 4 if deep else out)
-        elif kind == "prefilter":
-            tot += n * P * 2 + P * 12 + n * P * 4
-        elif kind == "combine" and deep:
-            tot += n * P * 4 + out
-    return tot
-
-
 def workload_shapes(workload):
     """(W, H, n) of every set of one step (of a scan: every point's 3 bands)."""
     if workload in SWEEPS:
@@ -224,9 +205,11 @@ def workload_shapes(workload):
     return [(W, H, n) for (n, W, H) in synth.batch_shapes(cfg["seed"])]
 
 
-def cpu_baseline(workload, steps, warmup, nthreads, as_reference=False):
+def cpu_baseline(workload, steps, warmup, nthreads, as_reference=False, best=False):
     """Times the oracle as it stands on a bounded sample: one set of the
-    workload, cropped to at most 256 rows (and 2048 columns), per step."""
+    workload (the one with the most frames), cropped to at most 256 rows and
+    2048 columns, per step; the mean time per sample, or the best with
+    ``best``."""
     import oracle
     from paper_2008_11486_gb300 import synth
     cfg = WORKLOADS[workload] if workload in WORKLOADS else SWEEPS[workload]
@@ -248,7 +231,7 @@ def cpu_baseline(workload, steps, warmup, nthreads, as_reference=False):
         if i >= warmup:
             times.append(dt)
     px = n * Ws * Hs
-    mean_t = float(np.mean(times))
+    mean_t = float(np.min(times) if best else np.mean(times))
     return dict(value=px / mean_t / 1e6, unit="Mpix/s", cores=nthreads, kind="oracle",
                 sample=f"{n} frames of {Ws}x{Hs} (one set of the workload cropped), "
                        f"{cfg['interp']}, FP64, OpenMP {nthreads} threads",
@@ -259,15 +242,18 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     nthreads = os.cpu_count() or 1
-    cb = cpu_baseline(args.workload, args.steps, args.warmup, nthreads, as_reference=True)
-    cfg = WORKLOADS[args.workload] if args.workload in WORKLOADS else SWEEPS[args.workload]
-    line = {"impl": "reference", "metric": "reduced Mpix/s", "value": cb["value"],
-            "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+    workload = "batch" if args.workload == "headline" else args.workload
+    steps = args.steps if args.steps is not None else 3
+    cb = cpu_baseline(workload, steps, args.warmup, nthreads, as_reference=True)
+    cfg = WORKLOADS[workload] if workload in WORKLOADS else SWEEPS[workload]
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"],
+            "unit": "Mpix/s", "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
             "ms_per_step": cb["seconds_per_sample"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": cfg["desc"]},
+            "config": {"workload": workload, "desc": cfg["desc"]},
             "cpu_baseline": {"value": cb["value"], "unit": "Mpix/s", "cores": cb["cores"],
-                             "kind": "oracle", "sample": cb["sample"]},
+                             "kind": "oracle", "sample": cb["sample"],
+                             "cpu_model": cpu_model()},
             "e2e": {"value": cb["value"], "unit": "Mpix/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -394,25 +380,34 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def roofline(prof, steps, bytes_per_step_by_kind, ms_per_step, path_bytes_per_step,
-             workload=None, sm_count=None):
-    """HBM roofline of the dominant kernel: its algorithmic bytes per step over
-    its device time per step (both summed over its launches in a step)."""
-    kinds = {k: v for k, v in prof.items() if v[1] > 0 and k in bytes_per_step_by_kind}
+def path_bytes(shapes, want_nkept=False):
+    """Bytes the fused path must move per step, the scope table's figure: per
+    set n*P*2 (raw frames, read once) + P*12 (bias, dark, flat) + P*8 (mean,
+    median), i.e. P (2n + 20).  Intermediate data a kernel writes and reads
+    back (spline coefficients, a stack) are overhead, not algorithmic bytes."""
+    return sum(W * H * (2 * n + 20 + (2 if want_nkept else 0)) for (W, H, n) in shapes)
+
+
+def roofline(prof, steps, path_bytes_per_step, ms_per_step, workload=None, sm_count=None):
+    """HBM roofline of the dominant kernel kind: the path's algorithmic bytes
+    per step over that kind's device time per step (summed over its launches
+    in a step).  ``path_frac`` divides the same bytes by the whole step."""
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms = kinds[dom][0] / steps
     peak, peak_src = measured_peaks()
-    achieved = bytes_per_step_by_kind[dom] / (dom_ms * 1e-3) / 1e9
+    achieved = path_bytes_per_step / (dom_ms * 1e-3) / 1e9
     traffic = None
     rec = TRAFFIC.get(workload)
     if rec and rec[1] == dom and rec[2] is not None and rec[0] == kernel_source_hash():
         traffic = rec[2]
     return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-            "algorithmic_bytes": bytes_per_step_by_kind[dom],
+            "algorithmic_bytes": path_bytes_per_step,
+            "bytes_basis": "P (2n + 20) per set: raw once, masters once, mean and median once",
             "peak_source": peak_src,
             "launches_per_step": round(kinds[dom][1] / steps, 3),
-            "kernel_ms": {k: round(v[0] / steps, 5) for k, v in prof.items() if v[1]},
+            "kernel_ms": {k: round(v[0] / steps, 5) for k, v in kinds.items()},
             "path_frac": round(path_bytes_per_step / (ms_per_step * 1e-3) / 1e9 / peak, 4),
             "issue": (issue_roofline(workload, dom, dom_ms, sm_count, sm_max_mhz())
                       if sm_count else None)}
@@ -452,15 +447,6 @@ def e2e_run(sets, params, ws, e2e_steps, stream, world):
             "d2h_bytes_per_step": sum(2 * s.H * s.W * 4 for s in sets)}
 
 
-def step_bytes(shapes, interp):
-    by = {"reduce": algorithmic_bytes("reduce", shapes, interp)}
-    if interp == "spline3":
-        by["prefilter"] = algorithmic_bytes("prefilter", shapes, interp)
-    if any(n > DEEP for (_, _, n) in shapes):
-        by["combine"] = algorithmic_bytes("combine", shapes, interp)
-    return by
-
-
 def sampled_errors(fs_host, outs, interp, npix=4000, seed=5):
     """Max abs/rel error of mean and median against the FP64 oracle on sampled
     pixels whose oracle clip margin is not within 1e-3 sigma of a threshold,
@@ -488,59 +474,68 @@ def sampled_errors(fs_host, outs, interp, npix=4000, seed=5):
     return res
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=None)
-    ap.add_argument("--warmup", type=int, default=None)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bands", choices=sorted(WORKLOADS) + sorted(SWEEPS))
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--requests", type=int, default=12, help="served: requests at the nominal rate")
-    ap.add_argument("--rate", type=float, default=0.5, help="served: Poisson arrival rate (1/s)")
-    args = ap.parse_args()
-    heavy = args.workload in ("deep", "precision", "batch", "served", "masked", "paper",
-                              "paper_band") or args.workload in SWEEPS
-    if args.steps is None:
-        args.steps = 10 if heavy else 2000
-    if args.warmup is None:
-        args.warmup = 3 if heavy else 20
-    if args.e2e_steps is None:
-        args.e2e_steps = 2 if heavy else 50
-    args.warmup = max(args.warmup, 3)
-    world, rank, local = dist_init()
-    if args.impl == "reference":
-        run_reference(args, world, rank)
-        return
-
+def choose_steps(step, stream, min_seconds, min_steps=3, max_steps=20000):
+    """Steps whose timed region lasts at least ``min_seconds`` (from the time
+    of three warm steps), so that the clock samples cover it."""
     import torch
-    from paper_2008_11486_gb300 import build as irp_build
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per = max(e0.elapsed_time(e1) / 3 * 1e-3, 1e-7)
+    return int(min(max_steps, max(min_steps, np.ceil(min_seconds / per))))
+
+
+def cpu_model():
+    """The host CPU's model name (x86 'model name', Arm 'CPU part' via lscpu)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline_both(workload):
+    """The oracle on one bounded sample of the workload, single-threaded and
+    on every host core, best of 3 each."""
+    nproc = os.cpu_count() or 1
+    one = cpu_baseline(workload, 3, 1, 1, best=True)
+    allc = cpu_baseline(workload, 3, 1, nproc, best=True)
+    return {"value": round(allc["value"], 3), "unit": "Mpix/s", "cores": nproc,
+            "kind": "oracle", "sample": allc["sample"].rsplit(",", 1)[0],
+            "timing": "best of 3 runs (after 1 warm-up) per thread count",
+            "single_thread": {"value": round(one["value"], 3), "cores": 1},
+            "all_cores": {"value": round(allc["value"], 3), "cores": nproc},
+            "cpu_model": cpu_model(), "nproc": nproc}
+
+
+def run_workload(args, name, dev, stream, world, rank, local, steps=None, min_seconds=1.0,
+                 with_cpu=True, with_e2e=True):
+    """Times one workload; returns its JSON record (rank 0) or None."""
+    import torch
     from paper_2008_11486_gb300 import core, shard
-    irp_build.build()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    cfg = WORKLOADS[args.workload] if args.workload in WORKLOADS else SWEEPS[args.workload]
+    cfg = WORKLOADS[name]
     interp = cfg["interp"]
-    stream = torch.cuda.Stream(dev)   # non-default stream: graph capture needs one
-    torch.cuda.set_stream(stream)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    heavy = name in HEAVY
+    flush = None if heavy else torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,
+                                           device=dev)
     extra = {}
-
-    if args.workload in SWEEPS:
-        line = run_sweep(args, dev, stream, world, rank, local)
-        if rank == 0:
-            print(json.dumps(line), flush=True)
-        return
-
-    if args.workload == "served":
-        line = run_served(args, cfg, dev, world, rank, local)
-        if rank == 0:
-            print(json.dumps(line), flush=True)
-        return
-
-    shapes = workload_shapes(args.workload)
-    if args.workload == "batch":  # sets are independent: disjoint shards per rank
+    shapes = workload_shapes(name)
+    if name == "batch":  # sets are independent: disjoint shards per rank
         costs = [shard.set_cost(n, W, H) for (W, H, n) in shapes]
         shapes = [shapes[i] for i in shard.rank_shard(costs, world, rank)]
         scaling = "strong"
@@ -558,29 +553,35 @@ def main():
     def joint_step():  # all of the step's sets in one call
         core.reduce_sets(sets, params, ws=ws)
 
-    step = plain_step if args.workload == "batch" else joint_step
-    if args.workload == "batch":
+    step = plain_step if name == "batch" else joint_step
+    if name == "batch":
         from paper_2008_11486_gb300 import batch
-        t_plain, _, _, _ = timed_steps(plain_step, max(2, args.steps // 2), 1, stream, None,
-                                       world, local)
-        plain_ms = t_plain / max(2, args.steps // 2)
+        for _ in range(args.warmup):
+            plain_step()
+        psteps = choose_steps(plain_step, stream, min_seconds)
+        t_plain, _, _, pclocks = timed_steps(plain_step, psteps, 1, stream, None, world, local)
+        plain_ms = t_plain / psteps
         tuner = batch.Autotuner(os.path.join(tempfile.gettempdir(), "irp_autotune.json"), reps=2)
         bparams, bcfg = tuner.params_for(sets, interp)
         br = batch.BatchReducer(sets, bparams, stream=stream)
         step = br.run
         extra["batch_status"] = br
-        extra["plain_ms_per_step"] = round(plain_ms, 4)
+        extra["plain"] = {"ms_per_step": round(plain_ms, 4), "steps": psteps,
+                          "launches": "one irp_reduce_set call per set", "clocks": pclocks}
         extra["autotuned"] = bcfg
-    if args.workload == "precision":
+    if name == "precision":
         extra["unfused"] = run_unfused(sets, interp, stream, world, local)
-    if args.workload in ("paper", "paper_band"):
+    if name in ("paper", "paper_band"):
         # the paper's own GPU timing of the same run shape (Sec. 3.2.1, table
         # "Breakdown of t", n = 540 on one TITAN X Pascal); context only
         extra["paper_context"] = {"gpu": "TITAN X (Pascal)", "alignment_s": 0.48,
                                   "combining_s": 0.14, "bias_dark_flat_s": 1.0e-3}
-
-    total_ms, wall, prof, clocks = timed_steps(step, args.steps, args.warmup, stream,
-                                               None if heavy else flush, world, local)
+    for _ in range(args.warmup):
+        step()
+    if steps is None:
+        steps = choose_steps(step, stream, min_seconds)
+    total_ms, wall, prof, clocks = timed_steps(step, steps, args.warmup, stream, flush, world,
+                                               local)
     assert core.sync_status(ws) == 0
     if "batch_status" in extra:
         br = extra.pop("batch_status")
@@ -593,41 +594,41 @@ def main():
         torch.cuda.synchronize()
         p3 = core.profile_read()
         core.profile_enable(False)
-        prof = {k: (v[0] / 3 * args.steps, v[1] // 3 * args.steps) for k, v in p3.items()}
+        prof = {k: (v[0] / 3 * steps, v[1] // 3 * steps) for k, v in p3.items()}
         extra["kernel_timing"] = "plain launches of the batch plan (graph replays are not traced)"
-    ms_per_step = total_ms / args.steps
+    ms_per_step = total_ms / steps
     px_local = sum(n * W * H for (W, H, n) in shapes)
-    value = (world if scaling == "weak" else 1) * px_local * args.steps / (total_ms * 1e-3) / 1e6
+    value = (world if scaling == "weak" else 1) * px_local * steps / (total_ms * 1e-3) / 1e6
     if scaling == "strong" and world > 1:
-        value = sum_over_ranks(float(px_local), world) * args.steps / (total_ms * 1e-3) / 1e6
-    if args.workload == "batch":
-        extra["plain_mpix_s"] = round(px_local / (extra["plain_ms_per_step"] * 1e-3) / 1e6, 1)
-        extra["batched_over_plain"] = round(extra["plain_ms_per_step"] / ms_per_step, 3)
-    rf = roofline(prof, args.steps, step_bytes(shapes, interp), ms_per_step,
-                  algorithmic_bytes("reduce", shapes, "bilinear"), args.workload,
+        value = sum_over_ranks(float(px_local), world) * steps / (total_ms * 1e-3) / 1e6
+    if name == "batch":
+        pl = extra["plain"]
+        pl["mpix_s"] = round(px_local / (pl["ms_per_step"] * 1e-3) / 1e6, 1)
+        extra["plain_mpix_s"] = pl["mpix_s"]
+        extra["batched_over_plain"] = round(pl["ms_per_step"] / ms_per_step, 3)
+    rf = roofline(prof, steps, path_bytes(shapes), ms_per_step, name,
                   sm_count=core.lib().irp_device_sm_count())
     gpu_launches = int(sum(v[1] for v in prof.values()))
-    e2e = e2e_run(sets, params, ws, args.e2e_steps, stream, world)
+    e2e = e2e_run(sets, params, ws, args.e2e_steps or (2 if heavy else 50), stream,
+                  world) if with_e2e else None
 
-    if args.workload == "precision" and rank == 0:
+    if name == "precision" and rank == 0:
         fs_host = host_frameset(sets[0])
         outs = {"fused_f32": (sets[0].mean.cpu().numpy(), sets[0].median.cpu().numpy())}
         outs.update(extra["unfused"].pop("outputs"))
         extra["errors_vs_oracle"] = sampled_errors(fs_host, outs, interp)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(args.workload, 2, 1, os.cpu_count() or 1)
-        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
-        cpu["value"] = round(cpu["value"], 3)
-
+    if rank == 0 and world == 1 and with_cpu and not args.no_cpu_baseline:
+        cpu = cpu_baseline_both(name)
+    line = None
     if rank == 0:
-        line = {"metric": "reduced Mpix/s", "value": round(value, 1), "unit": "Mpix/s",
-                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        line = {"metric": METRIC, "value": round(value, 1), "unit": "Mpix/s",
+                "n_gpus": world, "steps": steps, "warmup": args.warmup,
                 "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
                 "scaling": scaling, "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded device generator, paper-shaped frames)",
-                "config": {"workload": args.workload, "desc": cfg["desc"],
+                "config": {"workload": name, "desc": cfg["desc"],
                            "sets_per_step": len(shapes),
                            "frames_per_step": sum(n for (_, _, n) in shapes),
                            "raw_mpix_per_step": px_local / 1e6,
@@ -641,6 +642,95 @@ def main():
         if "paper_context" in extra:
             extra["paper_context"]["this_step_s"] = round(ms_per_step * 1e-3, 6)
         line.update(extra)
+    del sets, ws
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return line
+
+
+def _sub(line, keep=("value", "unit", "ms_per_step", "steps", "config", "roofline", "e2e",
+                     "gpu_launches", "clocks")):
+    """A sub-record: the workload's line without the keys of the whole run."""
+    return {k: v for k, v in line.items() if k in keep or k not in (
+        "metric", "n_gpus", "warmup", "higher_is_better", "scaling", "vs_baseline", "dtype",
+        "data", "cpu_baseline", "wall_s")}
+
+
+def run_headline(args, dev, stream, world, rank, local):
+    """The metric's own configuration: the batched form (value) against its
+    plain per-set launches, with the largest plain set, the spline bands and
+    the served form as sub-records."""
+    import torch
+    line = run_workload(args, "batch", dev, stream, world, rank, local, steps=args.steps,
+                        with_cpu=False)
+    subs = {}
+    for name in ("precision", "bands"):
+        sub = run_workload(args, name, dev, stream, world, rank, local, with_cpu=False,
+                           with_e2e=(name == "bands"))
+        if rank == 0:
+            subs["deep" if name == "precision" else name] = _sub(sub)
+    served = run_served(args, WORKLOADS["served"], dev, world, rank, local)
+    torch.cuda.empty_cache()
+    if rank == 0:
+        subs["served"] = _sub(served, keep=("value", "unit", "ms_per_step", "steps", "config",
+                                            "latency_s", "saturation", "batches", "e2e",
+                                            "clocks", "admission"))
+        line["subrecords"] = subs
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_both("batch")
+        line["config"]["workload"] = ("batch: " + line["config"]["workload"] + " (value); "
+                                      "subrecords deep, bands, served")
+    return line
+
+
+HEAVY = ("deep", "precision", "batch", "served", "masked", "paper", "paper_band")
+METRIC = ("reduced Mpix/s and HBM GB/s fraction on 1 GB300, batched vs plain; "
+          "p50/p99 set latency")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline"] + sorted(WORKLOADS) + sorted(SWEEPS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--requests", type=int, default=12, help="served: requests at the nominal rate")
+    ap.add_argument("--rate", type=float, default=0.5, help="served: Poisson arrival rate (1/s)")
+    args = ap.parse_args()
+    if args.warmup is None:
+        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_2008_11486_gb300 import build as irp_build
+    irp_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)   # non-default stream: graph capture needs one
+    torch.cuda.set_stream(stream)
+
+    if args.workload == "headline":
+        if args.steps is None:
+            args.steps = 20  # about one second of the batched form
+        line = run_headline(args, dev, stream, world, rank, local)
+    elif args.workload in SWEEPS:
+        if args.steps is None:
+            args.steps = 10
+        line = run_sweep(args, dev, stream, world, rank, local)
+    elif args.workload == "served":
+        line = run_served(args, WORKLOADS["served"], dev, world, rank, local)
+    else:
+        line = run_workload(args, args.workload, dev, stream, world, rank, local,
+                            steps=args.steps)
+    if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -751,7 +841,8 @@ def run_served(args, cfg, dev, world, rank, local):
         del d
     torch.cuda.empty_cache()
     rng = np.random.Generator(np.random.PCG64(cfg["seed"]))
-    srv = serve.Server(masters, depth=depth, max_inflight=2, interp=cfg["interp"], device=dev)
+    srv = serve.Server(masters, depth=depth, max_inflight=2, interp=cfg["interp"], device=dev,
+                       download=True)
 
     def make_requests(count, base):
         return [serve.Request(rid=base + r, frames=[host_frames[c][(base + r) % nvar]
@@ -767,10 +858,29 @@ def run_served(args, cfg, dev, world, rank, local):
     phase = {"queued_s": [r.admitted - r.arrival for r in reqs],
              "upload_wait_s": [r.launched - r.admitted for r in reqs],
              "device_s": [r.done - r.launched for r in reqs]}
+    nominal = {"batches": srv.batches, "batch_sizes": list(srv.batch_sizes),
+               "admitted_while_running": srv.admitted_while_running,
+               "held_for_memory": srv.held_for_memory}
     sat_n = max(8, args.requests)
+    from paper_2008_11486_gb300 import core
+    core.profile_enable(True)
+    core.profile_read()
+    b0, a0 = srv.batches, srv.admitted_while_running
     sat_lat, sat_wall = serve.run_poisson(srv, make_requests(sat_n, 1000), rate_hz=1e6)
+    prof = core.profile_read()
+    core.profile_enable(False)
     clocks = sampler.stop()
     assert srv.status() == 0
+    sizes = srv.batch_sizes[len(nominal["batch_sizes"]):]
+    admission = {"nominal_rate": nominal,
+                 "saturation": {"batches": srv.batches - b0,
+                                "max_requests_per_batch": max(sizes) if sizes else 0,
+                                "mean_requests_per_batch": round(float(np.mean(sizes)), 3)
+                                if sizes else 0.0,
+                                "admitted_while_running": srv.admitted_while_running - a0},
+                 "workspace_bytes_per_request": srv._ws_bytes_per_request(),
+                 "rule": "admitted while free HBM minus the request's batch workspace stays "
+                         "above the reserve and an in-flight slot is free"}
     new_px = nchips * W * H
     sustained = sat_n * new_px / sat_wall / 1e6
     return {"metric": "reduced Mpix/s", "value": round(sustained * world, 1), "unit": "Mpix/s",
@@ -790,11 +900,13 @@ def run_served(args, cfg, dev, world, rank, local):
             "saturation": {"requests": sat_n, "wall_s": round(sat_wall, 3),
                            "p50_s": round(float(np.percentile(sat_lat, 50)), 4),
                            "p99_s": round(float(np.percentile(sat_lat, 99)), 4)},
-            "batches": srv.batches,
+            "batches": srv.batches, "admission": admission,
             "e2e": {"value": round(sustained * world, 1), "unit": "Mpix/s",
-                    "h2d_bytes_per_step": new_px * 2, "d2h_bytes_per_step": 0},
-            "gpu_launches": None, "clocks": clocks, "cpu_baseline": None,
-            "roofline": None}
+                    "api": "serve.Server: pinned raw frames in, mean images back in pinned "
+                           "host memory; the value is end to end",
+                    "h2d_bytes_per_step": new_px * 2, "d2h_bytes_per_step": new_px * 4},
+            "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clocks,
+            "cpu_baseline": None, "roofline": None}
 
 
 if __name__ == "__main__":

@@ -60,6 +60,7 @@ class Request:
     launched: float = 0.0  # its reduction queued
     done: float = 0.0
     outputs: list = None  # per chip (mean, median) device tensors (views of the output ring)
+    host_means: list = None  # per chip pinned host mean images (servers that download)
     out_slot: int = 0
     status: int = 0       # device status of its reduction (0 = IRP_OK), set on completion
 
@@ -94,7 +95,7 @@ class Chip:
 
 class Server:
     def __init__(self, masters, depth=5, max_inflight=2, interp="bilinear", clip=None,
-                 hbm_reserve_bytes=2 << 30, device="cuda", out_slots=None):
+                 hbm_reserve_bytes=2 << 30, device="cuda", out_slots=None, download=False):
         self.device = torch.device(device)
         self.depth = depth
         self.max_inflight = max_inflight
@@ -130,6 +131,16 @@ class Server:
         self.failed = []                     # completed requests whose status is not OK
         self._ws_per_req = None              # workspace bytes of one request's sets
         self.held_for_memory = 0             # admissions deferred for lack of free HBM
+        self.batch_sizes = []                # requests per launched batch
+        self.admitted_while_running = 0      # admissions while a batch was on the device
+        # download: each request's mean images are copied back to pinned host
+        # memory behind its batch (Request.host_means), before it completes
+        self.download = download
+        self.host_out = None
+        if download:
+            pin = torch.cuda.is_available()
+            self.host_out = [[torch.empty((c.H, c.W), dtype=torch.float32, pin_memory=pin)
+                              for c in self.chips] for _ in range(self.out_slots)]
 
     # ---------------------------------------------------------------- intake
     def submit(self, req: Request):
@@ -238,6 +249,8 @@ class Server:
             req.admitted = time.perf_counter()
             req.out_slot = self.admitted % self.out_slots
             self.admitted += 1
+            if self.running:
+                self.admitted_while_running += 1
             self.uploading.append((req, nums, ev))
 
     def _launch(self):
@@ -282,6 +295,11 @@ class Server:
         plan.launch(self.compute_stream)
         with torch.cuda.stream(self.compute_stream):
             self.status_host[slot:slot + 1].copy_(status, non_blocking=True)
+            if self.download:
+                for r in reqs:
+                    r.host_means = self.host_out[r.out_slot]
+                    for c, (mean, _) in enumerate(r.outputs):
+                        r.host_means[c].copy_(mean, non_blocking=True)
         t = time.perf_counter()
         for r in reqs:
             r.launched = t
@@ -289,6 +307,7 @@ class Server:
         done_ev.record(self.compute_stream)
         self.running.append((reqs, done_ev, plan, ws, slot, per_req))
         self.batches += 1
+        self.batch_sizes.append(len(reqs))
 
     def _isolate(self, reqs, per_req, ws):
         """A batch reported a device error: each of its requests is reduced

@@ -14,6 +14,17 @@ Tolerances, each derived from the rounding steps of the FP32 arithmetic:
   * median on identical inputs: bit-exact; clip masks on identical inputs:
     identical except at pixels the oracle marks within 1e-5 sigma of a
     threshold.
+
+End to end (GPU from raw against the FP64 oracle from raw), ``gate_e2e``:
+  * clip results (kept counts) must agree, except where the oracle's smallest
+    threshold distance in ADU is within (2 + kappa) times the pixel's sample
+    bound: a sample error e moves |x - mu| by at most 2|e| and kappa sigma by
+    at most kappa |e|, so no larger distance can flip a decision;
+  * the mean and median within max(1e-3 ADU, 1e-6 |ref|) at every compared
+    pixel (the benchmark spec's bound, read as atol + rtol).  The a-priori
+    sample bound exceeds that tolerance at some pixels (near bright stars,
+    and for the spline at sky level); the gate does not widen there, and the
+    fraction of such pixels is reported beside the measured errors.
 """
 import numpy as np
 
@@ -66,3 +77,50 @@ def compare(name, got, ref, tol, mask=None):
     assert not bad.any(), (f"{name}: {bad.sum()} of {fin.sum()} outside tolerance, "
                            f"worst err {err[bad].max():.3g} at ratio {ratio:.3g}")
     return dict(max_err=float(err[fin].max()) if fin.any() else 0.0, max_ratio=float(ratio))
+
+
+def gate_e2e(name, got, ref, samp, kappa, meas=None, max_outside=0.0):
+    """End-to-end gate of one set's outputs (see the module docstring).
+
+    got: dict with mean, median, nkept (arrays over the compared pixels);
+    ref: the oracle's reduce_set dict (mean, median, nkept, margin, margin_adu);
+    samp: per-pixel a-priori sample bound (max over the pixel's frames);
+    meas: per-pixel measured largest sample error |gpu - oracle| (optional;
+    when given it replaces the a-priori bound in the mean/median gates);
+    max_outside: cap on the fraction of compared pixels outside the plain
+    tolerance (default 0: the plain tolerance gates every pixel; None: only
+    the plain tolerance plus the sample bound).  Returns the statistics."""
+    gm = np.asarray(got["mean"], np.float64)
+    gd = np.asarray(got["median"], np.float64)
+    samp = np.broadcast_to(np.asarray(samp, np.float64), gm.shape)
+    allowed = (ref["margin_adu"] < (2.0 + kappa) * samp) | (ref["margin"] < 1e-5)
+    if got.get("nkept") is None:
+        # no kept counts to compare: the mean is gated where no decision can flip
+        mismatch = allowed
+    else:
+        gk = np.asarray(got["nkept"]).astype(np.int64)
+        rk = np.asarray(ref["nkept"]).astype(np.int64)
+        mismatch = gk != rk
+        bad = mismatch & ~allowed
+        assert not bad.any(), (f"{name}: clip results differ at {int(bad.sum())} pixels whose "
+                               f"threshold distance exceeds the rounding reach")
+    extra = samp if meas is None else np.broadcast_to(np.asarray(meas, np.float64), gm.shape)
+    stats = {"pixels": int(gm.size), "clip_mismatch_frac": float(mismatch.mean())}
+    for key, g in (("mean", gm), ("median", gd)):
+        r = np.asarray(ref[key], np.float64)
+        cmp = ~mismatch if key == "mean" else np.ones(gm.shape, bool)
+        plain = mean_tolerance(r)
+        compare(f"{name} {key}", g, r, plain + extra, cmp)
+        attain = extra <= plain
+        compare(f"{name} {key} (plain tolerance)", g, r, plain, cmp & attain)
+        fin = cmp & np.isfinite(r)
+        err = np.abs(g - r)
+        outside = fin & (err > plain)
+        stats[f"{key}_max_abs"] = float(err[fin].max()) if fin.any() else 0.0
+        stats[f"{key}_max_rel"] = float((err[fin] / np.maximum(np.abs(r[fin]), 1e-30)).max()) \
+            if fin.any() else 0.0
+        stats[f"{key}_outside_plain_frac"] = float(outside.sum() / max(fin.sum(), 1))
+        stats[f"{key}_bound_above_plain_frac"] = float((fin & ~attain).sum() / max(fin.sum(), 1))
+        if max_outside is not None:
+            assert stats[f"{key}_outside_plain_frac"] <= max_outside, (name, key, stats)
+    return stats

@@ -1,0 +1,120 @@
+"""The paper's own check of the shift (Sec. 3.1.1) on the GPU: an image made
+of sampled 2-D cubic B-spline basis functions is shifted by sub-pixel offsets,
+and the result is compared with the same basis functions sampled at the
+shifted positions, which is the exact shift.  The paper reports a relative
+difference dI = (I - I_exact) / I_exact of about 1e-7 for its GPU pipeline.
+
+The basis functions sit on integer knots at least 3 px inside the frame, so
+the mirror boundary leaves them unchanged, and their amplitudes are multiples
+of 36, so that the sampled values (36 q times 4/9, 1/9, 1/36) are integers
+and the raw uint16 frames hold them exactly (bias 0, dark 0, flat 1).
+
+Both GPU forms are checked: irp_shift on FP32 frames (the unfused form) and
+the fused irp_reduce_set from raw (its aligned stack and its mean)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2008_11486_gb300 import build as irp_build
+from paper_2008_11486_gb300 import core, synth
+
+pytestmark = pytest.mark.gpu
+
+# Gates, from a few FP32 roundings (2^-24 = 6e-8) through the prefilter gain
+# (about 3 per axis): the central 90% range and the rms of dI, and the error
+# relative to the image's peak, stay within 1e-6.  At the fringe of a basis
+# function (|I_exact| down to 1e-3 of the peak) the same absolute rounding is
+# a larger fraction of the value: there |dI| stays within 1e-5.
+DI_BOUND = 1e-6
+DI_FRINGE = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _native():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    irp_build.build()
+
+
+def basis_image(W, H, spacing, seed):
+    """Knots (xm, ym) on a jittered grid >= 3 px inside the frame, amplitude
+    36 q (q <= 1800, so the peak 16 q stays below 2^15).  Returns the uint16
+    image and the knot list."""
+    rng = np.random.default_rng(seed)
+    knots = []
+    img = np.zeros((H, W), np.int64)
+    b = {-1: 1, 0: 4, 1: 1}  # 6 beta3 at the integer offsets -1, 0, 1
+    for ym in range(3, H - 3, spacing):
+        for xm in range(3, W - 3, spacing):
+            q = int(rng.integers(50, 1800))
+            knots.append((xm, ym, 36 * q))
+            for j in (-1, 0, 1):
+                for i in (-1, 0, 1):
+                    img[ym + j, xm + i] += q * b[i] * b[j]  # 36 q beta3(i) beta3(j)
+    assert img.max() < 65536
+    return img.astype(np.uint16), knots
+
+
+def exact_shift(knots, W, H, dx, dy):
+    """Sum of the basis functions sampled at (x + dx, y + dy): the exact value
+    the shift must produce (beta3 from the oracle)."""
+    out = np.zeros((H, W))
+    xs, ys = np.arange(W), np.arange(H)
+    for (xm, ym, A) in knots:
+        bx = np.array([oracle.bspline3(x + dx - xm) for x in xs])
+        by = np.array([oracle.bspline3(y + dy - ym) for y in ys])
+        out += A * np.outer(by, bx)
+    return out
+
+
+def _di_stats(got, want, valid):
+    """dI on the pixels carrying signal (|I_exact| >= 1e-3 of the peak), and
+    the error relative to the peak everywhere."""
+    peak = np.abs(want).max()
+    sig = valid & (np.abs(want) >= 1e-3 * peak)
+    dI = (got[sig] - want[sig]) / want[sig]
+    err_peak = np.abs(got - want)[valid].max() / peak
+    return dict(pixels=int(sig.sum()), dI_max=float(np.abs(dI).max()),
+                dI_90=[float(v) for v in np.percentile(dI, [5, 95])],
+                dI_rms=float(np.sqrt(np.mean(dI ** 2))), err_over_peak=float(err_peak))
+
+
+@pytest.mark.parametrize("W,H", [(96, 80), (70, 30)])  # row/column passes; tiled prefilter
+def test_shift_of_bspline_basis_image_is_exact(W, H):
+    n = 6
+    rng = np.random.default_rng(W * H)
+    dx = rng.uniform(-2.9, 2.9, n)
+    dy = rng.uniform(-2.9, 2.9, n)
+    imgs, knots = zip(*[basis_image(W, H, 5, 31 + k) for k in range(n)])
+    raw = np.stack(imgs)
+    want = np.stack([exact_shift(knots[k], W, H, dx[k], dy[k]) for k in range(n)])
+    fs = synth.FrameSet(raw=raw, bias=np.zeros((H, W), np.float32),
+                        dark=np.zeros((H, W), np.float32), flat=np.ones((H, W), np.float32),
+                        exptime=np.full(n, 60.0, np.float32), dx=dx, dy=dy)
+    # fused, from raw
+    s = core.device_set(fs).alloc_outputs(want_stack=True)
+    ws = core.reduce_sets([s], core.reduce_params("spline3", core.clip_params(3.0, 3)))
+    assert core.sync_status(ws) == 0
+    st = s.stack.cpu().numpy().astype(np.float64)
+    valid = ~np.isnan(st)
+    ref_valid = oracle.reduce_set(fs, interp="spline3", want_stack=True)["valid"]
+    assert np.array_equal(valid, ref_valid)
+    fused = _di_stats(np.nan_to_num(st), want, valid)
+    # unfused: irp_shift of the FP32 frames (here equal to the raw values)
+    frames = torch.from_numpy(raw.astype(np.float32)).cuda()
+    sh, va, _ = core.shift(frames, dx, dy, "spline3")
+    a = sh.cpu().numpy().astype(np.float64)
+    va = va.cpu().numpy().astype(bool)
+    assert np.array_equal(va, valid)
+    unfused = _di_stats(np.nan_to_num(a), want, va)
+    # the mean over the frames (n = 6 <= 10 at kappa 3: no sample can be rejected)
+    cnt = valid.sum(axis=0)
+    mean_want = np.where(cnt > 0, np.where(valid, want, 0.0).sum(axis=0) / np.maximum(cnt, 1), 0)
+    gm = s.mean.cpu().numpy().astype(np.float64)
+    mean = _di_stats(np.nan_to_num(gm), mean_want, cnt > 0)
+    print(f"\nB-spline basis shift {W}x{H}: fused {fused}\n  unfused {unfused}\n  mean {mean}")
+    for name, r in (("fused", fused), ("unfused", unfused), ("mean", mean)):
+        assert max(abs(v) for v in r["dI_90"]) <= DI_BOUND, (name, r)
+        assert r["dI_rms"] <= DI_BOUND, (name, r)
+        assert r["err_over_peak"] <= DI_BOUND, (name, r)
+        assert r["dI_max"] <= DI_FRINGE, (name, r)

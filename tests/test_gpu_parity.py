@@ -13,7 +13,7 @@ import torch
 import oracle
 from paper_2008_11486_gb300 import build as irp_build
 from paper_2008_11486_gb300 import core, synth
-from parity_util import compare, mean_tolerance, sample_tolerance
+from parity_util import compare, gate_e2e, mean_tolerance, sample_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -49,11 +49,11 @@ def check_against_oracle(fs, got, interp, kappa, max_iter, normalize_flat=False,
     gvalid = ~np.isnan(st)
     # validity of every sample is integer logic: bit-exact
     assert np.array_equal(gvalid, ref["valid"]), "sample validity differs"
-    if check_stack and not normalize_flat:
-        tol = sample_tolerance(fs, interp, oracle)
+    tol = sample_tolerance(fs, interp, oracle)
+    if normalize_flat:  # the normalised samples are larger by the flat's mean
+        tol = tol * max(1.0, float(np.mean(fs.flat, dtype=np.float64)))
+    if check_stack:
         stats["stack"] = compare("stack", st, np.where(ref["valid"], ref["stack"], np.nan), tol)
-    else:
-        tol = np.zeros(st.shape)
     # combine on identical inputs: the oracle fed with the GPU's FP32 samples
     same = oracle.combine_stack(np.where(gvalid, st, 0.0), gvalid, kappa=kappa,
                                 max_iter=max_iter)
@@ -69,14 +69,13 @@ def check_against_oracle(fs, got, interp, kappa, max_iter, normalize_flat=False,
     agree = (got["nkept"] == same["nkept"])
     stats["mean_same_inputs"] = compare("mean(same inputs)", got["mean"], same["mean"],
                                         mean_tolerance(same["mean"]), agree)
-    # end to end against the oracle's own FP64 samples
-    e2e_mask = (ref["margin"] >= 1e-3) & (got["nkept"] == ref["nkept"])
-    assert e2e_mask.mean() > 0.99
+    # end to end against the oracle's own FP64 samples: clip results agree
+    # except within rounding reach of a threshold; mean and median within the
+    # plain tolerance where the measured sample errors allow it
     samp = np.max(np.where(ref["valid"], tol, 0.0), axis=0)
-    stats["mean_e2e"] = compare("mean e2e", got["mean"], ref["mean"],
-                                mean_tolerance(ref["mean"]) + samp, e2e_mask)
-    stats["median_e2e"] = compare("median e2e", got["median"], ref["median"],
-                                  mean_tolerance(ref["median"]) + samp)
+    meas = np.max(np.where(ref["valid"], np.abs(np.where(gvalid, st, 0.0) - ref["stack"]), 0.0),
+                  axis=0)
+    stats["e2e"] = gate_e2e("e2e", got, ref, samp, kappa, meas=meas)
     return stats
 
 
@@ -107,13 +106,9 @@ def test_fused_spline_band_full_size_sampled():
     ys = np.concatenate([rng.integers(0, H, 3000), np.zeros(W, int), np.full(W, H - 1),
                          np.arange(H), np.arange(H)])
     ref = oracle.reduce_set(fs, interp="spline3", pixels=(xs, ys))
-    gm, gd, gk = got["mean"][ys, xs], got["median"][ys, xs], got["nkept"][ys, xs]
-    tol_full = sample_tolerance(fs, "spline3", oracle)
-    samp = tol_full.max(axis=0)[ys, xs]
-    assert np.array_equal(gk, ref["nkept"]) or np.all((gk == ref["nkept"]) | (ref["margin"] < 1e-3))
-    mask = ref["margin"] >= 1e-3
-    print(compare("spline mean", gm, ref["mean"], mean_tolerance(ref["mean"]) + samp, mask))
-    print(compare("spline median", gd, ref["median"], mean_tolerance(ref["median"]) + samp))
+    g = {k: got[k][ys, xs] for k in ("mean", "median", "nkept")}
+    samp = sample_tolerance(fs, "spline3", oracle).max(axis=0)[ys, xs]
+    print(gate_e2e("spline band", g, ref, samp, 3.0))
 
 
 def test_persistent_and_batch_invariance():
@@ -130,9 +125,8 @@ def test_persistent_and_batch_invariance():
     # and the batch matches the oracle
     for fs, b in zip(fss, batch):
         ref = oracle.reduce_set(fs, interp="bilinear", kappa=2.5)
-        m = (ref["margin"] >= 1e-3) & (b["nkept"] == ref["nkept"])
-        compare("batch mean", b["mean"], ref["mean"],
-                mean_tolerance(ref["mean"]) + 8 * 2.0 ** -24 * 7e4, m)
+        samp = sample_tolerance(fs, "bilinear", oracle).max(axis=0)
+        gate_e2e("batch", b, ref, samp, 2.5)
 
 
 def _padded_device_set(fs, pad_raw, pad_master):
@@ -194,10 +188,8 @@ def test_spline_batch_mixing_coefficient_paths():
         assert np.array_equal(a["mean"].view(np.uint32), b["mean"].view(np.uint32))
         assert np.array_equal(a["median"].view(np.uint32), b["median"].view(np.uint32))
         ref = oracle.reduce_set(fs, interp="spline3")
-        m = (ref["margin"] >= 1e-3) & (b["nkept"] == ref["nkept"])
-        assert m.mean() > 0.99
         samp = sample_tolerance(fs, "spline3", oracle).max(axis=0)
-        compare("mixed spline mean", b["mean"], ref["mean"], mean_tolerance(ref["mean"]) + samp, m)
+        gate_e2e("mixed spline", b, ref, samp, 3.0)
 
 
 def test_normalize_flat():
@@ -296,8 +288,9 @@ def test_bounded_wait_gives_up_with_timeout(interp, H):
     ws = core.reduce_sets([s], core.reduce_params(interp, wait_spin_limit=2000), ws=ws)
     assert core.sync_status(ws) == 0
     ref = oracle.reduce_set(fs, interp=interp)
-    compare("after timeout", s.mean.cpu().numpy(), ref["mean"],
-            mean_tolerance(ref["mean"]) + 1e-2)
+    got = dict(mean=s.mean.cpu().numpy(), median=s.median.cpu().numpy(),
+               nkept=s.nkept.cpu().numpy())
+    gate_e2e("after timeout", got, ref, sample_tolerance(fs, interp, oracle).max(axis=0), 3.0)
 
 
 def test_plan_launch_and_graph_capture():
@@ -438,13 +431,12 @@ def test_masked_reduction_matches_oracle(interp, offset):
     assert (~ref["valid"]).sum() > (~oracle.reduce_set(fs, interp=interp, want_stack=True)["valid"]).sum()
     tol = sample_tolerance(fs, interp, oracle)
     compare("masked stack", st, np.where(ref["valid"], ref["stack"], np.nan), tol)
-    kept = s.nkept.cpu().numpy().astype(np.int32)
-    m = (ref["margin"] >= 1e-3) & (kept == ref["nkept"])
-    assert m.mean() > 0.99
+    got = dict(mean=s.mean.cpu().numpy(), median=s.median.cpu().numpy(),
+               nkept=s.nkept.cpu().numpy())
     samp = np.max(np.where(ref["valid"], tol, 0.0), axis=0)
-    compare("masked mean", s.mean.cpu().numpy(), ref["mean"], mean_tolerance(ref["mean"]) + samp, m)
-    compare("masked median", s.median.cpu().numpy(), ref["median"],
-            mean_tolerance(ref["median"]) + samp)
+    meas = np.max(np.where(ref["valid"], np.abs(np.where(gvalid, st, 0.0) - ref["stack"]), 0.0),
+                  axis=0)
+    print(gate_e2e("masked", got, ref, samp, 2.5, meas=meas))
 
 
 # ------------------------------------------- overscan cutout (Sec. 2.1 geometry)
@@ -475,9 +467,7 @@ def test_overscan_cutout_roi_of_1074x1024_frames(interp):
     rng = np.random.default_rng(7)
     xs, ys = rng.integers(0, W, 3000), rng.integers(0, H, 3000)
     ref = oracle.reduce_set(fs, interp=interp, pixels=(xs, ys), nthreads=os.cpu_count() or 1)
-    m = ref["margin"] >= 1e-3
     samp = sample_tolerance(fs, interp, oracle).max(axis=0)[ys, xs]
-    compare("cutout mean", s.mean.cpu().numpy()[ys, xs], ref["mean"],
-            mean_tolerance(ref["mean"]) + samp, m)
-    compare("cutout median", s.median.cpu().numpy()[ys, xs], ref["median"],
-            mean_tolerance(ref["median"]) + samp)
+    g = dict(mean=s.mean.cpu().numpy()[ys, xs], median=s.median.cpu().numpy()[ys, xs],
+             nkept=s.nkept.cpu().numpy()[ys, xs])
+    print(gate_e2e("cutout", g, ref, samp, 3.0))

@@ -18,7 +18,7 @@ import torch
 import oracle
 from paper_2008_11486_gb300 import build as irp_build
 from paper_2008_11486_gb300 import core, synth
-from parity_util import compare, mean_tolerance, sample_tolerance
+from parity_util import gate_e2e, sample_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -49,9 +49,6 @@ def test_deep_workload_full_size_sampled():
     gm = s.mean.cpu().numpy()[ys, xs]
     gd = s.median.cpu().numpy()[ys, xs]
     gk = s.nkept.cpu().numpy().astype(np.int32)[ys, xs]
-    # clip decisions agree away from the thresholds; the mean is compared there
-    m = (ref["margin"] >= 1e-3) & (gk == ref["nkept"])
-    assert m.mean() > 0.98
+    # clip decisions agree except within rounding reach of a threshold
     samp = sample_tolerance(fs, "bilinear", oracle, pixels=(xs, ys)).max(axis=0)
-    print(compare("deep mean", gm, ref["mean"], mean_tolerance(ref["mean"]) + samp, m))
-    print(compare("deep median", gd, ref["median"], mean_tolerance(ref["median"]) + samp))
+    print(gate_e2e("deep", dict(mean=gm, median=gd, nkept=gk), ref, samp, 3.0))
