@@ -19,7 +19,8 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libirp.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["api.cu", "k_reduce.cu", "k_spline.cu", "k_unfused.cu", "k_wide.cu"] + [
+SOURCES = ["api.cu", "k_reduce.cu", "k_spline.cu", "k_spline_tile.cu", "k_unfused.cu",
+           "k_wide.cu"] + [
     f"k_reduce_{st}_{r}.cu" for st in ("bilinear", "bsplinev", "bspline", "nearest")
     for r in ("mid", "lo", "hi")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -149,6 +149,8 @@ bool fill_geometry(FrameDesc& F, double dx, double dy, int W, int H, int interp)
     F.wx[i] = ax.w[i];
     F.wy[i] = ay.w[i];
   }
+  F.last_tap = (ax.f > 0.0f || (dx - std::floor(dx)) > 0.0 ? 1 : 0) |
+               (ay.f > 0.0f || (dy - std::floor(dy)) > 0.0 ? 2 : 0);
   return true;
 }
 
@@ -223,6 +225,7 @@ struct Layout {
   size_t flat_off, plan_off, coef_off, total;
   std::vector<size_t> coef_frame_off;  // per set: offset of its first coefficient frame
   std::vector<size_t> crow_frame_off;  // per set: offset of its first row-pass frame
+  std::vector<size_t> bad_frame_off;   // per set: offset of its first bad-pixel bit plane
   std::vector<size_t> stack_off;       // per deep set: its aligned stack (0: caller's)
 };
 
@@ -253,16 +256,19 @@ struct PlanSets {
   std::vector<int> k0;        // per entry: first frame of the chunk in its deep set
   std::vector<DeepSet> deep;
   const irp_set* user;
+  int interp = 0;
   int nsets() const { return (int)sets.size(); }
 };
 
 int64_t deep_stack_pitch(int W) { return (int64_t)align_up((size_t)W, 32); }
 
 int spline_path(int W, int H);
+bool tile_path(const PlanSets& ps, int i);
 
 PlanSets expand_sets(const irp_set* sets, int nsets, int interp) {
   PlanSets ps;
   ps.user = sets;
+  ps.interp = interp;
   for (int i = 0; i < nsets; ++i) {
     const irp_set& s = sets[i];
     if (s.n <= IRP_MAX_FRAMES) {
@@ -316,7 +322,19 @@ PlanSets expand_sets(const irp_set* sets, int nsets, int interp) {
 int spline_path(int W, int H) {
   return (W >= kSplineMinSide && W <= kSplineMaxW && H >= kSplineMinSide) ? 1 : 0;
 }
+
+// A cubic-spline set on the row pass that the tile kernel reduces (not a
+// deep set or one of its chunks).
+bool tile_path(const PlanSets& ps, int i) {
+  return ps.interp == IRP_INTERP_SPLINE3 && ps.deep_of[i] < 0 &&
+         spline_path(ps.sets[i].W, ps.sets[i].H);
+}
 int64_t crow_pitch(int W) { return (int64_t)align_up((size_t)W, 4); }
+// Bad-pixel bits of a masked spline frame: one word per 32 columns and row.
+int64_t bad_pitch(int W) { return (W + 31) / 32; }
+size_t bad_frame_bytes(int W, int H) {
+  return align_up((size_t)H * (size_t)bad_pitch(W) * sizeof(uint32_t), kAlign);
+}
 size_t crow_frame_bytes(int W, int H) {
   return align_up((size_t)H * (size_t)crow_pitch(W) * sizeof(float), kAlign);
 }
@@ -377,13 +395,22 @@ Layout make_layout(const PlanSets& ps, const irp_reduce_params* p,
   L.coef_off = off;
   L.coef_frame_off.assign(nsets, 0);
   L.crow_frame_off.assign(nsets, 0);
+  L.bad_frame_off.assign(nsets, 0);
   if (p->interp == IRP_INTERP_SPLINE3) {
     for (int i = 0; i < nsets; ++i) {
-      L.coef_frame_off[i] = off;
-      off += (size_t)sets[i].n * coef_frame_bytes(sets[i].W, sets[i].H);
-      if (spline_path(sets[i].W, sets[i].H)) {
+      const irp_set& s = sets[i];
+      // sets on the tile kernel need no filtered frames, only the row pass's
+      if (!tile_path(ps, i)) {
+        L.coef_frame_off[i] = off;
+        off += (size_t)s.n * coef_frame_bytes(s.W, s.H);
+      }
+      if (spline_path(s.W, s.H)) {
         L.crow_frame_off[i] = off;
-        off += (size_t)sets[i].n * crow_frame_bytes(sets[i].W, sets[i].H);
+        off += (size_t)s.n * crow_frame_bytes(s.W, s.H);
+        if (tile_path(ps, i) && (s.mask || s.saturation > 0.0f)) {
+          L.bad_frame_off[i] = off;
+          off += (size_t)s.n * bad_frame_bytes(s.W, s.H);
+        }
       }
     }
   }
@@ -406,8 +433,10 @@ irp_status check_params(const irp_set* sets, int nsets, const irp_reduce_params*
   for (int i = 0; i < nsets; ++i) {
     irp_status st = check_set(sets[i]);
     if (st != IRP_OK) return st;
-    // bad-pixel masking is built for the nearest and bilinear stencils
-    if (p->interp == IRP_INTERP_SPLINE3 && (sets[i].mask || sets[i].saturation > 0.0f))
+    // with the cubic spline, bad-pixel masking is built for the sets the tile
+    // kernel reduces (34 <= W <= 2048, H >= 34, at most IRP_MAX_FRAMES frames)
+    if (p->interp == IRP_INTERP_SPLINE3 && (sets[i].mask || sets[i].saturation > 0.0f) &&
+        !(spline_path(sets[i].W, sets[i].H) && sets[i].n <= IRP_MAX_FRAMES))
       return IRP_ERR_UNSUPPORTED;
   }
   std::vector<std::vector<int>> groups;
@@ -522,7 +551,8 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     // arrive horizontally filtered and take the vertical taps only
     const bool spline = stencil == ST_BSPLINE;
     const bool gpath = spline && spline_path(sets[g[0]].W, sets[g[0]].H);
-    const int gstencil = gpath ? ST_BSPLINE_V : stencil;
+    const bool gtile = gpath && tile_path(ps, g[0]);  // the tile kernel (no column pass)
+    const int gstencil = gtile ? ST_BSPLINE_T : (gpath ? ST_BSPLINE_V : stencil);
     const int TWc = tile_cols(gstencil);
     // rows per warp: the caller's choice, else the bucket's default, unless the
     // group's tiles at the default would give fewer than two CTAs per SM; the
@@ -535,7 +565,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
                  ((sets[i].H + tile_rows(bucket, py) - 1) / tile_rows(bucket, py));
       if (tiles < 2 * (int64_t)sm_count()) py = rows_per_warp(bucket, rows_per_warp_alt(bucket));
     }
-    const int THr = tile_rows(bucket, py);
+    const int THr = gtile ? spline_tile_rows(bucket) : tile_rows(bucket, py);
     // prefilter work items: tiles x frame groups, enough groups to fill the GPU twice
     int pgroups = 1;
     if (stencil == ST_BSPLINE) {
@@ -608,9 +638,10 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
       S.crow_pitch = S.spath ? crow_pitch(s.W) : 0;
       S.row0 = nrows;
       S.colseg0 = ncolsegs;
+      S.bad_pitch = bad_pitch(s.W);
       if (S.spath) {
         nrows += ((s.n + kRowGroup - 1) / kRowGroup) * ((s.H + row_block(row_e) - 1) / row_block(row_e));
-        ncolsegs += s.n * ((s.W + 28) / 29) * ((s.H + kColRows - 1) / kColRows);
+        if (!gtile) ncolsegs += s.n * ((s.W + 28) / 29) * ((s.H + kColRows - 1) / kColRows);
       }
       int oxmin = INT32_MAX, oxmax = INT32_MIN, oymin = INT32_MAX, oymax = INT32_MIN;
       for (int k = 0; k < s.n; ++k) {
@@ -628,6 +659,11 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
         F.crow = (stencil == ST_BSPLINE && spline_path(s.W, s.H))
                      ? (float*)(ws + L.crow_frame_off[g[si]] + (size_t)k * crow_frame_bytes(s.W, s.H))
                      : nullptr;
+        F.bad = L.bad_frame_off[g[si]]
+                    ? (const uint32_t*)(ws + L.bad_frame_off[g[si]] +
+                                        (size_t)k * bad_frame_bytes(s.W, s.H))
+                    : nullptr;
+        if (gtile) F.coef = nullptr;
         oxmin = std::min(oxmin, F.ox);
         oxmax = std::max(oxmax, F.ox);
         oymin = std::min(oymin, F.oy);
@@ -673,8 +709,10 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     si.bucket = bucket;
     si.py = py;
     si.stencil = gstencil;
-    si.smem = reduce_smem_bytes(spline ? SRC_F32 : SRC_RAW, gstencil, py, max_n, mw_max, mh_max) -
-              (stack_only ? (size_t)max_n * THr * 32 * sizeof(float) : 0);
+    si.smem = gtile ? spline_tile_smem_bytes(bucket, max_n)
+                    : reduce_smem_bytes(spline ? SRC_F32 : SRC_RAW, gstencil, py, max_n, mw_max,
+                                        mh_max) -
+                          (stack_only ? (size_t)max_n * THr * 32 * sizeof(float) : 0);
     si.nitems = tile0;
     si.counter = gi;
     si.nsets = (int)g.size();
@@ -684,7 +722,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     si.ncolsegs = ncolsegs;
     si.row_e = row_e;
     if (si.smem > 227 * 1024 - 1024) return IRP_ERR_UNSUPPORTED;  // opt-in limit less static smem
-    if (p->persistent) {
+    if (p->persistent && !gtile) {
       const int occ = reduce_occupancy(si.bucket, si.py, gstencil, si.smem);
       int g_ctas = p->max_ctas > 0 ? p->max_ctas : occ * sm_count();
       si.grid = std::max(1, std::min(g_ctas, tile0));
@@ -695,6 +733,100 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     dev_off += align_up(si.bytes, kAlign);
   }
   return IRP_OK;
+}
+
+// Row-pass coefficients kept resident in L2 between the row pass and the
+// tile kernel (L2 holds about 126 MB; the raw frames, masters and outputs
+// stream through beside them).
+constexpr size_t kL2Budget = (size_t)48 << 20;
+
+// A sub-plan of cubic-spline sets reduced by the tile kernel.  Its sets go in
+// order, in runs of consecutive sets whose row-pass coefficients fit within
+// kL2Budget together: the row pass of a run, then the tile kernel of the run,
+// so that the tile kernel reads the coefficients from L2, and then the run's
+// coefficients are dropped from L2 without being written back.  A set larger
+// than the budget goes in stripes of rows: the row pass of a stripe, the
+// tiles whose rows (with the recursions' warm-up rows) are complete, and the
+// coefficient rows no later tile reads dropped.
+irp_status run_tile_subplan(const uint8_t* buf, const SubInfo& si, const InlinePlan* inl,
+                            const void* dev_plan, cudaStream_t s) {
+  const uint8_t* img = buf + si.img_off;
+  const SetDesc* sd = (const SetDesc*)(img + plan_sets_offset());
+  const FrameDesc* fd = (const FrameDesc*)(img + plan_frames_offset(si.nsets));
+  const int RB = row_block(si.row_e);
+  const int TH = spline_tile_rows(si.bucket);
+  auto set_bytes = [&](int j) {  // row-pass frames, then bad-pixel planes, contiguous
+    const SetDesc& S = sd[j];
+    return (size_t)S.n * (crow_frame_bytes(S.W, S.H) +
+                          (fd[S.frame0].bad ? bad_frame_bytes(S.W, S.H) : 0));
+  };
+  cudaError_t e = cudaSuccess;
+  auto rows = [&](int i0, int count) {
+    if (e != cudaSuccess || count <= 0) return;
+    TraceScope tr(IRP_KERNEL_PREFILTER, s);
+    e = launch_spline_rows(si.row_e, inl, dev_plan, i0, count, s);
+  };
+  auto tiles = [&](int i0, int count) {
+    if (e != cudaSuccess || count <= 0) return;
+    TraceScope tr(IRP_KERNEL_REDUCE, s);
+    e = launch_spline_tile(si.bucket, inl, dev_plan, i0, count, si.smem, s, false);
+  };
+  auto discard = [&](const void* p, size_t bytes, int count, size_t stride) {
+    if (e != cudaSuccess || bytes == 0) return;
+    TraceScope tr(IRP_KERNEL_PREFILTER, s);
+    e = launch_discard_l2(p, bytes, count, stride, s);
+  };
+  for (int a = 0; a < si.nsets && e == cudaSuccess;) {
+    size_t bytes = set_bytes(a);
+    int b = a + 1;
+    while (b < si.nsets && bytes + set_bytes(b) <= kL2Budget) bytes += set_bytes(b++);
+    if (b == a + 1 && bytes > kL2Budget) {
+      // one set in stripes of rows
+      const SetDesc& S = sd[a];
+      const int ngroups = (S.n + kRowGroup - 1) / kRowGroup;
+      const int nrb = (S.H + RB - 1) / RB;
+      int oymin = INT32_MAX, oymax = INT32_MIN;
+      for (int k = 0; k < S.n; ++k) {
+        oymin = std::min(oymin, fd[S.frame0 + k].oy);
+        oymax = std::max(oymax, fd[S.frame0 + k].oy);
+      }
+      const size_t row_bytes = (size_t)S.n * (size_t)S.crow_pitch * sizeof(float);
+      int R = (int)std::min<size_t>((size_t)S.H, kL2Budget / 2 / row_bytes);
+      R = std::max(TH, R / TH * TH);
+      int done_rows = 0, done_out = 0, dead = 0;
+      while (done_out < S.H && e == cudaSuccess) {
+        const int target = std::min(S.H, done_rows + R);
+        const int rb0 = done_rows / RB, rb1 = target >= S.H ? nrb : target / RB;
+        rows(S.row0 + rb0 * ngroups, (rb1 - rb0) * ngroups);
+        done_rows = rb1 >= nrb ? S.H : rb1 * RB;
+        // output rows whose taps and warm-up rows are all on hand
+        int out = done_rows >= S.H ? S.H : (done_rows - 3 - 16 - oymax) / TH * TH;
+        out = std::max(out, done_out);
+        if (out > done_out) {
+          const int ty0 = done_out / TH, ty1 = (out + TH - 1) / TH;
+          tiles(S.tile0 + ty0 * S.tiles_x, (ty1 - ty0) * S.tiles_x);
+          done_out = out;
+        }
+        // coefficient rows no later tile reads (the first later tile starts
+        // at done_out and reads from done_out + oymin - 16 on)
+        const int nd = std::min(done_rows, std::max(0, done_out + oymin - 16));
+        if (nd > dead && done_out < S.H) {
+          discard((const uint8_t*)fd[S.frame0].crow + (size_t)dead * S.crow_pitch * 4,
+                  (size_t)(nd - dead) * S.crow_pitch * 4, S.n, crow_frame_bytes(S.W, S.H));
+          dead = nd;
+        }
+      }
+      discard(fd[S.frame0].crow, set_bytes(a), 1, 0);
+    } else {
+      const int r0 = sd[a].row0, r1 = b < si.nsets ? sd[b].row0 : si.nrows;
+      const int t0 = sd[a].tile0, t1 = b < si.nsets ? sd[b].tile0 : si.nitems;
+      rows(r0, r1 - r0);
+      tiles(t0, t1 - t0);
+      for (int j = a; j < b; ++j) discard(fd[sd[j].frame0].crow, set_bytes(j), 1, 0);
+    }
+    a = b;
+  }
+  return cuda_status(e);
 }
 
 // Launches an encoded plan.  ``upload``: copy the sub-plan images into the
@@ -737,10 +869,16 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
     } else {
       std::memset(&inl.h, 0, sizeof(PlanHeader));
     }
+    if (si.stencil == ST_BSPLINE_T) {  // row pass and tile kernel, interleaved
+      const irp_status st = run_tile_subplan(buf, si, &inl, dev_plan, s);
+      if (st != IRP_OK) return st;
+      continue;
+    }
     if (si.pgrid > 0 || si.nrows > 0) {
       TraceScope tr(IRP_KERNEL_PREFILTER, s);
       if (si.pgrid > 0) e = launch_prefilter_raw(&inl, dev_plan, si.pgrid, s);
-      if (e == cudaSuccess && si.nrows > 0) e = launch_spline_rows(si.row_e, &inl, dev_plan, si.nrows, s);
+      if (e == cudaSuccess && si.nrows > 0)
+        e = launch_spline_rows(si.row_e, &inl, dev_plan, 0, si.nrows, s);
       if (e == cudaSuccess && si.ncolsegs > 0) e = launch_spline_cols(&inl, dev_plan, si.ncolsegs, s);
       if (e != cudaSuccess) return note_cuda(e);
     }

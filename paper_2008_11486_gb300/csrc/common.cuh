@@ -20,8 +20,12 @@ constexpr int kMaxInlineSets = 4;
 constexpr int kMaxInlineFrames = 64;
 
 // ST_BSPLINE: 4x4 cubic B-spline on padded coefficient frames; ST_BSPLINE_V:
-// its vertical 4 taps on frames whose rows already carry the horizontal taps.
-enum Stencil : int { ST_NEAREST = 0, ST_BILINEAR = 1, ST_BSPLINE = 2, ST_BSPLINE_V = 3 };
+// its vertical 4 taps on frames whose rows already carry the horizontal taps;
+// ST_BSPLINE_T: column recursion and all 16 taps in the tile kernel, from the
+// row-pass coefficients (k_spline_tile.cu).
+enum Stencil : int {
+  ST_NEAREST = 0, ST_BILINEAR = 1, ST_BSPLINE = 2, ST_BSPLINE_V = 3, ST_BSPLINE_T = 4
+};
 enum Source : int { SRC_RAW = 0, SRC_F32 = 1, SRC_F16 = 2 };
 
 // Cubic-spline prefilter (Sec. 3.2.1's per-line tridiagonal system, solved in
@@ -47,7 +51,10 @@ struct FrameDesc {
   int32_t flags;       // bit 0: raw frame 16-byte aligned with a pitch of 8k elements;
                        // bit 1: 8-byte aligned with a pitch of 4k elements
   float* crow;         // row-pass spline coefficients (workspace) or null
-  int32_t pad[6];
+  const uint32_t* bad; // bad-pixel bits of the frame (masked spline sets, workspace) or null
+  int32_t last_tap;    // bit 0 (1): the last tap along x (y) has non-zero weight, fx > 0
+                       // (fy > 0) in FP64; the FP32 weights may round such a weight to 0
+  int32_t pad[3];
 };
 static_assert(sizeof(FrameDesc) == 128, "FrameDesc layout");
 
@@ -86,8 +93,10 @@ struct SetDesc {
   int32_t masked;                // 1: mask or saturation level in use
   int32_t stack_only;            // 1: write stack_out only (a chunk of a deeper set)
   int32_t pad;
+  int64_t bad_pitch;             // words per row of the bad-pixel bits (masked spline sets)
+  int64_t pad2;
 };
-static_assert(sizeof(SetDesc) == 224, "SetDesc layout");
+static_assert(sizeof(SetDesc) == 240, "SetDesc layout");
 
 struct PlanHeader {
   int32_t nsets, nframes, nitems, stencil;

@@ -2,6 +2,7 @@
 // memory) and the cubic-spline prefilter launch of raw frames.
 #include "prefilter.cuh"
 #include "reduce_kernels.cuh"
+#include "spline.h"
 
 namespace irp {
 
@@ -14,6 +15,7 @@ int reduce_bucket(int n) {
 
 int tile_cols(int stencil) {
   switch (stencil) {
+    case ST_BSPLINE_T: return kSplineTileCols;
     case ST_NEAREST: return StencilShape<ST_NEAREST>::tw;
     case ST_BILINEAR: return StencilShape<ST_BILINEAR>::tw;
     case ST_BSPLINE: return StencilShape<ST_BSPLINE>::tw;

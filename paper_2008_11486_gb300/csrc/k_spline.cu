@@ -63,7 +63,7 @@ __device__ __forceinline__ int find_by(const SetDesc* sets, int nsets, int item,
 
 template <int E>
 __global__ void __launch_bounds__(256, 2)
-    k_spline_rows(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
+    k_spline_rows(const __grid_constant__ InlinePlan inl, const void* plan_dev, int item0) {
   constexpr int RB = row_block(E);   // rows per CTA
   constexpr int MQ = E / 4;          // float4 master chunks per lane and row
   constexpr int RQ = E / 8;          // 16-byte raw chunks per lane and row
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256, 2)
   // (conflict-free for the lane-wise writes and the row-order reads)
   float4* s_out = (float4*)(s_raw + 8 * kRowStages * RQ * 32) + (threadIdx.x >> 5) * 256;
   const PlanView P = make_view(inl, plan_dev);
-  const int item = blockIdx.x;
+  const int item = item0 + (int)blockIdx.x;
   if (item >= P.h->nrows) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const SetDesc& S = P.sets[find_by(P.sets, P.h->nsets, item, 0)];
@@ -89,9 +89,10 @@ __global__ void __launch_bounds__(256, 2)
     if (!s_ok) return;  // status latched
   }
   const int W = S.W, H = S.H;
-  const int nrb = (H + RB - 1) / RB;
+  // row block major, so that a range of row blocks is a range of work items
+  const int ngroups = (S.n + kRowGroup - 1) / kRowGroup;
   const int local = item - S.row0;
-  const int g = local / nrb, rb = local - g * nrb;  // frame chunk, row block
+  const int rb = local / ngroups, g = local - rb * ngroups;  // row block, frame chunk
   const int y0 = rb * RB, nr = min(RB, H - y0);
   const int k0 = g * kRowGroup, nk = min(kRowGroup, S.n - k0);
   const int x0 = lane * E;
@@ -128,13 +129,16 @@ __global__ void __launch_bounds__(256, 2)
   __shared__ float* s_crow[kRowGroup];
   __shared__ float s_t[kRowGroup];
   __shared__ int s_flags[kRowGroup];
+  __shared__ uint32_t* s_bad[kRowGroup];
   if (threadIdx.x < nk) {
     const FrameDesc& F = P.frames[S.frame0 + k0 + threadIdx.x];
     s_src[threadIdx.x] = (const uint16_t*)F.src;
     s_crow[threadIdx.x] = F.crow;
     s_t[threadIdx.x] = F.t;
     s_flags[threadIdx.x] = F.flags;
+    s_bad[threadIdx.x] = const_cast<uint32_t*>(F.bad);
   }
+  const bool masked = S.masked != 0;
   __syncthreads();
   // 2. the warp's tasks: (row, frame) pairs of the block, t = warp + 8 m
   const int ntask = nr * nk;
@@ -226,6 +230,24 @@ __global__ void __launch_bounds__(256, 2)
           const int x = x0 + 4 * i + e;
           v[4 * i + e] = x < W ? calibrate_px(__ldg(raw + x), bb[e], dd[e], tk, rf[e]) : 0.0f;
         }
+      }
+    }
+    if (masked) {
+      // this row's bad pixels (marked by the mask master, or raw at the
+      // saturation level) as bits, 32 columns per word, for the tile kernel
+      const uint8_t* mrow = S.mask ? S.mask + (int64_t)y * S.mask_pitch : nullptr;
+      const uint16_t* rrow = s_src[f] + (int64_t)y * S.src_pitch;
+      uint32_t* brow = s_bad[f] + (int64_t)y * S.bad_pitch;
+#pragma unroll
+      for (int wd = 0; wd < E / 32; ++wd) {
+        uint32_t bits = 0;
+#pragma unroll 1
+        for (int e = 0; e < 32; ++e) {
+          const int x = x0 + 32 * wd + e;
+          if (x < W && ((float)__ldg(rrow + x) >= S.saturation || (mrow && __ldg(mrow + x))))
+            bits |= 1u << e;
+        }
+        if (x0 + 32 * wd < W) brow[(x0 >> 5) + wd] = bits;
       }
     }
     // causal recursion within the lane, as two independent half-lane chains
@@ -489,10 +511,9 @@ __global__ void __launch_bounds__(kColRows, kColRows < 512 ? 512 / kColRows : 1)
   }
 }
 
-cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_dev, int nrows,
-                               cudaStream_t s) {  // nrows: (row block, frame group) work items
+cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_dev, int item0,
+                               int count, cudaStream_t s) {  // (row block, frame group) items
   static bool opted[2] = {false, false};
-  const int grid = nrows;
   const size_t smem = rows_smem_bytes(e);
   cudaError_t err = cudaSuccess;
   if (e == 32) {
@@ -502,7 +523,7 @@ cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_de
       if (err != cudaSuccess) return err;
       opted[0] = true;
     }
-    k_spline_rows<32><<<grid, 256, smem, s>>>(*inl, plan_dev);
+    k_spline_rows<32><<<count, 256, smem, s>>>(*inl, plan_dev, item0);
   } else {
     if (!opted[1]) {
       err = cudaFuncSetAttribute(k_spline_rows<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -510,8 +531,39 @@ cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_de
       if (err != cudaSuccess) return err;
       opted[1] = true;
     }
-    k_spline_rows<64><<<grid, 256, smem, s>>>(*inl, plan_dev);
+    k_spline_rows<64><<<count, 256, smem, s>>>(*inl, plan_dev, item0);
   }
+  return cudaGetLastError();
+}
+
+// One thread per 128-byte line of dead data: discard.global.L2 invalidates
+// the line in L2 without writing it back (the data is never read again).
+// Range i covers lines [first, first + lines) of the 128-byte-aligned base
+// p + i * stride.
+__global__ void k_discard_l2(const char* p, size_t first, size_t lines, int count,
+                             size_t stride) {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  const size_t total = lines * (size_t)count;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = t / lines, l = t - r * lines;
+    const char* a = p + r * stride + (first + l) * 128;
+    asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(a) : "memory");
+  }
+}
+
+cudaError_t launch_discard_l2(const void* p, size_t bytes, int count, size_t stride,
+                              cudaStream_t s) {
+  if (count <= 0 || bytes == 0) return cudaSuccess;
+  // lines wholly inside [p, p + bytes); stride is a multiple of 128 (or unused)
+  const uintptr_t a = (uintptr_t)p, b = a + bytes;
+  const uintptr_t first = (a + 127) / 128, last = b / 128;
+  if (last <= first) return cudaSuccess;
+  const uintptr_t base = (a / 128) * 128;
+  const size_t lines = last - first;
+  const size_t total = lines * (size_t)count;
+  const int grid = (int)std::min<size_t>((total + 255) / 256, 4096);
+  k_discard_l2<<<grid, 256, 0, s>>>((const char*)base, first - a / 128, lines, count, stride);
   return cudaGetLastError();
 }
 

@@ -21,8 +21,25 @@ __host__ __device__ constexpr size_t rows_smem_bytes(int E) {
          (size_t)8 * kRowStages * (E / 8) * 32 * 16 + (E == 32 ? (size_t)8 * 8 * 32 * 16 : 0);
 }
 
-cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_dev, int nrows,
-                               cudaStream_t s);
+// Row pass over the work items [item0, item0 + count) (row block major:
+// item = row0 + rb * frame_groups + g).
+cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_dev, int item0,
+                               int count, cudaStream_t s);
+
+// Tile kernel of sets on the row pass (n <= IRP_MAX_FRAMES): the column
+// recursion, the 16 taps and the combine per output tile of kSplineTileCols
+// columns x spline_tile_rows(bucket) rows, over the tiles [item0, item0 + grid).
+constexpr int kSplineTileCols = 29;  // lane l's horizontal taps reach lane l + 3
+int spline_tile_rows(int bucket);
+size_t spline_tile_smem_bytes(int bucket, int max_n);
+cudaError_t launch_spline_tile(int bucket, const InlinePlan* inl, const void* plan_dev, int item0,
+                               int grid, size_t smem, cudaStream_t s, bool pdl);
+
+// Drops dead intermediate data from L2 without writing it back to HBM
+// (discard.global.L2): `count` ranges of `bytes` at p + i * stride, each
+// shrunk to the 128-byte lines that lie wholly inside it.
+cudaError_t launch_discard_l2(const void* p, size_t bytes, int count, size_t stride,
+                              cudaStream_t s);
 cudaError_t launch_spline_cols(const InlinePlan* inl, const void* plan_dev, int ncolsegs,
                                cudaStream_t s);
 

@@ -413,7 +413,7 @@ def test_frame_stats_f64_wide_rows():
 
 
 # ------------------------------------------------ bad-pixel masking (Sec. 2.1)
-@pytest.mark.parametrize("interp", ["nearest", "bilinear"])
+@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3"])
 @pytest.mark.parametrize("offset", [4.0, 40.0])   # union master window / masters from HBM
 def test_masked_reduction_matches_oracle(interp, offset):
     fs = synth.make_set(101, 77, 14, offset, 1313, n_stars=40, n_cr=10)
@@ -471,3 +471,43 @@ def test_overscan_cutout_roi_of_1074x1024_frames(interp):
     g = dict(mean=s.mean.cpu().numpy()[ys, xs], median=s.median.cpu().numpy()[ys, xs],
              nkept=s.nkept.cpu().numpy()[ys, xs])
     print(gate_e2e("cutout", g, ref, samp, 3.0))
+
+
+def test_spline_tile_stripes_of_a_set_larger_than_the_l2_budget():
+    """A set whose row-pass coefficients exceed the share of L2 the launch
+    sequence keeps them in (12 frames of 2048 x 640: 63 MB) is reduced in
+    stripes of rows; the pixels on both sides of every stripe boundary, and a
+    random sample, match the oracle."""
+    W, H, n = 2048, 640, 12
+    fs = synth.make_set(W, H, n, 10.0, 2048640, n_stars=300, n_cr=20)
+    got = run_fused([fs], "spline3", want_stack=False)[0]
+    rng = np.random.default_rng(64)
+    band = np.arange(200, 320)  # around the first stripe ends (256 rows, less warm-up)
+    band2 = np.arange(440, 580)
+    rows = np.concatenate([band, band2, [0, 1, H - 2, H - 1]])
+    xs = np.concatenate([np.tile(np.arange(0, W, 16), rows.size), rng.integers(0, W, 4000)])
+    ys = np.concatenate([np.repeat(rows, W // 16), rng.integers(0, H, 4000)])
+    ref = oracle.reduce_set(fs, interp="spline3", pixels=(xs, ys), nthreads=os.cpu_count() or 1)
+    g = {k: got[k][ys, xs] for k in ("mean", "median", "nkept")}
+    samp = sample_tolerance(fs, "spline3", oracle, pixels=(xs, ys)).max(axis=0)
+    print(gate_e2e("spline stripes", g, ref, samp, 3.0))
+
+
+def test_masked_spline_edges_and_integer_shifts():
+    """Masked cubic spline at the frame edges (the footprint mirrored there)
+    and with integer offsets, where the fourth tap of an axis has zero weight
+    and the footprint is 3 taps wide: validity bit-exact against the oracle."""
+    fs = synth.make_set(70, 45, 6, 3.0, 4545, n_stars=15, n_cr=5)
+    fs.dx = np.array([0.0, 2.0, -1.0, 0.5, -2.25, 1.75])
+    fs.dy = np.array([0.0, -1.0, 3.0, 0.0, 1.5, -0.5])
+    mask = np.zeros((45, 70), np.uint8)
+    mask[0, 5] = mask[1, 30] = mask[44, 10] = mask[20, 0] = mask[22, 69] = mask[10, 40] = 1
+    mask[30:32, 50:52] = 1
+    s = core.device_set(fs, mask=mask, saturation=30000.0).alloc_outputs(want_stack=True)
+    ws = core.reduce_sets([s], core.reduce_params("spline3", core.clip_params(3.0, 3)))
+    assert core.sync_status(ws) == 0
+    ref = oracle.reduce_set(fs, interp="spline3", mask=mask, saturation=30000.0, want_stack=True)
+    st = s.stack.cpu().numpy()
+    assert np.array_equal(~np.isnan(st), ref["valid"]), "masked spline validity differs"
+    tol = sample_tolerance(fs, "spline3", oracle)
+    compare("masked spline stack", st, np.where(ref["valid"], ref["stack"], np.nan), tol)
