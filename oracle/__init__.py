@@ -26,8 +26,8 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-NEAREST, BILINEAR, SPLINE3 = 0, 1, 2
-INTERP = {"nearest": NEAREST, "bilinear": BILINEAR, "spline3": SPLINE3}
+NEAREST, BILINEAR, SPLINE3, CUBIC = 0, 1, 2, 3
+INTERP = {"nearest": NEAREST, "bilinear": BILINEAR, "spline3": SPLINE3, "cubic": CUBIC}
 
 
 class ClipParams(ctypes.Structure):
@@ -71,6 +71,8 @@ def load(path: str):
     d, i, i64, p = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
     L.oracle_bspline3.restype = d
     L.oracle_bspline3.argtypes = [d]
+    L.oracle_keys.restype = d
+    L.oracle_keys.argtypes = [d]
     L.oracle_mirror.restype = i64
     L.oracle_mirror.argtypes = [i64, i64]
     L.oracle_mean_f32.restype = d
@@ -118,6 +120,11 @@ def _ptr(a: np.ndarray):
 
 def bspline3(t: float) -> float:
     return lib().oracle_bspline3(float(t))
+
+
+def keys(t: float) -> float:
+    """Keys' cubic convolution kernel, a = -1/2."""
+    return lib().oracle_keys(float(t))
 
 
 def mirror(i: int, N: int) -> int:

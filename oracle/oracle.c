@@ -51,6 +51,14 @@ double oracle_bspline3(double t) {
   return 0.0;
 }
 
+double oracle_keys(double t) {
+  const double a = -0.5;
+  double x = fabs(t);
+  if (x <= 1.0) return 1.0 - (a + 3.0) * x * x + (a + 2.0) * x * x * x;
+  if (x < 2.0) return a * (x - 1.0) * (x - 2.0) * (x - 2.0);
+  return 0.0;
+}
+
 int64_t oracle_mirror(int64_t i, int64_t N) {
   if (N <= 1) return 0;
   int64_t period = 2 * (N - 1);
@@ -171,6 +179,13 @@ static int axis_valid_linear(int64_t i0, double fr, int64_t N) {
   return i0 + 1 <= N - 1;
 }
 
+/* Keys' cubic convolution: taps i0-1 .. i0+2 with weights W(fr + 1 - p); for
+ * fr = 0 only the tap at i0 has non-zero weight. */
+static int axis_valid_keys(int64_t i0, double fr, int64_t N) {
+  if (fr == 0.0) return i0 >= 0 && i0 <= N - 1;
+  return i0 - 1 >= 0 && i0 + 2 <= N - 1;
+}
+
 /* Nearest integer to i0 + fr, halves rounded away from zero. */
 static int64_t axis_nearest(int64_t i0, double fr) {
   if (fr < 0.5) return i0;
@@ -189,6 +204,23 @@ static int sample_src(const frame_src* s, int W, int H, int x, int y, double dx,
     if (i < 0 || i > W - 1 || j < 0 || j > H - 1) return 0;
     if (src_bad(s, i, j)) return 0;
     *a = src_value(s, W, i, j);
+    return 1;
+  }
+  if (interp == ORACLE_CUBIC) {
+    /* every tap with non-zero weight inside the frame and not bad */
+    if (!axis_valid_keys(i0, fx, W) || !axis_valid_keys(j0, fy, H)) return 0;
+    double acc = 0.0;
+    for (int q = 0; q < 4; ++q) {
+      double wyq = oracle_keys(fy + 1.0 - q);
+      if (wyq == 0.0) continue; /* zero-weight taps are not read */
+      for (int p = 0; p < 4; ++p) {
+        double wxp = oracle_keys(fx + 1.0 - p);
+        if (wxp == 0.0) continue;
+        if (src_bad(s, i0 - 1 + p, j0 - 1 + q)) return 0;
+        acc += wxp * wyq * src_value(s, W, i0 - 1 + p, j0 - 1 + q);
+      }
+    }
+    *a = acc;
     return 1;
   }
   if (!axis_valid_linear(i0, fx, W) || !axis_valid_linear(j0, fy, H)) return 0;
@@ -367,7 +399,7 @@ int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t fra
                              double* mean, double* median, int32_t* nkept, double* min_margin,
                              double* min_margin_adu, double* stack, uint8_t* valid) {
   if (W < 1 || H < 1 || n < 1 || raw_pitch < W || master_pitch < W) return 1;
-  if (interp < ORACLE_NEAREST || interp > ORACLE_SPLINE3) return 1;
+  if (interp < ORACLE_NEAREST || interp > ORACLE_CUBIC) return 1;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #else

@@ -20,7 +20,7 @@
 extern "C" {
 #endif
 
-enum { ORACLE_NEAREST = 0, ORACLE_BILINEAR = 1, ORACLE_SPLINE3 = 2 };
+enum { ORACLE_NEAREST = 0, ORACLE_BILINEAR = 1, ORACLE_SPLINE3 = 2, ORACLE_CUBIC = 3 };
 
 typedef struct {
   double kappa_lo;   /* reject x if (mu - x) >  kappa_lo * sigma            */
@@ -33,6 +33,13 @@ typedef struct {
 /* Cubic B-spline basis function beta3(t) (Sec. 3.1.1, the basis reproduced
  * exactly by cubic-spline interpolation). */
 double oracle_bspline3(double t);
+
+/* Keys' cubic convolution kernel with a = -1/2 (R. G. Keys, "Cubic
+ * convolution interpolation for digital image processing", IEEE Trans. ASSP
+ * 29, 1981): a cheaper alternative to the cubic spline that interpolates the
+ * data directly, with no prefilter.  W(t) = 1 - (5/2)|t|^2 + (3/2)|t|^3 for
+ * |t| <= 1, -(1/2)(|t| - 1)(|t| - 2)^2 for 1 < |t| < 2, 0 beyond. */
+double oracle_keys(double t);
 
 /* Whole-sample symmetric (mirror) index into [0, N). */
 int64_t oracle_mirror(int64_t i, int64_t N);

@@ -42,6 +42,46 @@ def test_bspline3_partition_of_unity_and_moments():
         assert sum(k * wk for k, wk in zip(range(-6, 7), w)) == pytest.approx(t, abs=1e-13)
 
 
+def test_keys_golden_values():
+    for row in _read_golden("keys_values.txt"):
+        t, num, den = row.split()
+        assert oracle.keys(float(t)) == pytest.approx(int(num) / int(den), abs=1e-15)
+
+
+def test_keys_reproduces_quadratics():
+    # a = -1/2 makes cubic convolution exact on polynomials up to degree 2:
+    # sum_k W(t - k) k^m = t^m for m = 0, 1, 2
+    for t in np.linspace(-3.0, 3.0, 61):
+        w = [oracle.keys(t - k) for k in range(-6, 7)]
+        for m in range(3):
+            assert sum(wk * k ** m for k, wk in zip(range(-6, 7), w)) == \
+                pytest.approx(t ** m, abs=1e-12)
+
+
+def test_keys_shift_of_a_quadratic_image_is_exact():
+    """Cubic convolution shifts a quadratic surface exactly wherever all its
+    taps lie inside the frame; integer offsets are pure pixel moves."""
+    H, W = 20, 24
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    surf = lambda X, Y: 3.0 + 0.5 * X - 0.25 * Y + 0.01 * X * X + 0.02 * X * Y - 0.03 * Y * Y
+    v = surf(xx, yy)
+    for dx, dy in [(0.3, -1.7), (2.25, 0.5), (-0.75, 3.1)]:
+        a, ok = oracle.shift(v, dx, dy, "cubic")
+        want = surf(xx + dx, yy + dy)
+        assert ok.sum() > 0
+        np.testing.assert_allclose(a[ok], want[ok], atol=1e-11)
+        # valid iff the 4 taps of each axis lie inside: i0 - 1 >= 0 and i0 + 2 <= N - 1
+        i0 = xx + np.floor(dx)
+        j0 = yy + np.floor(dy)
+        want_ok = (i0 >= 1) & (i0 <= W - 3) & (j0 >= 1) & (j0 <= H - 3)
+        assert np.array_equal(ok, want_ok)
+    # an integer shift reads only the tap it lands on: a pixel move, valid up
+    # to the frame edge
+    a, ok = oracle.shift(v, 2.0, -3.0, "cubic")
+    assert ok[3:, : W - 2].all() and not ok[:3].any() and not ok[:, W - 2:].any()
+    assert np.array_equal(a[3:, : W - 2], v[: H - 3, 2:])
+
+
 def test_mirror_index():
     assert [oracle.mirror(i, 5) for i in range(-4, 13)] == \
         [4, 3, 2, 1, 0, 1, 2, 3, 4, 3, 2, 1, 0, 1, 2, 3, 4]

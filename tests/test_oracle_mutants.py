@@ -69,6 +69,16 @@ MUTANTS = [
     # bad pixels (Sec. 2.1)
     ("bilinear ignores bad pixels", "        if (src_bad(s, i0 + p, j0 + q)) return 0;\n", ""),
     ("saturation only above the level", ">= s->saturation", "> s->saturation"),
+    # Keys cubic convolution
+    ("keys a = +1/2", "const double a = -0.5;", "const double a = 0.5;"),
+    ("keys inner branch squared term", "return 1.0 - (a + 3.0) * x * x + (a + 2.0) * x * x * x;",
+     "return 1.0 - (a + 2.0) * x * x + (a + 2.0) * x * x * x;"),
+    ("keys outer branch", "if (x < 2.0) return a * (x - 1.0) * (x - 2.0) * (x - 2.0);",
+     "if (x < 2.0) return a * (x - 1.0) * (x - 1.0) * (x - 2.0);"),
+    ("keys taps shifted", "double wxp = oracle_keys(fx + 1.0 - p);",
+     "double wxp = oracle_keys(fx - p);"),
+    ("keys validity ignores the last tap", "return i0 - 1 >= 0 && i0 + 2 <= N - 1;",
+     "return i0 - 1 >= 0 && i0 + 1 <= N - 1;"),
     # sigma clip and median
     ("clip rejects at the threshold", "if (fabs(d) > thr) {", "if (fabs(d) >= thr) {"),
     ("clip ignores ddof", "double sigma = sqrt(ss / (double)(m - p->ddof));",
