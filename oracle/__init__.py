@@ -28,6 +28,7 @@ _lib = None
 
 NEAREST, BILINEAR, SPLINE3, CUBIC = 0, 1, 2, 3
 INTERP = {"nearest": NEAREST, "bilinear": BILINEAR, "spline3": SPLINE3, "cubic": CUBIC}
+FRAME_NORM = {"none": 0, "zero": 1, "scale": 2}
 
 
 class ClipParams(ctypes.Structure):
@@ -102,7 +103,7 @@ def load(path: str):
     L.oracle_reduce_set_masked.argtypes = [p, i64, i64, i, i, i, p, p, p, i64, p, p, p,
                                            i, i, p, i64, d,
                                            ctypes.POINTER(ClipParams), i, i64, p, p,
-                                           p, p, p, p, p, p, p]
+                                           p, p, p, p, p, p, p, i]
     return L
 
 
@@ -230,7 +231,7 @@ def combine_stack(stack, valid, nthreads=1, **kw):
 
 def reduce_set(fs, interp="bilinear", kappa=3.0, max_iter=3, center="mean", ddof=0,
                normalize_flat=False, nthreads=1, pixels=None, want_stack=False,
-               kappa_lo=None, kappa_hi=None, mask=None, saturation=None):
+               kappa_lo=None, kappa_hi=None, mask=None, saturation=None, frame_norm="none"):
     """Whole frame set -> dict(mean, median, nkept, margin, margin_adu[, stack, valid]).
 
     ``mask`` ([H,W] uint8, non-zero = bad) and ``saturation`` (raw ADU) mark
@@ -239,7 +240,9 @@ def reduce_set(fs, interp="bilinear", kappa=3.0, max_iter=3, center="mean", ddof
 
     ``fs`` is a ``synth.FrameSet``-like object (raw [n,H,W] u16, masters [H,W]
     f32, exptime [n], dx/dy [n]).  ``pixels`` = (xs, ys) restricts the output
-    to those pixels (returned as 1-D arrays)."""
+    to those pixels (returned as 1-D arrays).  ``frame_norm`` ("none", "zero",
+    "scale") normalises each frame's samples to frame 0 by the frames' mean
+    calibrated levels before the combine."""
     raw = np.ascontiguousarray(fs.raw, dtype=np.uint16)
     n, H, W = raw.shape
     bias = np.ascontiguousarray(fs.bias, np.float32)
@@ -274,7 +277,10 @@ def reduce_set(fs, interp="bilinear", kappa=3.0, max_iter=3, center="mean", ddof
         ctypes.byref(cp), int(nthreads), int(npix), _ptr(px), _ptr(py),
         _ptr(mean), _ptr(med), _ptr(kept), _ptr(margin), _ptr(margin_adu),
         _ptr(stack) if stack is not None else None,
-        _ptr(valid) if valid is not None else None)
+        _ptr(valid) if valid is not None else None,
+        FRAME_NORM[frame_norm])
+    if rc == 2:
+        raise ValueError("oracle_reduce_set: a frame's mean is 0 or not finite (scale)")
     if rc != 0:
         raise ValueError("oracle_reduce_set rejected its arguments")
     out = dict(mean=mean, median=med, nkept=kept, margin=margin, margin_adu=margin_adu)

@@ -385,7 +385,7 @@ int oracle_reduce_set(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stri
   return oracle_reduce_set_masked(raw, raw_pitch, frame_stride, W, H, n, bias, dark, flat,
                                   master_pitch, exptime, dx, dy, interp, normalize_flat, NULL, 0,
                                   0.0, clip, nthreads, npix, px, py, mean, median, nkept,
-                                  min_margin, min_margin_adu, stack, valid);
+                                  min_margin, min_margin_adu, stack, valid, ORACLE_NORM_NONE);
 }
 
 int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stride,
@@ -397,8 +397,10 @@ int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t fra
                              const oracle_clip_params* clip, int nthreads,
                              int64_t npix, const int32_t* px, const int32_t* py,
                              double* mean, double* median, int32_t* nkept, double* min_margin,
-                             double* min_margin_adu, double* stack, uint8_t* valid) {
+                             double* min_margin_adu, double* stack, uint8_t* valid,
+                             int frame_norm) {
   if (W < 1 || H < 1 || n < 1 || raw_pitch < W || master_pitch < W) return 1;
+  if (frame_norm < ORACLE_NORM_NONE || frame_norm > ORACLE_NORM_SCALE) return 1;
   if (interp < ORACLE_NEAREST || interp > ORACLE_CUBIC) return 1;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -435,6 +437,41 @@ int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t fra
     }
     for (int k = 0; k < n; ++k) src[k].f = coef + (int64_t)k * P;
   }
+  /* per-frame normalisation before the combine: the frame statistic is the
+   * mean of the calibrated frame over all its pixels, the reference frame 0;
+   * zero: x + (m_0 - m_k), scale: x * (m_0 / m_k) */
+  double* nz = (double*)calloc((size_t)n, sizeof(double));
+  double* ns = (double*)malloc(sizeof(double) * (size_t)n);
+  for (int k = 0; k < n; ++k) ns[k] = 1.0;
+  if (frame_norm != ORACLE_NORM_NONE) {
+    double* m = (double*)malloc(sizeof(double) * (size_t)n);
+    double* v = (double*)malloc(sizeof(double) * (size_t)P);
+    for (int k = 0; k < n; ++k) {
+      oracle_calibrate(src[k].raw, raw_pitch, W, H, bias, dark, flat, master_pitch, src[k].t,
+                       flat_norm, v);
+      double sum = 0.0;
+      for (int64_t i = 0; i < P; ++i) sum += v[i];
+      m[k] = sum / (double)P;
+    }
+    int bad = 0;
+    for (int k = 0; k < n; ++k) {
+      if (frame_norm == ORACLE_NORM_ZERO) {
+        nz[k] = m[0] - m[k];
+      } else {
+        if (!(m[k] != 0.0) || !isfinite(m[k])) bad = 1;
+        ns[k] = m[0] / m[k];
+      }
+    }
+    free(v);
+    free(m);
+    if (bad) {
+      free(nz);
+      free(ns);
+      free(coef);
+      free(src);
+      return 2;
+    }
+  }
   int64_t nout = npix > 0 ? npix : P;
 #pragma omp parallel if (nthreads > 1)
   {
@@ -448,6 +485,8 @@ int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t fra
       for (int k = 0; k < n; ++k) {
         double a = 0.0;
         ok[k] = (uint8_t)sample_src(&src[k], W, H, x, y, dx[k], dy[k], interp, &a);
+        if (frame_norm == ORACLE_NORM_ZERO) a += nz[k];
+        if (frame_norm == ORACLE_NORM_SCALE) a *= ns[k];
         s[k] = ok[k] ? a : 0.0;
         if (stack && npix <= 0) stack[(int64_t)k * P + o] = s[k];
         if (valid && npix <= 0) valid[(int64_t)k * P + o] = ok[k];
@@ -468,6 +507,8 @@ int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t fra
     free(tmp);
     free(ok);
   }
+  free(nz);
+  free(ns);
   free(coef);
   free(src);
   return 0;

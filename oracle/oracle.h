@@ -22,6 +22,12 @@ extern "C" {
 
 enum { ORACLE_NEAREST = 0, ORACLE_BILINEAR = 1, ORACLE_SPLINE3 = 2, ORACLE_CUBIC = 3 };
 
+/* Per-frame normalisation before the combine (a combine variant): the
+ * statistic of frame k is m_k, the mean of its calibrated values over the
+ * whole frame, and frame 0 is the reference.  ZERO adds m_0 - m_k to every
+ * sample of frame k, SCALE multiplies it by m_0 / m_k. */
+enum { ORACLE_NORM_NONE = 0, ORACLE_NORM_ZERO = 1, ORACLE_NORM_SCALE = 2 };
+
 typedef struct {
   double kappa_lo;   /* reject x if (mu - x) >  kappa_lo * sigma            */
   double kappa_hi;   /* reject x if (x - mu) >  kappa_hi * sigma            */
@@ -106,7 +112,9 @@ int oracle_reduce_set(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stri
 /* oracle_reduce_set with bad-pixel masking (Sec. 2.1): a source pixel is bad
  * when mask[j*mask_pitch + i] != 0 (mask may be NULL) or its raw value is at
  * least `saturation` (<= 0: off); a sample whose taps with non-zero weight
- * include a bad pixel is invalid and left out of the combine. */
+ * include a bad pixel is invalid and left out of the combine.  frame_norm is
+ * an ORACLE_NORM_* mode; returns 2 when a SCALE statistic is 0 or not
+ * finite. */
 int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t frame_stride,
                              int W, int H, int n,
                              const float* bias, const float* dark, const float* flat,
@@ -116,7 +124,8 @@ int oracle_reduce_set_masked(const uint16_t* raw, int64_t raw_pitch, int64_t fra
                              const oracle_clip_params* clip, int nthreads,
                              int64_t npix, const int32_t* px, const int32_t* py,
                              double* mean, double* median, int32_t* nkept, double* min_margin,
-                             double* min_margin_adu, double* stack, uint8_t* valid);
+                             double* min_margin_adu, double* stack, uint8_t* valid,
+                             int frame_norm);
 
 #ifdef __cplusplus
 }

@@ -548,3 +548,56 @@ def test_masked_sample_leaves_the_combine():
     assert out["mean"][2, 3] == 1500.0
     assert out["nkept"][0, 0] == 3
     assert out["median"][0, 0] == 2000.0
+
+
+
+# ---------------------------------------------------- per-frame normalisation
+def _frames(vals, W=2, H=2):
+    """A set of frames with the given raw values, zero bias and dark, unit
+    flat and no offsets (calibrated value = raw)."""
+    raw = np.asarray(vals, np.uint16).reshape(len(vals), H, W)
+    n = raw.shape[0]
+    return synth.FrameSet(raw=raw, bias=np.zeros((H, W), np.float32),
+                          dark=np.zeros((H, W), np.float32), flat=np.ones((H, W), np.float32),
+                          exptime=np.full(n, 60.0, np.float32), dx=np.zeros(n), dy=np.zeros(n))
+
+
+def test_frame_normalisation_worked_by_hand():
+    # frame 0 = [[1, 2], [3, 4]] (mean 2.5), frame 1 = [[3, 4], [5, 6]] (mean 4.5)
+    fs = _frames([[1, 2, 3, 4], [3, 4, 5, 6]])
+    # zero: frame 1 gets 2.5 - 4.5 = -2 and equals frame 0; the mean is frame 0
+    r = oracle.reduce_set(fs, frame_norm="zero")
+    np.testing.assert_allclose(r["mean"], [[1, 2], [3, 4]], atol=1e-14)
+    np.testing.assert_allclose(r["median"], [[1, 2], [3, 4]], atol=1e-14)
+    # scale: frame 1 times 2.5 / 4.5 = 5/9: [[5/3, 20/9], [25/9, 30/9]];
+    # two samples, nothing clipped: the mean of frame 0 and that
+    r = oracle.reduce_set(fs, frame_norm="scale")
+    want = (np.array([[1, 2], [3, 4]]) + np.array([[15, 20], [25, 30]]) / 9.0) / 2.0
+    np.testing.assert_allclose(r["mean"], want, atol=1e-14)
+    # none leaves the samples alone
+    r = oracle.reduce_set(fs, frame_norm="none")
+    np.testing.assert_allclose(r["mean"], [[2, 3], [4, 5]], atol=1e-14)
+
+
+def test_frame_normalisation_levels_frames_of_different_levels():
+    """Frames that differ only by a level (zero) or a gain (scale) become
+    identical to frame 0, whatever the interpolation."""
+    rng = np.random.default_rng(3)
+    base = rng.integers(200, 2000, (6, 9)).astype(np.float64)
+    for interp in ("bilinear", "nearest", "cubic", "spline3"):
+        fs = _frames([base + d for d in (0, 150, -120, 400)], W=9, H=6)
+        r = oracle.reduce_set(fs, interp=interp, frame_norm="zero", want_stack=True)
+        np.testing.assert_allclose(r["stack"], np.broadcast_to(r["stack"][0], r["stack"].shape),
+                                   atol=1e-9)
+    fs = _frames([base * g for g in (1, 2, 4)], W=9, H=6)
+    r = oracle.reduce_set(fs, frame_norm="scale", want_stack=True)
+    np.testing.assert_allclose(r["stack"], np.broadcast_to(r["stack"][0], r["stack"].shape),
+                               rtol=1e-14)
+    np.testing.assert_allclose(r["mean"], base, rtol=1e-14)
+
+
+def test_frame_normalisation_rejects_a_zero_frame_mean_for_scale():
+    fs = _frames([[1, 2, 3, 4], [0, 0, 0, 0]])
+    with pytest.raises(ValueError):
+        oracle.reduce_set(fs, frame_norm="scale")
+    oracle.reduce_set(fs, frame_norm="zero")  # an additive level needs no division

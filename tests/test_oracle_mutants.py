@@ -79,6 +79,11 @@ MUTANTS = [
      "double wxp = oracle_keys(fx - p);"),
     ("keys validity ignores the last tap", "return i0 - 1 >= 0 && i0 + 2 <= N - 1;",
      "return i0 - 1 >= 0 && i0 + 1 <= N - 1;"),
+    # per-frame normalisation
+    ("normalisation zero sign", "nz[k] = m[0] - m[k];", "nz[k] = m[k] - m[0];"),
+    ("normalisation scale inverted", "ns[k] = m[0] / m[k];", "ns[k] = m[k] / m[0];"),
+    ("normalisation statistic not divided by the pixel count", "m[k] = sum / (double)P;",
+     "m[k] = sum;"),
     # sigma clip and median
     ("clip rejects at the threshold", "if (fabs(d) > thr) {", "if (fabs(d) >= thr) {"),
     ("clip ignores ddof", "double sigma = sqrt(ss / (double)(m - p->ddof));",
