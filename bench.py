@@ -841,8 +841,8 @@ def run_served(args, cfg, dev, world, rank, local):
         del d
     torch.cuda.empty_cache()
     rng = np.random.Generator(np.random.PCG64(cfg["seed"]))
-    srv = serve.Server(masters, depth=depth, max_inflight=2, interp=cfg["interp"], device=dev,
-                       download=True)
+    srv = serve.Server(masters, depth=depth, max_inflight=4, max_batch=2, interp=cfg["interp"],
+                       device=dev, download=True)
 
     def make_requests(count, base):
         return [serve.Request(rid=base + r, frames=[host_frames[c][(base + r) % nvar]

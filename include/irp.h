@@ -22,7 +22,7 @@
  *   - Offsets: output pixel (x, y) samples frame k at (x + dx[k], y + dy[k]).
  *     The offset is split as dx = ix + fx, ix = floor(dx), fx in [0, 1).
  *   - A sample is valid iff every tap with non-zero weight lies inside the
- *     frame (nearest, bilinear) or the source position lies inside
+ *     frame (nearest, bilinear, cubic convolution) or the source position lies inside
  *     [0, W-1] x [0, H-1] (cubic spline).  Invalid samples do not enter the
  *     combination; a pixel with no valid sample gets NaN (mean, median).
  *   - The cubic spline is the interpolating cubic B-spline with mirror
@@ -71,10 +71,18 @@ typedef enum {
   IRP_ERR_UNSUPPORTED = 4,   /* a valid request the library does not implement */
   IRP_ERR_BAD_MASTER = 5,    /* device: flat value <= 0 or not finite */
   IRP_ERR_CUDA = 6,          /* a CUDA runtime call failed */
-  IRP_ERR_TIMEOUT = 7        /* device: a bounded wait gave up */
+  IRP_ERR_TIMEOUT = 7,       /* device: a bounded wait gave up */
+  IRP_ERR_BAD_STATISTIC = 8  /* device: a frame's mean level is 0 or not finite (scale
+                                normalisation) */
 } irp_status;
 
-typedef enum { IRP_INTERP_NEAREST = 0, IRP_INTERP_BILINEAR = 1, IRP_INTERP_SPLINE3 = 2 } irp_interp;
+/* IRP_INTERP_CUBIC: Keys' cubic convolution (a = -1/2), 4 x 4 taps on the
+ * calibrated data with no prefilter; a cheaper alternative to the cubic
+ * spline (Keys, IEEE Trans. ASSP 29, 1981).  Its samples are valid when every
+ * tap with non-zero weight lies inside the frame, as for bilinear. */
+typedef enum {
+  IRP_INTERP_NEAREST = 0, IRP_INTERP_BILINEAR = 1, IRP_INTERP_SPLINE3 = 2, IRP_INTERP_CUBIC = 3
+} irp_interp;
 
 /* Element type of an intermediate (calibrated or aligned) stack.
  * IRP_F16_SCALED: value = (float)h * scale[k] + offset[k], h an IEEE half. */
@@ -214,6 +222,16 @@ typedef struct {
                                      of a group would give fewer than two CTAs per
                                      SM; the other accepted value is 2 (resp. 1);
                                      anything else falls back to the default */
+  int frame_norm;                 /* per-frame normalisation before the combine (a
+                                     combine variant; the paper has none): 0 none;
+                                     1 zero: each sample of frame k gets m_0 - m_k
+                                     added; 2 scale: it is multiplied by m_0 / m_k;
+                                     m_k = the FP64 mean of frame k's calibrated
+                                     values over the whole frame, frame 0 the set's
+                                     first.  The means take one more read of the raw
+                                     frames.  With scale, a mean of 0 or not finite
+                                     latches IRP_ERR_BAD_STATISTIC.  stack_out holds
+                                     the normalised samples. */
 } irp_reduce_params;
 
 size_t irp_workspace_size(const irp_set* sets, int nsets, const irp_reduce_params* p);

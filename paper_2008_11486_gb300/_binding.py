@@ -16,8 +16,9 @@ LIB_PATH = os.path.join(HERE, "_lib", "libirp.so")
 IRP_OK = 0
 STATUS_NAMES = {0: "IRP_OK", 1: "IRP_ERR_INVALID_ARG", 2: "IRP_ERR_ALIGNMENT",
                 3: "IRP_ERR_WORKSPACE", 4: "IRP_ERR_UNSUPPORTED", 5: "IRP_ERR_BAD_MASTER",
-                6: "IRP_ERR_CUDA", 7: "IRP_ERR_TIMEOUT"}
-INTERP = {"nearest": 0, "bilinear": 1, "spline3": 2}
+                6: "IRP_ERR_CUDA", 7: "IRP_ERR_TIMEOUT", 8: "IRP_ERR_BAD_STATISTIC"}
+INTERP = {"nearest": 0, "bilinear": 1, "spline3": 2, "cubic": 3}
+FRAME_NORM = {"none": 0, "zero": 1, "scale": 2}
 DTYPE = {"f32": 0, "f16": 1}
 MAX_FRAMES = 64
 KERNEL_KINDS = ("reduce", "prefilter", "stats", "calibrate", "shift", "combine")
@@ -58,7 +59,7 @@ class IrpHostIo(ctypes.Structure):
 class ReduceParams(ctypes.Structure):
     _fields_ = [("interp", c_i), ("clip", ClipParams), ("normalize_flat", c_i),
                 ("persistent", c_i), ("max_ctas", c_i), ("wait_spin_limit", c_i),
-                ("rows_per_warp", c_i)]
+                ("rows_per_warp", c_i), ("frame_norm", c_i)]
 
 
 _lock = threading.Lock()

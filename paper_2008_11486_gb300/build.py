@@ -21,7 +21,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 
 SOURCES = ["api.cu", "k_reduce.cu", "k_spline.cu", "k_spline_tile.cu", "k_unfused.cu",
            "k_wide.cu"] + [
-    f"k_reduce_{st}_{r}.cu" for st in ("bilinear", "bsplinev", "bspline", "nearest")
+    f"k_reduce_{st}_{r}.cu" for st in ("bilinear", "bsplinev", "bspline", "nearest", "cubic")
     for r in ("mid", "lo", "hi")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

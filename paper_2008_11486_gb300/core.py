@@ -12,7 +12,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from ._binding import (DTYPE, INTERP, KERNEL_KINDS, ClipParams, IrpHostIo, IrpSet, ReduceParams,
+from ._binding import (DTYPE, FRAME_NORM, INTERP, KERNEL_KINDS, ClipParams, IrpHostIo, IrpSet, ReduceParams,
                        check, lib)
 
 
@@ -219,10 +219,13 @@ def _irp_sets(sets):
 
 
 def reduce_params(interp="bilinear", clip=None, normalize_flat=False, persistent=False,
-                  max_ctas=0, wait_spin_limit=0, rows_per_warp=0) -> ReduceParams:
+                  max_ctas=0, wait_spin_limit=0, rows_per_warp=0,
+                  frame_norm="none") -> ReduceParams:
+    """``frame_norm``: "none", "zero" or "scale" per-frame normalisation of the
+    samples to the set's first frame before the combine."""
     return ReduceParams(INTERP[interp], clip if clip is not None else clip_params(),
                         int(normalize_flat), int(persistent), int(max_ctas), int(wait_spin_limit),
-                        int(rows_per_warp))
+                        int(rows_per_warp), FRAME_NORM[frame_norm])
 
 
 def workspace_size(sets, params: ReduceParams) -> int:

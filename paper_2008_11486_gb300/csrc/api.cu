@@ -114,6 +114,22 @@ bool split_axis(double d, int N, int interp, Axis& a) {
     a.w[0] = 1.0f;
     return true;
   }
+  if (interp == IRP_INTERP_CUBIC) {
+    // Keys' cubic convolution, a = -1/2: taps i0 - 1 .. i0 + 2 with weights
+    // W(f + 1 - i); all four are non-zero for f > 0, only the one at i0 for
+    // f = 0, and those must lie inside the frame
+    a.o = ifl - 1;
+    a.v0 = f > 0.0 ? 1 - ifl : -ifl;
+    a.v1 = f > 0.0 ? N - 3 - ifl : N - 1 - ifl;
+    for (int i = 0; i < 4; ++i) {
+      const double t = std::fabs(f + 1.0 - i);
+      double w = 0.0;
+      if (t <= 1.0) w = 1.0 - 2.5 * t * t + 1.5 * t * t * t;
+      else if (t < 2.0) w = -0.5 * (t - 1.0) * (t - 2.0) * (t - 2.0);
+      a.w[i] = (float)w;
+    }
+    return true;
+  }
   // taps with non-zero weight must lie inside: i0 >= 0, i0 + (f > 0) <= N - 1
   a.v0 = -ifl;
   a.v1 = N - 1 - ifl - (f > 0.0 ? 1 : 0);
@@ -155,7 +171,12 @@ bool fill_geometry(FrameDesc& F, double dx, double dy, int W, int H, int interp)
 }
 
 int stencil_of(irp_interp i) {
-  return i == IRP_INTERP_NEAREST ? ST_NEAREST : (i == IRP_INTERP_BILINEAR ? ST_BILINEAR : ST_BSPLINE);
+  switch (i) {
+    case IRP_INTERP_NEAREST: return ST_NEAREST;
+    case IRP_INTERP_BILINEAR: return ST_BILINEAR;
+    case IRP_INTERP_CUBIC: return ST_CUBIC;
+    default: return ST_BSPLINE;
+  }
 }
 
 bool clip_ok(const irp_clip_params& c) {
@@ -203,6 +224,7 @@ struct SubInfo {
   int32_t bucket, stencil, grid, pgrid;
   int32_t nitems, counter, nsets, nframes;
   int32_t nrows, ncolsegs, row_e, py;   // spline row / column passes, rows per warp
+  int32_t norm_rb, pad;                 // frame means: most row blocks of a set (0: none)
 };
 
 struct PlanFile {
@@ -212,6 +234,8 @@ struct PlanFile {
   uint64_t ws_required;
   uint64_t flat_off;    // FrameStats[nflat] in the workspace
   uint64_t deep_off;    // CombineArgs[ndeep] in the plan file: the deep sets' combines
+  uint64_t norm_off;    // FrameNorm records in the workspace (zeroed per call) ...
+  uint64_t norm_bytes;  // ... and their size (0: no per-frame normalisation)
   SubInfo sub[kMaxSub];
 };
 
@@ -226,6 +250,8 @@ struct Layout {
   std::vector<size_t> coef_frame_off;  // per set: offset of its first coefficient frame
   std::vector<size_t> crow_frame_off;  // per set: offset of its first row-pass frame
   std::vector<size_t> bad_frame_off;   // per set: offset of its first bad-pixel bit plane
+  size_t norm_off = 0, norm_bytes = 0;
+  std::vector<size_t> norm_user_off;   // per caller's set: its frames' FrameNorm records
   std::vector<size_t> stack_off;       // per deep set: its aligned stack (0: caller's)
 };
 
@@ -254,6 +280,7 @@ struct PlanSets {
   std::vector<irp_set> sets;  // plain sets and the chunks of deep sets, in call order
   std::vector<int> deep_of;   // per entry: its deep set, or -1
   std::vector<int> k0;        // per entry: first frame of the chunk in its deep set
+  std::vector<int> user_of;   // per entry: index of its set in the caller's array
   std::vector<DeepSet> deep;
   const irp_set* user;
   int interp = 0;
@@ -273,6 +300,7 @@ PlanSets expand_sets(const irp_set* sets, int nsets, int interp) {
     const irp_set& s = sets[i];
     if (s.n <= IRP_MAX_FRAMES) {
       ps.sets.push_back(s);
+      ps.user_of.push_back(i);
       ps.deep_of.push_back(-1);
       ps.k0.push_back(0);
       continue;
@@ -288,6 +316,7 @@ PlanSets expand_sets(const irp_set* sets, int nsets, int interp) {
       cs.median_out = nullptr;
       cs.nkept_out = nullptr;
       ps.sets.push_back(cs);
+      ps.user_of.push_back(i);
       ps.deep_of.push_back((int)ps.deep.size());
       ps.k0.push_back(0);
       ps.deep.push_back(d);
@@ -310,6 +339,7 @@ PlanSets expand_sets(const irp_set* sets, int nsets, int interp) {
       cs.stack_out = nullptr;  // placed in the stack by encode_plan
       cs.out_pitch = d.spitch;
       ps.sets.push_back(cs);
+      ps.user_of.push_back(i);
       ps.deep_of.push_back((int)ps.deep.size());
       ps.k0.push_back(a);
     }
@@ -386,6 +416,21 @@ Layout make_layout(const PlanSets& ps, const irp_reduce_params* p,
   size_t off = sizeof(WsHeader);
   L.flat_off = off;
   off += align_up((size_t)nsets * sizeof(FrameStats), kAlign);
+  // per-frame normalisation records, contiguous per caller's set (the chunks
+  // of a deep set share its set's records, frame 0 first)
+  L.norm_off = off;
+  L.norm_user_off.clear();
+  if (p->frame_norm) {
+    int nuser = 0;
+    for (int i = 0; i < nsets; ++i) nuser = std::max(nuser, ps.user_of[i] + 1);
+    L.norm_user_off.assign(nuser, 0);
+    for (int u = 0; u < nuser; ++u) {
+      L.norm_user_off[u] = off;
+      off += (size_t)ps.user[u].n * sizeof(FrameNorm);
+    }
+    off = align_up(off, kAlign);
+  }
+  L.norm_bytes = off - L.norm_off;
   L.plan_off = off;
   for (const auto& g : groups) {
     int nf = 0;
@@ -427,9 +472,10 @@ Layout make_layout(const PlanSets& ps, const irp_reduce_params* p,
 
 irp_status check_params(const irp_set* sets, int nsets, const irp_reduce_params* p) {
   if (!sets || !p || nsets < 1) return IRP_ERR_INVALID_ARG;
-  if (p->interp < IRP_INTERP_NEAREST || p->interp > IRP_INTERP_SPLINE3) return IRP_ERR_INVALID_ARG;
+  if (p->interp < IRP_INTERP_NEAREST || p->interp > IRP_INTERP_CUBIC) return IRP_ERR_INVALID_ARG;
   if (!clip_ok(p->clip)) return IRP_ERR_INVALID_ARG;
   if (p->max_ctas < 0 || p->wait_spin_limit < 0 || p->rows_per_warp < 0) return IRP_ERR_INVALID_ARG;
+  if (p->frame_norm < 0 || p->frame_norm > 2) return IRP_ERR_INVALID_ARG;
   for (int i = 0; i < nsets; ++i) {
     irp_status st = check_set(sets[i]);
     if (st != IRP_OK) return st;
@@ -505,6 +551,8 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
   pf->nsets = nsets;
   pf->ndeep = (int)ps.deep.size();
   pf->deep_off = deep_jobs_offset(nsets);
+  pf->norm_off = L.norm_off;
+  pf->norm_bytes = L.norm_bytes;
   // the deep sets' stacks and their lane-group combines
   std::vector<float*> stack_base(ps.deep.size());
   CombineArgs* dj = (CombineArgs*)(buf + pf->deep_off);
@@ -524,6 +572,9 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     a.median_out = u.median_out;
     a.nkept_out = u.nkept_out;
     a.out_pitch = u.out_pitch;
+    // samples formed from filtered rows in the combine take the frames'
+    // normalisation there; a stack already holds normalised samples
+    a.frame_norm = (ps.deep[d].rows && p->frame_norm) ? 1 : 0;
   }
   FlatJob* fj = (FlatJob*)(buf + sizeof(PlanFile));
   for (int i = 0; i < nsets; ++i) {
@@ -533,7 +584,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     fj[i].H = sets[i].H;
   }
   const int stencil = stencil_of(p->interp);
-  const int taps = stencil == ST_BSPLINE ? 4 : (stencil == ST_BILINEAR ? 2 : 1);
+  const int taps = (stencil == ST_BSPLINE || stencil == ST_CUBIC) ? 4 : (stencil == ST_BILINEAR ? 2 : 1);
   WsHeader* wsh = (WsHeader*)ws;
   size_t img_off = plan_images_offset(ps);
   size_t dev_off = L.plan_off;
@@ -578,7 +629,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     PlanHeader* h = (PlanHeader*)img;
     SetDesc* sd = (SetDesc*)(img + plan_sets_offset());
     FrameDesc* fd = (FrameDesc*)(img + plan_frames_offset((int)g.size()));
-    int frame0 = 0, tile0 = 0, ptile0 = 0, nrows = 0, ncolsegs = 0, row_e = 32;
+    int frame0 = 0, tile0 = 0, ptile0 = 0, nrows = 0, ncolsegs = 0, row_e = 32, norm_rb = 0;
     for (int si : g)  // row-pass width: 32 columns per lane, 64 when a frame is wider than 1024
       if (stencil == ST_BSPLINE && spline_path(sets[si].W, sets[si].H) && sets[si].W > 1024)
         row_e = 64;
@@ -639,6 +690,12 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
       S.row0 = nrows;
       S.colseg0 = ncolsegs;
       S.bad_pitch = bad_pitch(s.W);
+      const int user = ps.user_of[g[si]];
+      S.norm_ref = p->frame_norm ? (const FrameNorm*)(ws + L.norm_user_off[user]) : nullptr;
+      if (p->frame_norm) {
+        const int R = stats_rows(s.W, s.H);
+        norm_rb = std::max(norm_rb, (s.H + R - 1) / R);
+      }
       if (S.spath) {
         nrows += ((s.n + kRowGroup - 1) / kRowGroup) * ((s.H + row_block(row_e) - 1) / row_block(row_e));
         if (!gtile) ncolsegs += s.n * ((s.W + 28) / 29) * ((s.H + kColRows - 1) / kColRows);
@@ -664,6 +721,8 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
                                         (size_t)k * bad_frame_bytes(s.W, s.H))
                     : nullptr;
         if (gtile) F.coef = nullptr;
+        F.norm = p->frame_norm ? (FrameNorm*)(ws + L.norm_user_off[user]) + ps.k0[g[si]] + k
+                               : nullptr;
         oxmin = std::min(oxmin, F.ox);
         oxmax = std::max(oxmax, F.ox);
         oymin = std::min(oymin, F.oy);
@@ -698,6 +757,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     h->max_iter = p->clip.max_iter;
     h->center = p->clip.center;
     h->ddof = p->clip.ddof;
+    h->frame_norm = p->frame_norm;
     h->smem_samples = stack_only ? 0 : max_n * THr * 32;
     h->smem_master = mw_max * mh_max;  // float4 entries
     h->status = &wsh->status;
@@ -721,6 +781,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     si.nrows = nrows;
     si.ncolsegs = ncolsegs;
     si.row_e = row_e;
+    si.norm_rb = norm_rb;
     if (si.smem > 227 * 1024 - 1024) return IRP_ERR_UNSUPPORTED;  // opt-in limit less static smem
     if (p->persistent && !gtile) {
       const int occ = reduce_occupancy(si.bucket, si.py, gstencil, si.smem);
@@ -855,6 +916,10 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
                               nullptr, nullptr, nullptr, nullptr, st + i, s);
     if (e != cudaSuccess) return note_cuda(e);
   }
+  if (pf->norm_bytes > 0) {  // per-frame normalisation: the sums start at zero
+    e = cudaMemsetAsync(ws + pf->norm_off, 0, pf->norm_bytes, s);
+    if (e != cudaSuccess) return note_cuda(e);
+  }
   for (int i = 0; i < pf->nsub; ++i) {
     const SubInfo& si = pf->sub[i];
     const void* dev_plan = upload ? (const void*)(ws + si.dev_off) : nullptr;
@@ -868,6 +933,11 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
       std::memcpy(inl.frames, img + plan_frames_offset(si.nsets), (size_t)si.nframes * sizeof(FrameDesc));
     } else {
       std::memset(&inl.h, 0, sizeof(PlanHeader));
+    }
+    if (si.norm_rb > 0) {  // the frames' mean levels, then their normalisation factors
+      TraceScope tr(IRP_KERNEL_STATS, s);
+      e = launch_frame_norm(&inl, dev_plan, si.nframes, si.norm_rb, s);
+      if (e != cudaSuccess) return note_cuda(e);
     }
     if (si.stencil == ST_BSPLINE_T) {  // row pass and tile kernel, interleaved
       const irp_status st = run_tile_subplan(buf, si, &inl, dev_plan, s);
@@ -964,6 +1034,7 @@ const char* irp_status_string(irp_status s) {
     case IRP_ERR_BAD_MASTER: return "flat master value not finite or not positive";
     case IRP_ERR_CUDA: return "CUDA runtime error";
     case IRP_ERR_TIMEOUT: return "bounded device wait timed out";
+    case IRP_ERR_BAD_STATISTIC: return "a frame's mean level is zero or not finite";
   }
   return "unknown status";
 }
@@ -1247,7 +1318,7 @@ irp_status irp_shift(const void* in, int64_t in_pitch, int64_t in_frame_stride, 
   if (n > 1 && (in_frame_stride < in_pitch * H || out_frame_stride < out_pitch * H))
     return IRP_ERR_INVALID_ARG;
   if (dt != IRP_F32 && dt != IRP_F16_SCALED) return IRP_ERR_INVALID_ARG;
-  if (interp < IRP_INTERP_NEAREST || interp > IRP_INTERP_SPLINE3) return IRP_ERR_INVALID_ARG;
+  if (interp < IRP_INTERP_NEAREST || interp > IRP_INTERP_CUBIC) return IRP_ERR_INVALID_ARG;
   const size_t es = dt == IRP_F32 ? 4 : 2;
   if (!aligned(in, es) || !aligned(out, es)) return IRP_ERR_ALIGNMENT;
   if (in == out) return IRP_ERR_INVALID_ARG;

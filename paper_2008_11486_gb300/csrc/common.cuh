@@ -23,8 +23,10 @@ constexpr int kMaxInlineFrames = 64;
 // its vertical 4 taps on frames whose rows already carry the horizontal taps;
 // ST_BSPLINE_T: column recursion and all 16 taps in the tile kernel, from the
 // row-pass coefficients (k_spline_tile.cu).
+// ST_CUBIC: Keys' cubic convolution, 4x4 taps on the calibrated raw frame.
 enum Stencil : int {
-  ST_NEAREST = 0, ST_BILINEAR = 1, ST_BSPLINE = 2, ST_BSPLINE_V = 3, ST_BSPLINE_T = 4
+  ST_NEAREST = 0, ST_BILINEAR = 1, ST_BSPLINE = 2, ST_BSPLINE_V = 3, ST_BSPLINE_T = 4,
+  ST_CUBIC = 5
 };
 enum Source : int { SRC_RAW = 0, SRC_F32 = 1, SRC_F16 = 2 };
 
@@ -35,6 +37,16 @@ constexpr float kZ1 = -0.26794919243112270f;
 constexpr float kSqrt3 = 1.7320508075688772f;
 constexpr int kPrefHalo = 16;  // recursion warm-up; |z1|^17 / (1 - |z1|) < 3e-10
 constexpr int kPrefTile = 64;  // prefilter output tile (square)
+
+// Per-frame normalisation before the combine (workspace, 16 bytes): the FP64
+// sum of the calibrated frame, and the factors every sample of the frame gets,
+// x' = fma(x, na, nz): (1, m_0 - m_k) for a zero offset, (m_0 / m_k, 0) for a
+// scale, m_k the frame's mean calibrated value and m_0 that of the set's
+// first frame.
+struct FrameNorm {
+  double sum;
+  float na, nz;
+};
 
 // One frame of a set, as the kernels see it (128 bytes).
 struct FrameDesc {
@@ -54,7 +66,8 @@ struct FrameDesc {
   const uint32_t* bad; // bad-pixel bits of the frame (masked spline sets, workspace) or null
   int32_t last_tap;    // bit 0 (1): the last tap along x (y) has non-zero weight, fx > 0
                        // (fy > 0) in FP64; the FP32 weights may round such a weight to 0
-  int32_t pad[3];
+  int32_t pad1;
+  struct FrameNorm* norm;  // per-frame normalisation record (workspace) or null
 };
 static_assert(sizeof(FrameDesc) == 128, "FrameDesc layout");
 
@@ -94,7 +107,7 @@ struct SetDesc {
   int32_t stack_only;            // 1: write stack_out only (a chunk of a deeper set)
   int32_t pad;
   int64_t bad_pitch;             // words per row of the bad-pixel bits (masked spline sets)
-  int64_t pad2;
+  const FrameNorm* norm_ref;     // normalisation record of the set's first frame, or null
 };
 static_assert(sizeof(SetDesc) == 240, "SetDesc layout");
 
@@ -107,7 +120,8 @@ struct PlanHeader {
   int32_t smem_master;           // float4 entries reserved per CTA for master windows
   int32_t npitems;               // tiled prefilter work items (spline)
   int32_t nrows, ncolsegs;       // row-pass and column-pass work items (spline)
-  int32_t pad[2];
+  int32_t frame_norm;            // per-frame normalisation: 0 none, 1 zero, 2 scale
+  int32_t pad;
   uint32_t* status;              // device status word (workspace)
   uint32_t* counter;             // persistent work counter (workspace)
 };

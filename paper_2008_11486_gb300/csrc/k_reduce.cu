@@ -16,6 +16,7 @@ int reduce_bucket(int n) {
 int tile_cols(int stencil) {
   switch (stencil) {
     case ST_BSPLINE_T: return kSplineTileCols;
+    case ST_CUBIC: return StencilShape<ST_CUBIC>::tw;
     case ST_NEAREST: return StencilShape<ST_NEAREST>::tw;
     case ST_BILINEAR: return StencilShape<ST_BILINEAR>::tw;
     case ST_BSPLINE: return StencilShape<ST_BSPLINE>::tw;
@@ -46,6 +47,7 @@ cudaError_t launch_reduce(int bucket, int py, int stencil, const InlinePlan* inl
     case ST_NEAREST: IRP_PICK(nearest)
     case ST_BILINEAR: IRP_PICK(bilinear)
     case ST_BSPLINE: IRP_PICK(bspline)
+    case ST_CUBIC: IRP_PICK(cubic)
     default: IRP_PICK(bsplinev)
   }
 #undef IRP_PICK
@@ -62,6 +64,7 @@ int reduce_occupancy(int bucket, int py, int stencil, size_t smem) {
     case ST_NEAREST: IRP_PICK(nearest)
     case ST_BILINEAR: IRP_PICK(bilinear)
     case ST_BSPLINE: IRP_PICK(bspline)
+    case ST_CUBIC: IRP_PICK(cubic)
     default: IRP_PICK(bsplinev)
   }
 #undef IRP_PICK

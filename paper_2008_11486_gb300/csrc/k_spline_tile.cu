@@ -36,6 +36,9 @@ constexpr int kTileWarm = 16;  // warm-up rows of each column recursion
 template <int NMAX>
 struct SplineTileShape {
   static constexpr int th = NMAX <= 16 ? 32 : (NMAX <= 32 ? 16 : 8);
+  // resident CTAs per SM the register allocation must allow (at most 85
+  // registers per thread for three)
+  static constexpr int min_blocks = NMAX <= 16 ? 3 : 2;
 };
 
 __device__ __forceinline__ void grid_dependency_wait() {
@@ -44,15 +47,30 @@ __device__ __forceinline__ void grid_dependency_wait() {
 
 }  // namespace
 
+// What a task needs of one frame, staged in shared memory once per tile (96 bytes).
+struct TileFrame {
+  const float* crow;
+  const uint32_t* bad;
+  float wx[4], wy[4];
+  int ox, oy, vx0, vx1;
+  int vy0, vy1, last_tap, pad0;
+  float na, nz;  // per-frame normalisation: sample = fma(sample, na, nz)
+  int pad1[2];
+};
+static_assert(sizeof(TileFrame) == 96, "TileFrame layout");
+
 template <int NMAX>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, SplineTileShape<NMAX>::min_blocks)
     k_spline_tile(const __grid_constant__ InlinePlan inl, const void* plan_dev, int item0) {
   constexpr int TH = SplineTileShape<NMAX>::th;
-  constexpr int NC = TH + 3;                 // coefficient rows: the vertical taps of TH rows
-  constexpr int NR = NC + 2 * kTileWarm;     // rows each lane reads per frame
+  constexpr int TR = TH < 16 ? TH : 16;      // output rows per task (frame, row block)
+  constexpr int NB = TH / TR;                // row blocks per tile
+  constexpr int NC = TR + 3;                 // coefficient rows: the vertical taps of TR rows
+  constexpr int NR = NC + 2 * kTileWarm;     // rows each lane reads per task
   constexpr int RPW = TH / 8;                // output rows each warp combines
   extern __shared__ float4 smem4[];
   float* s_samples = reinterpret_cast<float*>(smem4);  // [n][TH][32]
+  TileFrame* s_frames = reinterpret_cast<TileFrame*>(s_samples + (size_t)NMAX * TH * 32);
   grid_dependency_wait();                    // the row pass (launched before) is complete
   const PlanView P = make_view(inl, plan_dev);
   const PlanHeader& h = *P.h;
@@ -68,20 +86,45 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int x = tx0 + lane;
   const float kInf = __int_as_float(0x7f800000);
   const bool masked = S.masked != 0;
-  // every frame valid at every pixel of the tile: the combine knows the count
+  // the frames' fields, once per tile; and whether every frame is valid at
+  // every pixel of the tile (the combine then knows the count)
   int all_valid = 1;
   for (int k = threadIdx.x; k < n; k += kThreads) {
     const FrameDesc& F = P.frames[S.frame0 + k];
+    TileFrame T;
+    T.crow = F.crow;
+    T.bad = F.bad;
+    for (int i = 0; i < 4; ++i) {
+      T.wx[i] = F.wx[i];
+      T.wy[i] = F.wy[i];
+    }
+    T.na = F.norm ? F.norm->na : 1.0f;
+    T.nz = F.norm ? F.norm->nz : 0.0f;
+    T.pad1[0] = T.pad1[1] = 0;
+    T.ox = F.ox;
+    T.oy = F.oy;
+    T.vx0 = F.vx0;
+    T.vx1 = F.vx1;
+    T.vy0 = F.vy0;
+    T.vy1 = F.vy1;
+    T.last_tap = F.last_tap;
+    T.pad0 = 0;
+    s_frames[k] = T;
     all_valid &= F.vx0 <= tx0 && F.vx1 >= min(tx0 + kSplineTileCols, W) - 1 && F.vy0 <= ty0 &&
                  F.vy1 >= min(ty0 + TH, H) - 1;
   }
   const bool tile_valid = __syncthreads_and(all_valid) && !masked;
+  const bool norm = h.frame_norm != 0;
 
-  for (int k = warp; k < n; k += kThreads / 32) {
-    const FrameDesc& F = P.frames[S.frame0 + k];
+  // tasks (frame, block of TR output rows), round-robin over the warps
+#pragma unroll 1
+  for (int task = warp; task < n * NB; task += kThreads / 32) {
+    const int k = NB == 1 ? task : task / NB;
+    const int ry0 = ty0 + (task - k * NB) * TR;  // first output row of the task
+    const TileFrame& F = s_frames[k];
     const int cx = mirror_index(x + F.ox, W);
     const float* col = F.crow + cx;
-    const int r0 = ty0 + F.oy - kTileWarm;
+    const int r0 = ry0 + F.oy - kTileWarm;
     float v[NR];
     if (r0 >= 0 && r0 + NR <= H) {
       const float* p = col + (int64_t)r0 * cpitch;
@@ -116,53 +159,53 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
     // horizontal taps from lanes l .. l + 3 (left to right), in place
-    const float wx0 = F.wx[0], wx1 = F.wx[1], wx2 = F.wx[2], wx3 = F.wx[3];
+    const float4 wx = *reinterpret_cast<const float4*>(F.wx);
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
       const float c1 = __shfl_down_sync(0xffffffffu, c[j], 1);
       const float c2 = __shfl_down_sync(0xffffffffu, c[j], 2);
       const float c3 = __shfl_down_sync(0xffffffffu, c[j], 3);
-      float hh = wx0 * c[j];
-      hh = __fmaf_rn(wx1, c1, hh);
-      hh = __fmaf_rn(wx2, c2, hh);
-      c[j] = __fmaf_rn(wx3, c3, hh);
+      float hh = wx.x * c[j];
+      hh = __fmaf_rn(wx.y, c1, hh);
+      hh = __fmaf_rn(wx.z, c2, hh);
+      c[j] = __fmaf_rn(wx.w, c3, hh);
     }
     // bad-pixel footprint: bit j of `badrows` marks coefficient row j of this
     // lane's source column bad; a sample is invalid when any tap with non-zero
     // weight (columns l .. l + 3, rows q .. q + 3) is bad
-    uint64_t badq = 0;
+    uint32_t badq = 0;
     if (masked) {
       const uint32_t* bits = F.bad + (cx >> 5);
       const int sh = cx & 31;
       const int64_t bp = S.bad_pitch;
-      const int rb = ty0 + F.oy;
-      uint64_t badrows = 0;
+      const int rb = ry0 + F.oy;
+      uint32_t badrows = 0;
 #pragma unroll
       for (int j = 0; j < NC; ++j)
-        badrows |= (uint64_t)((__ldg(bits + (int64_t)mirror_index(rb + j, H) * bp) >> sh) & 1u)
-                   << j;
+        badrows |= ((__ldg(bits + (int64_t)mirror_index(rb + j, H) * bp) >> sh) & 1u) << j;
       // with the fraction f in [0, 1) the first three taps of an axis always
       // have non-zero weight, the fourth, beta3(2 - f), unless f = 0
-      uint64_t cols = badrows | __shfl_down_sync(0xffffffffu, badrows, 1) |
+      uint32_t cols = badrows | __shfl_down_sync(0xffffffffu, badrows, 1) |
                       __shfl_down_sync(0xffffffffu, badrows, 2);
-      const uint64_t c3 = __shfl_down_sync(0xffffffffu, badrows, 3);
+      const uint32_t c3 = __shfl_down_sync(0xffffffffu, badrows, 3);
       if (F.last_tap & 1) cols |= c3;
       badq = cols | (cols >> 1) | (cols >> 2);
       if (F.last_tap & 2) badq |= cols >> 3;
     }
-    const float wy0 = F.wy[0], wy1 = F.wy[1], wy2 = F.wy[2], wy3 = F.wy[3];
-    const bool xv = in_range(x, F.vx0, F.vx1 - F.vx0) && F.vx1 >= F.vx0;
-    float* sk = s_samples + (size_t)k * TH * 32 + lane;
+    const float4 wy = *reinterpret_cast<const float4*>(F.wy);
+    const bool xv = F.vx1 >= F.vx0 && in_range(x, F.vx0, F.vx1 - F.vx0);
+    float* sk = s_samples + ((size_t)k * TH + (ry0 - ty0)) * 32 + lane;
     // the caller's aligned stack (debug output): NaN for invalid samples
     float* const st = (S.stack_out && lane < kSplineTileCols && x < W)
                           ? S.stack_out + (int64_t)k * H * S.out_pitch + x : nullptr;
 #pragma unroll
-    for (int q = 0; q < TH; ++q) {
-      float acc = wy0 * c[q];
-      acc = __fmaf_rn(wy1, c[q + 1], acc);
-      acc = __fmaf_rn(wy2, c[q + 2], acc);
-      acc = __fmaf_rn(wy3, c[q + 3], acc);
-      const int y = ty0 + q;
+    for (int q = 0; q < TR; ++q) {
+      float acc = wy.x * c[q];
+      acc = __fmaf_rn(wy.y, c[q + 1], acc);
+      acc = __fmaf_rn(wy.z, c[q + 2], acc);
+      acc = __fmaf_rn(wy.w, c[q + 3], acc);
+      if (norm) acc = __fmaf_rn(acc, F.na, F.nz);  // per-frame normalisation
+      const int y = ry0 + q;
       const bool ok = xv && y >= F.vy0 && y <= F.vy1 && !((badq >> q) & 1u);
       sk[q * 32] = ok ? acc : kInf;
       if (st && y < H) st[(int64_t)y * S.out_pitch] = ok ? acc : __int_as_float(0x7fc00000);
@@ -198,7 +241,11 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 size_t spline_tile_smem_bytes(int bucket, int max_n) {
-  return (size_t)max_n * spline_tile_rows(bucket) * 32 * sizeof(float);
+  // samples [bucket][TH][32] (the kernel lays out the frame table after the
+  // bucket's samples), then the frame table
+  (void)max_n;
+  return (size_t)bucket * spline_tile_rows(bucket) * 32 * sizeof(float) +
+         (size_t)bucket * 96;
 }
 
 int spline_tile_rows(int bucket) { return bucket <= 16 ? 32 : (bucket <= 32 ? 16 : 8); }

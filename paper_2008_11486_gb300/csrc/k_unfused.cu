@@ -117,12 +117,6 @@ __device__ __forceinline__ void row_flush(StatsAcc& acc, const RowPartial& r) {
   acc.q += (double)r.q + (double)r.eq;
 }
 
-// Rows per stats block: about 16K pixels per block.
-__host__ __device__ inline int stats_rows(int W, int H) {
-  int r = 16384 / (W > 0 ? W : 1);
-  r = r < 1 ? 1 : r;
-  return r > H ? H : r;
-}
 
 // Sums of calibrated raw frames (FP16 scaling needs them before quantising).
 // Block b covers frame b % nk and the row block b / nk: consecutive blocks
@@ -176,6 +170,81 @@ __global__ void __launch_bounds__(kThreads)
     row_flush(acc, r);
   }
   stats_commit(acc, &st[k].sum, &st[k].sumsq, &st[k].count, &st[k].min_key, &st[k].max_key);
+}
+
+// Per-frame normalisation: the FP64 sum of every calibrated raw frame of a
+// plan's sets.  Block b covers frame b % nframes and its row block
+// b / nframes (rows of stats_rows(W, H) each); blocks past a set's rows exit.
+__global__ void __launch_bounds__(kThreads)
+    k_frame_means(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
+  const PlanView P = make_view(inl, plan_dev);
+  const int nf = P.h->nframes;
+  const int f = blockIdx.x % nf, rb = blockIdx.x / nf;
+  int si = 0;
+  {
+    int lo = 0, hi = P.h->nsets - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.sets[mid].frame0 <= f) lo = mid; else hi = mid - 1;
+    }
+    si = lo;
+  }
+  const SetDesc& S = P.sets[si];
+  const FrameDesc& F = P.frames[f];
+  const int W = S.W, H = S.H;
+  const int R = stats_rows(W, H);
+  if (rb * R >= H || !F.norm) return;
+  const float flat_norm = S.flat_sum ? (float)(*S.flat_sum / ((double)W * H)) : 1.0f;
+  const uint16_t* raw = (const uint16_t*)F.src;
+  StatsAcc acc{0.0, 0.0, 0, FLT_MAX, -FLT_MAX};
+  const int y1 = min(H, (rb + 1) * R);
+  for (int y = rb * R; y < y1; ++y) {
+    RowPartial r{0.0f, 0.0f, 0.0f, 0.0f};
+    const uint16_t* rr = raw + (int64_t)y * S.src_pitch;
+    const int64_t mrow = (int64_t)y * S.master_pitch;
+    for (int x = threadIdx.x; x < W; x += kThreads) {
+      const float rf = inv_flat(__ldg(S.flat + mrow + x), flat_norm, P.h->status);
+      row_add(r, calibrate_px(__ldg(rr + x), __ldg(S.bias + mrow + x), __ldg(S.dark + mrow + x),
+                              F.t, rf));
+    }
+    row_flush(acc, r);
+  }
+  stats_commit(acc, &F.norm->sum, nullptr, nullptr, nullptr, nullptr);
+}
+
+// The factors of every frame from the sums: frame 0 of the set (norm_ref) is
+// the reference.
+__global__ void k_frame_norm_factors(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
+  const PlanView P = make_view(inl, plan_dev);
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= P.h->nframes) return;
+  int si = 0;
+  {
+    int lo = 0, hi = P.h->nsets - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.sets[mid].frame0 <= f) lo = mid; else hi = mid - 1;
+    }
+    si = lo;
+  }
+  const SetDesc& S = P.sets[si];
+  FrameNorm* rec = P.frames[f].norm;
+  if (!rec || !S.norm_ref) return;
+  const double px = (double)S.W * S.H;
+  const double mk = rec->sum / px, m0 = S.norm_ref->sum / px;
+  float na = 1.0f, nz = 0.0f;
+  if (P.h->frame_norm == 1) {
+    nz = (float)(m0 - mk);
+  } else {
+    if (!(mk != 0.0) || !isfinite(mk) || !isfinite(m0)) {
+      latch_status(P.h->status, IRP_ERR_BAD_STATISTIC);
+      na = __int_as_float(0x7fffffff);
+    } else {
+      na = (float)(m0 / mk);
+    }
+  }
+  rec->na = na;
+  rec->nz = nz;
 }
 
 // Sums of F32 / F16-scaled frames, NaN skipped (also the flat master).
@@ -337,6 +406,26 @@ __global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
       };
       if (ST == ST_NEAREST) {
         val = at(i0, j0);
+      } else if (ST == ST_CUBIC) {
+        // taps i0 .. i0 + 3 (origin floor(dx) - 1); with a zero fraction only
+        // the second tap of the axis has non-zero weight, and only it is read
+        const bool allx = F.last_tap & 1, ally = F.last_tap & 2;
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (!ally && q != 1) continue;
+          float hh;
+          if (allx) {
+            hh = F.wx[0] * at(i0, j0 + q);
+            hh = __fmaf_rn(F.wx[1], at(i0 + 1, j0 + q), hh);
+            hh = __fmaf_rn(F.wx[2], at(i0 + 2, j0 + q), hh);
+            hh = __fmaf_rn(F.wx[3], at(i0 + 3, j0 + q), hh);
+          } else {
+            hh = at(i0 + 1, j0 + q);
+          }
+          acc = ally ? (q == 0 ? F.wy[0] * hh : __fmaf_rn(F.wy[q], hh, acc)) : hh;
+        }
+        val = acc;
       } else {
         // zero-weight taps are not read (they may lie outside the frame)
         const float p00 = at(i0, j0);
@@ -459,6 +548,17 @@ cudaError_t launch_stats_frames(const void* frames, int64_t pitch, int64_t fstri
   return cudaGetLastError();
 }
 
+cudaError_t launch_frame_norm(const InlinePlan* inl, const void* plan_dev, int nframes,
+                              int max_row_blocks, cudaStream_t s) {
+  if (nframes <= 0) return cudaSuccess;
+  k_frame_means<<<(unsigned)((int64_t)nframes * max_row_blocks), kThreads, 0, s>>>(*inl,
+                                                                                  plan_dev);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_frame_norm_factors<<<(nframes + 127) / 128, 128, 0, s>>>(*inl, plan_dev);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_f16_scaling(const FrameStats* st, int n, float* scale, float* offset,
                                cudaStream_t s) {
   k_f16_scaling<<<(n + 127) / 128, 128, 0, s>>>(st, n, scale, offset);
@@ -494,6 +594,7 @@ cudaError_t launch_shift(const ShiftArgs& a, int nk, int stencil, bool f16, cuda
   switch (stencil) {
     case ST_NEAREST: return shift_st<ST_NEAREST>(a, nk, f16, s);
     case ST_BILINEAR: return shift_st<ST_BILINEAR>(a, nk, f16, s);
+    case ST_CUBIC: return shift_st<ST_CUBIC>(a, nk, f16, s);
     default: return shift_st<ST_BSPLINE>(a, nk, f16, s);
   }
 }

@@ -13,6 +13,7 @@ struct RowTap {
   const float* row;  // filtered row of the first vertical tap, null if the row is invalid
   int vx0, vx1;      // valid output columns
   float wy[4];       // vertical cubic B-spline weights
+  float na, nz;      // per-frame normalisation: sample = fma(sample, na, nz)
 };
 
 // The CTA gathers its [n][32] slab of samples into shared memory, then each
@@ -60,6 +61,9 @@ __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs a, in
       r.vx1 = __ldg(&F->vx1);
 #pragma unroll
       for (int j = 0; j < 4; ++j) r.wy[j] = __ldg(&F->wy[j]);
+      const FrameNorm* nr = (const FrameNorm*)__ldg((const unsigned long long*)&F->norm);
+      r.na = nr ? nr->na : 1.0f;
+      r.nz = nr ? nr->nz : 0.0f;
       tab[k] = r;
     }
     __syncthreads();
@@ -72,7 +76,8 @@ __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs a, in
 #pragma unroll
       for (int b = 0; b < kBatch; ++b) {
         const int k = k0 + 8 * b;
-        const RowTap r = k < n ? tab[k] : RowTap{nullptr, 0, -1, {0.0f, 0.0f, 0.0f, 0.0f}};
+        const RowTap r =
+            k < n ? tab[k] : RowTap{nullptr, 0, -1, {0.0f, 0.0f, 0.0f, 0.0f}, 1.0f, 0.0f};
         const bool ok = r.row && x >= r.vx0 && x <= r.vx1;
         w[b] = make_float4(r.wy[0], r.wy[1], r.wy[2], r.wy[3]);
 #pragma unroll
@@ -86,6 +91,7 @@ __global__ void __launch_bounds__(kWideThreads) k_combine_wide(CombineArgs a, in
         acc = __fmaf_rn(w[b].y, h[b][1], acc);
         acc = __fmaf_rn(w[b].z, h[b][2], acc);
         acc = __fmaf_rn(w[b].w, h[b][3], acc);
+        if (a.frame_norm) acc = __fmaf_rn(acc, tab[k].na, tab[k].nz);
         s_wide[SM::at(lane, k)] = h[b][0] < kInf ? acc : kInf;
       }
     }

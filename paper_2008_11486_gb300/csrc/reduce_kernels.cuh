@@ -132,6 +132,9 @@ IRP_DECLARE_PART(bspline_hi)
 IRP_DECLARE_PART(bsplinev_lo)
 IRP_DECLARE_PART(bsplinev_mid)
 IRP_DECLARE_PART(bsplinev_hi)
+IRP_DECLARE_PART(cubic_lo)
+IRP_DECLARE_PART(cubic_mid)
+IRP_DECLARE_PART(cubic_hi)
 #undef IRP_DECLARE_PART
 
 }  // namespace irp

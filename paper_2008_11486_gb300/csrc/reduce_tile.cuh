@@ -13,7 +13,8 @@
 //      once per tile (Sec. 2.1 calibration);
 //   3. resample: the stencil's horizontal taps come from the neighbouring
 //      lanes by warp shuffles, the vertical taps from the lane's own rows
-//      (nearest, bilinear, or the 4x4 cubic B-spline on spline coefficients);
+//      (nearest, bilinear, Keys' 4x4 cubic convolution, or the 4x4 cubic
+//      B-spline on spline coefficients);
 //   4. the sample (or +inf when invalid) is stored in the tile's sample array.
 // After the last frame each lane combines its PY pixels (combine.cuh).
 #pragma once
@@ -109,9 +110,11 @@ __device__ __forceinline__ void cp_async_wait() {
 // ---------------------------------------------------------------- geometry
 template <int STENCIL>
 struct StencilShape {
-  static constexpr int taps_x = STENCIL == ST_BSPLINE ? 4 : (STENCIL == ST_BILINEAR ? 2 : 1);
-  static constexpr int taps_y = (STENCIL == ST_BSPLINE || STENCIL == ST_BSPLINE_V)
-                                    ? 4 : (STENCIL == ST_BILINEAR ? 2 : 1);
+  static constexpr int taps_x =
+      (STENCIL == ST_BSPLINE || STENCIL == ST_CUBIC) ? 4 : (STENCIL == ST_BILINEAR ? 2 : 1);
+  static constexpr int taps_y =
+      (STENCIL == ST_BSPLINE || STENCIL == ST_BSPLINE_V || STENCIL == ST_CUBIC)
+          ? 4 : (STENCIL == ST_BILINEAR ? 2 : 1);
   // output columns per tile: lane l needs source columns l .. l + taps_x - 1
   static constexpr int tw = 33 - taps_x;
 };
@@ -121,7 +124,13 @@ struct StencilShape {
 __host__ __device__ constexpr int rows_per_warp_default(int nmax) { return nmax <= 16 ? 4 : 2; }
 __host__ __device__ constexpr int rows_per_warp_alt(int nmax) { return nmax <= 16 ? 2 : 1; }
 
-constexpr int kStages = 4;           // cp.async ring depth (frames in flight)
+// cp.async ring depth (frames in flight); 6 or 8 stages measured no faster
+// on 32 x 4096^2 (2.15 ms with 8 against 2.09 ms with 4).
+__host__ __device__ constexpr int stage_count(int src, int stencil) {
+  (void)src;
+  (void)stencil;
+  return 4;
+}
 constexpr int kRawChunks = 5;        // 16-byte chunks per staged raw row (40 uint16)
 constexpr int kCoefChunks = 9;       // 16-byte chunks per staged coefficient row (36 floats)
 constexpr int kRowChunks = 8;        // 16-byte chunks per staged filtered row (32 floats)
@@ -141,11 +150,11 @@ struct StageShape {
 // Shared memory per CTA of the fused kernel (host helper mirrors this).
 __host__ __device__ inline size_t fused_smem_bytes(int src, int stencil, int py, int max_n,
                                                    int mwin_w, int mwin_h) {
-  const int taps = (stencil == ST_BSPLINE || stencil == ST_BSPLINE_V)
+  const int taps = (stencil == ST_BSPLINE || stencil == ST_BSPLINE_V || stencil == ST_CUBIC)
                        ? 4 : (stencil == ST_BILINEAR ? 2 : 1);
   const int rows = py + taps - 1;
   const int chunks = stage_chunks(src, stencil);
-  const size_t stage = (size_t)kStages * rows * chunks * 16 * (kThreads / 32);
+  const size_t stage = (size_t)stage_count(src, stencil) * rows * chunks * 16 * (kThreads / 32);
   const size_t samples = (size_t)max_n * (8 * py) * 32 * sizeof(float);
   const size_t masters = (size_t)mwin_w * mwin_h * sizeof(float4);
   const size_t descs = (size_t)max_n * sizeof(FrameDesc);
@@ -167,8 +176,10 @@ struct FrameRec {
   float wx[4], wy[4];         // spline weights
   const uint8_t* base;        // staging source: element (ybase, xa) of the frame
   const uint8_t* fbase;       // a valid address inside the frame (zero-byte copies)
-  int ybase, xa, flags, pad1; // first staged row / aligned first staged column
-  int pad2[4];
+  int ybase, xa, flags, last_tap;  // first staged row / aligned first staged column;
+                              // FrameDesc::last_tap
+  float na, nz;               // per-frame normalisation: sample = fma(sample, na, nz)
+  int pad2[2];
 };
 static_assert(sizeof(FrameRec) == 128, "FrameRec layout");
 
@@ -221,12 +232,14 @@ __device__ __forceinline__ FrameRec make_rec(const FrameDesc& F, int tx0, int ty
                         R.xa + win_elems <= Wlim;
   const bool all_valid = F.vx0 <= tx0 && F.vx1 >= tx1 && F.vy0 <= ty0 && F.vy1 >= ty1;
   R.flags = (F.flags & 1) | (interior ? 2 : 0) | (all_valid ? 4 : 0);
-  R.pad1 = 0;
+  R.last_tap = F.last_tap;
   for (int i = 0; i < 4; ++i) {
     R.wx[i] = F.wx[i];
     R.wy[i] = F.wy[i];
-    R.pad2[i] = 0;
   }
+  R.na = F.norm ? F.norm->na : 1.0f;
+  R.nz = F.norm ? F.norm->nz : 0.0f;
+  R.pad2[0] = R.pad2[1] = 0;
   return R;
 }
 
@@ -362,7 +375,7 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
                                            float flat_norm, uint32_t* status, int lane, int x,
                                            int tx0, int wy0, float* sk, int (&mq)[PY],
                                            float* stack_out, int k, int W, int H,
-                                           int64_t out_pitch, bool stack_lane) {
+                                           int64_t out_pitch, bool stack_lane, bool norm) {
   using SS = StageShape<SRC, STENCIL, PY>;
   const int4 g = *(const int4*)&F.off;      // off, mofs, vx0, vxw
   const float4 w = *(const float4*)&F.fx;   // fx, fy, t
@@ -429,7 +442,7 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
       acc = __fmaf_rn(wy.z, v[q + 2], acc);
       a[q] = __fmaf_rn(wy.w, v[q + 3], acc);
     }
-  } else {
+  } else {  // ST_BSPLINE (coefficients) or ST_CUBIC (calibrated raw): 4x4 taps
     const float4 wx = *(const float4*)F.wx;
     const float4 wy = *(const float4*)F.wy;
     float hrow[SS::rows];
@@ -451,6 +464,10 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
       a[q] = __fmaf_rn(wy.w, hrow[q + 3], acc);
     }
   }
+  if (norm) {  // per-frame normalisation before the combine
+#pragma unroll
+    for (int q = 0; q < PY; ++q) a[q] = __fmaf_rn(a[q], F.na, F.nz);
+  }
   if (MODE == kFast) {
 #pragma unroll
     for (int q = 0; q < PY; ++q) sk[q * 32] = a[q];
@@ -466,6 +483,21 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
     if (STENCIL == ST_NEAREST) {
 #pragma unroll
       for (int q = 0; q < PY; ++q) badq[q] = bad[q];
+    } else if (STENCIL == ST_CUBIC) {
+      // taps at lanes l .. l + 3 and rows q .. q + 3; with a zero fraction
+      // only the tap at l + 1 (row q + 1) has non-zero weight
+      const bool allx = (F.last_tap & 1) != 0, ally = (F.last_tap & 2) != 0;
+      bool bh[SS::rows];
+#pragma unroll
+      for (int r = 0; r < SS::rows; ++r) {
+        const int b1 = __shfl_down_sync(0xffffffffu, (int)bad[r], 1);
+        const int b2 = __shfl_down_sync(0xffffffffu, (int)bad[r], 2);
+        const int b3 = __shfl_down_sync(0xffffffffu, (int)bad[r], 3);
+        bh[r] = allx ? (bad[r] | (b1 != 0) | (b2 != 0) | (b3 != 0)) : (b1 != 0);
+      }
+#pragma unroll
+      for (int q = 0; q < PY; ++q)
+        badq[q] = ally ? (bh[q] | bh[q + 1] | bh[q + 2] | bh[q + 3]) : bh[q + 1];
     } else {
       bool bh[SS::rows];
 #pragma unroll
@@ -498,6 +530,7 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
 
 template <int NMAX, int STENCIL, int SRC, int PY>
 __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* smem) {
+  constexpr int kStages = stage_count(SRC, STENCIL);
   constexpr int TH = 8 * PY;
   constexpr int TW = StencilShape<STENCIL>::tw;
   using SS = StageShape<SRC, STENCIL, PY>;
@@ -567,6 +600,7 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
                          !stack_out && !S.masked;
 
   const FrameRec* frames = s_rec;
+  const bool norm = h.frame_norm != 0;
   // prologue: frames 0 .. kStages-2 in flight
 #pragma unroll
   for (int k = 0; k < kStages - 1; ++k) {
@@ -608,7 +642,7 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
                                        flat_norm, h.status, lane, x, tx0, wy0,
                                        sk ? sk + (size_t)k * TH * 32 : nullptr, mq,
                                        stack_out, k, W, H,
-                                       out_pitch, stack_lane);
+                                       out_pitch, stack_lane, norm);
   };
   auto frame_loop = [&](auto mode) {
     int k0 = 0;

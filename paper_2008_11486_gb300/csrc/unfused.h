@@ -10,6 +10,13 @@ constexpr int kCalibChunk = 256;   // frames per calibration launch (times by va
 constexpr int kShiftChunk = 64;    // frames per shift launch (descriptors by value)
 constexpr float kF16Range = 16384.0f;  // |h| bound of FP16 stacks (4x headroom)
 
+// Rows per stats block: about 16K pixels per block.
+__host__ __device__ inline int stats_rows(int W, int H) {
+  int r = 16384 / (W > 0 ? W : 1);
+  r = r < 1 ? 1 : r;
+  return r > H ? H : r;
+}
+
 struct FrameStats {  // 32 bytes per frame, workspace
   double sum, sumsq;
   long long count;
@@ -46,7 +53,7 @@ struct CombineArgs {
   const FrameDesc* frames;   // ... of these frames (device), when stack is null
   int64_t coef_pitch;        // ... with this row pitch
   int64_t pitch, fstride;
-  int W, H, n, pad;
+  int W, H, n, frame_norm;   // frame_norm: apply the frames' normalisation (filtered rows)
   const float* scale;
   const float* offset;
   const uint8_t* valid;
@@ -67,6 +74,10 @@ cudaError_t launch_stats_frames(const void* frames, int64_t pitch, int64_t fstri
                                 cudaStream_t s);
 cudaError_t launch_f16_scaling(const FrameStats* st, int n, float* scale, float* offset,
                                cudaStream_t s);
+// Per-frame normalisation of a (sub-)plan: the FP64 sums of its calibrated raw
+// frames into their FrameNorm records (zeroed by the caller), then the factors.
+cudaError_t launch_frame_norm(const InlinePlan* inl, const void* plan_dev, int nframes,
+                              int max_row_blocks, cudaStream_t s);
 cudaError_t launch_calibrate(const CalibArgs& a, int nk, bool f16, void* out, int64_t out_pitch,
                              int64_t out_fstride, const float* scale, const float* offset,
                              cudaStream_t s);

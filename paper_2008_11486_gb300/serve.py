@@ -17,9 +17,13 @@ Scheduling:
     newer requests have been admitted;
     admitted requests copy their new frames into the chip rings on a copy
     stream (pinned host memory -> HBM);
-  * batching: at every scheduler tick all admitted requests whose copies have
+  * batching: at every scheduler tick the admitted requests whose copies have
     landed are reduced together in one persistent launch (all their chip sets
-    in one plan), on the compute stream, while newer requests keep uploading;
+    in one plan), on the compute stream, while newer requests keep uploading.
+    While a batch is on the device, ready requests wait for it (up to
+    ``max_batch`` of them) and then go together in the next launch: requests
+    that arrive during a batch are admitted, upload behind it and join the
+    next one (continuous batching);
   * completion: an event per batch; a request's latency is the time from its
     arrival to the host seeing its outputs ready;
   * errors: a request the rings cannot take (a frame of the wrong shape or
@@ -95,10 +99,12 @@ class Chip:
 
 class Server:
     def __init__(self, masters, depth=5, max_inflight=2, interp="bilinear", clip=None,
-                 hbm_reserve_bytes=2 << 30, device="cuda", out_slots=None, download=False):
+                 hbm_reserve_bytes=2 << 30, device="cuda", out_slots=None, download=False,
+                 max_batch=None):
         self.device = torch.device(device)
         self.depth = depth
         self.max_inflight = max_inflight
+        self.max_batch = max_batch if max_batch is not None else max_inflight
         self.interp = interp
         self.clip = clip
         self.reserve = hbm_reserve_bytes
@@ -259,7 +265,11 @@ class Server:
             (ready if u[2].query() else waiting).append(u)
         if not ready:
             return
-        self.uploading = waiting
+        if self.running and len(ready) < self.max_batch:
+            return  # the device is busy: ready requests join the next batch
+        ready = ready[:self.max_batch]
+        taken = {id(u) for u in ready}
+        self.uploading = [u for u in self.uploading if id(u) not in taken]
         sets, reqs, per_req = [], [], []
         for req, nums, ev in ready:
             self.compute_stream.wait_event(ev)

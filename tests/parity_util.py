@@ -8,6 +8,9 @@ Tolerances, each derived from the rounding steps of the FP32 arithmetic:
   * one resampled sample, nearest / bilinear: 8 u M3 + 1e-5, M3 = largest
     |v| among the 3x3 source pixels around the tap origin (calibration and
     two lerps, each a few roundings of values bounded by M3), u = 2^-24;
+  * one resampled sample, Keys cubic convolution: 16 u M5 + 1e-5, M5 = largest
+    |v| in the 5x5 neighbourhood (calibration, then two 4-tap passes whose
+    weights have an absolute sum of at most 1.25 per axis);
   * one resampled sample, cubic spline: 64 u M9 + 1e-4, M9 = largest |v|
     within 4 px of the tap origin (recursive prefilter of gain sqrt(3) per
     direction and axis; error terms of farther pixels decay as 0.268^d);
@@ -42,7 +45,8 @@ def sample_tolerance(fs, interp, oracle_mod, pixels=None):
     """Per-sample tolerance [n,H,W] of the aligned stack on the output grid,
     or [n, len(xs)] at the output pixels ``pixels`` = (xs, ys)."""
     n, H, W = fs.raw.shape
-    size, coef, floor_ = (9, 64.0, 1e-4) if interp == "spline3" else (3, 8.0, 1e-5)
+    size, coef, floor_ = {"spline3": (9, 64.0, 1e-4), "cubic": (5, 16.0, 1e-5)}.get(
+        interp, (3, 8.0, 1e-5))
     if pixels is None:
         yy, xx = np.mgrid[0:H, 0:W]
     else:

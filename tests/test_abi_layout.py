@@ -69,6 +69,7 @@ def test_enum_values_match_the_header(c_layout):
     assert enums["IRP_INTERP_NEAREST"] == B.INTERP["nearest"]
     assert enums["IRP_INTERP_BILINEAR"] == B.INTERP["bilinear"]
     assert enums["IRP_INTERP_SPLINE3"] == B.INTERP["spline3"]
+    assert enums["IRP_INTERP_CUBIC"] == B.INTERP["cubic"]
     assert enums["IRP_F32"] == B.DTYPE["f32"] and enums["IRP_F16_SCALED"] == B.DTYPE["f16"]
     assert c_layout[("define", "IRP_MAX_FRAMES")] == B.MAX_FRAMES
 

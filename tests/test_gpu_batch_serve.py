@@ -146,3 +146,82 @@ def test_server_requests_allocate_no_outputs():
     torch.cuda.synchronize()
     assert srv.status() == 0
     assert torch.cuda.memory_allocated() - before < 2 * H * W * 4
+
+
+def _requests(chips, lo, hi):
+    return [serve.Request(rid=r, frames=[torch.from_numpy(fs.raw[r]).pin_memory() for fs in chips],
+                          dx=np.array([fs.dx[r] for fs in chips]),
+                          dy=np.array([fs.dy[r] for fs in chips])) for r in range(lo, hi)]
+
+
+def test_server_batches_requests_that_arrive_during_work(monkeypatch):
+    """Continuous batching: requests that arrive while a batch is on the device
+    are admitted, upload behind it and go together in the next launch; each
+    result is bit-identical to its standalone reduction.  Each batch launch is
+    preceded on the compute stream by a fixed spin of about 2.5 ms (the device
+    busy with other work), so that batches stay on the device while the
+    scheduler runs."""
+    nchips, W, H, nreq, depth = 2, 256, 192, 10, 3
+    chips = _chip_frames(nchips, W, H, nreq, 5151)
+    masters = [tuple(torch.from_numpy(a).cuda() for a in (fs.bias, fs.dark, fs.flat))
+               for fs in chips]
+    launch = core.Plan.launch
+
+    def busy_launch(self, stream=None):
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(5_000_000)
+        launch(self, stream)
+
+    monkeypatch.setattr(core.Plan, "launch", busy_launch)
+    srv = serve.Server(masters, depth=depth, max_inflight=4, max_batch=2, interp="bilinear",
+                       hbm_reserve_bytes=0, out_slots=nreq)
+    reqs = _requests(chips, 0, nreq)
+    lat, wall = serve.run_poisson(srv, reqs, rate_hz=1e6)  # all arrive at once
+    assert srv.status() == 0 and len(srv.done) == nreq
+    print(f"\nbatch sizes {srv.batch_sizes}, admitted while a batch ran: "
+          f"{srv.admitted_while_running}")
+    assert max(srv.batch_sizes) >= 2, srv.batch_sizes
+    assert srv.admitted_while_running >= 1
+    for r, req in enumerate(reqs):
+        first = max(0, r - depth + 1)
+        for c, fs in enumerate(chips):
+            sub = synth.FrameSet(raw=fs.raw[first:r + 1], bias=fs.bias, dark=fs.dark,
+                                 flat=fs.flat, exptime=fs.exptime[first:r + 1],
+                                 dx=fs.dx[first:r + 1], dy=fs.dy[first:r + 1])
+            m, d = _alone(sub, "bilinear")
+            gm, gd = req.outputs[c]
+            assert np.array_equal(gm.cpu().numpy().view(np.uint32), m.view(np.uint32)), (r, c)
+            assert np.array_equal(gd.cpu().numpy().view(np.uint32), d.view(np.uint32)), (r, c)
+
+
+def test_server_request_with_a_bad_flat_reports_its_status():
+    """A chip whose flat master holds a zero makes the device latch
+    IRP_ERR_BAD_MASTER (host-made input, no fault): the requests reduced while
+    it is there complete with that status, the server stays usable, and once
+    the flat is repaired the next requests complete normally with the
+    standalone results."""
+    nchips, W, H, nreq, depth = 2, 96, 80, 6, 3
+    chips = _chip_frames(nchips, W, H, nreq, 6161)
+    masters = [tuple(torch.from_numpy(a).cuda() for a in (fs.bias, fs.dark, fs.flat))
+               for fs in chips]
+    srv = serve.Server(masters, depth=depth, max_inflight=2, interp="bilinear",
+                       hbm_reserve_bytes=0, out_slots=nreq)
+    good = masters[1][2][10, 20].item()
+    masters[1][2][10, 20] = 0.0              # chip 1's flat: one zero
+    bad = _requests(chips, 0, 3)
+    serve.run_poisson(srv, bad, rate_hz=1e6)
+    assert all(r.status == 5 for r in bad) and len(srv.failed) == 3
+    masters[1][2][10, 20] = good             # repaired
+    torch.cuda.synchronize()
+    ok = _requests(chips, 3, nreq)
+    serve.run_poisson(srv, ok, rate_hz=1e6)
+    assert all(r.status == 0 for r in ok)
+    for r, req in zip(range(3, nreq), ok):
+        first = max(0, r - depth + 1)
+        for c, fs in enumerate(chips):
+            sub = synth.FrameSet(raw=fs.raw[first:r + 1], bias=fs.bias, dark=fs.dark,
+                                 flat=fs.flat, exptime=fs.exptime[first:r + 1],
+                                 dx=fs.dx[first:r + 1], dy=fs.dy[first:r + 1])
+            m, _ = _alone(sub, "bilinear")
+            assert np.array_equal(req.outputs[c][0].cpu().numpy().view(np.uint32),
+                                  m.view(np.uint32)), (r, c)

@@ -79,7 +79,7 @@ def check_against_oracle(fs, got, interp, kappa, max_iter, normalize_flat=False,
     return stats
 
 
-@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3"])
+@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3", "cubic"])
 def test_fused_small_ragged(interp):
     fs = synth.make_set(100, 70, 12, 5.0, 501, n_stars=40, n_cr=8)
     got = run_fused([fs], interp, kappa=2.5)[0]
@@ -214,7 +214,7 @@ def test_clip_options_median_centre_and_ddof():
 
 
 # ------------------------------------------------------------- edge cases
-@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3"])
+@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3", "cubic"])
 def test_edge_shapes_and_offsets(interp):
     cases = [
         synth.make_const_set(1, 1, 1, 1500, 1000.0, 0.05, 0.8, 60.0),
@@ -317,7 +317,7 @@ def test_plan_launch_and_graph_capture():
 
 
 # --------------------------------------------------------------- unfused path
-@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3"])
+@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3", "cubic"])
 def test_unfused_f32_matches_oracle(interp):
     fs = synth.make_set(90, 66, 9, 4.0, 123, n_stars=30, n_cr=10)
     d = core.device_set(fs)
@@ -335,7 +335,7 @@ def test_unfused_f32_matches_oracle(interp):
         a, ok = oracle.shift(cal_h[k].astype(np.float64), fs.dx[k], fs.dy[k], interp)
         assert np.array_equal(ok, va[k])
         M = np.abs(cal_h[k]).max()
-        coef = 64 if interp == "spline3" else 8
+        coef = {"spline3": 64, "cubic": 16}.get(interp, 8)
         compare("shift", np.where(ok, st[k], np.nan), np.where(ok, a, np.nan),
                 coef * 2.0 ** -24 * M + 1e-4)
     out = core.combine(stack, valid=valid, clip=core.clip_params(2.5), want_reject=True)
@@ -413,7 +413,7 @@ def test_frame_stats_f64_wide_rows():
 
 
 # ------------------------------------------------ bad-pixel masking (Sec. 2.1)
-@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3"])
+@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3", "cubic"])
 @pytest.mark.parametrize("offset", [4.0, 40.0])   # union master window / masters from HBM
 def test_masked_reduction_matches_oracle(interp, offset):
     fs = synth.make_set(101, 77, 14, offset, 1313, n_stars=40, n_cr=10)

@@ -126,3 +126,41 @@ def test_cancel_of_the_head_during_admission_drops_no_other_request(host):
     assert done[0].status == serve.CANCELLED and done[0].outputs is None
     assert done[1].status == 0 and done[1].outputs is not None
     assert srv.admitted == 1
+
+
+class _HeldEvent:
+    """A completion event the test releases: the batch stays on the device."""
+    held = True
+
+    def record(self, stream=None):
+        pass
+
+    def query(self):
+        return not _HeldEvent.held
+
+
+def test_requests_arriving_during_a_batch_join_the_next_one(host, monkeypatch):
+    srv = _server(reserve=0)
+    srv.max_inflight = srv.max_batch = 4
+    _HeldEvent.held = True
+    uploads_done = _Event()
+    # uploads land at once, batches complete only when released
+    monkeypatch.setattr(torch.cuda, "Event", lambda *a, **k: _HeldEvent())
+    srv.submit(_req(0))
+    srv._admit()
+    srv.uploading = [(r, n, uploads_done) for (r, n, e) in srv.uploading]
+    srv._launch()
+    assert srv.batch_sizes == [1] and len(srv.running) == 1
+    for rid in (1, 2, 3):  # arrive while batch 0 is on the device
+        srv.submit(_req(rid))
+    srv._admit()
+    assert srv.admitted_while_running == 3
+    srv.uploading = [(r, n, uploads_done) for (r, n, e) in srv.uploading]
+    srv._launch()  # the device is busy: they wait
+    assert srv.batch_sizes == [1] and len(srv.uploading) == 3
+    _HeldEvent.held = False
+    srv.tick()     # batch 0 completes; the three go together
+    assert srv.batch_sizes == [1, 3]
+    srv.drain(timeout_s=10.0)
+    assert sorted(r.rid for r in srv.done) == [0, 1, 2, 3]
+    assert all(r.status == 0 and r.outputs is not None for r in srv.done)
