@@ -806,10 +806,12 @@ def run_unfused(sets, interp, stream, world, local):
                                                      dtype=dt, out=bufs.get("cal"),
                                                      ws=bufs.get("ws"))
             bufs["cal"] = cal
-            st, va, bufs["sws"] = core.shift(cal, s.dx, s.dy, interp, dtype=dt, scale=sc,
-                                             offset=of, out=bufs.get("st"), ws=bufs.get("sws"))
+            # invalid samples are NaN in the stack: no separate validity mask
+            st, _, bufs["sws"] = core.shift(cal, s.dx, s.dy, interp, dtype=dt, scale=sc,
+                                            offset=of, out=bufs.get("st"), want_valid=False,
+                                            ws=bufs.get("sws"))
             bufs["st"] = st
-            bufs["out"] = core.combine(st, dtype=dt, scale=sc, offset=of, valid=va,
+            bufs["out"] = core.combine(st, dtype=dt, scale=sc, offset=of,
                                        clip=core.clip_params(3.0, 3))
 
         total_ms, _, prof, _ = timed_steps(step, 3, 1, stream, None, world, local)

@@ -697,9 +697,22 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
         norm_rb = std::max(norm_rb, (s.H + R - 1) / R);
       }
       if (S.spath) {
-        nrows += ((s.n + kRowGroup - 1) / kRowGroup) * ((s.H + row_block(row_e) - 1) / row_block(row_e));
+        // frames per row-pass work item: up to kRowGroup, fewer when the
+        // set's row blocks times its frame groups would not fill the GPU twice
+        // with two CTAs per SM (each work item re-reads its block's masters)
+        const int nrb = (s.H + row_block(row_e) - 1) / row_block(row_e);
+        int rg = kRowGroup;
+        while (rg > 1 && (int64_t)nrb * ((s.n + rg - 1) / rg) < 4 * (int64_t)sm_count())
+          rg = (rg + 1) / 2;
+        S.rgroup = std::min(rg, s.n);
+        nrows += ((s.n + S.rgroup - 1) / S.rgroup) * nrb;
         if (!gtile) ncolsegs += s.n * ((s.W + 28) / 29) * ((s.H + kColRows - 1) / kColRows);
       }
+      // premerged master window {bias + dark*t, rf}: raw sources of one
+      // exposure time without a bad-pixel mask or saturation level
+      bool one_t = true;
+      for (int k = 1; k < s.n; ++k) one_t = one_t && s.exptime[k] == s.exptime[0];
+      if (stencil != ST_BSPLINE && !S.masked && one_t) S.mflags |= 2;
       int oxmin = INT32_MAX, oxmax = INT32_MIN, oymin = INT32_MAX, oymax = INT32_MIN;
       for (int k = 0; k < s.n; ++k) {
         FrameDesc& F = fd[frame0 + k];
@@ -728,10 +741,11 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
         oymin = std::min(oymin, F.oy);
         oymax = std::max(oymax, F.oy);
       }
-      // master union window over all frames' taps ({bias, dark, 1/flat}, 16 B each),
-      // kept unless the offsets are so spread that it would exceed 64 KB
+      // master union window over all frames' taps ({bias, dark, 1/flat, mask},
+      // 16 B each, or premerged), kept unless the offsets are so spread that
+      // it would exceed 64 KB
       const int mw = 32 + (oxmax - oxmin), mh = THr + (oymax - oymin) + taps - 1;
-      if (stencil != ST_BSPLINE && (size_t)mw * mh * 16 <= (size_t)64 * 1024) {
+      if (stencil != ST_BSPLINE && mw * mh <= kMaxWindowPx) {
         S.mwin_w = mw;
         S.mwin_h = mh;
         S.mox = oxmin;
@@ -759,7 +773,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     h->ddof = p->clip.ddof;
     h->frame_norm = p->frame_norm;
     h->smem_samples = stack_only ? 0 : max_n * THr * 32;
-    h->smem_master = mw_max * mh_max;  // float4 entries
+    h->smem_master = master_window_f4(mw_max, mh_max);  // float4 entries
     h->status = &wsh->status;
     h->counter = &wsh->counters[gi];
     SubInfo& si = pf->sub[gi];
@@ -844,7 +858,7 @@ irp_status run_tile_subplan(const uint8_t* buf, const SubInfo& si, const InlineP
     if (b == a + 1 && bytes > kL2Budget) {
       // one set in stripes of rows
       const SetDesc& S = sd[a];
-      const int ngroups = (S.n + kRowGroup - 1) / kRowGroup;
+      const int ngroups = (S.n + S.rgroup - 1) / S.rgroup;
       const int nrb = (S.H + RB - 1) / RB;
       int oymin = INT32_MAX, oymax = INT32_MIN;
       for (int k = 0; k < S.n; ++k) {
@@ -1253,12 +1267,19 @@ irp_status irp_calibrate(const uint16_t* raw, int64_t raw_pitch, int64_t raw_fra
            master_pitch % 4 == 0 && aligned(bias, 16) && aligned(dark_rate, 16) &&
            aligned(flat, 16) && out_pitch % 4 == 0 && out_frame_stride % 4 == 0 &&
            aligned(out, dt == IRP_F32 ? 16 : 8)) ? 1 : 0;
+  // eight pixels per thread over all frames of a launch when every row of
+  // every operand starts on an 8-pixel boundary (16-byte vectors)
+  const size_t oes = dt == IRP_F32 ? 4 : 2;
+  const bool vec8 = W % 8 == 0 && raw_pitch % 8 == 0 && raw_frame_stride % 8 == 0 &&
+                    aligned(raw, 16) && master_pitch % 4 == 0 && aligned(bias, 16) &&
+                    aligned(dark_rate, 16) && aligned(flat, 16) && aligned(out, 16) &&
+                    (out_pitch * (int64_t)oes) % 16 == 0 && (out_frame_stride * (int64_t)oes) % 16 == 0;
   for (int k0 = 0; k0 < n; k0 += kCalibChunk) {
     const int nk = std::min(kCalibChunk, n - k0);
     a.k0 = k0;
     for (int j = 0; j < nk; ++j) a.t[j] = exptime_host[k0 + j];
     if (dt == IRP_F16_SCALED) {
-      e = launch_stats_raw(a, nk, st, s);
+      e = vec8 ? launch_f16_stats8(a, nk, st, s) : launch_stats_raw(a, nk, st, s);
       if (e != cudaSuccess) return note_cuda(e);
     }
   }
@@ -1270,8 +1291,10 @@ irp_status irp_calibrate(const uint16_t* raw, int64_t raw_pitch, int64_t raw_fra
     const int nk = std::min(kCalibChunk, n - k0);
     a.k0 = k0;
     for (int j = 0; j < nk; ++j) a.t[j] = exptime_host[k0 + j];
-    e = launch_calibrate(a, nk, dt == IRP_F16_SCALED, out, out_pitch, out_frame_stride, scale_out,
-                         offset_out, s);
+    e = vec8 ? launch_calibrate8(a, nk, dt == IRP_F16_SCALED, out, out_pitch, out_frame_stride,
+                                 scale_out, offset_out, s)
+             : launch_calibrate(a, nk, dt == IRP_F16_SCALED, out, out_pitch, out_frame_stride,
+                                scale_out, offset_out, s);
     if (e != cudaSuccess) return note_cuda(e);
   }
   return IRP_OK;
@@ -1345,6 +1368,8 @@ irp_status irp_shift(const void* in, int64_t in_pitch, int64_t in_frame_stride, 
   sa.out_fstride = out_frame_stride;
   sa.valid_out = valid_out;
   sa.coef_pitch = coef_pitch(W);
+  const int vec = (aligned(out, 4 * es) && out_pitch % 4 == 0 && out_frame_stride % 4 == 0 &&
+                   (!valid_out || aligned(valid_out, 4))) ? 1 : 0;
   for (int k0 = 0; k0 < n; k0 += kShiftChunk) {
     const int nk = std::min(kShiftChunk, n - k0);
     sa.k0 = k0;
@@ -1376,7 +1401,7 @@ irp_status irp_shift(const void* in, int64_t in_pitch, int64_t in_frame_stride, 
       for (int j = 0; j < nk; ++j) inl.frames[j] = sa.frames[j];
       e = launch_prefilter_frames(&inl, inl.h.npitems, f16, s);
     }
-    if (e == cudaSuccess) e = launch_shift(sa, nk, stencil, f16, s);
+    if (e == cudaSuccess) e = launch_shift(sa, nk, stencil, f16, vec, s);
     if (e != cudaSuccess) return note_cuda(e);
   }
   return IRP_OK;

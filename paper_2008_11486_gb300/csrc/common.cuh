@@ -98,14 +98,15 @@ struct SetDesc {
   int64_t crow_pitch;            // row-pass coefficient frames (spath 1)
   int32_t row0;                  // first row-pass work item (row block x frame chunk)
   int32_t colseg0;               // first column-pass work item
-  int32_t mflags;                // bit 0: masters 16-byte aligned, pitch of 4k elements
+  int32_t mflags;                // bit 0: masters 16-byte aligned, pitch of 4k elements;
+                                 // bit 1: premerged master window (one exposure time, no mask)
   int32_t spath;                 // spline prefilter: 0 tiled, 1 row + column passes
   const uint8_t* mask;           // bad-pixel mask master or null
   int64_t mask_pitch;
   float saturation;              // raw level marking a pixel bad (+inf: none)
   int32_t masked;                // 1: mask or saturation level in use
   int32_t stack_only;            // 1: write stack_out only (a chunk of a deeper set)
-  int32_t pad;
+  int32_t rgroup;                // frames per row-pass work item (at most kRowGroup)
   int64_t bad_pitch;             // words per row of the bad-pixel bits (masked spline sets)
   const FrameNorm* norm_ref;     // normalisation record of the set's first frame, or null
 };

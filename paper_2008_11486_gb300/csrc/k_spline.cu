@@ -7,7 +7,8 @@
 // y+[i] = v[i] + z1 y+[i-1] and y-[i] = v[i] + z1 y-[i+1], z1 = sqrt(3) - 2.
 //
 // Row pass: one CTA per block of rows (4, or 2 for frames wider than 1024)
-// and chunk of kRowGroup frames.  The block's master rows are copied into
+// and chunk of at most kRowGroup frames (fewer when a set has too few row
+// blocks to fill the GPU twice).  The block's master rows are copied into
 // shared memory asynchronously and 1/flat is formed in place; the warps take
 // the block's (row, frame) tasks round-robin and prefetch the next task's raw
 // row with cp.async while computing the current one.  Lane l calibrates and
@@ -90,11 +91,12 @@ __global__ void __launch_bounds__(256, 2)
   }
   const int W = S.W, H = S.H;
   // row block major, so that a range of row blocks is a range of work items
-  const int ngroups = (S.n + kRowGroup - 1) / kRowGroup;
+  const int rg = S.rgroup;
+  const int ngroups = (S.n + rg - 1) / rg;
   const int local = item - S.row0;
   const int rb = local / ngroups, g = local - rb * ngroups;  // row block, frame chunk
   const int y0 = rb * RB, nr = min(RB, H - y0);
-  const int k0 = g * kRowGroup, nk = min(kRowGroup, S.n - k0);
+  const int k0 = g * rg, nk = min(rg, S.n - k0);
   const int x0 = lane * E;
   // 1. the block's master rows, asynchronously (zero beyond the frame)
   {

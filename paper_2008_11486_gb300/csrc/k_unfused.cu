@@ -368,6 +368,264 @@ __global__ void __launch_bounds__(kThreads) k_calibrate(CalibArgs a, int nk, voi
 }
 
 // ---------------------------------------------------------------------------
+// Eight-pixel forms of the FP16 scaling sums and of calibration, for frames
+// whose rows (raw, masters and outputs) start on 8-pixel boundaries.  Block b
+// covers kSeg8 pixels of one row (eight consecutive pixels per thread) in
+// every frame of the launch: the masters and flat_norm/flat are read and
+// formed once per pixel, not once per frame, and kFrames8 frames' raw
+// vectors are requested before any of them is used.
+// ---------------------------------------------------------------------------
+constexpr int kSeg8 = 8 * kThreads;
+constexpr int kFrames8 = 4;
+
+struct Masters8 {
+  float b[8], d[8], rf[8];
+};
+
+__device__ __forceinline__ void load_masters8(const CalibArgs& a, int64_t mo, float flat_norm,
+                                              Masters8& m) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float4 b = __ldg((const float4*)(a.bias + mo) + h);
+    const float4 d = __ldg((const float4*)(a.dark + mo) + h);
+    const float4 f = __ldg((const float4*)(a.flat + mo) + h);
+    const float bb[4] = {b.x, b.y, b.z, b.w}, dd[4] = {d.x, d.y, d.z, d.w},
+                ff[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      m.b[4 * h + e] = bb[e];
+      m.d[4 * h + e] = dd[e];
+      m.rf[4 * h + e] = inv_flat(ff[e], flat_norm, a.status);
+    }
+  }
+}
+
+// The eight calibrated values of one raw vector (pixel e in the low half of
+// word e / 2 for even e).
+__device__ __forceinline__ void calibrate8(const uint4& q, const Masters8& m, float t,
+                                           float (&v)[8]) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const float r = (e & 1) ? u16_hi_to_float(w[e >> 1]) : u16_lo_to_float(w[e >> 1]);
+    v[e] = calibrate_pxf(r, m.b[e], m.d[e], t, m.rf[e]);
+  }
+}
+
+// The sums that choose each frame's FP16 scaling: sum, minimum and maximum of
+// the calibrated frame.  Each thread adds its eight values in FP32, the warp
+// adds its 32 partials in FP32 (256 pixels), and the block's eight warp sums
+// are added in FP64 and into the frame's FP64 sum.
+__global__ void __launch_bounds__(kThreads) k_f16_stats8(CalibArgs a, int nk, FrameStats* st) {
+  const int nseg = (a.W + kSeg8 - 1) / kSeg8;
+  const int y = blockIdx.x / nseg;
+  const int xs = (blockIdx.x - y * nseg) * kSeg8;
+  const int x = xs + 8 * threadIdx.x;
+  const bool act = x < a.W;
+  const float flat_norm = a.flat_sum ? (float)(*a.flat_sum / ((double)a.W * a.H)) : 1.0f;
+  Masters8 m;
+  if (act) load_masters8(a, (int64_t)y * a.master_pitch + x, flat_norm, m);
+  const uint16_t* rr = a.raw + (int64_t)a.k0 * a.raw_frame_stride + (int64_t)y * a.raw_pitch + x;
+  const unsigned long long npx = (unsigned long long)min(kSeg8, a.W - xs);
+  __shared__ float sh[kThreads / 32][3 * kFrames8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k0 = 0; k0 < nk; k0 += kFrames8) {
+    uint4 q[kFrames8];
+#pragma unroll
+    for (int j = 0; j < kFrames8; ++j)
+      q[j] = (act && k0 + j < nk) ? __ldg((const uint4*)(rr + (int64_t)(k0 + j) * a.raw_frame_stride))
+                                  : make_uint4(0u, 0u, 0u, 0u);
+    float acc[3 * kFrames8];  // per frame: sum, minimum, maximum
+#pragma unroll
+    for (int j = 0; j < kFrames8; ++j) {
+      float sm = 0.0f, mn = FLT_MAX, mx = -FLT_MAX;
+      if (act && k0 + j < nk) {
+        float v[8];
+        calibrate8(q[j], m, a.t[k0 + j], v);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          sm = __fadd_rn(sm, v[e]);
+          mn = fminf(mn, v[e]);
+          mx = fmaxf(mx, v[e]);
+        }
+      }
+      acc[3 * j] = sm;
+      acc[3 * j + 1] = mn;
+      acc[3 * j + 2] = mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int j = 0; j < kFrames8; ++j) {
+        acc[3 * j] = __fadd_rn(acc[3 * j], __shfl_down_sync(0xffffffffu, acc[3 * j], o));
+        acc[3 * j + 1] = fminf(acc[3 * j + 1], __shfl_down_sync(0xffffffffu, acc[3 * j + 1], o));
+        acc[3 * j + 2] = fmaxf(acc[3 * j + 2], __shfl_down_sync(0xffffffffu, acc[3 * j + 2], o));
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < 3 * kFrames8; ++i) sh[warp][i] = acc[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < kFrames8 && k0 + (int)threadIdx.x < nk) {
+      const int j = threadIdx.x;
+      double sm = 0.0;
+      float mn = FLT_MAX, mx = -FLT_MAX;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        sm += (double)sh[w][3 * j];
+        mn = fminf(mn, sh[w][3 * j + 1]);
+        mx = fmaxf(mx, sh[w][3 * j + 2]);
+      }
+      FrameStats& f = st[a.k0 + k0 + j];
+      atomicAdd(&f.sum, sm);
+      atomicAdd((unsigned long long*)&f.count, npx);
+      atomicMin(&f.min_key, float_key(mn));
+      atomicMax(&f.max_key, float_key(mx));
+    }
+    __syncthreads();
+  }
+}
+
+template <bool F16>
+__global__ void __launch_bounds__(kThreads) k_calibrate8(CalibArgs a, int nk, void* out,
+                                                         int64_t out_pitch, int64_t out_fstride,
+                                                         const float* scale,
+                                                         const float* offset) {
+  const int nseg = (a.W + kSeg8 - 1) / kSeg8;
+  const int y = blockIdx.x / nseg;
+  const int x = (blockIdx.x - y * nseg) * kSeg8 + 8 * threadIdx.x;
+  if (x >= a.W) return;
+  const float flat_norm = a.flat_sum ? (float)(*a.flat_sum / ((double)a.W * a.H)) : 1.0f;
+  Masters8 m;
+  load_masters8(a, (int64_t)y * a.master_pitch + x, flat_norm, m);
+  const uint16_t* rr = a.raw + (int64_t)a.k0 * a.raw_frame_stride + (int64_t)y * a.raw_pitch + x;
+  for (int k0 = 0; k0 < nk; k0 += kFrames8) {
+    uint4 q[kFrames8];
+#pragma unroll
+    for (int j = 0; j < kFrames8; ++j)
+      if (k0 + j < nk) q[j] = __ldg((const uint4*)(rr + (int64_t)(k0 + j) * a.raw_frame_stride));
+#pragma unroll
+    for (int j = 0; j < kFrames8; ++j) {
+      if (k0 + j >= nk) break;
+      const int k = a.k0 + k0 + j;
+      float v[8];
+      calibrate8(q[j], m, a.t[k0 + j], v);
+      const int64_t o = (int64_t)k * out_fstride + (int64_t)y * out_pitch + x;
+      if (F16) {
+        const float inv = __frcp_rn(__ldg(scale + k));  // exact: a power of two
+        const float off = __ldg(offset + k);
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const __half lo = __float2half_rn(__fmul_rn(__fsub_rn(v[2 * e], off), inv));
+          const __half hi = __float2half_rn(__fmul_rn(__fsub_rn(v[2 * e + 1], off), inv));
+          w[e] = (uint32_t)__half_as_ushort(lo) | ((uint32_t)__half_as_ushort(hi) << 16);
+        }
+        *(uint4*)((__half*)out + o) = make_uint4(w[0], w[1], w[2], w[3]);
+      } else {
+        float4* po = (float4*)((float*)out + o);
+        po[0] = make_float4(v[0], v[1], v[2], v[3]);
+        po[1] = make_float4(v[4], v[5], v[6], v[7]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Shift, four output pixels per thread (nearest, bilinear).  The taps of four
+// neighbouring outputs overlap, so each tap of a row is read once for the
+// four (five reads per row for bilinear instead of eight); taps of zero
+// weight and taps only invalid outputs would use are not read.  The outputs
+// (and validity bytes) leave as one vector store when vec is set and the
+// four lie inside the row.  Each output is the value k_shift gives.
+// ---------------------------------------------------------------------------
+template <int ST, bool F16>
+__global__ void __launch_bounds__(kThreads) k_shift4(ShiftArgs a, int vec) {
+  const int x0 = 4 * (blockIdx.x * kThreads + threadIdx.x);
+  const int y = blockIdx.y;
+  const int kl = blockIdx.z;
+  if (x0 >= a.W) return;
+  const FrameDesc& F = a.frames[kl];
+  const int k = a.k0 + kl;
+  const bool yok = (y >= F.vy0) & (y <= F.vy1);
+  bool ok[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int x = x0 + c;
+    ok[c] = yok & (x >= F.vx0) & (x <= F.vx1) & (x < a.W);
+  }
+  const int i0 = x0 + F.ox, j0 = y + F.oy;
+  auto at = [&](int i, int j) -> float {
+    const int64_t o = (int64_t)k * a.in_fstride + (int64_t)j * a.in_pitch + i;
+    if (F16) return __half2float(((const __half*)a.in)[o]);
+    return __ldg((const float*)a.in + o);
+  };
+  float val[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) val[c] = __int_as_float(0x7fc00000);
+  if (ST == ST_NEAREST) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (ok[c]) val[c] = at(i0 + c, j0);
+  } else {
+    const float fx = F.fx, fy = F.fy;
+    const bool hx = fx != 0.0f, hy = fy != 0.0f;
+    // column c of the taps serves output c (weight 1 - fx) and output c - 1
+    // (weight fx)
+    bool need[5];
+    need[0] = ok[0];
+#pragma unroll
+    for (int c = 1; c < 4; ++c) need[c] = ok[c] || (hx && ok[c - 1]);
+    need[4] = hx && ok[3];
+    float r0[5], r1[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      r0[c] = need[c] ? at(i0 + c, j0) : 0.0f;
+      r1[c] = (need[c] && hy) ? at(i0 + c, j0 + 1) : 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (!ok[c]) continue;
+      const float p00 = r0[c];
+      const float p10 = hx ? r0[c + 1] : p00;
+      const float h0 = __fmaf_rn(fx, __fsub_rn(p10, p00), p00);
+      float h1 = h0;
+      if (hy) {
+        const float p01 = r1[c];
+        const float p11 = hx ? r1[c + 1] : p01;
+        h1 = __fmaf_rn(fx, __fsub_rn(p11, p01), p01);
+      }
+      val[c] = __fmaf_rn(fy, __fsub_rn(h1, h0), h0);
+    }
+  }
+  const int64_t o = (int64_t)k * a.out_fstride + (int64_t)y * a.out_pitch + x0;
+  if (vec && x0 + 3 < a.W) {
+    if (F16) {
+      const uint32_t w0 = (uint32_t)__half_as_ushort(__float2half_rn(val[0])) |
+                          ((uint32_t)__half_as_ushort(__float2half_rn(val[1])) << 16);
+      const uint32_t w1 = (uint32_t)__half_as_ushort(__float2half_rn(val[2])) |
+                          ((uint32_t)__half_as_ushort(__float2half_rn(val[3])) << 16);
+      *(uint2*)((__half*)a.out + o) = make_uint2(w0, w1);
+    } else {
+      *(float4*)((float*)a.out + o) = make_float4(val[0], val[1], val[2], val[3]);
+    }
+    if (a.valid_out)
+      *(uint32_t*)(a.valid_out + o) = (ok[0] ? 1u : 0u) | (ok[1] ? 0x100u : 0u) |
+                                      (ok[2] ? 0x10000u : 0u) | (ok[3] ? 0x1000000u : 0u);
+    return;
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (x0 + c >= a.W) break;
+    if (F16)
+      ((__half*)a.out)[o + c] = __float2half_rn(val[c]);
+    else
+      ((float*)a.out)[o + c] = val[c];
+    if (a.valid_out) a.valid_out[o + c] = ok[c] ? 1 : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Shift (Sec. 2.1 alignment) of calibrated frames, one thread per output
 // pixel; taps are read from the frame (nearest, bilinear) or from the frame's
 // spline coefficients (cubic spline, mirror-extended).
@@ -565,6 +823,27 @@ cudaError_t launch_f16_scaling(const FrameStats* st, int n, float* scale, float*
   return cudaGetLastError();
 }
 
+cudaError_t launch_f16_stats8(const CalibArgs& a, int nk, FrameStats* st, cudaStream_t s) {
+  const int64_t grid = (int64_t)((a.W + kSeg8 - 1) / kSeg8) * a.H;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  k_f16_stats8<<<(unsigned)grid, kThreads, 0, s>>>(a, nk, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_calibrate8(const CalibArgs& a, int nk, bool f16, void* out, int64_t out_pitch,
+                              int64_t out_fstride, const float* scale, const float* offset,
+                              cudaStream_t s) {
+  const int64_t grid = (int64_t)((a.W + kSeg8 - 1) / kSeg8) * a.H;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (f16)
+    k_calibrate8<true><<<(unsigned)grid, kThreads, 0, s>>>(a, nk, out, out_pitch, out_fstride,
+                                                           scale, offset);
+  else
+    k_calibrate8<false><<<(unsigned)grid, kThreads, 0, s>>>(a, nk, out, out_pitch, out_fstride,
+                                                            scale, offset);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_calibrate(const CalibArgs& a, int nk, bool f16, void* out, int64_t out_pitch,
                              int64_t out_fstride, const float* scale, const float* offset,
                              cudaStream_t s) {
@@ -590,10 +869,21 @@ static cudaError_t shift_st(const ShiftArgs& a, int nk, bool f16, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_shift(const ShiftArgs& a, int nk, int stencil, bool f16, cudaStream_t s) {
+template <int ST>
+static cudaError_t shift4_st(const ShiftArgs& a, int nk, bool f16, int vec, cudaStream_t s) {
+  dim3 grid((a.W + 4 * kThreads - 1) / (4 * kThreads), a.H, nk);
+  if (f16)
+    k_shift4<ST, true><<<grid, kThreads, 0, s>>>(a, vec);
+  else
+    k_shift4<ST, false><<<grid, kThreads, 0, s>>>(a, vec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift(const ShiftArgs& a, int nk, int stencil, bool f16, int vec,
+                         cudaStream_t s) {
   switch (stencil) {
-    case ST_NEAREST: return shift_st<ST_NEAREST>(a, nk, f16, s);
-    case ST_BILINEAR: return shift_st<ST_BILINEAR>(a, nk, f16, s);
+    case ST_NEAREST: return shift4_st<ST_NEAREST>(a, nk, f16, vec, s);
+    case ST_BILINEAR: return shift4_st<ST_BILINEAR>(a, nk, f16, vec, s);
     case ST_CUBIC: return shift_st<ST_CUBIC>(a, nk, f16, s);
     default: return shift_st<ST_BSPLINE>(a, nk, f16, s);
   }

@@ -8,9 +8,11 @@
 //      chunks, zero-filled outside the frame), so S-1 frames are in flight
 //      while frame k is computed;
 //   2. calibrate (raw source): lane l holds source column l of the window and
-//      computes v = ((raw - bias) - dark*t) * (flat_norm/flat) in registers,
+//      computes v = (raw - (bias + dark*t)) * (flat_norm/flat) in registers,
 //      the masters coming from a union window in shared memory that is loaded
-//      once per tile (Sec. 2.1 calibration);
+//      once per tile (Sec. 2.1 calibration); for a set of one exposure time
+//      and no bad-pixel mask the window holds {bias + dark*t, flat_norm/flat}
+//      (8 bytes a pixel) instead of {bias, dark, flat_norm/flat, mask};
 //   3. resample: the stencil's horizontal taps come from the neighbouring
 //      lanes by warp shuffles, the vertical taps from the lane's own rows
 //      (nearest, bilinear, Keys' 4x4 cubic convolution, or the 4x4 cubic
@@ -67,17 +69,22 @@ __device__ __forceinline__ float u16_hi_to_float(uint32_t w) {
   return __fsub_rn(__int_as_float(__byte_perm(w, 0x4B00u, 0x5432u)), 8388608.0f);
 }
 
+// Calibration of one pixel: (raw - (bias + dark*t)) * (flat_norm/flat).  The
+// level removed from the raw count, bias + dark*t, is one correctly rounded
+// fma, so that the frames of one exposure time can share it (the premerged
+// master window of the fused kernel gives bit-identical values).
+__device__ __forceinline__ float calib_level(float bias, float dark, float t) {
+  return __fmaf_rn(dark, t, bias);
+}
+
 __device__ __forceinline__ float calibrate_pxf(float rawf, float bias, float dark, float t,
                                                float rf) {
-  const float s = __fmaf_rn(-dark, t, __fsub_rn(rawf, bias));
-  return __fmul_rn(s, rf);
+  return __fmul_rn(__fsub_rn(rawf, calib_level(bias, dark, t)), rf);
 }
 
 __device__ __forceinline__ float calibrate_px(uint16_t raw, float bias, float dark, float t,
                                               float rf) {
-  // (raw - bias) - dark*t, then times flat_norm/flat
-  const float s = __fmaf_rn(-dark, t, __fsub_rn(u16_to_float(raw), bias));
-  return __fmul_rn(s, rf);
+  return calibrate_pxf(u16_to_float(raw), bias, dark, t, rf);
 }
 
 // ------------------------------------------------------------------ cp.async
@@ -124,12 +131,15 @@ struct StencilShape {
 __host__ __device__ constexpr int rows_per_warp_default(int nmax) { return nmax <= 16 ? 4 : 2; }
 __host__ __device__ constexpr int rows_per_warp_alt(int nmax) { return nmax <= 16 ? 2 : 1; }
 
-// cp.async ring depth (frames in flight); 6 or 8 stages measured no faster
-// on 32 x 4096^2 (2.15 ms with 8 against 2.09 ms with 4).
-__host__ __device__ constexpr int stage_count(int src, int stencil) {
-  (void)src;
+// Interior tiles of raw sources with at most 2 output rows per warp take the
+// frames two at a time (more independent work per warp between waits).
+__host__ __device__ constexpr bool pair_frames(int src, int py) { return src == SRC_RAW && py <= 2; }
+
+// cp.async ring depth: 6 stages when the frames go in pairs (four frames in
+// flight while a pair is computed), else 4 (three in flight while a frame is).
+__host__ __device__ constexpr int stage_count(int src, int stencil, int py) {
   (void)stencil;
-  return 4;
+  return pair_frames(src, py) ? 6 : 4;
 }
 constexpr int kRawChunks = 5;        // 16-byte chunks per staged raw row (40 uint16)
 constexpr int kCoefChunks = 9;       // 16-byte chunks per staged coefficient row (36 floats)
@@ -147,6 +157,17 @@ struct StageShape {
   static constexpr int bytes = rows * chunks * 16;                  // per stage
 };
 
+// Frame records per CTA: 144 bytes each (9 x 16), so that the 16-byte stores
+// of consecutive records fall into distinct bank groups.
+constexpr int kRecBytes = 144;
+
+// Float4 entries reserved for a master union window of w x h pixels: the
+// {bias, dark, rf, mask} window (16 bytes a pixel), or the premerged
+// {bias + dark*t, rf} window (8 bytes a pixel) and, before it is formed, the
+// planar copies of the three masters (12 bytes a pixel).
+__host__ __device__ constexpr int master_window_f4(int w, int h) { return w * h; }
+constexpr int kMaxWindowPx = 4096;  // 64 KB of float4 entries
+
 // Shared memory per CTA of the fused kernel (host helper mirrors this).
 __host__ __device__ inline size_t fused_smem_bytes(int src, int stencil, int py, int max_n,
                                                    int mwin_w, int mwin_h) {
@@ -154,16 +175,16 @@ __host__ __device__ inline size_t fused_smem_bytes(int src, int stencil, int py,
                        ? 4 : (stencil == ST_BILINEAR ? 2 : 1);
   const int rows = py + taps - 1;
   const int chunks = stage_chunks(src, stencil);
-  const size_t stage = (size_t)stage_count(src, stencil) * rows * chunks * 16 * (kThreads / 32);
+  const size_t stage = (size_t)stage_count(src, stencil, py) * rows * chunks * 16 * (kThreads / 32);
   const size_t samples = (size_t)max_n * (8 * py) * 32 * sizeof(float);
-  const size_t masters = (size_t)mwin_w * mwin_h * sizeof(float4);
-  const size_t descs = (size_t)max_n * sizeof(FrameDesc);
+  const size_t masters = (size_t)master_window_f4(mwin_w, mwin_h) * sizeof(float4);
+  const size_t descs = (size_t)max_n * kRecBytes;
   return samples + stage + masters + descs;
 }
 
 // ------------------------------------------------------------------ staging
 // What the frame loop needs of one frame for the current tile, built once per
-// tile in shared memory (128 bytes).  The fields the loop reads every frame
+// tile in shared memory (kRecBytes).  The fields the loop reads every frame
 // are grouped into 16-byte vectors, so each group is one broadcast load.
 struct FrameRec {
   // compute: tile's first source column inside the staged row, union-window
@@ -179,9 +200,9 @@ struct FrameRec {
   int ybase, xa, flags, last_tap;  // first staged row / aligned first staged column;
                               // FrameDesc::last_tap
   float na, nz;               // per-frame normalisation: sample = fma(sample, na, nz)
-  int pad2[2];
+  int pad2[6];
 };
-static_assert(sizeof(FrameRec) == 128, "FrameRec layout");
+static_assert(sizeof(FrameRec) == kRecBytes, "FrameRec layout");
 
 // flags: bit 0 = raw frame 16-byte aligned with a pitch of 8k elements;
 // bit 1 = the tile's whole staging window (rows x elems from (ybase, xa)) lies
@@ -239,7 +260,7 @@ __device__ __forceinline__ FrameRec make_rec(const FrameDesc& F, int tx0, int ty
   }
   R.na = F.norm ? F.norm->na : 1.0f;
   R.nz = F.norm ? F.norm->nz : 0.0f;
-  R.pad2[0] = R.pad2[1] = 0;
+  for (int i = 0; i < 6; ++i) R.pad2[i] = 0;
   return R;
 }
 
@@ -317,14 +338,18 @@ __device__ __forceinline__ void issue_stage_inside(const FrameRec& R,
   for (int it = 0; it < kIt; ++it) cp_async16_if(L.has[it], stage + L.soff[it], base + L.goff[it], 16);
 }
 
-// The union window of the masters for this tile as {bias, dark, rf}: the
-// three masters are copied asynchronously into the float4 slots (zero outside
-// the frame), then finish_masters turns the flat into flat_norm/flat.
+// The union window of the masters for this tile.  Unpacked: the three
+// masters are copied asynchronously into the float4 slots {bias, dark, rf,
+// mask} (zero outside the frame), then finish_masters turns the flat into
+// flat_norm/flat and sets the mask flag.  Packed (pk): they are copied into
+// three planar arrays, which finish_masters reads and then overwrites with
+// the float2 window {bias + dark*t, flat_norm/flat}.
 __device__ __forceinline__ void issue_masters(const SetDesc& S, int tx0, int ty0,
-                                              float4* s_mast) {
-  const int mw = S.mwin_w, mh = S.mwin_h;
+                                              float4* s_mast, bool pk) {
+  const int mw = S.mwin_w, mh = S.mwin_h, np = mw * mh;
   const int gx0 = tx0 + S.mox, gy0 = ty0 + S.moy;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* const planar = (float*)s_mast;  // bias, dark, flat: np floats each
   for (int r = warp; r < mh; r += kThreads / 32) {
     const int gy = gy0 + r;
     const bool yin = gy >= 0 && gy < S.H;
@@ -333,98 +358,85 @@ __device__ __forceinline__ void issue_masters(const SetDesc& S, int tx0, int ty0
       const bool in = yin && gx >= 0 && gx < S.W;
       const int64_t o = in ? (int64_t)gy * S.master_pitch + gx : 0;
       const int nb = in ? 4 : 0;
-      float* d = (float*)(s_mast + r * mw + c);
-      cp_async4(d + 0, S.bias + o, nb);
-      cp_async4(d + 1, S.dark + o, nb);
-      cp_async4(d + 2, S.flat + o, nb);
+      const int e = r * mw + c;
+      if (pk) {
+        cp_async4(planar + e, S.bias + o, nb);
+        cp_async4(planar + np + e, S.dark + o, nb);
+        cp_async4(planar + 2 * np + e, S.flat + o, nb);
+      } else {
+        float* d = (float*)(s_mast + e);
+        cp_async4(d + 0, S.bias + o, nb);
+        cp_async4(d + 1, S.dark + o, nb);
+        cp_async4(d + 2, S.flat + o, nb);
+      }
     }
   }
 }
 
+// Called by all threads of the CTA after the masters' copies have landed;
+// ends with the window complete (a CTA barrier inside).
 __device__ __forceinline__ void finish_masters(const SetDesc& S, int tx0, int ty0,
-                                               float flat_norm, float4* s_mast,
-                                               uint32_t* status) {
-  const int mw = S.mwin_w, mh = S.mwin_h;
+                                               float flat_norm, float4* s_mast, bool pk,
+                                               float t, uint32_t* status) {
+  const int mw = S.mwin_w, mh = S.mwin_h, np = mw * mh;
   const int gx0 = tx0 + S.mox, gy0 = ty0 + S.moy;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = warp; r < mh; r += kThreads / 32) {
-    const int gy = gy0 + r;
-    const bool yin = gy >= 0 && gy < S.H;
-    for (int c = lane; c < mw; c += 32) {
-      const int gx = gx0 + c;
-      float* d = (float*)(s_mast + r * mw + c);
-      const bool in = yin && gx >= 0 && gx < S.W;
-      if (in) d[2] = inv_flat(d[2], flat_norm, status);
-      // fourth component: 1 for a pixel the bad-pixel mask marks
-      d[3] = (in && S.mask && __ldg(S.mask + (int64_t)gy * S.mask_pitch + gx)) ? 1.0f : 0.0f;
+  if (pk) {
+    // every thread reads its pixels (threadIdx.x + kThreads * i) into
+    // registers, then, after a barrier, writes them to the window in place
+    constexpr int kPer = kMaxWindowPx / kThreads;
+    const float* const planar = (const float*)s_mast;
+    float lv[kPer], rf[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int e = threadIdx.x + kThreads * i;
+      lv[i] = rf[i] = 0.0f;
+      if (e < np) {
+        const int r = e / mw, c = e - r * mw;
+        const int gy = gy0 + r, gx = gx0 + c;
+        const bool in = gy >= 0 && gy < S.H && gx >= 0 && gx < S.W;
+        lv[i] = calib_level(planar[e], planar[np + e], t);
+        if (in) rf[i] = inv_flat(planar[2 * np + e], flat_norm, status);
+      }
     }
-  }
-}
-
-// One frame of the warp's strip: calibrate the staged source rows, resample
-// them to the strip's PY output rows, store the samples (+inf when invalid)
-// and count the valid ones per row.
-// MODE kFast: every sample of the tile valid, masters from the union window,
-// no stack output (the interior of a set: no validity tests or counts);
-// MODE kGeneral: validity per sample, masters and stack output decided per call.
-constexpr int kFast = 0, kGeneral = 1;
-
-template <int STENCIL, int SRC, int PY, int MODE>
-__device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
-                                           const float4* s_mast_w, int mrow, const SetDesc& S,
-                                           float flat_norm, uint32_t* status, int lane, int x,
-                                           int tx0, int wy0, float* sk, int (&mq)[PY],
-                                           float* stack_out, int k, int W, int H,
-                                           int64_t out_pitch, bool stack_lane, bool norm) {
-  using SS = StageShape<SRC, STENCIL, PY>;
-  const int4 g = *(const int4*)&F.off;      // off, mofs, vx0, vxw
-  const float4 w = *(const float4*)&F.fx;   // fx, fy, t
-  const int4 gy = *(const int4*)&F.vy0;     // vy0, vyw, ox, oy
-  float v[SS::rows];
-  bool bad[SS::rows];  // bad source pixels (mask or saturation), general mode only
+    __syncthreads();
 #pragma unroll
-  for (int r = 0; r < SS::rows; ++r) bad[r] = false;
-  const bool masked = MODE == kGeneral && S.masked;
-  if (SRC == SRC_RAW) {
-    const uint16_t* raw = (const uint16_t*)st + lane + g.x;
-    if (MODE == kFast || mrow > 0) {
-      const float4* mp = s_mast_w + g.y;
-#pragma unroll
-      for (int r = 0; r < SS::rows; ++r) {
-        const float4 m = mp[r * mrow];
-        const uint16_t q = raw[r * SS::elems];
-        v[r] = calibrate_px(q, m.x, m.y, w.z, m.z);
-        if (MODE == kGeneral) bad[r] = masked && (m.w != 0.0f || (float)q >= S.saturation);
-      }
-    } else {  // offsets too spread for a union window: masters from global memory
-      const int gx = tx0 + gy.z + lane;
-#pragma unroll
-      for (int r = 0; r < SS::rows; ++r) {
-        const int yy = wy0 + gy.w + r;
-        float b = 0.0f, d = 0.0f, rf = 0.0f;
-        bool mb = false;
-        if (gx >= 0 && gx < S.W && yy >= 0 && yy < S.H) {
-          const int64_t o = (int64_t)yy * S.master_pitch + gx;
-          b = __ldg(S.bias + o);
-          d = __ldg(S.dark + o);
-          rf = inv_flat(__ldg(S.flat + o), flat_norm, status);
-          mb = S.mask && __ldg(S.mask + (int64_t)yy * S.mask_pitch + gx);
-        }
-        const uint16_t q = raw[r * SS::elems];
-        v[r] = calibrate_px(q, b, d, w.z, rf);
-        bad[r] = masked && (mb || (float)q >= S.saturation);
-      }
+    for (int i = 0; i < kPer; ++i) {
+      const int e = threadIdx.x + kThreads * i;
+      if (e < np) ((float2*)s_mast)[e] = make_float2(lv[i], rf[i]);
     }
   } else {
-    const float* cf = (const float*)st + lane + g.x;
-#pragma unroll
-    for (int r = 0; r < SS::rows; ++r) v[r] = cf[r * SS::elems];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < mh; r += kThreads / 32) {
+      const int gy = gy0 + r;
+      const bool yin = gy >= 0 && gy < S.H;
+      for (int c = lane; c < mw; c += 32) {
+        const int gx = gx0 + c;
+        float* dp = (float*)(s_mast + r * mw + c);
+        const bool in = yin && gx >= 0 && gx < S.W;
+        const float rf = in ? inv_flat(dp[2], flat_norm, status) : 0.0f;
+        // fourth component: 1 for a pixel the bad-pixel mask marks
+        const float mb =
+            (in && S.mask && __ldg(S.mask + (int64_t)gy * S.mask_pitch + gx)) ? 1.0f : 0.0f;
+        *(float2*)(dp + 2) = make_float2(rf, mb);
+      }
+    }
   }
-  float a[PY];
+  __syncthreads();
+}
+
+// The stencil over the lane's calibrated source rows v: the PY samples of
+// the lane's output column (horizontal taps from the neighbouring lanes by
+// shuffles, vertical taps from the lane's own rows).
+template <int STENCIL, int SRC, int PY>
+__device__ __forceinline__ void resample_rows(const FrameRec& F,
+                                              const float (&v)[StageShape<SRC, STENCIL, PY>::rows],
+                                              float (&a)[PY]) {
+  using SS = StageShape<SRC, STENCIL, PY>;
   if (STENCIL == ST_NEAREST) {
 #pragma unroll
     for (int q = 0; q < PY; ++q) a[q] = v[q];
   } else if (STENCIL == ST_BILINEAR) {
+    const float2 w = *(const float2*)&F.fx;
     float hrow[SS::rows];
 #pragma unroll
     for (int r = 0; r < SS::rows; ++r) {
@@ -464,14 +476,117 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
       a[q] = __fmaf_rn(wy.w, hrow[q + 3], acc);
     }
   }
-  if (norm) {  // per-frame normalisation before the combine
+}
+
+// The lane's staged source rows of one frame of an interior tile (every
+// pixel inside the frame, no mask): raw sources calibrated with the premerged
+// window {bias + dark*t, rf} (PK = 1), coefficient sources as staged.
+template <int STENCIL, int SRC, int PY, int PK>
+__device__ __forceinline__ void load_rows_fast(const FrameRec& F, const uint8_t* st,
+                                               const void* s_mast_w, int mrow, int lane,
+                                               float (&v)[StageShape<SRC, STENCIL, PY>::rows]) {
+  static_assert(SRC != SRC_RAW || PK == 1, "interior raw tiles read the premerged window");
+  using SS = StageShape<SRC, STENCIL, PY>;
+  const int2 g = *(const int2*)&F.off;  // off, mofs
+  if (SRC == SRC_RAW) {
+    const uint16_t* raw = (const uint16_t*)st + lane + g.x;
+    const float2* mp = (const float2*)s_mast_w + g.y;
 #pragma unroll
-    for (int q = 0; q < PY; ++q) a[q] = __fmaf_rn(a[q], F.na, F.nz);
+    for (int r = 0; r < SS::rows; ++r) {
+      const float2 m = mp[r * mrow];
+      v[r] = __fmul_rn(__fsub_rn(u16_to_float(raw[r * SS::elems]), m.x), m.y);
+    }
+  } else {
+    const float* cf = (const float*)st + lane + g.x;
+#pragma unroll
+    for (int r = 0; r < SS::rows; ++r) v[r] = cf[r * SS::elems];
   }
-  if (MODE == kFast) {
+}
+
+// One frame of the warp's strip: calibrate the staged source rows, resample
+// them to the strip's PY output rows, store the samples (+inf when invalid)
+// and count the valid ones per row.
+// MODE kFast: every sample of the tile valid, masters from the union window,
+// no stack output (the interior of a set: no validity tests or counts);
+// MODE kGeneral: validity per sample, masters and stack output decided per call.
+// s_mast_w points at the warp's lane in the union window: float4 entries, or
+// float2 entries when the window is premerged (PK = 1, or PK = 2 with pk set).
+constexpr int kFast = 0, kGeneral = 1;
+
+template <int STENCIL, int SRC, int PY, int MODE, int PK>
+__device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
+                                           const void* s_mast_w, int mrow, bool pk,
+                                           const SetDesc& S, float flat_norm, uint32_t* status,
+                                           int lane, int x, int tx0, int wy0, float* sk,
+                                           int (&mq)[PY], float* stack_out, int k, int W, int H,
+                                           int64_t out_pitch, bool stack_lane, bool norm) {
+  using SS = StageShape<SRC, STENCIL, PY>;
+  float v[SS::rows];
+  float a[PY];
+  if constexpr (MODE == kFast) {
+    load_rows_fast<STENCIL, SRC, PY, PK>(F, st, s_mast_w, mrow, lane, v);
+    resample_rows<STENCIL, SRC, PY>(F, v, a);
+    if (norm) {
+#pragma unroll
+      for (int q = 0; q < PY; ++q) a[q] = __fmaf_rn(a[q], F.na, F.nz);
+    }
 #pragma unroll
     for (int q = 0; q < PY; ++q) sk[q * 32] = a[q];
     return;
+  }
+  const int4 g = *(const int4*)&F.off;      // off, mofs, vx0, vxw
+  const float4 w = *(const float4*)&F.fx;   // fx, fy, t
+  const int4 gy = *(const int4*)&F.vy0;     // vy0, vyw, ox, oy
+  bool bad[SS::rows];  // bad source pixels (mask or saturation)
+#pragma unroll
+  for (int r = 0; r < SS::rows; ++r) bad[r] = false;
+  const bool masked = S.masked;
+  if (SRC == SRC_RAW) {
+    const uint16_t* raw = (const uint16_t*)st + lane + g.x;
+    if (mrow > 0 && (PK == 1 || (PK == 2 && pk))) {  // premerged window: never masked
+      const float2* mp = (const float2*)s_mast_w + g.y;
+#pragma unroll
+      for (int r = 0; r < SS::rows; ++r) {
+        const float2 m = mp[r * mrow];
+        v[r] = __fmul_rn(__fsub_rn(u16_to_float(raw[r * SS::elems]), m.x), m.y);
+      }
+    } else if (mrow > 0) {
+      const float4* mp = (const float4*)s_mast_w + g.y;
+#pragma unroll
+      for (int r = 0; r < SS::rows; ++r) {
+        const float4 m = mp[r * mrow];
+        const uint16_t q = raw[r * SS::elems];
+        v[r] = calibrate_px(q, m.x, m.y, w.z, m.z);
+        bad[r] = masked && (m.w != 0.0f || (float)q >= S.saturation);
+      }
+    } else {  // offsets too spread for a union window: masters from global memory
+      const int gx = tx0 + gy.z + lane;
+#pragma unroll
+      for (int r = 0; r < SS::rows; ++r) {
+        const int yy = wy0 + gy.w + r;
+        float b = 0.0f, d = 0.0f, rf = 0.0f;
+        bool mb = false;
+        if (gx >= 0 && gx < S.W && yy >= 0 && yy < S.H) {
+          const int64_t o = (int64_t)yy * S.master_pitch + gx;
+          b = __ldg(S.bias + o);
+          d = __ldg(S.dark + o);
+          rf = inv_flat(__ldg(S.flat + o), flat_norm, status);
+          mb = S.mask && __ldg(S.mask + (int64_t)yy * S.mask_pitch + gx);
+        }
+        const uint16_t q = raw[r * SS::elems];
+        v[r] = calibrate_px(q, b, d, w.z, rf);
+        bad[r] = masked && (mb || (float)q >= S.saturation);
+      }
+    }
+  } else {
+    const float* cf = (const float*)st + lane + g.x;
+#pragma unroll
+    for (int r = 0; r < SS::rows; ++r) v[r] = cf[r * SS::elems];
+  }
+  resample_rows<STENCIL, SRC, PY>(F, v, a);
+  if (norm) {  // per-frame normalisation before the combine
+#pragma unroll
+    for (int q = 0; q < PY; ++q) a[q] = __fmaf_rn(a[q], F.na, F.nz);
   }
   const float kInf = __int_as_float(0x7f800000);
   const bool xv = in_range(x, g.z, g.w);
@@ -528,9 +643,38 @@ __device__ __forceinline__ void frame_step(const FrameRec& F, const uint8_t* st,
   }
 }
 
+// Two frames of an interior tile at once: both frames' rows are loaded before
+// either is resampled and both results are stored last, so that the two
+// dependency chains interleave.
+template <int STENCIL, int SRC, int PY, int PK>
+__device__ __forceinline__ void frame_pair_fast(const FrameRec& F0, const FrameRec& F1,
+                                                const uint8_t* st0, const uint8_t* st1,
+                                                const void* s_mast_w, int mrow, int lane,
+                                                float* sk0, float* sk1, bool norm) {
+  using SS = StageShape<SRC, STENCIL, PY>;
+  float v0[SS::rows], v1[SS::rows];
+  load_rows_fast<STENCIL, SRC, PY, PK>(F0, st0, s_mast_w, mrow, lane, v0);
+  load_rows_fast<STENCIL, SRC, PY, PK>(F1, st1, s_mast_w, mrow, lane, v1);
+  float a0[PY], a1[PY];
+  resample_rows<STENCIL, SRC, PY>(F0, v0, a0);
+  resample_rows<STENCIL, SRC, PY>(F1, v1, a1);
+  if (norm) {
+#pragma unroll
+    for (int q = 0; q < PY; ++q) {
+      a0[q] = __fmaf_rn(a0[q], F0.na, F0.nz);
+      a1[q] = __fmaf_rn(a1[q], F1.na, F1.nz);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < PY; ++q) {
+    sk0[q * 32] = a0[q];
+    sk1[q * 32] = a1[q];
+  }
+}
+
 template <int NMAX, int STENCIL, int SRC, int PY>
 __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* smem) {
-  constexpr int kStages = stage_count(SRC, STENCIL);
+  constexpr int kStages = stage_count(SRC, STENCIL, PY);
   constexpr int TH = 8 * PY;
   constexpr int TW = StencilShape<STENCIL>::tw;
   using SS = StageShape<SRC, STENCIL, PY>;
@@ -568,7 +712,8 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
   // the masters' window first (one cp.async group), so that its latency
   // overlaps the frame records and the first frames' staging
   const bool uwin = SRC == SRC_RAW && mwin_w > 0;
-  if (uwin) issue_masters(S, tx0, ty0, s_mast);
+  const bool pk = uwin && (S.mflags & 2);  // premerged {bias + dark*t, rf} window
+  if (uwin) issue_masters(S, tx0, ty0, s_mast, pk);
   cp_async_commit();
   int rec_fast = 1;
   for (int k = threadIdx.x; k < n; k += kThreads) {
@@ -597,26 +742,44 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
   // the tile's class: interior tiles (every frame aligned, staged without
   // bounds checks and valid at every pixel) take the branch-free loop
   const bool tile_fast = __syncthreads_and(rec_fast) && (SRC != SRC_RAW || mwin_w > 0) &&
-                         !stack_out && !S.masked;
+                         !stack_out && !S.masked && !S.stack_only;
 
   const FrameRec* frames = s_rec;
   const bool norm = h.frame_norm != 0;
-  // prologue: frames 0 .. kStages-2 in flight
+  // interior tiles of raw sources with a premerged master window take the
+  // frames two at a time; those of several exposure times take the general
+  // loop
+  constexpr bool kPairs = pair_frames(SRC, PY) && kStages % 2 == 0 && kStages >= 4;
+  const bool pairs = kPairs && tile_fast && pk;
+  // prologue: frames 0 .. kStages-2 in flight, one group each (single
+  // steps), or frames 0 .. kStages-3 in groups of two (pairs); then wait for
+  // the masters' group, the oldest, alone and turn it into the window
+  if (pairs) {
 #pragma unroll
-  for (int k = 0; k < kStages - 1; ++k) {
-    if (k < n)
-      issue_stage<SRC, STENCIL, PY>(frames[k], LC, Hlim, Wlim, pitch, s_stage + k * SS::bytes,
-                                    lane, warp * PY);
-    cp_async_commit();
+    for (int j = 0; j < (kStages - 2) / 2; ++j) {
+      if (2 * j < n)
+        issue_stage_inside<SRC, kIt>(frames[2 * j], LC, s_stage + (2 * j) * SS::bytes);
+      if (2 * j + 1 < n)
+        issue_stage_inside<SRC, kIt>(frames[2 * j + 1], LC, s_stage + (2 * j + 1) * SS::bytes);
+      cp_async_commit();
+    }
+    cp_async_wait<(kStages - 2) / 2>();
+  } else {
+#pragma unroll
+    for (int k = 0; k < kStages - 1; ++k) {
+      if (k < n)
+        issue_stage<SRC, STENCIL, PY>(frames[k], LC, Hlim, Wlim, pitch, s_stage + k * SS::bytes,
+                                      lane, warp * PY);
+      cp_async_commit();
+    }
+    cp_async_wait<kStages - 1>();
   }
-  // the masters' group is the oldest: wait for it alone, then 1/flat in place
-  cp_async_wait<kStages - 1>();
   __syncthreads();
-  if (uwin) {
-    finish_masters(S, tx0, ty0, flat_norm, s_mast, h.status);
-    __syncthreads();
-  }
-  const float4* s_mast_w = s_mast + warp * PY * mwin_w + lane;
+  if (uwin) finish_masters(S, tx0, ty0, flat_norm, s_mast, pk, frames[0].t, h.status);
+  // the warp's lane in the union window: float2 entries when premerged, else
+  // float4 entries
+  const void* s_mast_w = pk ? (const void*)((const float2*)s_mast + warp * PY * mwin_w + lane)
+                            : (const void*)(s_mast + warp * PY * mwin_w + lane);
   const bool stack_lane = lane < TW && x < W;
   int mq[PY];
 #pragma unroll
@@ -624,9 +787,10 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
   // a stack-only set (a chunk of a set deeper than the register buckets) keeps
   // no samples: its group reserves no shared memory for them
   float* sk = S.stack_only ? nullptr : s_samples + (size_t)warp * PY * 32 + lane;
-  // frames in groups of kStages, so that every stage slot is a constant
-  auto step = [&](auto mode, int k, int u, bool issue_next) {
+  // single frames in groups of kStages (slots constant in the unrolled groups)
+  auto step = [&](auto mode, auto packed, int k, int u, bool issue_next) {
     constexpr int MODE = decltype(mode)::value;
+    constexpr int PK = decltype(packed)::value;
     cp_async_wait<kStages - 2>();
     __syncwarp();
     if (issue_next) {
@@ -638,29 +802,81 @@ __device__ __forceinline__ void reduce_tile(const PlanView& P, int item, float* 
                                       warp * PY);
     }
     cp_async_commit();
-    frame_step<STENCIL, SRC, PY, MODE>(frames[k], s_stage + u * SS::bytes, s_mast_w, mwin_w, S,
-                                       flat_norm, h.status, lane, x, tx0, wy0,
-                                       sk ? sk + (size_t)k * TH * 32 : nullptr, mq,
-                                       stack_out, k, W, H,
-                                       out_pitch, stack_lane, norm);
+    frame_step<STENCIL, SRC, PY, MODE, PK>(frames[k], s_stage + u * SS::bytes, s_mast_w, mwin_w,
+                                           pk, S, flat_norm, h.status, lane, x, tx0, wy0,
+                                           sk ? sk + (size_t)k * TH * 32 : nullptr, mq,
+                                           stack_out, k, W, H, out_pitch, stack_lane, norm);
   };
-  auto frame_loop = [&](auto mode) {
+  auto frame_loop = [&](auto mode, auto packed) {
     int k0 = 0;
     // groups whose frames and whose successors' copies all exist: no tests
     for (; k0 + 2 * kStages - 1 <= n; k0 += kStages) {
 #pragma unroll
-      for (int u = 0; u < kStages; ++u) step(mode, k0 + u, u, true);
+      for (int u = 0; u < kStages; ++u) step(mode, packed, k0 + u, u, true);
     }
     for (; k0 < n; k0 += kStages) {
-#pragma unroll
+#pragma unroll 1
       for (int u = 0; u < kStages; ++u)
-        if (k0 + u < n) step(mode, k0 + u, u, k0 + u + kStages - 1 < n);
+        if (k0 + u < n) step(mode, packed, k0 + u, u, k0 + u + kStages - 1 < n);
     }
   };
-  if (tile_fast)
-    frame_loop(std::integral_constant<int, kFast>{});
-  else
-    frame_loop(std::integral_constant<int, kGeneral>{});
+  // frame pairs (k, k + 1) in stage slots (u, u + 1): wait for the pair,
+  // issue frames k + kStages - 2 and k + kStages - 1 into the slots of the
+  // previous pair, then compute the pair (or the last, odd frame alone)
+  auto pair_step = [&](auto packed, int k, int u, bool full) {
+    constexpr int PK = decltype(packed)::value;
+    cp_async_wait<(kStages - 4) / 2>();
+    __syncwarp();
+    const int ka = k + kStages - 2, kb = k + kStages - 1;
+    if (full || ka < n)
+      issue_stage_inside<SRC, kIt>(frames[ka], LC,
+                                   s_stage + ((u + kStages - 2) % kStages) * SS::bytes);
+    if (full || kb < n)
+      issue_stage_inside<SRC, kIt>(frames[kb], LC,
+                                   s_stage + ((u + kStages - 1) % kStages) * SS::bytes);
+    cp_async_commit();
+    float* sk0 = sk + (size_t)k * TH * 32;
+    if (full || k + 1 < n) {
+      frame_pair_fast<STENCIL, SRC, PY, PK>(frames[k], frames[k + 1], s_stage + u * SS::bytes,
+                                            s_stage + (u + 1) * SS::bytes, s_mast_w, mwin_w,
+                                            lane, sk0, sk0 + TH * 32, norm);
+    } else {
+      frame_step<STENCIL, SRC, PY, kFast, PK>(frames[k], s_stage + u * SS::bytes, s_mast_w,
+                                              mwin_w, pk, S, flat_norm, h.status, lane, x, tx0,
+                                              wy0, sk0, mq, nullptr, k, W, H, out_pitch,
+                                              stack_lane, norm);
+    }
+  };
+  auto pair_loop = [&](auto packed) {
+    int k0 = 0;
+    // groups of kStages frames whose successors' copies all exist: no tests
+    for (; k0 + 2 * kStages - 2 <= n; k0 += kStages) {
+#pragma unroll
+      for (int u = 0; u < kStages; u += 2) pair_step(packed, k0 + u, u, true);
+    }
+    for (; k0 < n; k0 += kStages) {
+#pragma unroll 1
+      for (int u = 0; u < kStages; u += 2)
+        if (k0 + u < n) pair_step(packed, k0 + u, u, false);
+    }
+  };
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  // interior tiles of raw sources need the premerged window (frames of
+  // several exposure times take the general loop); coefficient sources read
+  // no masters
+  const bool fast = tile_fast && (pk || SRC != SRC_RAW);
+  if constexpr (kPairs) {
+    if (pairs)
+      pair_loop(I1{});
+    else
+      frame_loop(std::integral_constant<int, kGeneral>{}, I2{});
+  } else {
+    if (fast)
+      frame_loop(std::integral_constant<int, kFast>{}, I1{});
+    else
+      frame_loop(std::integral_constant<int, kGeneral>{}, I2{});
+  }
   cp_async_wait<0>();
   __syncwarp();
 

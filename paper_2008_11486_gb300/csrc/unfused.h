@@ -67,6 +67,13 @@ struct CombineArgs {
 
 cudaError_t launch_stats_init(FrameStats* st, int n, cudaStream_t s);
 cudaError_t launch_stats_raw(const CalibArgs& a, int nk, FrameStats* st, cudaStream_t s);
+// Eight-pixel forms (rows of raw, masters and outputs on 8-pixel boundaries):
+// the FP16 scaling sums (sum, minimum, maximum) and calibration, each block
+// over every frame of the launch.
+cudaError_t launch_f16_stats8(const CalibArgs& a, int nk, FrameStats* st, cudaStream_t s);
+cudaError_t launch_calibrate8(const CalibArgs& a, int nk, bool f16, void* out, int64_t out_pitch,
+                              int64_t out_fstride, const float* scale, const float* offset,
+                              cudaStream_t s);
 // Sums into FrameStats (st != null) or into the separate arrays sum/sumsq/count.
 cudaError_t launch_stats_frames(const void* frames, int64_t pitch, int64_t fstride, int W, int H,
                                 int n, bool f16, const float* scale, const float* offset,
@@ -81,7 +88,10 @@ cudaError_t launch_frame_norm(const InlinePlan* inl, const void* plan_dev, int n
 cudaError_t launch_calibrate(const CalibArgs& a, int nk, bool f16, void* out, int64_t out_pitch,
                              int64_t out_fstride, const float* scale, const float* offset,
                              cudaStream_t s);
-cudaError_t launch_shift(const ShiftArgs& a, int nk, int stencil, bool f16, cudaStream_t s);
+// vec: outputs (and validity bytes) 16-byte (FP32) or 8-byte (FP16) aligned
+// with pitches of 4k pixels, so that four outputs leave as one store
+cudaError_t launch_shift(const ShiftArgs& a, int nk, int stencil, bool f16, int vec,
+                         cudaStream_t s);
 cudaError_t launch_prefilter_frames(const InlinePlan* inl, int grid, bool f16, cudaStream_t s);
 cudaError_t launch_combine(const CombineArgs& a, bool f16, cudaStream_t s);
 // More than IRP_MAX_FRAMES frames (up to IRP_MAX_WIDE_FRAMES): a group of lanes per pixel.

@@ -1,7 +1,10 @@
 """Shared helpers of the GPU parity tests: uploads, oracle runs and the
 tolerances derived from the FP32 arithmetic of the kernels.
 
-Tolerances, each derived from the rounding steps of the FP32 arithmetic:
+Tolerances, each derived from the rounding steps of the FP32 arithmetic.
+Calibration is v = (raw - L) * rf with the level L = bias + dark*t rounded
+once (an fma) and rf = flat_norm/flat: its error is at most
+u (|L| rf + 3 |v|), so below "|v|" stands for |v| + |L| rf.
   * clipped mean / median end to end:  |gpu - ref| <= max(1e-3 ADU, 1e-6 |ref|)
     plus the per-sample bound below (the mean of samples is off by at most
     the largest sample error);
@@ -54,7 +57,8 @@ def sample_tolerance(fs, interp, oracle_mod, pixels=None):
     tol = np.empty((n,) + xx.shape)
     for k in range(n):
         v = oracle_mod.calibrate(fs.raw[k], fs.bias, fs.dark, fs.flat, fs.exptime[k])
-        M = maxfilter(v, size)
+        lv = np.abs(fs.bias.astype(np.float64) + fs.dark.astype(np.float64) * float(fs.exptime[k]))
+        M = maxfilter(np.abs(v) + lv / np.abs(fs.flat.astype(np.float64)), size)
         sx = np.clip(xx + int(np.floor(fs.dx[k])), 0, W - 1)
         sy = np.clip(yy + int(np.floor(fs.dy[k])), 0, H - 1)
         # the tap origin and its right/upper neighbour

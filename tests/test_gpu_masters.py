@@ -53,13 +53,15 @@ def _oracle_master(raw, bias, dark, flat, t, kappa=3.0):
     return st, oracle.combine_stack(st, np.ones(st.shape, np.uint8), kappa=kappa)
 
 
-def _check(name, gcal, g, ocal, o):
+def _check(name, gcal, g, ocal, o, level=0.0):
     # identical calibrated inputs give the same median bit for bit
     same = oracle.combine_stack(gcal.astype(np.float64), np.ones(gcal.shape, np.uint8))
     assert np.array_equal(g["median"].view(np.uint32),
                           same["median"].astype(np.float32).view(np.uint32)), name
-    # end to end against the oracle's FP64 calibration: a few roundings per sample
-    samp = 8 * 2.0 ** -24 * np.abs(ocal).max(axis=0) + 1e-6
+    # end to end against the oracle's FP64 calibration: a few roundings per
+    # sample, of the calibrated value and of the level removed (bias + dark*t,
+    # divided by the flat: `level`)
+    samp = 8 * 2.0 ** -24 * (np.abs(ocal).max(axis=0) + level) + 1e-6
     return gate_e2e(name, g, o, samp, 3.0)
 
 
@@ -81,7 +83,7 @@ def test_bias_dark_flat_masters_with_irp_combine():
     tflat = np.full((H, W), td, np.float32)
     gcal, gd = _gpu_master(draw, bias_m, zeros, tflat, td)
     ocal, od = _oracle_master(draw, bias_m, zeros, tflat, td)
-    print(_check("dark master", gcal, gd, ocal, od))
+    print(_check("dark master", gcal, gd, ocal, od, np.abs(bias_m) / td))
     dark_m = gd["median"]  # 7 exposures: the median, as for the bias
     # flat: 11 twilight exposures of 5 s at 20000 e-
     tf = 5.0
@@ -89,7 +91,8 @@ def test_bias_dark_flat_masters_with_irp_combine():
     fraw = _exposures(rng, 11, level, 140.0, tf, n_cr=4)
     gcal, gf = _gpu_master(fraw, bias_m, dark_m, ones, tf)
     ocal, of = _oracle_master(fraw, bias_m, dark_m, ones, tf)
-    print(_check("flat master", gcal, gf, ocal, of))
+    print(_check("flat master", gcal, gf, ocal, of,
+                 np.abs(bias_m + dark_m.astype(np.float64) * tf)))
     # two cosmic rays can land on one pixel of the 11 exposures, which a 3-sigma
     # clip of 11 samples cannot both reject: the median is the master here too
     flat_m = gf["median"]

@@ -317,16 +317,19 @@ def test_plan_launch_and_graph_capture():
 
 
 # --------------------------------------------------------------- unfused path
+@pytest.mark.parametrize("W", [90, 96])  # scalar rows / 8-pixel vector rows
 @pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3", "cubic"])
-def test_unfused_f32_matches_oracle(interp):
-    fs = synth.make_set(90, 66, 9, 4.0, 123, n_stars=30, n_cr=10)
+def test_unfused_f32_matches_oracle(interp, W):
+    fs = synth.make_set(W, 66, 9, 4.0, 123, n_stars=30, n_cr=10)
     d = core.device_set(fs)
     raw = torch.stack(d.frames)
     cal, _, _, _ = core.calibrate(raw, d.bias, d.dark, d.flat, fs.exptime)
     cal_h = cal.cpu().numpy()
     for k in range(fs.n):
         v = oracle.calibrate(fs.raw[k], fs.bias, fs.dark, fs.flat, fs.exptime[k])
-        compare("calibrate", cal_h[k], v, 4 * 2.0 ** -24 * np.abs(v) + 1e-5)
+        lv = np.abs(fs.bias.astype(np.float64) + fs.dark.astype(np.float64) * fs.exptime[k])
+        compare("calibrate", cal_h[k], v,
+                4 * 2.0 ** -24 * (np.abs(v) + lv / fs.flat.astype(np.float64)) + 1e-5)
     stack, valid, _ = core.shift(cal, fs.dx, fs.dy, interp)
     st = stack.cpu().numpy()
     va = valid.cpu().numpy().astype(bool)
