@@ -858,7 +858,8 @@ def run_served(args, cfg, dev, world, rank, local):
     reqs = make_requests(args.requests, 100)
     lat, wall = serve.run_poisson(srv, reqs, rate_hz=args.rate)
     phase = {"queued_s": [r.admitted - r.arrival for r in reqs],
-             "upload_wait_s": [r.launched - r.admitted for r in reqs],
+             "upload_s": [r.uploaded - r.admitted for r in reqs],
+             "prepare_s": [r.launched - r.uploaded for r in reqs],
              "device_s": [r.done - r.launched for r in reqs]}
     nominal = {"batches": srv.batches, "batch_sizes": list(srv.batch_sizes),
                "admitted_while_running": srv.admitted_while_running,

@@ -697,14 +697,11 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
         norm_rb = std::max(norm_rb, (s.H + R - 1) / R);
       }
       if (S.spath) {
-        // frames per row-pass work item: up to kRowGroup, fewer when the
-        // set's row blocks times its frame groups would not fill the GPU twice
-        // with two CTAs per SM (each work item re-reads its block's masters)
+        // frames per row-pass work item (each work item reads its block's
+        // masters once; smaller groups measured slower on 10 x 1024^2 sets:
+        // more CTAs than one wave)
         const int nrb = (s.H + row_block(row_e) - 1) / row_block(row_e);
-        int rg = kRowGroup;
-        while (rg > 1 && (int64_t)nrb * ((s.n + rg - 1) / rg) < 4 * (int64_t)sm_count())
-          rg = (rg + 1) / 2;
-        S.rgroup = std::min(rg, s.n);
+        S.rgroup = std::min(kRowGroup, s.n);
         nrows += ((s.n + S.rgroup - 1) / S.rgroup) * nrb;
         if (!gtile) ncolsegs += s.n * ((s.W + 28) / 29) * ((s.H + kColRows - 1) / kColRows);
       }

@@ -7,8 +7,7 @@
 // y+[i] = v[i] + z1 y+[i-1] and y-[i] = v[i] + z1 y-[i+1], z1 = sqrt(3) - 2.
 //
 // Row pass: one CTA per block of rows (4, or 2 for frames wider than 1024)
-// and chunk of at most kRowGroup frames (fewer when a set has too few row
-// blocks to fill the GPU twice).  The block's master rows are copied into
+// and chunk of at most kRowGroup frames.  The block's master rows are copied into
 // shared memory asynchronously and 1/flat is formed in place; the warps take
 // the block's (row, frame) tasks round-robin and prefetch the next task's raw
 // row with cp.async while computing the current one.  Lane l calibrates and

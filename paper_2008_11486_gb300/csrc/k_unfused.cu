@@ -3,6 +3,9 @@
 // and the FP64 frame-wide sums that choose that scaling.
 #include <float.h>
 
+#include <algorithm>
+#include <type_traits>
+
 #include "combine.cuh"
 #include "prefilter.cuh"
 #include "reduce_kernels.cuh"
@@ -427,7 +430,8 @@ __global__ void __launch_bounds__(kThreads) k_f16_stats8(CalibArgs a, int nk, Fr
   if (act) load_masters8(a, (int64_t)y * a.master_pitch + x, flat_norm, m);
   const uint16_t* rr = a.raw + (int64_t)a.k0 * a.raw_frame_stride + (int64_t)y * a.raw_pitch + x;
   const unsigned long long npx = (unsigned long long)min(kSeg8, a.W - xs);
-  __shared__ float sh[kThreads / 32][3 * kFrames8];
+  __shared__ float sh_sum[kThreads / 32][kFrames8];
+  __shared__ int sh_min[kThreads / 32][kFrames8], sh_max[kThreads / 32][kFrames8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k0 = 0; k0 < nk; k0 += kFrames8) {
     uint4 q[kFrames8];
@@ -435,7 +439,6 @@ __global__ void __launch_bounds__(kThreads) k_f16_stats8(CalibArgs a, int nk, Fr
     for (int j = 0; j < kFrames8; ++j)
       q[j] = (act && k0 + j < nk) ? __ldg((const uint4*)(rr + (int64_t)(k0 + j) * a.raw_frame_stride))
                                   : make_uint4(0u, 0u, 0u, 0u);
-    float acc[3 * kFrames8];  // per frame: sum, minimum, maximum
 #pragma unroll
     for (int j = 0; j < kFrames8; ++j) {
       float sm = 0.0f, mn = FLT_MAX, mx = -FLT_MAX;
@@ -449,38 +452,33 @@ __global__ void __launch_bounds__(kThreads) k_f16_stats8(CalibArgs a, int nk, Fr
           mx = fmaxf(mx, v[e]);
         }
       }
-      acc[3 * j] = sm;
-      acc[3 * j + 1] = mn;
-      acc[3 * j + 2] = mx;
-    }
+      // the warp's 256 pixels: FP32 sum by shuffles, extremes as ordered keys
+      // in one warp reduction each
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-      for (int j = 0; j < kFrames8; ++j) {
-        acc[3 * j] = __fadd_rn(acc[3 * j], __shfl_down_sync(0xffffffffu, acc[3 * j], o));
-        acc[3 * j + 1] = fminf(acc[3 * j + 1], __shfl_down_sync(0xffffffffu, acc[3 * j + 1], o));
-        acc[3 * j + 2] = fmaxf(acc[3 * j + 2], __shfl_down_sync(0xffffffffu, acc[3 * j + 2], o));
+      for (int o = 16; o > 0; o >>= 1) sm = __fadd_rn(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+      const int kmn = __reduce_min_sync(0xffffffffu, float_key(mn));
+      const int kmx = __reduce_max_sync(0xffffffffu, float_key(mx));
+      if (lane == 0) {
+        sh_sum[warp][j] = sm;
+        sh_min[warp][j] = kmn;
+        sh_max[warp][j] = kmx;
       }
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int i = 0; i < 3 * kFrames8; ++i) sh[warp][i] = acc[i];
     }
     __syncthreads();
     if (threadIdx.x < kFrames8 && k0 + (int)threadIdx.x < nk) {
       const int j = threadIdx.x;
       double sm = 0.0;
-      float mn = FLT_MAX, mx = -FLT_MAX;
+      int kmn = INT_MAX, kmx = INT_MIN;
       for (int w = 0; w < kThreads / 32; ++w) {
-        sm += (double)sh[w][3 * j];
-        mn = fminf(mn, sh[w][3 * j + 1]);
-        mx = fmaxf(mx, sh[w][3 * j + 2]);
+        sm += (double)sh_sum[w][j];
+        kmn = min(kmn, sh_min[w][j]);
+        kmx = max(kmx, sh_max[w][j]);
       }
       FrameStats& f = st[a.k0 + k0 + j];
       atomicAdd(&f.sum, sm);
       atomicAdd((unsigned long long*)&f.count, npx);
-      atomicMin(&f.min_key, float_key(mn));
-      atomicMax(&f.max_key, float_key(mx));
+      atomicMin(&f.min_key, kmn);
+      atomicMax(&f.max_key, kmx);
     }
     __syncthreads();
   }
@@ -532,96 +530,103 @@ __global__ void __launch_bounds__(kThreads) k_calibrate8(CalibArgs a, int nk, vo
 }
 
 // ---------------------------------------------------------------------------
-// Shift, four output pixels per thread (nearest, bilinear).  The taps of four
+// Shift, four output pixels of each of kShiftRows rows per thread (nearest,
+// bilinear).  The taps of four
 // neighbouring outputs overlap, so each tap of a row is read once for the
 // four (five reads per row for bilinear instead of eight); taps of zero
 // weight and taps only invalid outputs would use are not read.  The outputs
 // (and validity bytes) leave as one vector store when vec is set and the
 // four lie inside the row.  Each output is the value k_shift gives.
 // ---------------------------------------------------------------------------
+constexpr int kShiftRows = 4;  // output rows per thread
+
 template <int ST, bool F16>
 __global__ void __launch_bounds__(kThreads) k_shift4(ShiftArgs a, int vec) {
   const int x0 = 4 * (blockIdx.x * kThreads + threadIdx.x);
-  const int y = blockIdx.y;
   const int kl = blockIdx.z;
   if (x0 >= a.W) return;
   const FrameDesc& F = a.frames[kl];
   const int k = a.k0 + kl;
-  const bool yok = (y >= F.vy0) & (y <= F.vy1);
-  bool ok[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int x = x0 + c;
-    ok[c] = yok & (x >= F.vx0) & (x <= F.vx1) & (x < a.W);
-  }
-  const int i0 = x0 + F.ox, j0 = y + F.oy;
   auto at = [&](int i, int j) -> float {
     const int64_t o = (int64_t)k * a.in_fstride + (int64_t)j * a.in_pitch + i;
-    if (F16) return __half2float(((const __half*)a.in)[o]);
+    if (F16) return __half2float(__ldg((const __half*)a.in + o));
     return __ldg((const float*)a.in + o);
   };
-  float val[4];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) val[c] = __int_as_float(0x7fc00000);
-  if (ST == ST_NEAREST) {
+  for (int ry = 0; ry < kShiftRows; ++ry) {
+    const int y = blockIdx.y * kShiftRows + ry;
+    if (y >= a.H) break;
+    const bool yok = (y >= F.vy0) & (y <= F.vy1);
+    bool ok[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-      if (ok[c]) val[c] = at(i0 + c, j0);
-  } else {
-    const float fx = F.fx, fy = F.fy;
-    const bool hx = fx != 0.0f, hy = fy != 0.0f;
-    // column c of the taps serves output c (weight 1 - fx) and output c - 1
-    // (weight fx)
-    bool need[5];
-    need[0] = ok[0];
+    for (int c = 0; c < 4; ++c) {
+      const int x = x0 + c;
+      ok[c] = yok & (x >= F.vx0) & (x <= F.vx1) & (x < a.W);
+    }
+    const int i0 = x0 + F.ox, j0 = y + F.oy;
+    float val[4];
 #pragma unroll
-    for (int c = 1; c < 4; ++c) need[c] = ok[c] || (hx && ok[c - 1]);
-    need[4] = hx && ok[3];
-    float r0[5], r1[5];
+    for (int c = 0; c < 4; ++c) val[c] = __int_as_float(0x7fc00000);
+    if (ST == ST_NEAREST) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      r0[c] = need[c] ? at(i0 + c, j0) : 0.0f;
-      r1[c] = (need[c] && hy) ? at(i0 + c, j0 + 1) : 0.0f;
+      for (int c = 0; c < 4; ++c)
+        if (ok[c]) val[c] = at(i0 + c, j0);
+    } else {
+      const float fx = F.fx, fy = F.fy;
+      const bool hx = fx != 0.0f, hy = fy != 0.0f;
+      // column c of the taps serves output c (weight 1 - fx) and output c - 1
+      // (weight fx)
+      bool need[5];
+      need[0] = ok[0];
+#pragma unroll
+      for (int c = 1; c < 4; ++c) need[c] = ok[c] || (hx && ok[c - 1]);
+      need[4] = hx && ok[3];
+      float r0[5], r1[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        r0[c] = need[c] ? at(i0 + c, j0) : 0.0f;
+        r1[c] = (need[c] && hy) ? at(i0 + c, j0 + 1) : 0.0f;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (!ok[c]) continue;
+        const float p00 = r0[c];
+        const float p10 = hx ? r0[c + 1] : p00;
+        const float h0 = __fmaf_rn(fx, __fsub_rn(p10, p00), p00);
+        float h1 = h0;
+        if (hy) {
+          const float p01 = r1[c];
+          const float p11 = hx ? r1[c + 1] : p01;
+          h1 = __fmaf_rn(fx, __fsub_rn(p11, p01), p01);
+        }
+        val[c] = __fmaf_rn(fy, __fsub_rn(h1, h0), h0);
+      }
+    }
+    const int64_t o = (int64_t)k * a.out_fstride + (int64_t)y * a.out_pitch + x0;
+    if (vec && x0 + 3 < a.W) {
+      if (F16) {
+        const uint32_t w0 = (uint32_t)__half_as_ushort(__float2half_rn(val[0])) |
+                            ((uint32_t)__half_as_ushort(__float2half_rn(val[1])) << 16);
+        const uint32_t w1 = (uint32_t)__half_as_ushort(__float2half_rn(val[2])) |
+                            ((uint32_t)__half_as_ushort(__float2half_rn(val[3])) << 16);
+        *(uint2*)((__half*)a.out + o) = make_uint2(w0, w1);
+      } else {
+        *(float4*)((float*)a.out + o) = make_float4(val[0], val[1], val[2], val[3]);
+      }
+      if (a.valid_out)
+        *(uint32_t*)(a.valid_out + o) = (ok[0] ? 1u : 0u) | (ok[1] ? 0x100u : 0u) |
+                                        (ok[2] ? 0x10000u : 0u) | (ok[3] ? 0x1000000u : 0u);
+      continue;
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      if (!ok[c]) continue;
-      const float p00 = r0[c];
-      const float p10 = hx ? r0[c + 1] : p00;
-      const float h0 = __fmaf_rn(fx, __fsub_rn(p10, p00), p00);
-      float h1 = h0;
-      if (hy) {
-        const float p01 = r1[c];
-        const float p11 = hx ? r1[c + 1] : p01;
-        h1 = __fmaf_rn(fx, __fsub_rn(p11, p01), p01);
-      }
-      val[c] = __fmaf_rn(fy, __fsub_rn(h1, h0), h0);
+      if (x0 + c >= a.W) break;
+      if (F16)
+        ((__half*)a.out)[o + c] = __float2half_rn(val[c]);
+      else
+        ((float*)a.out)[o + c] = val[c];
+      if (a.valid_out) a.valid_out[o + c] = ok[c] ? 1 : 0;
     }
-  }
-  const int64_t o = (int64_t)k * a.out_fstride + (int64_t)y * a.out_pitch + x0;
-  if (vec && x0 + 3 < a.W) {
-    if (F16) {
-      const uint32_t w0 = (uint32_t)__half_as_ushort(__float2half_rn(val[0])) |
-                          ((uint32_t)__half_as_ushort(__float2half_rn(val[1])) << 16);
-      const uint32_t w1 = (uint32_t)__half_as_ushort(__float2half_rn(val[2])) |
-                          ((uint32_t)__half_as_ushort(__float2half_rn(val[3])) << 16);
-      *(uint2*)((__half*)a.out + o) = make_uint2(w0, w1);
-    } else {
-      *(float4*)((float*)a.out + o) = make_float4(val[0], val[1], val[2], val[3]);
-    }
-    if (a.valid_out)
-      *(uint32_t*)(a.valid_out + o) = (ok[0] ? 1u : 0u) | (ok[1] ? 0x100u : 0u) |
-                                      (ok[2] ? 0x10000u : 0u) | (ok[3] ? 0x1000000u : 0u);
-    return;
-  }
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    if (x0 + c >= a.W) break;
-    if (F16)
-      ((__half*)a.out)[o + c] = __float2half_rn(val[c]);
-    else
-      ((float*)a.out)[o + c] = val[c];
-    if (a.valid_out) a.valid_out[o + c] = ok[c] ? 1 : 0;
   }
 }
 
@@ -711,41 +716,10 @@ __global__ void __launch_bounds__(kThreads) k_shift(ShiftArgs a) {
 // Combine (Sec. 2.1 co-adding) of a materialised stack, one thread per pixel.
 // ---------------------------------------------------------------------------
 template <int NMAX, bool F16>
-__global__ void __launch_bounds__(kThreads) k_combine(CombineArgs a) {
-  const int x = blockIdx.x * kThreads + threadIdx.x;
-  const int y = blockIdx.y;
-  __shared__ float s_sc[NMAX], s_of[NMAX];  // F16: per-frame scale and offset
-  if (F16) {
-    if (threadIdx.x < a.n) {
-      s_sc[threadIdx.x] = a.scale[threadIdx.x];
-      s_of[threadIdx.x] = a.offset[threadIdx.x];
-    }
-    __syncthreads();
-  }
-  if (x >= a.W) return;
+__device__ __forceinline__ void combine_pixel(const CombineArgs& a, float (&s)[NMAX], int x,
+                                              int y, const float* s_sc, const float* s_of) {
   const float kInf = __int_as_float(0x7f800000);
-  auto load = [&](int k) -> float {
-    const int64_t o = (int64_t)k * a.fstride + (int64_t)y * a.pitch + x;
-    float v;
-    if (F16)
-      v = __fmaf_rn(__half2float(((const __half*)a.stack)[o]), __ldg(a.scale + k), __ldg(a.offset + k));
-    else
-      v = __ldg((const float*)a.stack + o);
-    if (a.valid && !a.valid[o]) v = kInf;
-    return (v == v) ? v : kInf;
-  };
-  // every frame's value and validity requested before any is used
   const int64_t o0 = (int64_t)y * a.pitch + x;
-  float s[NMAX];
-#pragma unroll
-  for (int j = 0; j < NMAX; ++j) {
-    if (j < a.n) {
-      const int64_t o = (int64_t)j * a.fstride + o0;
-      s[j] = F16 ? __half2float(((const __half*)a.stack)[o]) : __ldg((const float*)a.stack + o);
-    } else {
-      s[j] = kInf;
-    }
-  }
   // validity as one bit per frame
   uint64_t ok = ~0ull;
   if (a.valid) {
@@ -768,13 +742,117 @@ __global__ void __launch_bounds__(kThreads) k_combine(CombineArgs a) {
   if (a.mean_out) a.mean_out[oi] = o.mean;
   if (a.median_out) a.median_out[oi] = o.median;
   if (a.nkept_out) a.nkept_out[oi] = (uint16_t)o.kept;
-  if (a.reject_out) {
+  if (a.reject_out) {  // debug output: the samples again, in frame order
     for (int k = 0; k < a.n; ++k) {
-      const float v = load(k);
+      const int64_t ok_ = (int64_t)k * a.fstride + o0;
+      float v = F16 ? __fmaf_rn(__half2float(((const __half*)a.stack)[ok_]), s_sc[k], s_of[k])
+                    : __ldg((const float*)a.stack + ok_);
+      if (a.valid && !a.valid[ok_]) v = kInf;
+      v = (v == v) ? v : kInf;
       const bool rej = (v < kInf) & ((v < o.lo_val) | (v > o.hi_val));
       a.reject_out[((int64_t)k * a.H + y) * a.out_pitch + x] = rej ? 1 : 0;
     }
   }
+}
+
+template <int NMAX, bool F16>
+__global__ void __launch_bounds__(kThreads) k_combine(CombineArgs a) {
+  const int x = blockIdx.x * kThreads + threadIdx.x;
+  const int y = blockIdx.y;
+  __shared__ float s_sc[NMAX], s_of[NMAX];  // F16: per-frame scale and offset
+  if (F16) {
+    if (threadIdx.x < a.n) {
+      s_sc[threadIdx.x] = a.scale[threadIdx.x];
+      s_of[threadIdx.x] = a.offset[threadIdx.x];
+    }
+    __syncthreads();
+  }
+  if (x >= a.W) return;
+  const float kInf = __int_as_float(0x7f800000);
+  // every frame's value requested before any is used
+  const int64_t o0 = (int64_t)y * a.pitch + x;
+  float s[NMAX];
+#pragma unroll
+  for (int j = 0; j < NMAX; ++j) {
+    if (j < a.n) {
+      const int64_t o = (int64_t)j * a.fstride + o0;
+      s[j] = F16 ? __half2float(((const __half*)a.stack)[o]) : __ldg((const float*)a.stack + o);
+    } else {
+      s[j] = kInf;
+    }
+  }
+  combine_pixel<NMAX, F16>(a, s, x, y, s_sc, s_of);
+}
+
+// The same combine with the stack staged through shared memory, one warp per
+// item of 32 pixels of a row: each warp of a persistent CTA takes items in
+// turn and copies the next item's samples ([n][32], 16-byte cp.async,
+// zero-filled past the row) into its own second slab while it sorts the
+// current one.  The warps never wait for one another, so the loads of some
+// overlap the sorts of others as well as their own.  Needs rows on 16-byte
+// boundaries (pitches of 4k FP32 / 8k FP16 values).
+template <int NMAX, bool F16>
+__global__ void __launch_bounds__(kThreads) k_combine_staged(CombineArgs a, int tiles_x,
+                                                             int nitems) {
+  using T = std::conditional_t<F16, __half, float>;
+  constexpr int kPer = 16 / sizeof(T);  // values per 16-byte chunk
+  constexpr int kChunks = 32 / kPer;    // chunks per frame and item
+  extern __shared__ __align__(16) uint8_t s_stage[];
+  __shared__ float s_sc[NMAX], s_of[NMAX];
+  if (F16) {
+    if (threadIdx.x < a.n) {
+      s_sc[threadIdx.x] = a.scale[threadIdx.x];
+      s_of[threadIdx.x] = a.offset[threadIdx.x];
+    }
+    __syncthreads();
+  }
+  const int n = a.n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* const wslab = (T*)s_stage + (size_t)warp * 2 * n * 32;  // this warp's two slabs
+  const float kInf = __int_as_float(0x7f800000);
+  auto issue = [&](int item, T* dst) {
+    const int y = item / tiles_x, x0 = (item - y * tiles_x) * 32;
+    for (int c = lane; c < n * kChunks; c += 32) {
+      const int k = c / kChunks, j = c - k * kChunks;
+      const int xc = x0 + j * kPer;
+      const int nb = min(max(a.W - xc, 0), kPer) * (int)sizeof(T);
+      const T* src = (const T*)a.stack + (int64_t)k * a.fstride + (int64_t)y * a.pitch +
+                     (nb > 0 ? xc : 0);
+      cp_async16(dst + (size_t)k * 32 + j * kPer, src, nb);
+    }
+    cp_async_commit();
+  };
+  const int stride = gridDim.x * (kThreads / 32);
+  int item = blockIdx.x * (kThreads / 32) + warp;
+  if (item < nitems) issue(item, wslab);
+  for (int it = 0; item < nitems; ++it, item += stride) {
+    const int nxt = item + stride;
+    if (nxt < nitems)
+      issue(nxt, wslab + (size_t)((it + 1) & 1) * n * 32);
+    else
+      cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+    const int y = item / tiles_x, x = (item - y * tiles_x) * 32 + lane;
+    if (x < a.W) {
+      const T* col = wslab + (size_t)(it & 1) * n * 32 + lane;
+      float sv[NMAX];
+#pragma unroll
+      for (int j = 0; j < NMAX; ++j) {
+        if (j < n) {
+          if (F16)
+            sv[j] = __half2float(((const __half*)col)[(size_t)j * 32]);
+          else
+            sv[j] = ((const float*)col)[(size_t)j * 32];
+        } else {
+          sv[j] = kInf;
+        }
+      }
+      combine_pixel<NMAX, F16>(a, sv, x, y, s_sc, s_of);
+    }
+    __syncwarp();  // the slab is refilled two items later
+  }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -871,7 +949,7 @@ static cudaError_t shift_st(const ShiftArgs& a, int nk, bool f16, cudaStream_t s
 
 template <int ST>
 static cudaError_t shift4_st(const ShiftArgs& a, int nk, bool f16, int vec, cudaStream_t s) {
-  dim3 grid((a.W + 4 * kThreads - 1) / (4 * kThreads), a.H, nk);
+  dim3 grid((a.W + 4 * kThreads - 1) / (4 * kThreads), (a.H + kShiftRows - 1) / kShiftRows, nk);
   if (f16)
     k_shift4<ST, true><<<grid, kThreads, 0, s>>>(a, vec);
   else
@@ -903,8 +981,47 @@ cudaError_t launch_prefilter_frames(const InlinePlan* inl, int grid, bool f16, c
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+static int device_sms() {  // cached per process
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 1;
+  }
+  return sms;
+}
+
+template <int NMAX, bool F16>
+static cudaError_t combine_staged(const CombineArgs& a, cudaStream_t s) {
+  static size_t granted = 0;
+  static int occ_smem = -1, occ = 0;
+  const size_t smem = (size_t)2 * a.n * kThreads * (F16 ? 2 : 4);  // two [n][32] slabs per warp
+  auto fn = k_combine_staged<NMAX, F16>;
+  cudaError_t e = ensure_smem(fn, smem, granted);
+  if (e != cudaSuccess) return e;
+  if (occ_smem != (int)smem) {  // resident CTAs per SM for this shared-memory size
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    occ_smem = (int)smem;
+  }
+  const int tiles_x = (a.W + 31) / 32;
+  const int64_t nitems = (int64_t)tiles_x * a.H;
+  if (nitems > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const int64_t ctas = (nitems + kThreads / 32 - 1) / (kThreads / 32);
+  const int grid = (int)std::min<int64_t>(ctas, (int64_t)std::max(occ, 1) * device_sms());
+  fn<<<grid, kThreads, smem, s>>>(a, tiles_x, (int)nitems);
+  return cudaGetLastError();
+}
+
 template <int NMAX>
 static cudaError_t combine_n(const CombineArgs& a, bool f16, cudaStream_t s) {
+  // the staged form: rows on 16-byte boundaries and two slabs per warp in shared memory
+  const int per = f16 ? 8 : 4;
+  const bool staged = ((uintptr_t)a.stack & 15) == 0 && a.pitch % per == 0 &&
+                      a.fstride % per == 0 &&
+                      (size_t)2 * a.n * kThreads * (f16 ? 2 : 4) <= (size_t)200 * 1024;
+  if (staged) return f16 ? combine_staged<NMAX, true>(a, s) : combine_staged<NMAX, false>(a, s);
   dim3 grid((a.W + kThreads - 1) / kThreads, a.H);
   if (f16)
     k_combine<NMAX, true><<<grid, kThreads, 0, s>>>(a);

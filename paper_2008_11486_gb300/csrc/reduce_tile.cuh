@@ -386,16 +386,24 @@ __device__ __forceinline__ void finish_masters(const SetDesc& S, int tx0, int ty
     constexpr int kPer = kMaxWindowPx / kThreads;
     const float* const planar = (const float*)s_mast;
     float lv[kPer], rf[kPer];
+    // (row, column) of pixel e, stepped by kThreads without divisions
+    const int dr = kThreads / mw, dc = kThreads - dr * mw;
+    int r = threadIdx.x / mw, c = threadIdx.x - r * mw;
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
       const int e = threadIdx.x + kThreads * i;
       lv[i] = rf[i] = 0.0f;
       if (e < np) {
-        const int r = e / mw, c = e - r * mw;
         const int gy = gy0 + r, gx = gx0 + c;
         const bool in = gy >= 0 && gy < S.H && gx >= 0 && gx < S.W;
         lv[i] = calib_level(planar[e], planar[np + e], t);
         if (in) rf[i] = inv_flat(planar[2 * np + e], flat_norm, status);
+      }
+      c += dc;
+      r += dr;
+      if (c >= mw) {
+        c -= mw;
+        ++r;
       }
     }
     __syncthreads();

@@ -61,6 +61,7 @@ class Request:
     exptime: float = 60.0
     arrival: float = 0.0
     admitted: float = 0.0  # its frames' copies queued
+    uploaded: float = 0.0  # the scheduler saw its copies complete
     launched: float = 0.0  # its reduction queued
     done: float = 0.0
     outputs: list = None  # per chip (mean, median) device tensors (views of the output ring)
@@ -261,8 +262,14 @@ class Server:
 
     def _launch(self):
         ready, waiting = [], []
+        now = time.perf_counter()
         for u in self.uploading:  # one query per upload, so none is lost in between
-            (ready if u[2].query() else waiting).append(u)
+            if u[2].query():
+                if not u[0].uploaded:
+                    u[0].uploaded = now
+                ready.append(u)
+            else:
+                waiting.append(u)
         if not ready:
             return
         if self.running and len(ready) < self.max_batch:
