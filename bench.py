@@ -658,17 +658,18 @@ def _sub(line, keep=("value", "unit", "ms_per_step", "steps", "config", "rooflin
 
 def run_headline(args, dev, stream, world, rank, local):
     """The metric's own configuration: the batched form (value) against its
-    plain per-set launches, with the largest plain set, the spline bands and
-    the served form as sub-records."""
+    plain per-set launches, with the largest plain set, the spline bands, one
+    band of the paper's run and the served form as sub-records."""
     import torch
     line = run_workload(args, "batch", dev, stream, world, rank, local, steps=args.steps,
                         with_cpu=False)
     subs = {}
-    for name in ("precision", "bands"):
+    for name in ("precision", "bands", "paper_band"):
         sub = run_workload(args, name, dev, stream, world, rank, local, with_cpu=False,
                            with_e2e=(name == "bands"))
         if rank == 0:
             subs["deep" if name == "precision" else name] = _sub(sub)
+        torch.cuda.empty_cache()
     served = run_served(args, WORKLOADS["served"], dev, world, rank, local)
     torch.cuda.empty_cache()
     if rank == 0:
@@ -679,7 +680,7 @@ def run_headline(args, dev, stream, world, rank, local):
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_both("batch")
         line["config"]["workload"] = ("batch: " + line["config"]["workload"] + " (value); "
-                                      "subrecords deep, bands, served")
+                                      "subrecords deep, bands, paper_band, served")
     return line
 
 

@@ -168,14 +168,18 @@ irp_status irp_combine(const void* stack, int64_t pitch, int64_t frame_stride,
  * one or more frame sets, each raw pixel read from HBM once (bilinear and
  * nearest; cubic spline computes the spline coefficients of every calibrated
  * frame into the workspace first and then resamples and combines them).
- * A set of more than IRP_MAX_FRAMES frames (up to IRP_MAX_WIDE_FRAMES) is
- * resampled in chunks of at most 16 frames into its aligned FP32 stack
- * [n][H][pitch] -- stack_out when given (pitch out_pitch), else the workspace
- * (pitch W rounded up to 32) -- and the stack is then combined by a group of
- * lanes per pixel.  A cubic-spline set whose frames take the row and column
- * passes (W from 34 to 2048, H at least 34) writes no stack unless stack_out
- * is given: its combine forms each sample from the horizontally filtered
- * rows.  irp_workspace_size accounts for what each set needs.
+ * A cubic-spline set whose frames take the row pass (W from 34 to 2048, H at
+ * least 34) is reduced from the row-pass coefficients by one tile kernel,
+ * which keeps each tile's samples on chip: up to IRP_MAX_FRAMES frames, and
+ * masked sets up to 256 frames (a group of 4 or 8 lanes then combines a
+ * pixel).  Any other set of more than IRP_MAX_FRAMES frames (up to
+ * IRP_MAX_WIDE_FRAMES) is resampled in chunks of at most 16 frames into its
+ * aligned FP32 stack [n][H][pitch] -- stack_out when given (pitch
+ * out_pitch), else the workspace (pitch W rounded up to 32) -- and the stack
+ * is then combined by a group of lanes per pixel; an unmasked cubic-spline
+ * set on the row and column passes writes no stack unless stack_out is
+ * given: its combine forms each sample from the horizontally filtered rows.
+ * irp_workspace_size accounts for what each set needs.
  * ------------------------------------------------------------------------- */
 typedef struct {
   const uint16_t* const* frames;  /* host array of n device pointers           */
@@ -200,8 +204,9 @@ typedef struct {
   /* Bad-pixel masking (Sec. 2.1, bad-pixel masking before alignment): a source
    * pixel is bad when mask[y*mask_pitch + x] != 0 or its raw value is at least
    * `saturation`; a sample whose taps with non-zero weight include a bad pixel
-   * is invalid (left out of the combine, NaN in stack_out).  Nearest and
-   * bilinear only: with the cubic spline a mask or level returns
+   * is invalid (left out of the combine, NaN in stack_out).  Every
+   * resampler; with the cubic spline only for sets on the row pass (W from
+   * 34 to 2048, H at least 34) of at most 256 frames, others returning
    * IRP_ERR_UNSUPPORTED. */
   const uint8_t* mask;            /* device [H][mask_pitch] uint8, nullable */
   int64_t mask_pitch;             /* elements (>= W when mask is set) */

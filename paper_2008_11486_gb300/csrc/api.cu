@@ -224,7 +224,8 @@ struct SubInfo {
   int32_t bucket, stencil, grid, pgrid;
   int32_t nitems, counter, nsets, nframes;
   int32_t nrows, ncolsegs, row_e, py;   // spline row / column passes, rows per warp
-  int32_t norm_rb, pad;                 // frame means: most row blocks of a set (0: none)
+  int32_t norm_rb;                      // frame means: most row blocks of a set (0: none)
+  int32_t tile_rows;                    // output rows per tile
 };
 
 struct PlanFile {
@@ -256,9 +257,12 @@ struct Layout {
 };
 
 // Sets deeper than the register buckets (IRP_MAX_FRAMES < n <=
-// IRP_MAX_WIDE_FRAMES) are reduced in two steps, and groups of lanes
-// combine them.
-// * Cubic spline on the row + column passes, without a caller stack: the
+// IRP_MAX_WIDE_FRAMES) are combined by groups of lanes.
+// * Masked cubic-spline sets on the row pass with at most kWideTileMax
+//   frames: the tile kernel's lane-group form, one kernel from the row-pass
+//   coefficients like the shallower sets (a plain entry of its own bucket).
+// * Other cubic-spline sets on the row + column passes, without a caller
+//   stack, are reduced in two steps: the
 //   column pass already leaves each frame's rows filtered along x on the
 //   output grid, so the set only runs its prefilter, and the combine applies
 //   the four vertical taps itself while it gathers the samples.
@@ -292,13 +296,26 @@ int64_t deep_stack_pitch(int W) { return (int64_t)align_up((size_t)W, 32); }
 int spline_path(int W, int H);
 bool tile_path(const PlanSets& ps, int i);
 
+// A set deeper than the register buckets that the wide tile kernel reduces:
+// masked cubic-spline sets on the row pass (the two-step path below has no
+// bad-pixel footprint).  Unmasked ones keep the two-step path, measured
+// faster on 180 x 1020^2 (2.24 ms against 4.9 to 5.8 ms for the tile form,
+// which holds a tile's samples on chip at one or two CTAs per SM).
+bool wide_tile_set(const irp_set& s, int interp) {
+  return s.n > IRP_MAX_FRAMES && s.n <= kWideTileMax && interp == IRP_INTERP_SPLINE3 &&
+         spline_path(s.W, s.H) && (s.mask || s.saturation > 0.0f);
+}
+
+// Bucket of a plan entry: the register bucket, or the wide tile kernel's.
+int set_bucket(int n) { return n <= IRP_MAX_FRAMES ? reduce_bucket(n) : wide_tile_bucket(n); }
+
 PlanSets expand_sets(const irp_set* sets, int nsets, int interp) {
   PlanSets ps;
   ps.user = sets;
   ps.interp = interp;
   for (int i = 0; i < nsets; ++i) {
     const irp_set& s = sets[i];
-    if (s.n <= IRP_MAX_FRAMES) {
+    if (s.n <= IRP_MAX_FRAMES || wide_tile_set(s, interp)) {
       ps.sets.push_back(s);
       ps.user_of.push_back(i);
       ps.deep_of.push_back(-1);
@@ -369,6 +386,9 @@ size_t crow_frame_bytes(int W, int H) {
   return align_up((size_t)H * (size_t)crow_pitch(W) * sizeof(float), kAlign);
 }
 
+// Share of L2 a launch sequence keeps row-pass frames resident in.
+constexpr size_t kL2Budget = (size_t)48 << 20;
+
 // Spline coefficients are stored with a 2-sample mirrored border on every side.
 int64_t coef_pitch(int W) { return (int64_t)align_up((size_t)W + 4, 4); }
 size_t coef_frame_bytes(int W, int H) {
@@ -381,7 +401,7 @@ size_t coef_frame_bytes(int W, int H) {
 // samples), and whole deep sets that only run their prefilter another.
 int group_key(const PlanSets& ps, int i, int interp) {
   const irp_set& s = ps.sets[i];
-  const int b = reduce_bucket(s.n);
+  const int b = set_bucket(s.n);
   const int key = interp == IRP_INTERP_SPLINE3 ? 2 * b + spline_path(s.W, s.H) : 2 * b;
   if (ps.deep_of[i] < 0) return key;
   return ps.deep[ps.deep_of[i]].rows ? 2000 : key + 1000;
@@ -480,9 +500,9 @@ irp_status check_params(const irp_set* sets, int nsets, const irp_reduce_params*
     irp_status st = check_set(sets[i]);
     if (st != IRP_OK) return st;
     // with the cubic spline, bad-pixel masking is built for the sets the tile
-    // kernel reduces (34 <= W <= 2048, H >= 34, at most IRP_MAX_FRAMES frames)
+    // kernel reduces (34 <= W <= 2048, H >= 34, at most kWideTileMax frames)
     if (p->interp == IRP_INTERP_SPLINE3 && (sets[i].mask || sets[i].saturation > 0.0f) &&
-        !(spline_path(sets[i].W, sets[i].H) && sets[i].n <= IRP_MAX_FRAMES))
+        !(spline_path(sets[i].W, sets[i].H) && sets[i].n <= kWideTileMax))
       return IRP_ERR_UNSUPPORTED;
   }
   std::vector<std::vector<int>> groups;
@@ -595,7 +615,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
       nf += sets[i].n;
       max_n = std::max(max_n, sets[i].n);
     }
-    const int bucket = reduce_bucket(max_n);
+    const int bucket = set_bucket(max_n);
     const bool stack_only = ps.deep_of[g[0]] >= 0;  // the group holds deep-set chunks
     const bool pre_only = stack_only && ps.deep[ps.deep_of[g[0]]].rows;  // ... or whole sets
     // the group's reduction stencil: spline sets on the row + column passes
@@ -616,7 +636,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
                  ((sets[i].H + tile_rows(bucket, py) - 1) / tile_rows(bucket, py));
       if (tiles < 2 * (int64_t)sm_count()) py = rows_per_warp(bucket, rows_per_warp_alt(bucket));
     }
-    const int THr = gtile ? spline_tile_rows(bucket) : tile_rows(bucket, py);
+    const int THr = gtile ? spline_tile_rows(bucket, max_n) : tile_rows(bucket, py);
     // prefilter work items: tiles x frame groups, enough groups to fill the GPU twice
     int pgroups = 1;
     if (stencil == ST_BSPLINE) {
@@ -793,6 +813,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     si.ncolsegs = ncolsegs;
     si.row_e = row_e;
     si.norm_rb = norm_rb;
+    si.tile_rows = THr;
     if (si.smem > 227 * 1024 - 1024) return IRP_ERR_UNSUPPORTED;  // opt-in limit less static smem
     if (p->persistent && !gtile) {
       const int occ = reduce_occupancy(si.bucket, si.py, gstencil, si.smem);
@@ -810,7 +831,6 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
 // Row-pass coefficients kept resident in L2 between the row pass and the
 // tile kernel (L2 holds about 126 MB; the raw frames, masters and outputs
 // stream through beside them).
-constexpr size_t kL2Budget = (size_t)48 << 20;
 
 // A sub-plan of cubic-spline sets reduced by the tile kernel.  Its sets go in
 // order, in runs of consecutive sets whose row-pass coefficients fit within
@@ -826,7 +846,7 @@ irp_status run_tile_subplan(const uint8_t* buf, const SubInfo& si, const InlineP
   const SetDesc* sd = (const SetDesc*)(img + plan_sets_offset());
   const FrameDesc* fd = (const FrameDesc*)(img + plan_frames_offset(si.nsets));
   const int RB = row_block(si.row_e);
-  const int TH = spline_tile_rows(si.bucket);
+  const int TH = si.tile_rows;
   auto set_bytes = [&](int j) {  // row-pass frames, then bad-pixel planes, contiguous
     const SetDesc& S = sd[j];
     return (size_t)S.n * (crow_frame_bytes(S.W, S.H) +
@@ -841,7 +861,7 @@ irp_status run_tile_subplan(const uint8_t* buf, const SubInfo& si, const InlineP
   auto tiles = [&](int i0, int count) {
     if (e != cudaSuccess || count <= 0) return;
     TraceScope tr(IRP_KERNEL_REDUCE, s);
-    e = launch_spline_tile(si.bucket, inl, dev_plan, i0, count, si.smem, s, false);
+    e = launch_spline_tile(si.bucket, si.tile_rows, inl, dev_plan, i0, count, si.smem, s, false);
   };
   auto discard = [&](const void* p, size_t bytes, int count, size_t stride) {
     if (e != cudaSuccess || bytes == 0) return;
@@ -960,7 +980,8 @@ irp_status run_plan(const uint8_t* buf, uint8_t* ws, size_t ws_bytes, cudaStream
       if (si.pgrid > 0) e = launch_prefilter_raw(&inl, dev_plan, si.pgrid, s);
       if (e == cudaSuccess && si.nrows > 0)
         e = launch_spline_rows(si.row_e, &inl, dev_plan, 0, si.nrows, s);
-      if (e == cudaSuccess && si.ncolsegs > 0) e = launch_spline_cols(&inl, dev_plan, si.ncolsegs, s);
+      if (e == cudaSuccess && si.ncolsegs > 0)
+        e = launch_spline_cols(&inl, dev_plan, 0, si.ncolsegs, s);
       if (e != cudaSuccess) return note_cuda(e);
     }
     if (si.nitems == 0) continue;  // prefilter-only sub-plan (deep spline sets)

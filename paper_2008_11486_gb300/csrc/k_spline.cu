@@ -63,7 +63,8 @@ __device__ __forceinline__ int find_by(const SetDesc* sets, int nsets, int item,
 
 template <int E>
 __global__ void __launch_bounds__(256, 2)
-    k_spline_rows(const __grid_constant__ InlinePlan inl, const void* plan_dev, int item0) {
+    k_spline_rows(const __grid_constant__ InlinePlan inl, const void* plan_dev, int item0,
+                  int stride) {
   constexpr int RB = row_block(E);   // rows per CTA
   constexpr int MQ = E / 4;          // float4 master chunks per lane and row
   constexpr int RQ = E / 8;          // 16-byte raw chunks per lane and row
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(256, 2)
   // (conflict-free for the lane-wise writes and the row-order reads)
   float4* s_out = (float4*)(s_raw + 8 * kRowStages * RQ * 32) + (threadIdx.x >> 5) * 256;
   const PlanView P = make_view(inl, plan_dev);
-  const int item = item0 + (int)blockIdx.x;
+  const int item = item0 + (int)blockIdx.x * stride;
   if (item >= P.h->nrows) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const SetDesc& S = P.sets[find_by(P.sets, P.h->nsets, item, 0)];
@@ -377,10 +378,10 @@ constexpr int kColWarm = 16;   // warm-up rows above and below the CTA's rows
 constexpr int kColOut = 29;    // output columns per CTA: lanes 0..28 (taps reach lane + 3)
 
 __global__ void __launch_bounds__(kColRows, kColRows < 512 ? 512 / kColRows : 1)
-    k_spline_cols(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
+    k_spline_cols(const __grid_constant__ InlinePlan inl, const void* plan_dev, int item0) {
   __shared__ float s_c[kColWarps][32], s_a[kColWarps][32];  // each warp's recursion ends
   const PlanView P = make_view(inl, plan_dev);
-  const int item = blockIdx.x;
+  const int item = item0 + (int)blockIdx.x;
   if (item >= P.h->ncolsegs) return;
   const SetDesc& S = P.sets[find_by(P.sets, P.h->nsets, item, 1)];
   const int W = S.W, H = S.H;
@@ -513,7 +514,7 @@ __global__ void __launch_bounds__(kColRows, kColRows < 512 ? 512 / kColRows : 1)
 }
 
 cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_dev, int item0,
-                               int count, cudaStream_t s) {  // (row block, frame group) items
+                               int count, cudaStream_t s, int stride) {  // (row block, frame group) items
   static bool opted[2] = {false, false};
   const size_t smem = rows_smem_bytes(e);
   cudaError_t err = cudaSuccess;
@@ -524,7 +525,7 @@ cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_de
       if (err != cudaSuccess) return err;
       opted[0] = true;
     }
-    k_spline_rows<32><<<count, 256, smem, s>>>(*inl, plan_dev, item0);
+    k_spline_rows<32><<<count, 256, smem, s>>>(*inl, plan_dev, item0, stride);
   } else {
     if (!opted[1]) {
       err = cudaFuncSetAttribute(k_spline_rows<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -532,7 +533,7 @@ cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_de
       if (err != cudaSuccess) return err;
       opted[1] = true;
     }
-    k_spline_rows<64><<<count, 256, smem, s>>>(*inl, plan_dev, item0);
+    k_spline_rows<64><<<count, 256, smem, s>>>(*inl, plan_dev, item0, stride);
   }
   return cudaGetLastError();
 }
@@ -568,9 +569,9 @@ cudaError_t launch_discard_l2(const void* p, size_t bytes, int count, size_t str
   return cudaGetLastError();
 }
 
-cudaError_t launch_spline_cols(const InlinePlan* inl, const void* plan_dev, int ncolsegs,
-                               cudaStream_t s) {  // ncolsegs: (frame, 29 columns, kColRows rows) items
-  k_spline_cols<<<ncolsegs, kColRows, 0, s>>>(*inl, plan_dev);
+cudaError_t launch_spline_cols(const InlinePlan* inl, const void* plan_dev, int item0, int count,
+                               cudaStream_t s) {  // (frame, 29 columns, kColRows rows) items
+  k_spline_cols<<<count, kColRows, 0, s>>>(*inl, plan_dev, item0);
   return cudaGetLastError();
 }
 

@@ -3,9 +3,6 @@
 // and the FP64 frame-wide sums that choose that scaling.
 #include <float.h>
 
-#include <algorithm>
-#include <type_traits>
-
 #include "combine.cuh"
 #include "prefilter.cuh"
 #include "reduce_kernels.cuh"
@@ -784,77 +781,6 @@ __global__ void __launch_bounds__(kThreads) k_combine(CombineArgs a) {
   combine_pixel<NMAX, F16>(a, s, x, y, s_sc, s_of);
 }
 
-// The same combine with the stack staged through shared memory, one warp per
-// item of 32 pixels of a row: each warp of a persistent CTA takes items in
-// turn and copies the next item's samples ([n][32], 16-byte cp.async,
-// zero-filled past the row) into its own second slab while it sorts the
-// current one.  The warps never wait for one another, so the loads of some
-// overlap the sorts of others as well as their own.  Needs rows on 16-byte
-// boundaries (pitches of 4k FP32 / 8k FP16 values).
-template <int NMAX, bool F16>
-__global__ void __launch_bounds__(kThreads) k_combine_staged(CombineArgs a, int tiles_x,
-                                                             int nitems) {
-  using T = std::conditional_t<F16, __half, float>;
-  constexpr int kPer = 16 / sizeof(T);  // values per 16-byte chunk
-  constexpr int kChunks = 32 / kPer;    // chunks per frame and item
-  extern __shared__ __align__(16) uint8_t s_stage[];
-  __shared__ float s_sc[NMAX], s_of[NMAX];
-  if (F16) {
-    if (threadIdx.x < a.n) {
-      s_sc[threadIdx.x] = a.scale[threadIdx.x];
-      s_of[threadIdx.x] = a.offset[threadIdx.x];
-    }
-    __syncthreads();
-  }
-  const int n = a.n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* const wslab = (T*)s_stage + (size_t)warp * 2 * n * 32;  // this warp's two slabs
-  const float kInf = __int_as_float(0x7f800000);
-  auto issue = [&](int item, T* dst) {
-    const int y = item / tiles_x, x0 = (item - y * tiles_x) * 32;
-    for (int c = lane; c < n * kChunks; c += 32) {
-      const int k = c / kChunks, j = c - k * kChunks;
-      const int xc = x0 + j * kPer;
-      const int nb = min(max(a.W - xc, 0), kPer) * (int)sizeof(T);
-      const T* src = (const T*)a.stack + (int64_t)k * a.fstride + (int64_t)y * a.pitch +
-                     (nb > 0 ? xc : 0);
-      cp_async16(dst + (size_t)k * 32 + j * kPer, src, nb);
-    }
-    cp_async_commit();
-  };
-  const int stride = gridDim.x * (kThreads / 32);
-  int item = blockIdx.x * (kThreads / 32) + warp;
-  if (item < nitems) issue(item, wslab);
-  for (int it = 0; item < nitems; ++it, item += stride) {
-    const int nxt = item + stride;
-    if (nxt < nitems)
-      issue(nxt, wslab + (size_t)((it + 1) & 1) * n * 32);
-    else
-      cp_async_commit();
-    cp_async_wait<1>();
-    __syncwarp();
-    const int y = item / tiles_x, x = (item - y * tiles_x) * 32 + lane;
-    if (x < a.W) {
-      const T* col = wslab + (size_t)(it & 1) * n * 32 + lane;
-      float sv[NMAX];
-#pragma unroll
-      for (int j = 0; j < NMAX; ++j) {
-        if (j < n) {
-          if (F16)
-            sv[j] = __half2float(((const __half*)col)[(size_t)j * 32]);
-          else
-            sv[j] = ((const float*)col)[(size_t)j * 32];
-        } else {
-          sv[j] = kInf;
-        }
-      }
-      combine_pixel<NMAX, F16>(a, sv, x, y, s_sc, s_of);
-    }
-    __syncwarp();  // the slab is refilled two items later
-  }
-  cp_async_wait<0>();
-}
-
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
@@ -981,47 +907,8 @@ cudaError_t launch_prefilter_frames(const InlinePlan* inl, int grid, bool f16, c
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-static int device_sms() {  // cached per process
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 1;
-  }
-  return sms;
-}
-
-template <int NMAX, bool F16>
-static cudaError_t combine_staged(const CombineArgs& a, cudaStream_t s) {
-  static size_t granted = 0;
-  static int occ_smem = -1, occ = 0;
-  const size_t smem = (size_t)2 * a.n * kThreads * (F16 ? 2 : 4);  // two [n][32] slabs per warp
-  auto fn = k_combine_staged<NMAX, F16>;
-  cudaError_t e = ensure_smem(fn, smem, granted);
-  if (e != cudaSuccess) return e;
-  if (occ_smem != (int)smem) {  // resident CTAs per SM for this shared-memory size
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    occ_smem = (int)smem;
-  }
-  const int tiles_x = (a.W + 31) / 32;
-  const int64_t nitems = (int64_t)tiles_x * a.H;
-  if (nitems > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  const int64_t ctas = (nitems + kThreads / 32 - 1) / (kThreads / 32);
-  const int grid = (int)std::min<int64_t>(ctas, (int64_t)std::max(occ, 1) * device_sms());
-  fn<<<grid, kThreads, smem, s>>>(a, tiles_x, (int)nitems);
-  return cudaGetLastError();
-}
-
 template <int NMAX>
 static cudaError_t combine_n(const CombineArgs& a, bool f16, cudaStream_t s) {
-  // the staged form: rows on 16-byte boundaries and two slabs per warp in shared memory
-  const int per = f16 ? 8 : 4;
-  const bool staged = ((uintptr_t)a.stack & 15) == 0 && a.pitch % per == 0 &&
-                      a.fstride % per == 0 &&
-                      (size_t)2 * a.n * kThreads * (f16 ? 2 : 4) <= (size_t)200 * 1024;
-  if (staged) return f16 ? combine_staged<NMAX, true>(a, s) : combine_staged<NMAX, false>(a, s);
   dim3 grid((a.W + kThreads - 1) / kThreads, a.H);
   if (f16)
     k_combine<NMAX, true><<<grid, kThreads, 0, s>>>(a);

@@ -21,26 +21,38 @@ __host__ __device__ constexpr size_t rows_smem_bytes(int E) {
          (size_t)8 * kRowStages * (E / 8) * 32 * 16 + (E == 32 ? (size_t)8 * 8 * 32 * 16 : 0);
 }
 
-// Row pass over the work items [item0, item0 + count) (row block major:
-// item = row0 + rb * frame_groups + g).
+// Row pass over the work items item0 + i * stride, i in [0, count) (row
+// block major: item = row0 + rb * frame_groups + g, so stride frame_groups
+// walks one frame group's row blocks).
 cudaError_t launch_spline_rows(int e, const InlinePlan* inl, const void* plan_dev, int item0,
-                               int count, cudaStream_t s);
+                               int count, cudaStream_t s, int stride = 1);
 
-// Tile kernel of sets on the row pass (n <= IRP_MAX_FRAMES): the column
-// recursion, the 16 taps and the combine per output tile of kSplineTileCols
-// columns x spline_tile_rows(bucket) rows, over the tiles [item0, item0 + grid).
+// Tile kernel of sets on the row pass: the column recursion, the 16 taps and
+// the combine per output tile of kSplineTileCols columns x
+// spline_tile_rows(bucket, max_n) rows, over the tiles [item0, item0 + grid).
+// Sets of up to IRP_MAX_FRAMES frames combine in registers (bucket = the
+// register bucket); deeper sets, to kWideTileMax frames, in groups of G lanes
+// per pixel (bucket = wide_tile_bucket(n): 128 for G = 4, 256 for G = 8).
 constexpr int kSplineTileCols = 29;  // lane l's horizontal taps reach lane l + 3
-int spline_tile_rows(int bucket);
+constexpr int kWideTileMax = 256;
+constexpr size_t kWideTileSmem = 220 * 1024;  // dynamic shared memory of a wide tile CTA
+__host__ __device__ constexpr int wide_tile_bucket(int n) { return n <= 128 ? 128 : 256; }
+__host__ __device__ constexpr int wide_tile_g(int bucket) { return bucket <= 128 ? 4 : 8; }
+// Words per pixel of the wide tile kernel's samples: n, a pad word per 32, odd.
+__host__ __device__ constexpr int wide_tile_stride(int n) { return (n + (n + 31) / 32) | 1; }
+int spline_tile_rows(int bucket, int max_n);
 size_t spline_tile_smem_bytes(int bucket, int max_n);
-cudaError_t launch_spline_tile(int bucket, const InlinePlan* inl, const void* plan_dev, int item0,
-                               int grid, size_t smem, cudaStream_t s, bool pdl);
+cudaError_t launch_spline_tile(int bucket, int th, const InlinePlan* inl, const void* plan_dev,
+                               int item0, int grid, size_t smem, cudaStream_t s, bool pdl);
 
 // Drops dead intermediate data from L2 without writing it back to HBM
 // (discard.global.L2): `count` ranges of `bytes` at p + i * stride, each
 // shrunk to the 128-byte lines that lie wholly inside it.
 cudaError_t launch_discard_l2(const void* p, size_t bytes, int count, size_t stride,
                               cudaStream_t s);
-cudaError_t launch_spline_cols(const InlinePlan* inl, const void* plan_dev, int ncolsegs,
+// Column pass over the work items [item0, item0 + count) (frame major:
+// item = colseg0 + (k * row_segments + rs) * col_blocks + cb).
+cudaError_t launch_spline_cols(const InlinePlan* inl, const void* plan_dev, int item0, int count,
                                cudaStream_t s);
 
 }  // namespace irp

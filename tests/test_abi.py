@@ -108,9 +108,9 @@ def test_reduce_set_validation_codes(L):
     assert _reduce(L, [_set(mask=FAKE, mask_pitch=10)], _params()) == 1    # mask pitch < W
     assert _reduce(L, [_set(saturation=-1.0)], _params()) == 1              # negative level
     # the cubic spline masks the sets its tile kernel reduces (row pass: 34 <= W
-    # <= 2048, H >= 34; at most 64 frames); others return IRP_ERR_UNSUPPORTED
+    # <= 2048, H >= 34; at most 256 frames); others return IRP_ERR_UNSUPPORTED
     assert _reduce(L, [_set(W=20, mask=FAKE, mask_pitch=64)], _params(interp=2)) == 4
-    assert _reduce(L, [_set(n=65, saturation=6e4)], _params(interp=2)) == 4
+    assert _reduce(L, [_set(n=257, saturation=6e4)], _params(interp=2)) == 4
     ok = (B.IrpSet * 1)(_set(mask=FAKE, mask_pitch=64, saturation=6e4))
     assert L.irp_workspace_size(ok, 1, ctypes.byref(_params(interp=2))) > 0
 

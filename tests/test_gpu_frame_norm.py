@@ -64,8 +64,8 @@ def test_frame_normalisation_matches_oracle(interp, mode):
 
 @pytest.mark.parametrize("interp", ["bilinear", "spline3"])
 def test_frame_normalisation_of_a_deep_set(interp):
-    """70 frames: the stack chunks (bilinear) and the combine from filtered
-    spline rows both take each frame's factors."""
+    """70 frames: the stack chunks (bilinear) and the spline tile kernel's
+    lane-group form both take each frame's factors."""
     fs = _levelled_set(64, 48, 70, 8900, "zero")
     s = core.device_set(fs).alloc_outputs()
     ws = core.reduce_sets([s], core.reduce_params(interp, frame_norm="zero"))
