@@ -860,6 +860,7 @@ def run_served(args, cfg, dev, world, rank, local):
     lat, wall = serve.run_poisson(srv, reqs, rate_hz=args.rate)
     phase = {"queued_s": [r.admitted - r.arrival for r in reqs],
              "upload_s": [r.uploaded - r.admitted for r in reqs],
+             "upload_device_s": [r.upload_device_ms * 1e-3 for r in reqs],
              "prepare_s": [r.launched - r.uploaded for r in reqs],
              "device_s": [r.done - r.launched for r in reqs]}
     nominal = {"batches": srv.batches, "batch_sizes": list(srv.batch_sizes),
@@ -900,6 +901,8 @@ def run_served(args, cfg, dev, world, rank, local):
                           "p99": round(float(np.percentile(lat, 99)), 4),
                           "max": round(float(lat.max()), 4), "rate_hz": args.rate,
                           "p50_phases": {k: round(float(np.percentile(v, 50)), 4)
+                                         for k, v in phase.items()},
+                          "p99_phases": {k: round(float(np.percentile(v, 99)), 4)
                                          for k, v in phase.items()}},
             "saturation": {"requests": sat_n, "wall_s": round(sat_wall, 3),
                            "p50_s": round(float(np.percentile(sat_lat, 50)), 4),

@@ -62,12 +62,14 @@ class Request:
     arrival: float = 0.0
     admitted: float = 0.0  # its frames' copies queued
     uploaded: float = 0.0  # the scheduler saw its copies complete
+    upload_device_ms: float = 0.0  # device time of its copies (CUDA events on the copy stream)
     launched: float = 0.0  # its reduction queued
     done: float = 0.0
     outputs: list = None  # per chip (mean, median) device tensors (views of the output ring)
     host_means: list = None  # per chip pinned host mean images (servers that download)
     out_slot: int = 0
     status: int = 0       # device status of its reduction (0 = IRP_OK), set on completion
+    _copy_events: tuple = dataclasses.field(default=None, repr=False)  # (start, end) of its upload
 
 
 class Chip:
@@ -243,6 +245,8 @@ class Server:
                 self.pending.popleft()
             nums = []
             with torch.cuda.stream(self.copy_stream):
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev0.record(self.copy_stream)
                 for c, (chip, frame) in enumerate(zip(self.chips, req.frames)):
                     slot = chip.next_slot()
                     chip.ring[slot].copy_(frame, non_blocking=True)
@@ -251,9 +255,10 @@ class Server:
                     chip.slot_t[slot] = req.exptime
                     nums.append(chip.count)
                     chip.count += 1
-                ev = torch.cuda.Event()
+                ev = torch.cuda.Event(enable_timing=True)
                 ev.record(self.copy_stream)
             req.admitted = time.perf_counter()
+            req._copy_events = (ev0, ev)
             req.out_slot = self.admitted % self.out_slots
             self.admitted += 1
             if self.running:
@@ -351,6 +356,9 @@ class Server:
                 t = time.perf_counter()
                 for r in reqs:
                     r.done = t
+                    ev0, ev1 = r._copy_events
+                    r.upload_device_ms = ev0.elapsed_time(ev1)
+                    r._copy_events = None
                     self.done.append(r)
                 self.ws_free.append(ws)
             else:

@@ -22,8 +22,14 @@ ERR = 5     # IRP_ERR_BAD_MASTER
 
 
 class _Event:
+    def __init__(self, *args, **kwargs):
+        pass
+
     def record(self, stream=None):
         pass
+
+    def elapsed_time(self, other):
+        return 0.0
 
     def query(self):
         return True
