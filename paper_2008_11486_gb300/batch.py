@@ -3,9 +3,12 @@
 ``BatchReducer`` encodes all sets into one plan (pinned host memory), launches
 it as persistent CTAs pulling (set, tile) work items longest-first, and
 captures that launch in a CUDA graph so that every later pass is one graph
-replay.  ``Autotuner`` picks the tile height (rows per warp) and the persistent
-grid size for a batch signature by timing the candidates on the batch itself
-with CUDA events, and keeps the winners in a JSON cache.
+replay.  ``Autotuner`` picks the work distribution (persistent CTAs pulling
+tiles, or one CTA per tile), the tile height (rows per warp) and the
+persistent grid size for a batch signature by timing the candidates on the
+batch itself with CUDA events, and keeps the winners in a JSON cache.  The
+tile width is one warp (a lane per output column) and the frames a CTA
+stages at once are fixed by its shared memory, so they are not tuned.
 """
 from __future__ import annotations
 
@@ -39,7 +42,7 @@ class Autotuner:
 
     Candidates: rows per warp (0 = bucket default, or the alternative height)
     and, for persistent launches, the grid as 1x / 2x / 4x the SM count
-    (0 = occupancy-derived)."""
+    (0 = occupancy-derived), or one CTA per tile (persistent False)."""
 
     def __init__(self, cache_path: str | None = None, reps: int = 3):
         self.cache_path = cache_path
@@ -62,7 +65,11 @@ class Autotuner:
         alts = {2 if _bucket(s.n) <= 16 else 1 for s in sets}
         rows += sorted(alts)
         grids = [0, sms, 2 * sms, 4 * sms] if persistent else [0]
-        return [dict(rows_per_warp=r, max_ctas=g) for r in rows for g in grids]
+        cands = [dict(rows_per_warp=r, max_ctas=g, persistent=persistent)
+                 for r in rows for g in grids]
+        if persistent:
+            cands += [dict(rows_per_warp=r, max_ctas=0, persistent=False) for r in rows]
+        return cands
 
     def _time(self, sets, params, stream) -> float:
         plan = core.Plan(sets, params)
@@ -84,7 +91,7 @@ class Autotuner:
         stream = stream if stream is not None else torch.cuda.current_stream()
         results = {}
         for cand in self.candidates(sets, persistent):
-            p = core.reduce_params(interp, clip, persistent=persistent, **cand)
+            p = core.reduce_params(interp, clip, **cand)
             results[json.dumps(cand, sort_keys=True)] = self._time(sets, p, stream)
         best = min(results, key=results.get)
         return json.loads(best), results
@@ -102,7 +109,8 @@ class Autotuner:
                     with open(tmp, "w") as f:
                         json.dump(self.cache, f, indent=1, sort_keys=True)
                     os.replace(tmp, self.cache_path)
-        return core.reduce_params(interp, clip, persistent=persistent, **cfg), cfg
+        cfg = {"persistent": persistent, **cfg}  # caches written before the knob existed
+        return core.reduce_params(interp, clip, **cfg), cfg
 
 
 class BatchReducer:
