@@ -313,20 +313,22 @@ def timed_steps(step, steps, warmup, stream, flush, world, local):
     return total_ms, wall, prof, clocks
 
 
-# DRAM bytes (read + write) per step of the dominant kernel kind, from one ncu
-# capture of the workload (summaries in profiles/).  A figure holds only for
-# the kernel sources it was taken on, identified by their hash; otherwise the
-# line reports null.
-# The figures were captured on sources 7d03a8604e4f95fd.  The current sources
-# differ from those in comments and in the plan's choice of shorter tiles for
-# groups of fewer than two tiles per SM, which none of these workloads forms:
-# their kernels and launches are the ones captured.
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture
+# with --cache-control none so that L2 carries over between a step's kernels
+# as in a run) of the dominant kernel kind per step, and of every kernel of
+# the step, keyed by the hash of the kernel sources they were taken on:
+# (source hash, dominant kind, kind bytes per step, path bytes per step).
+# The captures and their commands are summarised under profiles/.
 TRAFFIC = {
-    "bands": ("01544d57caae0ba5", "prefilter", 374_298_316),  # row + column pass
-    "deep": ("01544d57caae0ba5", "reduce", 1_417_629_525),
-    "paper_band": ("01544d57caae0ba5", "combine", 758_102_912),
-    # three bands of the paper_band shape: three launches of the same traffic
-    "paper": ("01544d57caae0ba5", "combine", 3 * 758_102_912),
+    # 3 bands: per band the row pass 40.84 MB, the tile kernel 10.35 MB, the
+    # discard 0.01 MB
+    "bands": ("b870d68c7ef1775e", "reduce", 3 * 10_350_000, 3 * 51_200_000),
+    "deep": ("b870d68c7ef1775e", "reduce", 1_423_320_000, 1_423_320_000),
+    "precision": ("b870d68c7ef1775e", "reduce", 1_423_320_000, 1_423_320_000),
+    # row pass 1105.56 MB, column pass 1519.06 MB, combine 803.58 MB
+    "paper_band": ("b870d68c7ef1775e", "combine", 803_580_000, 3_428_200_000),
+    # three bands of the paper_band shape: three launches of each kind
+    "paper": ("b870d68c7ef1775e", "combine", 3 * 803_580_000, 3 * 3_428_200_000),
 }
 
 
@@ -337,10 +339,11 @@ TRAFFIC = {
 # clock -- they give the roofline of kernels that instruction issue, rather
 # than HBM, limits.
 ISSUE = {
-    "bands": ("01544d57caae0ba5", "prefilter", 35_221_760 + 38_887_200),  # rows + columns
-    "deep": ("01544d57caae0ba5", "reduce", 1_292_075_776),
-    "paper_band": ("01544d57caae0ba5", "combine", 1_195_229_264),
-    "paper": ("01544d57caae0ba5", "combine", 3 * 1_195_229_264),
+    "bands": ("b870d68c7ef1775e", "reduce", 3 * 39_700_000),
+    "deep": ("b870d68c7ef1775e", "reduce", 1_324_180_000),
+    "precision": ("b870d68c7ef1775e", "reduce", 1_324_180_000),
+    "paper_band": ("b870d68c7ef1775e", "combine", 1_215_470_000),
+    "paper": ("b870d68c7ef1775e", "combine", 3 * 1_215_470_000),
 }
 
 
@@ -398,11 +401,14 @@ def roofline(prof, steps, path_bytes_per_step, ms_per_step, workload=None, sm_co
     peak, peak_src = measured_peaks()
     achieved = path_bytes_per_step / (dom_ms * 1e-3) / 1e9
     traffic = None
+    path_traffic = None
     rec = TRAFFIC.get(workload)
     if rec and rec[1] == dom and rec[2] is not None and rec[0] == kernel_source_hash():
         traffic = rec[2]
+        path_traffic = rec[3] if len(rec) > 3 else None
     return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "path_traffic": path_traffic,
             "algorithmic_bytes": path_bytes_per_step,
             "bytes_basis": "P (2n + 20) per set: raw once, masters once, mean and median once",
             "peak_source": peak_src,
