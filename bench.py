@@ -41,6 +41,11 @@ WORKLOADS = {
                        "shift, 3-sigma clipped mean (3 passes) + median, the three bands in one call",
                   sets=[(1024, 1024, 10)] * 3, offset=10.0, interp="spline3", persistent=False,
                   seed=11486001),
+    "bands_onchip": dict(desc="the bands workload with spline_onchip: the row pass, then one "
+                              "tile kernel solving the columns and combining on chip, the "
+                              "row-pass frames kept in L2",
+                         sets=[(1024, 1024, 10)] * 3, offset=10.0, interp="spline3",
+                         persistent=False, seed=11486001, onchip=True),
     "small": dict(desc="5 frames of 512x512 uint16, offsets +-5 px, bilinear shift, 3-sigma "
                        "clipped mean (3 passes) + median",
                   sets=[(512, 512, 5)], offset=5.0, interp="bilinear", persistent=False,
@@ -320,15 +325,17 @@ def timed_steps(step, steps, warmup, stream, flush, world, local):
 # (source hash, dominant kind, kind bytes per step, path bytes per step).
 # The captures and their commands are summarised under profiles/.
 TRAFFIC = {
-    # 3 bands: per band the row pass 40.84 MB, the tile kernel 10.35 MB, the
-    # discard 0.01 MB
-    "bands": ("b870d68c7ef1775e", "reduce", 3 * 10_350_000, 3 * 51_200_000),
-    "deep": ("b870d68c7ef1775e", "reduce", 1_423_320_000, 1_423_320_000),
-    "precision": ("b870d68c7ef1775e", "reduce", 1_423_320_000, 1_423_320_000),
-    # row pass 1105.56 MB, column pass 1519.06 MB, combine 803.58 MB
-    "paper_band": ("b870d68c7ef1775e", "combine", 803_580_000, 3_428_200_000),
+    # 3 bands in one call: row pass 141.60 MB, column pass 156.13 MB, the
+    # vertical-tap reduction 108.29 MB
+    "bands": ("e3b70a8af7d860dd", "prefilter", 141_600_000 + 156_130_000, 406_020_000),
+    # per band: row pass 40.75 MB, tile kernel 10.50 MB, discard 0.01 MB
+    "bands_onchip": ("e3b70a8af7d860dd", "reduce", 3 * 10_500_000, 3 * 51_260_000),
+    "deep": ("e3b70a8af7d860dd", "reduce", 1_423_170_000, 1_423_170_000),
+    "precision": ("e3b70a8af7d860dd", "reduce", 1_423_170_000, 1_423_170_000),
+    # row pass 1104.92 MB, column pass 1518.99 MB, combine 803.71 MB
+    "paper_band": ("e3b70a8af7d860dd", "combine", 803_710_000, 3_427_620_000),
     # three bands of the paper_band shape: three launches of each kind
-    "paper": ("b870d68c7ef1775e", "combine", 3 * 803_580_000, 3 * 3_428_200_000),
+    "paper": ("e3b70a8af7d860dd", "combine", 3 * 803_710_000, 3 * 3_427_620_000),
 }
 
 
@@ -339,11 +346,12 @@ TRAFFIC = {
 # clock -- they give the roofline of kernels that instruction issue, rather
 # than HBM, limits.
 ISSUE = {
-    "bands": ("b870d68c7ef1775e", "reduce", 3 * 39_700_000),
-    "deep": ("b870d68c7ef1775e", "reduce", 1_324_180_000),
-    "precision": ("b870d68c7ef1775e", "reduce", 1_324_180_000),
-    "paper_band": ("b870d68c7ef1775e", "combine", 1_215_470_000),
-    "paper": ("b870d68c7ef1775e", "combine", 3 * 1_215_470_000),
+    "bands": ("e3b70a8af7d860dd", "prefilter", 24_520_000 + 26_840_000),  # rows + columns
+    "bands_onchip": ("e3b70a8af7d860dd", "reduce", 3 * 39_700_000),
+    "deep": ("e3b70a8af7d860dd", "reduce", 1_324_180_000),
+    "precision": ("e3b70a8af7d860dd", "reduce", 1_324_180_000),
+    "paper_band": ("e3b70a8af7d860dd", "combine", 1_215_470_000),
+    "paper": ("e3b70a8af7d860dd", "combine", 3 * 1_215_470_000),
 }
 
 
@@ -552,7 +560,8 @@ def run_workload(args, name, dev, stream, world, rank, local, steps=None, min_se
     # workloads launch as their config says (persistent CTAs pulling tiles
     # from an atomic counter measured 3% faster on 32 x 4096^2)
     persistent = bool(cfg["persistent"]) and name != "batch"
-    params = core.reduce_params(interp, core.clip_params(3.0, 3), persistent=persistent)
+    params = core.reduce_params(interp, core.clip_params(3.0, 3), persistent=persistent,
+                                spline_onchip=cfg.get("onchip", False))
     ws = core.workspace(max([core.workspace_size([s], params) for s in sets] +
                             [core.workspace_size(sets, params)]), dev)
 
@@ -676,7 +685,7 @@ def run_headline(args, dev, stream, world, rank, local):
     line = run_workload(args, "batch", dev, stream, world, rank, local, steps=args.steps,
                         with_cpu=False)
     subs = {}
-    for name in ("precision", "bands", "paper_band"):
+    for name in ("precision", "bands", "bands_onchip", "paper_band"):
         sub = run_workload(args, name, dev, stream, world, rank, local, with_cpu=False,
                            with_e2e=(name == "bands"))
         if rank == 0:
@@ -692,7 +701,8 @@ def run_headline(args, dev, stream, world, rank, local):
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_both("batch")
         line["config"]["workload"] = ("batch: " + line["config"]["workload"] + " (value); "
-                                      "subrecords deep, bands, paper_band, served")
+                                      "subrecords deep, bands, bands_onchip, paper_band, "
+                                      "served")
     return line
 
 

@@ -237,6 +237,17 @@ typedef struct {
                                      frames.  With scale, a mean of 0 or not finite
                                      latches IRP_ERR_BAD_STATISTIC.  stack_out holds
                                      the normalised samples. */
+  int spline_onchip;              /* cubic spline, unmasked sets on the row pass
+                                     (34 <= W <= 2048, H >= 34, up to IRP_MAX_FRAMES
+                                     frames): 0 = row pass, column pass (the
+                                     filtered rows in the workspace) and the
+                                     reduction of the vertical taps, the faster
+                                     form; 1 = row pass, then one tile kernel that
+                                     solves the columns and combines on chip, with
+                                     the row-pass frames kept in L2: about 1.2x
+                                     the algorithmic DRAM bytes instead of about
+                                     4x, for callers that share HBM bandwidth.
+                                     Masked sets always take the tile kernel. */
 } irp_reduce_params;
 
 size_t irp_workspace_size(const irp_set* sets, int nsets, const irp_reduce_params* p);

@@ -59,7 +59,7 @@ class IrpHostIo(ctypes.Structure):
 class ReduceParams(ctypes.Structure):
     _fields_ = [("interp", c_i), ("clip", ClipParams), ("normalize_flat", c_i),
                 ("persistent", c_i), ("max_ctas", c_i), ("wait_spin_limit", c_i),
-                ("rows_per_warp", c_i), ("frame_norm", c_i)]
+                ("rows_per_warp", c_i), ("frame_norm", c_i), ("spline_onchip", c_i)]
 
 
 _lock = threading.Lock()

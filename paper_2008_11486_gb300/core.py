@@ -220,12 +220,14 @@ def _irp_sets(sets):
 
 def reduce_params(interp="bilinear", clip=None, normalize_flat=False, persistent=False,
                   max_ctas=0, wait_spin_limit=0, rows_per_warp=0,
-                  frame_norm="none") -> ReduceParams:
+                  frame_norm="none", spline_onchip=False) -> ReduceParams:
     """``frame_norm``: "none", "zero" or "scale" per-frame normalisation of the
-    samples to the set's first frame before the combine."""
+    samples to the set's first frame before the combine.  ``spline_onchip``:
+    unmasked cubic-spline sets on the row pass take the tile kernel (less DRAM
+    traffic) instead of the column pass and vertical-tap reduction (faster)."""
     return ReduceParams(INTERP[interp], clip if clip is not None else clip_params(),
                         int(normalize_flat), int(persistent), int(max_ctas), int(wait_spin_limit),
-                        int(rows_per_warp), FRAME_NORM[frame_norm])
+                        int(rows_per_warp), FRAME_NORM[frame_norm], int(bool(spline_onchip)))
 
 
 def workspace_size(sets, params: ReduceParams) -> int:

@@ -79,8 +79,9 @@ def _di_stats(got, want, valid):
                 dI_rms=float(np.sqrt(np.mean(dI ** 2))), err_over_peak=float(err_peak))
 
 
-@pytest.mark.parametrize("W,H", [(96, 80), (70, 30)])  # row/column passes; tiled prefilter
-def test_shift_of_bspline_basis_image_is_exact(W, H):
+# row and column passes, the on-chip tile kernel, the tiled prefilter (H < 34)
+@pytest.mark.parametrize("W,H,onchip", [(96, 80, False), (96, 80, True), (70, 30, False)])
+def test_shift_of_bspline_basis_image_is_exact(W, H, onchip):
     n = 6
     rng = np.random.default_rng(W * H)
     dx = rng.uniform(-2.9, 2.9, n)
@@ -93,7 +94,8 @@ def test_shift_of_bspline_basis_image_is_exact(W, H):
                         exptime=np.full(n, 60.0, np.float32), dx=dx, dy=dy)
     # fused, from raw
     s = core.device_set(fs).alloc_outputs(want_stack=True)
-    ws = core.reduce_sets([s], core.reduce_params("spline3", core.clip_params(3.0, 3)))
+    ws = core.reduce_sets([s], core.reduce_params("spline3", core.clip_params(3.0, 3),
+                                                  spline_onchip=onchip))
     assert core.sync_status(ws) == 0
     st = s.stack.cpu().numpy().astype(np.float64)
     valid = ~np.isnan(st)

@@ -25,10 +25,10 @@ def _native():
 
 
 def run_fused(fs_list, interp, *, kappa=3.0, max_iter=3, persistent=False, want_stack=True,
-              normalize_flat=False, center="mean", ddof=0):
+              normalize_flat=False, center="mean", ddof=0, onchip=False):
     sets = [core.device_set(fs).alloc_outputs(want_stack=want_stack) for fs in fs_list]
     params = core.reduce_params(interp, core.clip_params(kappa, max_iter, center, ddof),
-                                normalize_flat, persistent)
+                                normalize_flat, persistent, spline_onchip=onchip)
     ws = core.reduce_sets(sets, params)
     assert core.sync_status(ws) == 0
     out = []
@@ -79,12 +79,14 @@ def check_against_oracle(fs, got, interp, kappa, max_iter, normalize_flat=False,
     return stats
 
 
-@pytest.mark.parametrize("interp", ["nearest", "bilinear", "spline3", "cubic"])
-def test_fused_small_ragged(interp):
+@pytest.mark.parametrize("interp,onchip", [("nearest", False), ("bilinear", False),
+                                           ("spline3", False), ("spline3", True),
+                                           ("cubic", False)])
+def test_fused_small_ragged(interp, onchip):
     fs = synth.make_set(100, 70, 12, 5.0, 501, n_stars=40, n_cr=8)
-    got = run_fused([fs], interp, kappa=2.5)[0]
+    got = run_fused([fs], interp, kappa=2.5, onchip=onchip)[0]
     stats = check_against_oracle(fs, got, interp, 2.5, 3)
-    print(interp, stats)
+    print(interp, onchip, stats)
 
 
 def test_fused_small_config_full_size():
@@ -94,11 +96,13 @@ def test_fused_small_config_full_size():
     print(check_against_oracle(fs, got, "bilinear", 3.0, 3))
 
 
-def test_fused_spline_band_full_size_sampled():
+@pytest.mark.parametrize("onchip", [False, True])
+def test_fused_spline_band_full_size_sampled(onchip):
     """One band of the multi-band workload: 10 frames of 1024^2, +-10 px,
-    spline; the oracle evaluates sampled pixels (and every edge pixel)."""
+    spline (column pass and vertical taps, or the on-chip tile kernel); the
+    oracle evaluates sampled pixels (and every edge pixel)."""
     fs = synth.workload_bands(n=10)[0]
-    got = run_fused([fs], "spline3", want_stack=False)[0]
+    got = run_fused([fs], "spline3", want_stack=False, onchip=onchip)[0]
     rng = np.random.default_rng(7)
     H, W = fs.H, fs.W
     xs = np.concatenate([rng.integers(0, W, 3000), np.arange(W), np.arange(W),
@@ -156,10 +160,12 @@ def _padded_device_set(fs, pad_raw, pad_master):
     (1000, 36, 3, 0, 0),     # 16-byte rows, the last lane's chunks partly past the row
     (1018, 36, 3, 2, 0),     # 8-byte rows, a chunk cut inside its first half
 ])
-def test_spline_row_pass_shapes(W, H, n, pad_raw, pad_master):
+@pytest.mark.parametrize("onchip", [False, True])
+def test_spline_row_pass_shapes(W, H, n, pad_raw, pad_master, onchip):
     fs = synth.make_set(W, H, n, 6.0, 4100 + W + n, n_stars=30, n_cr=6)
     s = _padded_device_set(fs, pad_raw, pad_master)
-    ws = core.reduce_sets([s], core.reduce_params("spline3", core.clip_params(3.0, 3)))
+    ws = core.reduce_sets([s], core.reduce_params("spline3", core.clip_params(3.0, 3),
+                                                  spline_onchip=onchip))
     assert core.sync_status(ws) == 0
     got = dict(mean=s.mean.cpu().numpy(), median=s.median.cpu().numpy(),
                nkept=s.nkept.cpu().numpy().astype(np.int32), stack=s.stack.cpu().numpy())
@@ -483,7 +489,7 @@ def test_spline_tile_stripes_of_a_set_larger_than_the_l2_budget():
     random sample, match the oracle."""
     W, H, n = 2048, 640, 12
     fs = synth.make_set(W, H, n, 10.0, 2048640, n_stars=300, n_cr=20)
-    got = run_fused([fs], "spline3", want_stack=False)[0]
+    got = run_fused([fs], "spline3", want_stack=False, onchip=True)[0]
     rng = np.random.default_rng(64)
     band = np.arange(200, 320)  # around the first stripe ends (256 rows, less warm-up)
     band2 = np.arange(440, 580)
