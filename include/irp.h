@@ -168,7 +168,7 @@ irp_status irp_combine(const void* stack, int64_t pitch, int64_t frame_stride,
  * one or more frame sets, each raw pixel read from HBM once (bilinear and
  * nearest; cubic spline computes the spline coefficients of every calibrated
  * frame into the workspace first and then resamples and combines them).
- * A cubic-spline set whose frames take the row pass (W from 34 to 2048, H at
+ * A cubic-spline set whose frames take the row pass (W from 34 to 8192, H at
  * least 34) is reduced from the row-pass coefficients by one tile kernel,
  * which keeps each tile's samples on chip: up to IRP_MAX_FRAMES frames, and
  * masked sets up to 256 frames (a group of 4 or 8 lanes then combines a
@@ -206,7 +206,7 @@ typedef struct {
    * `saturation`; a sample whose taps with non-zero weight include a bad pixel
    * is invalid (left out of the combine, NaN in stack_out).  Every
    * resampler; with the cubic spline only for sets on the row pass (W from
-   * 34 to 2048, H at least 34) of at most 256 frames, others returning
+   * 34 to 8192, H at least 34) of at most 256 frames, others returning
    * IRP_ERR_UNSUPPORTED. */
   const uint8_t* mask;            /* device [H][mask_pitch] uint8, nullable */
   int64_t mask_pitch;             /* elements (>= W when mask is set) */
@@ -238,7 +238,7 @@ typedef struct {
                                      latches IRP_ERR_BAD_STATISTIC.  stack_out holds
                                      the normalised samples. */
   int spline_onchip;              /* cubic spline, unmasked sets on the row pass
-                                     (34 <= W <= 2048, H >= 34, up to IRP_MAX_FRAMES
+                                     (34 <= W <= 8192, H >= 34, up to IRP_MAX_FRAMES
                                      frames): 0 = row pass, column pass (the
                                      filtered rows in the workspace) and the
                                      reduction of the vertical taps, the faster

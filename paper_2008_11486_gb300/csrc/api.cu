@@ -512,7 +512,7 @@ irp_status check_params(const irp_set* sets, int nsets, const irp_reduce_params*
     irp_status st = check_set(sets[i]);
     if (st != IRP_OK) return st;
     // with the cubic spline, bad-pixel masking is built for the sets the tile
-    // kernel reduces (34 <= W <= 2048, H >= 34, at most kWideTileMax frames)
+    // kernel reduces (34 <= W <= 8192, H >= 34, at most kWideTileMax frames)
     if (p->interp == IRP_INTERP_SPLINE3 && (sets[i].mask || sets[i].saturation > 0.0f) &&
         !(spline_path(sets[i].W, sets[i].H) && sets[i].n <= kWideTileMax))
       return IRP_ERR_UNSUPPORTED;
@@ -734,7 +734,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
         // more CTAs than one wave)
         const int nrb = (s.H + row_block(row_e) - 1) / row_block(row_e);
         S.rgroup = std::min(kRowGroup, s.n);
-        nrows += ((s.n + S.rgroup - 1) / S.rgroup) * nrb;
+        nrows += ((s.n + S.rgroup - 1) / S.rgroup) * row_segments(s.W) * nrb;
         if (!gtile) ncolsegs += s.n * ((s.W + 28) / 29) * ((s.H + kColRows - 1) / kColRows);
       }
       // premerged master window {bias + dark*t, rf}: raw sources of one
@@ -887,7 +887,8 @@ irp_status run_tile_subplan(const uint8_t* buf, const SubInfo& si, const InlineP
     if (b == a + 1 && bytes > kL2Budget) {
       // one set in stripes of rows
       const SetDesc& S = sd[a];
-      const int ngroups = (S.n + S.rgroup - 1) / S.rgroup;
+      // row-pass work items per row block: frame groups x row segments
+      const int ngroups = (S.n + S.rgroup - 1) / S.rgroup * row_segments(S.W);
       const int nrb = (S.H + RB - 1) / RB;
       int oymin = INT32_MAX, oymax = INT32_MIN;
       for (int k = 0; k < S.n; ++k) {

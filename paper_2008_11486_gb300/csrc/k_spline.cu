@@ -89,12 +89,22 @@ __global__ void __launch_bounds__(256, 2)
     __syncthreads();
     if (!s_ok) return;  // status latched
   }
-  const int W = S.W, H = S.H;
-  // row block major, so that a range of row blocks is a range of work items
+  const int H = S.H;
+  // row block major, so that a range of row blocks is a range of work items;
+  // within a row block, segment major
   const int rg = S.rgroup;
   const int ngroups = (S.n + rg - 1) / rg;
+  const int nseg = row_segments(S.W);
   const int local = item - S.row0;
-  const int rb = local / ngroups, g = local - rb * ngroups;  // row block, frame chunk
+  const int rb = local / (ngroups * nseg);
+  const int rem = local - rb * (ngroups * nseg);
+  const int sg = rem / ngroups, g = rem - sg * ngroups;  // segment, frame chunk
+  // this item's columns: source [xs, xs + W) of the row, coefficients kept
+  // for the core [c0, c1) (relative: [cl, cr))
+  int c0, c1, xs;
+  row_segment(S.W, sg, c0, c1, xs);
+  const int W = min(S.W - xs, kSegCols);
+  const int cl = c0 - xs, cr = c1 - xs;
   const int y0 = rb * RB, nr = min(RB, H - y0);
   const int k0 = g * rg, nk = min(rg, S.n - k0);
   const int x0 = lane * E;
@@ -109,7 +119,7 @@ __global__ void __launch_bounds__(256, 2)
         const int y = y0 + rr;
         const int nb = (rr < nr && x < W) ? 4 * min(4, W - x) : 0;
         const float* base = a == 0 ? S.bias : (a == 1 ? S.dark : S.flat);
-        const float* gp = nb ? base + (int64_t)y * S.master_pitch + x : S.bias;
+        const float* gp = nb ? base + (int64_t)y * S.master_pitch + xs + x : S.bias;
         cp_async16(s_m + ((rr * 3 + a) * MQ + i) * 32 + l, gp, nb);
       }
     } else {
@@ -120,7 +130,7 @@ __global__ void __launch_bounds__(256, 2)
         const int y = y0 + rr;
         const int nb = (rr < nr && x < W) ? 4 : 0;
         const float* base = a == 0 ? S.bias : (a == 1 ? S.dark : S.flat);
-        const float* gp = nb ? base + (int64_t)y * S.master_pitch + x : S.bias;
+        const float* gp = nb ? base + (int64_t)y * S.master_pitch + xs + x : S.bias;
         cp_async4((float*)(s_m + ((rr * 3 + a) * MQ + (j >> 2)) * 32 + l) + (j & 3), gp, nb);
       }
     }
@@ -152,7 +162,7 @@ __global__ void __launch_bounds__(256, 2)
   auto issue = [&](int t, int slot) {
     const int rr = t / nk, f = t - rr * nk;
     const int fl = s_flags[f];
-    const uint16_t* raw = s_src[f] + (int64_t)(y0 + rr) * S.src_pitch;
+    const uint16_t* raw = s_src[f] + (int64_t)(y0 + rr) * S.src_pitch + xs;
 #pragma unroll
     for (int k = 0; k < RQ; ++k) {
       const int c = 32 * k + lane, lc = c / RQ, ic = c - lc * RQ;
@@ -175,7 +185,7 @@ __global__ void __launch_bounds__(256, 2)
   cp_async_wait<kRowStages - 1>();
   __syncthreads();
   {
-    const float flat_norm = S.flat_sum ? (float)(*S.flat_sum / ((double)W * H)) : 1.0f;
+    const float flat_norm = S.flat_sum ? (float)(*S.flat_sum / ((double)S.W * H)) : 1.0f;
     for (int c = threadIdx.x; c < RB * MQ * 32; c += 256) {
       const int rr = c / (MQ * 32), rem = c - rr * (MQ * 32);
       const int i = rem >> 5, l = rem & 31;
@@ -221,7 +231,7 @@ __global__ void __launch_bounds__(256, 2)
                                        bb[e], dd[e], tk, rf[e]);
       }
     } else {
-      const uint16_t* raw = s_src[f] + (int64_t)y * S.src_pitch;
+      const uint16_t* raw = s_src[f] + (int64_t)y * S.src_pitch + xs;
 #pragma unroll
       for (int i = 0; i < MQ; ++i) {
         const float4 b = mb[i * 32], d = md[i * 32], r = mr[i * 32];
@@ -237,9 +247,9 @@ __global__ void __launch_bounds__(256, 2)
     if (masked) {
       // this row's bad pixels (marked by the mask master, or raw at the
       // saturation level) as bits, 32 columns per word, for the tile kernel
-      const uint8_t* mrow = S.mask ? S.mask + (int64_t)y * S.mask_pitch : nullptr;
-      const uint16_t* rrow = s_src[f] + (int64_t)y * S.src_pitch;
-      uint32_t* brow = s_bad[f] + (int64_t)y * S.bad_pitch;
+      const uint8_t* mrow = S.mask ? S.mask + (int64_t)y * S.mask_pitch + xs : nullptr;
+      const uint16_t* rrow = s_src[f] + (int64_t)y * S.src_pitch + xs;
+      uint32_t* brow = s_bad[f] + (int64_t)y * S.bad_pitch + (xs >> 5);
 #pragma unroll
       for (int wd = 0; wd < E / 32; ++wd) {
         uint32_t bits = 0;
@@ -280,7 +290,7 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
       for (int j = 0; j < E; ++j) yp[j] = __fmaf_rn(zp.p[j + 1], carry, yp[j]);
     }
-    float* out = s_crow[f] + (int64_t)y * S.crow_pitch + x0;
+    float* out = s_crow[f] + (int64_t)y * S.crow_pitch + xs + x0;
     if (W % E == 0) {
       // the frame ends at the end of lane `last`: y-[W-1] = y+[W-1] is set at a
       // fixed position, and the lanes past it (zeros) pass no carry
@@ -298,7 +308,7 @@ __global__ void __launch_bounds__(256, 2)
       auto put = [&](int j, float4 c) {
         if (E == 32)
           s_out[8 * lane + ((j >> 2) ^ (lane & 7))] = c;
-        else
+        else if (x0 + j >= cl && x0 + j < cr)  // the segment's core (4 | cl, cr)
           *(float4*)(out + j) = c;
       };
       if (lane <= last) {
@@ -361,8 +371,9 @@ __global__ void __launch_bounds__(256, 2)
         const float c = __fmul_rn(kSqrt3, __fsub_rn(__fadd_rn(yp[j], acc), v[j]));
         if (vst) {
           c4[j & 3] = c;
-          if ((j & 3) == 0) *(float4*)(out + j) = make_float4(c4[0], c4[1], c4[2], c4[3]);
-        } else if (x < W) {
+          if ((j & 3) == 0 && x >= cl && x < cr)
+            *(float4*)(out + j) = make_float4(c4[0], c4[1], c4[2], c4[3]);
+        } else if (x >= cl && x < cr) {
           out[j] = c;
         }
       }

@@ -6,7 +6,33 @@
 namespace irp {
 
 constexpr int kSplineMinSide = 34;  // the row/column passes need W, H >= 34 ...
-constexpr int kSplineMaxW = 2048;   // ... and W <= 32 lanes x 64 columns
+constexpr int kSplineMaxW = 8192;   // ... and W <= 8192
+
+// Rows wider than 32 lanes x 64 columns take the row pass in segments of at
+// most kSegCols source columns: segment s keeps the coefficients of its core
+// columns and reads kSegHalo more on each side (except at the frame's edges),
+// where its recursions start as if the row ended there.  The error of that
+// start is multiplied by |z1|^64 = 3e-37 before it reaches the core, far
+// below FP32 rounding.  Cores: [0, kSegCols - kSegHalo), then kSegCore each.
+constexpr int kSegCols = 2048;
+constexpr int kSegHalo = 64;
+constexpr int kSegCore = kSegCols - 2 * kSegHalo;
+__host__ __device__ constexpr int row_segments(int W) {
+  return W <= kSegCols ? 1 : 1 + (W - (kSegCols - kSegHalo) + kSegCore - 1) / kSegCore;
+}
+// Core [c0, c1) and source start xs of segment s of a row of W columns.
+__host__ __device__ inline void row_segment(int W, int s, int& c0, int& c1, int& xs) {
+  if (W <= kSegCols) {
+    c0 = 0;
+    c1 = W;
+    xs = 0;
+    return;
+  }
+  c0 = s == 0 ? 0 : (kSegCols - kSegHalo) + (s - 1) * kSegCore;
+  c1 = s == 0 ? kSegCols - kSegHalo : c0 + kSegCore;
+  if (c1 > W) c1 = W;
+  xs = c0 == 0 ? 0 : c0 - kSegHalo;
+}
 constexpr int kRowGroup = 16;       // frames per row-pass CTA
 
 // Row pass: rows per CTA for E columns per lane, and its shared memory (the

@@ -482,6 +482,31 @@ def test_overscan_cutout_roi_of_1074x1024_frames(interp):
     print(gate_e2e("cutout", g, ref, samp, 3.0))
 
 
+@pytest.mark.parametrize("W,onchip", [(2049, False), (4100, False), (4100, True), (6000, False)])
+def test_spline_rows_wider_than_2048_in_segments(W, onchip):
+    """Rows wider than 2048 columns take the row pass in overlapping segments
+    (64-column halos, recursions started at the segment's ends); every
+    sample, and the combined outputs, match the oracle's whole-row solve."""
+    fs = synth.make_set(W, 40, 3, 8.0, 7700 + W, n_stars=40, n_cr=6)
+    got = run_fused([fs], "spline3", kappa=2.5, onchip=onchip)[0]
+    print(W, onchip, check_against_oracle(fs, got, "spline3", 2.5, 3))
+
+
+def test_masked_spline_rows_wider_than_2048():
+    fs = synth.make_set(4100, 40, 4, 8.0, 7790, n_stars=40, n_cr=6)
+    rng = np.random.default_rng(77)
+    mask = (rng.random((40, 4100)) < 0.01).astype(np.uint8)
+    s = core.device_set(fs, mask=mask, saturation=20000.0).alloc_outputs(want_stack=True)
+    ws = core.reduce_sets([s], core.reduce_params("spline3", core.clip_params(2.5, 3)))
+    assert core.sync_status(ws) == 0
+    ref = oracle.reduce_set(fs, interp="spline3", kappa=2.5, mask=mask, saturation=20000.0,
+                            want_stack=True)
+    st = s.stack.cpu().numpy()
+    assert np.array_equal(~np.isnan(st), ref["valid"]), "masked validity differs"
+    tol = sample_tolerance(fs, "spline3", oracle)
+    compare("wide masked stack", st, np.where(ref["valid"], ref["stack"], np.nan), tol)
+
+
 def test_spline_tile_stripes_of_a_set_larger_than_the_l2_budget():
     """A set whose row-pass coefficients exceed the share of L2 the launch
     sequence keeps them in (12 frames of 2048 x 640: 63 MB) is reduced in
