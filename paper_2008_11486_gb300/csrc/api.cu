@@ -622,7 +622,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
   size_t dev_off = L.plan_off;
   for (int gi = 0; gi < (int)groups.size(); ++gi) {
     const auto& g = groups[gi];
-    int nf = 0, max_n = 0, mw_max = 0, mh_max = 0;
+    int nf = 0, max_n = 0, mwin_f4 = 0;  // mwin_f4: the largest master window (float4 entries)
     for (int i : g) {
       nf += sets[i].n;
       max_n = std::max(max_n, sets[i].n);
@@ -771,16 +771,15 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
         oymax = std::max(oymax, F.oy);
       }
       // master union window over all frames' taps ({bias, dark, 1/flat, mask},
-      // 16 B each, or premerged), kept unless the offsets are so spread that
-      // it would exceed 64 KB
+      // 16 B each, or 12 B staged and premerged), kept unless the offsets are
+      // so spread that it would exceed 64 KB
       const int mw = 32 + (oxmax - oxmin), mh = THr + (oymax - oymin) + taps - 1;
       if (stencil != ST_BSPLINE && mw * mh <= kMaxWindowPx) {
         S.mwin_w = mw;
         S.mwin_h = mh;
         S.mox = oxmin;
         S.moy = oymin;
-        mw_max = std::max(mw_max, mw);
-        mh_max = std::max(mh_max, mh);
+        mwin_f4 = std::max(mwin_f4, master_window_f4(mw, mh, (S.mflags & 2) != 0));
       }
       frame0 += s.n;
     }
@@ -802,7 +801,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     h->ddof = p->clip.ddof;
     h->frame_norm = p->frame_norm;
     h->smem_samples = stack_only ? 0 : max_n * THr * 32;
-    h->smem_master = master_window_f4(mw_max, mh_max);  // float4 entries
+    h->smem_master = mwin_f4;
     h->status = &wsh->status;
     h->counter = &wsh->counters[gi];
     SubInfo& si = pf->sub[gi];
@@ -813,8 +812,7 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     si.py = py;
     si.stencil = gstencil;
     si.smem = gtile ? spline_tile_smem_bytes(bucket, max_n)
-                    : reduce_smem_bytes(spline ? SRC_F32 : SRC_RAW, gstencil, py, max_n, mw_max,
-                                        mh_max) -
+                    : reduce_smem_bytes(spline ? SRC_F32 : SRC_RAW, gstencil, py, max_n, mwin_f4) -
                           (stack_only ? (size_t)max_n * THr * 32 * sizeof(float) : 0);
     si.nitems = tile0;
     si.counter = gi;

@@ -214,7 +214,7 @@ int reduce_bucket(int n);                  // register bucket (sort size) for n 
 int rows_per_warp(int bucket, int requested);  // requested if valid for the bucket, else default
 int tile_cols(int stencil);                // output columns per tile
 int tile_rows(int bucket, int py);         // output rows per tile
-size_t reduce_smem_bytes(int src, int stencil, int py, int max_n, int mwin_w, int mwin_h);
+size_t reduce_smem_bytes(int src, int stencil, int py, int max_n, int mwin_f4);
 int reduce_occupancy(int bucket, int py, int stencil, size_t smem);
 cudaError_t launch_reduce(int bucket, int py, int stencil, const InlinePlan* inl,
                           const void* plan_dev, int grid, size_t smem, cudaStream_t s);

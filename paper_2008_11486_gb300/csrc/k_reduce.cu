@@ -31,8 +31,8 @@ int rows_per_warp(int bucket, int requested) {
 
 int tile_rows(int bucket, int py) { return 8 * py; }
 
-size_t reduce_smem_bytes(int src, int stencil, int py, int max_n, int mwin_w, int mwin_h) {
-  return fused_smem_bytes(src, stencil, py, max_n, mwin_w, mwin_h);
+size_t reduce_smem_bytes(int src, int stencil, int py, int max_n, int mwin_f4) {
+  return fused_smem_bytes(src, stencil, py, max_n, mwin_f4);
 }
 
 cudaError_t launch_reduce(int bucket, int py, int stencil, const InlinePlan* inl,

@@ -9,13 +9,14 @@ namespace irp {
 // One CTA per work item (plain) or persistent CTAs pulling work items from an
 // atomic counter in ascending order; the host orders the sets by decreasing
 // frame count, so the longest items are handed out first.
-// Resident CTAs per SM the register allocation must allow (2 up to 32
-// samples per pixel: at most 128 registers per thread).
+// Resident CTAs per SM the register allocation must allow (2 up to 40
+// samples per pixel: at most 128 registers per thread; whether the second
+// CTA fits is then up to the group's shared memory).
 // The vertical spline taps on filtered rows stage no master window, so up to
 // 12 samples per pixel three CTAs fit per SM (at most 85 registers per thread).
 template <int NMAX, int STENCIL>
 struct MinBlocks {
-  static constexpr int value = (STENCIL == ST_BSPLINE_V && NMAX <= 12) ? 3 : (NMAX <= 32 ? 2 : 1);
+  static constexpr int value = (STENCIL == ST_BSPLINE_V && NMAX <= 12) ? 3 : (NMAX <= 40 ? 2 : 1);
 };
 
 template <int NMAX, int STENCIL, int SRC, int PY>

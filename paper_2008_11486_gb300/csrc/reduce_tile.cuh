@@ -162,22 +162,24 @@ struct StageShape {
 constexpr int kRecBytes = 144;
 
 // Float4 entries reserved for a master union window of w x h pixels: the
-// {bias, dark, rf, mask} window (16 bytes a pixel), or the premerged
-// {bias + dark*t, rf} window (8 bytes a pixel) and, before it is formed, the
-// planar copies of the three masters (12 bytes a pixel).
-__host__ __device__ constexpr int master_window_f4(int w, int h) { return w * h; }
+// {bias, dark, rf, mask} window (16 bytes a pixel), or, packed, the planar
+// copies of the three masters (12 bytes a pixel) that become the premerged
+// {bias + dark*t, rf} window (8 bytes a pixel) in place.
+__host__ __device__ constexpr int master_window_f4(int w, int h, bool packed) {
+  return packed ? (3 * w * h + 3) / 4 : w * h;
+}
 constexpr int kMaxWindowPx = 4096;  // 64 KB of float4 entries
 
 // Shared memory per CTA of the fused kernel (host helper mirrors this).
 __host__ __device__ inline size_t fused_smem_bytes(int src, int stencil, int py, int max_n,
-                                                   int mwin_w, int mwin_h) {
+                                                   int mwin_f4) {
   const int taps = (stencil == ST_BSPLINE || stencil == ST_BSPLINE_V || stencil == ST_CUBIC)
                        ? 4 : (stencil == ST_BILINEAR ? 2 : 1);
   const int rows = py + taps - 1;
   const int chunks = stage_chunks(src, stencil);
   const size_t stage = (size_t)stage_count(src, stencil, py) * rows * chunks * 16 * (kThreads / 32);
   const size_t samples = (size_t)max_n * (8 * py) * 32 * sizeof(float);
-  const size_t masters = (size_t)master_window_f4(mwin_w, mwin_h) * sizeof(float4);
+  const size_t masters = (size_t)mwin_f4 * sizeof(float4);  // master_window_f4 entries
   const size_t descs = (size_t)max_n * kRecBytes;
   return samples + stage + masters + descs;
 }
