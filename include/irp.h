@@ -222,11 +222,14 @@ typedef struct {
   int max_ctas;                   /* persistent grid size; 0 = SMs x occupancy  */
   int wait_spin_limit;            /* bounded-wait polls before IRP_ERR_TIMEOUT; 0 = default */
   int rows_per_warp;              /* tile height / 8: 0 = default of the frame-count
-                                     bucket (4 up to 16 frames, else 2), or the
-                                     bucket's other value when the default tiles
-                                     of a group would give fewer than two CTAs per
-                                     SM; the other accepted value is 2 (resp. 1);
-                                     anything else falls back to the default */
+                                     bucket and stencil (4 up to 16 frames; 2 up to
+                                     40 frames, and above for the Keys stencil and
+                                     the tiled spline; else 1), or the bucket's
+                                     other value when it is the shorter and the
+                                     default tiles of a group would give fewer than
+                                     two CTAs per SM; the other accepted value is 2
+                                     (resp. 1; resp. 2); anything else falls back
+                                     to the default */
   int frame_norm;                 /* per-frame normalisation before the combine (a
                                      combine variant; the paper has none): 0 none;
                                      1 zero: each sample of frame k gets m_0 - m_k

@@ -30,6 +30,15 @@ def _bucket(n: int) -> int:
     return 64
 
 
+def _alt_rows(bucket: int, interp: str) -> int:
+    """The bucket's other rows-per-warp choice (the library's default is the
+    first): 4 / 2 up to 16 frames; above, 2 / 1 up to 40 frames and for the
+    Keys stencil, else 1 / 2."""
+    if bucket <= 16:
+        return 2
+    return 1 if bucket <= 40 or interp == "cubic" else 2
+
+
 def signature(sets, interp: str) -> str:
     """Batch signature: interpolation, and the multiset of (frame-count bucket,
     log2 size class) of the sets."""
@@ -59,10 +68,10 @@ class Autotuner:
                 pass  # an unreadable cache is re-tuned, not fatal
 
     @staticmethod
-    def candidates(sets, persistent: bool):
+    def candidates(sets, persistent: bool, interp: str = "bilinear"):
         sms = int(lib().irp_device_sm_count()) or 1
         rows = [0]
-        alts = {2 if _bucket(s.n) <= 16 else 1 for s in sets}
+        alts = {_alt_rows(_bucket(s.n), interp) for s in sets}
         rows += sorted(alts)
         grids = [0, sms, 2 * sms, 4 * sms] if persistent else [0]
         cands = [dict(rows_per_warp=r, max_ctas=g, persistent=persistent)
@@ -90,7 +99,7 @@ class Autotuner:
         """Returns (best config dict, {config: ms}) after timing every candidate."""
         stream = stream if stream is not None else torch.cuda.current_stream()
         results = {}
-        for cand in self.candidates(sets, persistent):
+        for cand in self.candidates(sets, persistent, interp):
             p = core.reduce_params(interp, clip, **cand)
             results[json.dumps(cand, sort_keys=True)] = self._time(sets, p, stream)
         best = min(results, key=results.get)

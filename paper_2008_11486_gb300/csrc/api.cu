@@ -639,14 +639,15 @@ irp_status encode_plan(const PlanSets& ps, const irp_reduce_params* p, uint8_t* 
     const int TWc = tile_cols(gstencil);
     // rows per warp: the caller's choice, else the bucket's default, unless the
     // group's tiles at the default would give fewer than two CTAs per SM; the
-    // bucket's shorter tiles then spread the group further
-    int py = rows_per_warp(bucket, p->rows_per_warp);
-    if (p->rows_per_warp == 0) {
+    // bucket's shorter tiles (where the other choice is shorter) then spread
+    // the group further
+    int py = rows_per_warp(bucket, gstencil, p->rows_per_warp);
+    if (p->rows_per_warp == 0 && rows_per_warp_alt(bucket, gstencil) < py) {
       int64_t tiles = 0;
       for (int i : g)
         tiles += (int64_t)((sets[i].W + TWc - 1) / TWc) *
                  ((sets[i].H + tile_rows(bucket, py) - 1) / tile_rows(bucket, py));
-      if (tiles < 2 * (int64_t)sm_count()) py = rows_per_warp(bucket, rows_per_warp_alt(bucket));
+      if (tiles < 2 * (int64_t)sm_count()) py = rows_per_warp_alt(bucket, gstencil);
     }
     const int THr = gtile ? spline_tile_rows(bucket, max_n) : tile_rows(bucket, py);
     // prefilter work items: tiles x frame groups, enough groups to fill the GPU twice

@@ -211,7 +211,7 @@ __device__ __forceinline__ bool wait_ready(const uint32_t* flag, uint32_t value,
 // Host-side launchers and geometry (implemented in the kernel files).
 // ---------------------------------------------------------------------------
 int reduce_bucket(int n);                  // register bucket (sort size) for n frames
-int rows_per_warp(int bucket, int requested);  // requested if valid for the bucket, else default
+int rows_per_warp(int bucket, int stencil, int requested);  // requested if valid, else default
 int tile_cols(int stencil);                // output columns per tile
 int tile_rows(int bucket, int py);         // output rows per tile
 size_t reduce_smem_bytes(int src, int stencil, int py, int max_n, int mwin_f4);

@@ -24,9 +24,9 @@ int tile_cols(int stencil) {
   }
 }
 
-int rows_per_warp(int bucket, int requested) {
-  if (requested == rows_per_warp_alt(bucket)) return requested;
-  return rows_per_warp_default(bucket);
+int rows_per_warp(int bucket, int stencil, int requested) {
+  if (requested == rows_per_warp_alt(bucket, stencil)) return requested;
+  return rows_per_warp_default(bucket, stencil);
 }
 
 int tile_rows(int bucket, int py) { return 8 * py; }

@@ -10,17 +10,19 @@ namespace irp {
 // atomic counter in ascending order; the host orders the sets by decreasing
 // frame count, so the longest items are handed out first.
 // Resident CTAs per SM the register allocation must allow (2 up to 40
-// samples per pixel: at most 128 registers per thread; whether the second
-// CTA fits is then up to the group's shared memory).
+// samples per pixel, and above with one row per warp: at most 128 registers
+// per thread; whether the second CTA fits is then up to the group's shared
+// memory).
 // The vertical spline taps on filtered rows stage no master window, so up to
 // 12 samples per pixel three CTAs fit per SM (at most 85 registers per thread).
-template <int NMAX, int STENCIL>
+template <int NMAX, int STENCIL, int PY>
 struct MinBlocks {
-  static constexpr int value = (STENCIL == ST_BSPLINE_V && NMAX <= 12) ? 3 : (NMAX <= 40 ? 2 : 1);
+  static constexpr int value =
+      (STENCIL == ST_BSPLINE_V && NMAX <= 12) ? 3 : (NMAX <= 40 || PY == 1 ? 2 : 1);
 };
 
 template <int NMAX, int STENCIL, int SRC, int PY>
-__global__ void __launch_bounds__(kThreads, MinBlocks<NMAX, STENCIL>::value)
+__global__ void __launch_bounds__(kThreads, MinBlocks<NMAX, STENCIL, PY>::value)
     k_reduce(const __grid_constant__ InlinePlan inl, const void* plan_dev) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
@@ -88,30 +90,30 @@ struct ReduceLauncher {
 inline int bucket_range(int bucket) { return bucket <= 12 ? 0 : (bucket <= 32 ? 1 : 2); }
 
 // Defines launch_reduce_<NAME> and occupancy_reduce_<NAME> over the buckets
-// of LIST; py: rows per warp, rows_per_warp_default(bucket) or
-// rows_per_warp_alt(bucket).
+// of LIST; py: rows per warp, rows_per_warp_default(bucket, stencil) or
+// rows_per_warp_alt(bucket, stencil).
 #define IRP_CASE_LAUNCH(B)                                                                    \
   case B:                                                                                     \
-    return alt ? ReduceLauncher<B, ST, SRC, rows_per_warp_alt(B)>::launch(inl, plan_dev, grid, \
+    return alt ? ReduceLauncher<B, ST, SRC, rows_per_warp_alt(B, ST)>::launch(inl, plan_dev, grid, \
                                                                           smem, s)            \
-               : ReduceLauncher<B, ST, SRC, rows_per_warp_default(B)>::launch(inl, plan_dev,  \
+               : ReduceLauncher<B, ST, SRC, rows_per_warp_default(B, ST)>::launch(inl, plan_dev,  \
                                                                               grid, smem, s);
 #define IRP_CASE_OCC(B)                                                           \
   case B:                                                                         \
-    return alt ? ReduceLauncher<B, ST, SRC, rows_per_warp_alt(B)>::occupancy(smem) \
-               : ReduceLauncher<B, ST, SRC, rows_per_warp_default(B)>::occupancy(smem);
+    return alt ? ReduceLauncher<B, ST, SRC, rows_per_warp_alt(B, ST)>::occupancy(smem) \
+               : ReduceLauncher<B, ST, SRC, rows_per_warp_default(B, ST)>::occupancy(smem);
 #define IRP_REDUCE_PART(NAME, STENCIL, SOURCE, LIST)                                          \
   cudaError_t launch_reduce_##NAME(int bucket, int py, const InlinePlan* inl,                 \
                                    const void* plan_dev, int grid, size_t smem,                \
                                    cudaStream_t s) {                                           \
     constexpr int ST = STENCIL, SRC = SOURCE;                                                 \
-    const bool alt = py != rows_per_warp_default(bucket);                                     \
+    const bool alt = py != rows_per_warp_default(bucket, ST);                                     \
     switch (bucket) { LIST(IRP_CASE_LAUNCH) }                                                 \
     return cudaErrorInvalidValue;                                                             \
   }                                                                                           \
   int occupancy_reduce_##NAME(int bucket, int py, size_t smem) {                              \
     constexpr int ST = STENCIL, SRC = SOURCE;                                                 \
-    const bool alt = py != rows_per_warp_default(bucket);                                     \
+    const bool alt = py != rows_per_warp_default(bucket, ST);                                     \
     switch (bucket) { LIST(IRP_CASE_OCC) }                                                    \
     return 1;                                                                                 \
   }

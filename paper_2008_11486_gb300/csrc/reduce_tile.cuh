@@ -127,9 +127,21 @@ struct StencilShape {
 };
 
 // Output rows per warp (tile height / 8): the two choices of each register
-// bucket (the autotuner picks one; the first is the default).
-__host__ __device__ constexpr int rows_per_warp_default(int nmax) { return nmax <= 16 ? 4 : 2; }
-__host__ __device__ constexpr int rows_per_warp_alt(int nmax) { return nmax <= 16 ? 2 : 1; }
+// bucket and stencil (the autotuner picks one; the first is the default).
+// Above 40 frames one row per warp lets two CTAs share an SM (half the
+// samples in shared memory, at most 128 registers), measured faster for the
+// 2-tap and filtered-row stencils on 48 and 64 x 4096^2 sets (3 to 6%); the
+// 4-tap Keys stencil, whose single rows stage four source rows each, keeps
+// two rows per warp (4 to 8% faster so).
+__host__ __device__ constexpr bool tall_tiles(int nmax, int stencil) {
+  return nmax <= 40 || stencil == ST_CUBIC || stencil == ST_BSPLINE;
+}
+__host__ __device__ constexpr int rows_per_warp_default(int nmax, int stencil) {
+  return nmax <= 16 ? 4 : (tall_tiles(nmax, stencil) ? 2 : 1);
+}
+__host__ __device__ constexpr int rows_per_warp_alt(int nmax, int stencil) {
+  return nmax <= 16 ? 2 : (tall_tiles(nmax, stencil) ? 1 : 2);
+}
 
 // Interior tiles of raw sources with at most 2 output rows per warp take the
 // frames two at a time (more independent work per warp between waits).

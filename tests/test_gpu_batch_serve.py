@@ -36,7 +36,7 @@ def test_graph_batch_autotuned_equals_per_set(interp, tmp_path):
     sets = [core.device_set(fs).alloc_outputs() for fs in fss]
     tuner = batch.Autotuner(str(tmp_path / "tune.json"), reps=1)
     params, cfg = tuner.params_for(sets, interp)
-    assert cfg in batch.Autotuner.candidates(sets, True)
+    assert cfg in batch.Autotuner.candidates(sets, True, interp)
     br = batch.BatchReducer(sets, params)
     for _ in range(3):
         br.run()
