@@ -39,7 +39,8 @@ def _run(fs, interp, rows_per_warp, want_stack):
 
 
 # (frames, rows per warp): 0 is the bucket's default (4 up to 16 frames, else 2)
-CASES = [(5, 0), (12, 0), (7, 2), (12, 2), (24, 0), (33, 0), (24, 1), (40, 1)]
+CASES = [(5, 0), (12, 0), (7, 2), (12, 2), (24, 0), (33, 0), (24, 1), (40, 1),
+         (48, 0), (48, 2), (64, 0), (57, 1)]  # above 40: both tile heights of each stencil
 
 
 @pytest.mark.parametrize("interp", ["nearest", "bilinear", "cubic"])

@@ -89,6 +89,28 @@ def test_fused_small_ragged(interp, onchip):
     print(interp, onchip, stats)
 
 
+@pytest.mark.parametrize("n", [48, 64])
+def test_fused_spline_above_40_frames_both_tile_heights(n):
+    """Filtered-row spline sets of 41 to 64 frames: one row per warp (the
+    default) and two rows (the other choice) agree bit for bit and with the
+    oracle."""
+    fs = synth.make_set(90, 60, n, 5.0, 6400 + n, n_stars=25, n_cr=8)
+    outs = []
+    for rpw in (0, 2):
+        s = core.device_set(fs).alloc_outputs(want_stack=False)
+        ws = core.reduce_sets([s], core.reduce_params("spline3", core.clip_params(2.5, 3),
+                                                      rows_per_warp=rpw))
+        assert core.sync_status(ws) == 0
+        outs.append(dict(mean=s.mean.cpu().numpy(), median=s.median.cpu().numpy(),
+                         nkept=s.nkept.cpu().numpy().astype(np.int32)))
+    for k in ("mean", "median", "nkept"):
+        assert np.array_equal(outs[0][k].view(np.uint32), outs[1][k].view(np.uint32)), k
+    got = run_fused([fs], "spline3", kappa=2.5)[0]
+    print(check_against_oracle(fs, got, "spline3", 2.5, 3))
+    for k in ("mean", "median"):
+        assert np.array_equal(got[k].view(np.uint32), outs[0][k].view(np.uint32)), k
+
+
 def test_fused_small_config_full_size():
     """5 frames of 512x512, offsets +-5 px, bilinear, 3-sigma 3 iterations."""
     fs = synth.workload_small()
