@@ -325,17 +325,20 @@ def timed_steps(step, steps, warmup, stream, flush, world, local):
 # (source hash, dominant kind, kind bytes per step, path bytes per step).
 # The captures and their commands are summarised under profiles/.
 TRAFFIC = {
-    # 3 bands in one call: row pass 141.60 MB, column pass 156.13 MB, the
-    # vertical-tap reduction 108.29 MB
-    "bands": ("e3b70a8af7d860dd", "prefilter", 141_600_000 + 156_130_000, 406_020_000),
-    # per band: row pass 40.75 MB, tile kernel 10.50 MB, discard 0.01 MB
-    "bands_onchip": ("e3b70a8af7d860dd", "reduce", 3 * 10_500_000, 3 * 51_260_000),
-    "deep": ("e3b70a8af7d860dd", "reduce", 1_423_170_000, 1_423_170_000),
-    "precision": ("e3b70a8af7d860dd", "reduce", 1_423_170_000, 1_423_170_000),
-    # row pass 1104.92 MB, column pass 1518.99 MB, combine 803.71 MB
-    "paper_band": ("e3b70a8af7d860dd", "combine", 803_710_000, 3_427_620_000),
+    # 3 bands in one call: row pass 122.39 MB, column pass 118.03 MB, the
+    # vertical-tap reduction 80.01 MB
+    "bands": ("ee967b6dddcc837a", "prefilter", 122_390_000 + 118_030_000, 320_420_000),
+    # per band: row pass 38.38 MB, tile kernel 9.12 MB, discard 0.01 MB
+    "bands_onchip": ("ee967b6dddcc837a", "reduce", 3 * 9_120_000, 3 * 47_510_000),
+    "deep": ("ee967b6dddcc837a", "reduce", 1_422_410_000, 1_422_410_000),
+    "precision": ("ee967b6dddcc837a", "reduce", 1_422_410_000, 1_422_410_000),
+    # row pass 1131.89 MB, column pass 1519.42 MB, combine 803.59 MB
+    "paper_band": ("ee967b6dddcc837a", "combine", 803_590_000, 3_454_900_000),
     # three bands of the paper_band shape: three launches of each kind
-    "paper": ("e3b70a8af7d860dd", "combine", 3 * 803_710_000, 3 * 3_427_620_000),
+    "paper": ("ee967b6dddcc837a", "combine", 3 * 803_590_000, 3 * 3_454_900_000),
+    # the 64 sets' own launches (one plain step, the first 64 of the run): the
+    # batched step reduces the same tiles of the same sets, bucket by bucket
+    "batch": ("ee967b6dddcc837a", "reduce", 30_563_540_000, 30_563_540_000),
 }
 
 
@@ -346,12 +349,13 @@ TRAFFIC = {
 # clock -- they give the roofline of kernels that instruction issue, rather
 # than HBM, limits.
 ISSUE = {
-    "bands": ("e3b70a8af7d860dd", "prefilter", 24_520_000 + 26_840_000),  # rows + columns
-    "bands_onchip": ("e3b70a8af7d860dd", "reduce", 3 * 39_700_000),
-    "deep": ("e3b70a8af7d860dd", "reduce", 1_324_180_000),
-    "precision": ("e3b70a8af7d860dd", "reduce", 1_324_180_000),
-    "paper_band": ("e3b70a8af7d860dd", "combine", 1_215_470_000),
-    "paper": ("e3b70a8af7d860dd", "combine", 3 * 1_215_470_000),
+    "bands": ("ee967b6dddcc837a", "prefilter", 21_110_000 + 22_380_000),  # rows + columns
+    "bands_onchip": ("ee967b6dddcc837a", "reduce", 3 * 39_670_000),
+    "deep": ("ee967b6dddcc837a", "reduce", 1_324_180_000),
+    "precision": ("ee967b6dddcc837a", "reduce", 1_324_180_000),
+    "paper_band": ("ee967b6dddcc837a", "combine", 1_215_470_000),
+    "paper": ("ee967b6dddcc837a", "combine", 3 * 1_215_470_000),
+    "batch": ("ee967b6dddcc837a", "reduce", 29_005_400_000),
 }
 
 
