@@ -297,8 +297,7 @@ irp_status irp_plan_launch(const void* plan_host, size_t plan_bytes, void* works
  *     a request returns IRP_ERR_UNSUPPORTED with nothing enqueued, since the
  *     recorded copy would read that buffer after the call has returned.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture on the device.
+ *     (cudaGetSymbolAddress) with that device current.
  *   - All calls on a device share the one array, which keeps the contents of
  *     the last call; each call clears the status word and work counters
  *     before its kernels run.  Calls whose work overlaps on the GPU (other
