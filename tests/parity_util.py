@@ -26,8 +26,8 @@ End to end (GPU from raw against the FP64 oracle from raw), ``gate_e2e``:
     threshold distance in ADU is within (2 + kappa) times the pixel's sample
     bound: a sample error e moves |x - mu| by at most 2|e| and kappa sigma by
     at most kappa |e|, so no larger distance can flip a decision;
-  * the mean and median within max(1e-3 ADU, 1e-6 |ref|) (the benchmark spec's
-    bound, read as atol + rtol) at every compared pixel where the sample
+  * the mean and median within max(1e-3 ADU, 1e-6 |ref|) (the target
+    bound of the path, read as atol + rtol) at every compared pixel where the sample
     rounding bound (a-priori, or the measured sample errors when the stack
     is at hand) stays inside it; elsewhere -- next to bright stars, where the
     spline's FP32 prefilter carries rounding from coefficients far larger
