@@ -15,7 +15,8 @@ against the FP64 oracle), the three 10-frame bands of 1024^2 with the cubic
 spline, and the served form (16-chip exposures at Poisson arrivals, p50/p99
 latency).  The metric is reduced raw megapixels per second (sum of n*W*H over
 a step's sets); each step is timed with CUDA events on the launch stream, L2
-flushed (256 MB write) before every step whose data fit in L2.
+flushed (a 256 MB write, then a 256 MB read of a second buffer) before every
+step whose data fit in L2.
 
 --impl reference times the FP64 CPU oracle on the same workload (a bounded
 sample per step) on this machine's cores.
@@ -286,6 +287,23 @@ def make_device_sets(shapes, cfg, dev, rank):
     return sets
 
 
+class L2Flush:
+    """Run between timed steps: a 256 MB write (twice the 129 MB L2), then a
+    256 MB read of a second buffer.  The step then finds none of its data in
+    L2, and no dirty line of the write is left for its kernels to write back
+    (the read leaves L2 holding clean lines only)."""
+
+    def __init__(self, dev):
+        import torch
+        n = 256 * 1024 * 1024 // 4
+        self.w = torch.empty(n, dtype=torch.float32, device=dev)
+        self.r = torch.zeros(n, dtype=torch.float32, device=dev)
+
+    def __call__(self, i):
+        self.w.fill_(float(i))
+        self.r.sum()
+
+
 def timed_steps(step, steps, warmup, stream, flush, world, local):
     """W untimed steps, then K steps each bracketed by CUDA events on the launch
     stream (L2 flushed before each), with launch tracing and clock sampling."""
@@ -304,7 +322,7 @@ def timed_steps(step, steps, warmup, stream, flush, world, local):
     wall0 = time.perf_counter()
     for i in range(steps):
         if flush is not None:
-            flush.fill_(float(i))
+            flush(i)
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
@@ -550,8 +568,7 @@ def run_workload(args, name, dev, stream, world, rank, local, steps=None, min_se
     cfg = WORKLOADS[name]
     interp = cfg["interp"]
     heavy = name in HEAVY
-    flush = None if heavy else torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,
-                                           device=dev)
+    flush = None if heavy else L2Flush(dev)
     extra = {}
     shapes = workload_shapes(name)
     if name == "batch":  # sets are independent: disjoint shards per rank
@@ -659,7 +676,7 @@ def run_workload(args, name, dev, stream, world, rank, local, steps=None, min_se
                            "launch": ("autotuned persistent, CUDA graph" if name == "batch" else
                                       "persistent" if persistent else "plain"),
                            "l2": ("inputs larger than L2" if heavy else
-                                  "flushed by a 256 MB write before every timed step"),
+                                  "flushed before every timed step: a 256 MB write, then a 256 MB read of a second buffer"),
                            "parallelism": (f"replicas x{world} (sets independent per GPU)"
                                            if scaling == "weak" else
                                            f"disjoint set shards x{world}")},
@@ -773,7 +790,7 @@ def run_sweep(args, dev, stream, world, rank, local):
     import torch
     from paper_2008_11486_gb300 import core
     cfg = SWEEPS[args.workload]
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     params = core.reduce_params(cfg["interp"], core.clip_params(3.0, 3), persistent=False)
     points, t_ms, px_all, clocks = [], 0.0, 0, None
     for (W, H, nb) in cfg["points"]:
@@ -804,7 +821,7 @@ def run_sweep(args, dev, stream, world, rank, local):
             "data": "synthetic (seeded device generator, paper-shaped frames)",
             "config": {"workload": args.workload, "desc": cfg["desc"],
                        "value": "all points' pixels over the sum of their step times",
-                       "l2": "flushed by a 256 MB write before every timed step",
+                       "l2": "flushed before every timed step: a 256 MB write, then a 256 MB read of a second buffer",
                        "parallelism": f"replicas x{world} (sets independent per GPU)"},
             "points": points,
             "linear_fit": {"ms_offset": round(float(a), 4), "ms_per_mpix": round(float(b), 6),
