@@ -255,7 +255,8 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"],
             "unit": "Mpix/s", "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
             "ms_per_step": cb["seconds_per_sample"] * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "strong" if workload == "batch" else "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload, "desc": cfg["desc"]},
             "cpu_baseline": {"value": cb["value"], "unit": "Mpix/s", "cores": cb["cores"],
                              "kind": "oracle", "sample": cb["sample"],
