@@ -155,6 +155,47 @@ def test_persistent_and_batch_invariance():
         gate_e2e("batch", b, ref, samp, 2.5)
 
 
+def test_batch_mixing_master_window_forms():
+    """Sets of one frame-count bucket (33 to 40 frames) whose master windows
+    take different forms share one launch: a premerged window (one exposure
+    time, no mask; staged at 12 B a pixel, the largest offsets), a masked set
+    and a set of several exposure times (16 B a pixel).  Each set's outputs
+    equal its reduction alone bit for bit, in plain and persistent launches,
+    and the unmasked ones match the oracle."""
+    fa = synth.make_set(90, 70, 36, 9.0, 7301, n_stars=20, n_cr=6)
+    fb = synth.make_set(90, 70, 38, 3.0, 7302, n_stars=20, n_cr=6)
+    fc = synth.make_set(90, 70, 40, 3.0, 7303, n_stars=20, n_cr=6)
+    fc.exptime = np.linspace(30.0, 90.0, 40).astype(np.float32)
+    mask = (np.random.default_rng(7).random((70, 90)) < 0.02).astype(np.uint8)
+
+    def dev_sets():
+        return [core.device_set(fa).alloc_outputs(want_stack=False),
+                core.device_set(fb, mask=mask).alloc_outputs(want_stack=False),
+                core.device_set(fc).alloc_outputs(want_stack=False)]
+
+    def outs(sets):
+        return [dict(mean=s.mean.cpu().numpy(), median=s.median.cpu().numpy(),
+                     nkept=s.nkept.cpu().numpy().astype(np.int32)) for s in sets]
+
+    alone = []
+    for s in dev_sets():
+        ws = core.reduce_sets([s], core.reduce_params("bilinear", core.clip_params(2.5, 3)))
+        assert core.sync_status(ws) == 0
+        alone += outs([s])
+    for persistent in (False, True):
+        sets = dev_sets()
+        ws = core.reduce_sets(sets, core.reduce_params("bilinear", core.clip_params(2.5, 3),
+                                                       persistent=persistent))
+        assert core.sync_status(ws) == 0
+        for a, b in zip(alone, outs(sets)):
+            for key in ("mean", "median", "nkept"):
+                assert np.array_equal(a[key].view(np.uint8), b[key].view(np.uint8)), key
+    for fs, got in ((fa, alone[0]), (fc, alone[2])):
+        ref = oracle.reduce_set(fs, interp="bilinear", kappa=2.5)
+        samp = sample_tolerance(fs, "bilinear", oracle).max(axis=0)
+        print(gate_e2e("window forms", got, ref, samp, 2.5))
+
+
 def _padded_device_set(fs, pad_raw, pad_master):
     """Device set whose raw frames and masters are views into wider buffers
     (row pitch W + pad), so that neither need be 16-byte aligned per row."""
