@@ -50,10 +50,9 @@ def sample_tolerance(fs, interp, oracle_mod, pixels=None):
     n, H, W = fs.raw.shape
     size, coef, floor_ = {"spline3": (9, 64.0, 1e-4), "cubic": (5, 16.0, 1e-5)}.get(
         interp, (3, 8.0, 1e-5))
-    if pixels is None:
-        yy, xx = np.mgrid[0:H, 0:W]
-    else:
-        xx, yy = (np.asarray(a) for a in pixels)
+    if pixels is not None:
+        return _sample_tolerance_at(fs, oracle_mod, pixels, size, coef, floor_)
+    yy, xx = np.mgrid[0:H, 0:W]
     tol = np.empty((n,) + xx.shape)
     for k in range(n):
         v = oracle_mod.calibrate(fs.raw[k], fs.bias, fs.dark, fs.flat, fs.exptime[k])
@@ -66,6 +65,36 @@ def sample_tolerance(fs, interp, oracle_mod, pixels=None):
         sy1 = np.clip(sy + 1, 0, H - 1)
         m = np.maximum(np.maximum(M[sy, sx], M[sy, sx1]), np.maximum(M[sy1, sx], M[sy1, sx1]))
         tol[k] = coef * U * m + floor_
+    return tol
+
+
+def _sample_tolerance_at(fs, oracle_mod, pixels, size, coef, floor_):
+    """sample_tolerance at the given output pixels only: the same maxima,
+    taken over each pixel's own window of calibrated values (the size x size
+    maxima at the tap origin and its right/upper neighbour cover rows and
+    columns origin - h .. origin + h + 1, clamped to the frame as the
+    full-frame filter's nearest mode clamps them), so that a full-size set
+    needs no pass over whole frames."""
+    n, H, W = fs.raw.shape
+    xx, yy = (np.asarray(a) for a in pixels)
+    h = size // 2
+    offs = np.arange(-h, h + 2)
+    K = offs.size
+    tol = np.empty((n,) + xx.shape)
+    for k in range(n):
+        sx = np.clip(xx + int(np.floor(fs.dx[k])), 0, W - 1).reshape(-1)
+        sy = np.clip(yy + int(np.floor(fs.dy[k])), 0, H - 1).reshape(-1)
+        Y = np.clip(sy[:, None] + offs[None, :], 0, H - 1)[:, :, None]
+        X = np.clip(sx[:, None] + offs[None, :], 0, W - 1)[:, None, :]
+        shape2 = (sx.size, K * K)
+        raw = np.ascontiguousarray(fs.raw[k][Y, X].reshape(shape2))
+        bias = fs.bias[Y, X].reshape(shape2)
+        dark = fs.dark[Y, X].reshape(shape2)
+        flat = fs.flat[Y, X].reshape(shape2)
+        v = oracle_mod.calibrate(raw, bias, dark, flat, fs.exptime[k])
+        lv = np.abs(bias.astype(np.float64) + dark.astype(np.float64) * float(fs.exptime[k]))
+        m = (np.abs(v) + lv / np.abs(flat.astype(np.float64))).max(axis=1)
+        tol[k] = (coef * U * m + floor_).reshape(xx.shape)
     return tol
 
 
