@@ -49,6 +49,23 @@ def test_autotuner_caches_per_signature(tmp_path, monkeypatch):
     assert calls == [2]
 
 
+def test_autotuner_candidates_offer_each_bucket_its_other_tile_height(monkeypatch):
+    """Rows per warp: 0 (the library's default) and the bucket's other
+    choice -- 2 up to 16 frames (default 4), 1 up to 40 frames (default 2),
+    above 40 frames 2 (default 1) except for the Keys stencil (1, default 2);
+    the persistent grid as 0, 1x, 2x and 4x the SM count, or plain launches."""
+    monkeypatch.setattr(batch, "lib", lambda: types.SimpleNamespace(irp_device_sm_count=lambda: 152))
+    cases = [((5,), "bilinear", [0, 2]), ((24,), "bilinear", [0, 1]), ((40,), "cubic", [0, 1]),
+             ((48,), "bilinear", [0, 2]), ((64,), "spline3", [0, 2]), ((57,), "cubic", [0, 1]),
+             ((3, 33, 60), "bilinear", [0, 1, 2])]
+    for ns, interp, rows in cases:
+        cands = batch.Autotuner.candidates(_fake_sets([(n, 64, 64) for n in ns]), True, interp)
+        assert sorted({c["rows_per_warp"] for c in cands}) == rows, (ns, interp)
+        grids = sorted({c["max_ctas"] for c in cands if c["persistent"]})
+        assert grids == [0, 152, 304, 608]
+        assert {c["rows_per_warp"] for c in cands if not c["persistent"]} == set(rows)
+
+
 def test_autotuner_ignores_an_unreadable_cache(tmp_path):
     for text in ("{not json", "[1, 2]", ""):
         path = tmp_path / "tune.json"
