@@ -225,3 +225,36 @@ def test_server_request_with_a_bad_flat_reports_its_status():
             m, _ = _alone(sub, "bilinear")
             assert np.array_equal(req.outputs[c][0].cpu().numpy().view(np.uint32),
                                   m.view(np.uint32)), (r, c)
+
+
+def test_server_snapshot_restores_the_rolling_stacks():
+    """Checkpoint and resume on the GPU: a server restored from another's
+    snapshot reduces the next requests to the same bits as the first server,
+    and differently from a fresh server that lacks the earlier frames."""
+    nchips, W, H, depth = 2, 96, 80, 3
+    chips = _chip_frames(nchips, W, H, 7, 6161)
+    masters = [tuple(torch.from_numpy(a).cuda() for a in (fs.bias, fs.dark, fs.flat))
+               for fs in chips]
+
+    def server():
+        return serve.Server(masters, depth=depth, max_inflight=2, hbm_reserve_bytes=0)
+
+    def run(srv, lo, hi):
+        reqs = _requests(chips, lo, hi)
+        serve.run_poisson(srv, reqs, rate_hz=2000.0)
+        srv.drain()
+        assert srv.status() == 0
+        return [[(m.clone(), d.clone()) for (m, d) in q.outputs] for q in reqs]
+
+    a = server()
+    run(a, 0, 5)
+    b = server()
+    b.restore(a.snapshot())
+    fresh = server()
+    got_a, got_b, got_f = run(a, 5, 7), run(b, 5, 7), run(fresh, 5, 7)
+    for ra, rb in zip(got_a, got_b):
+        for (ma, da), (mb, db) in zip(ra, rb):
+            assert torch.equal(ma.view(torch.int32), mb.view(torch.int32))
+            assert torch.equal(da.view(torch.int32), db.view(torch.int32))
+    # the second request reduces frames 4, 5 and 6; the fresh server has 5 and 6 only
+    assert not torch.equal(got_b[1][0][0].view(torch.int32), got_f[1][0][0].view(torch.int32))
